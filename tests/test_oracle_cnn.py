@@ -1,0 +1,123 @@
+"""Pins of the oracle's CNN layers: float64 network, transforms, layouts and
+the homomorphic evaluation of the small network."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import ckks as C
+from oracle import cnn
+
+
+def test_conv2d_matches_scipy_correlate():
+    signal = pytest.importorskip("scipy.signal")
+    rng = np.random.default_rng(0)
+    x = rng.normal(size=(3, 9, 9))
+    w = rng.normal(size=(4, 3, 3, 3))
+    got = cnn.conv2d(x, w, 1, 1)
+    xp = np.pad(x, ((0, 0), (1, 1), (1, 1)))
+    for o in range(4):
+        ref = sum(signal.correlate2d(xp[i], w[o, i], mode="valid") for i in range(3))
+        assert np.allclose(got[o], ref)
+    got2 = cnn.conv2d(x, w, 2, 1)
+    assert np.allclose(got2, got[:, ::2, ::2])
+
+
+def test_avgpool_by_hand():
+    x = np.arange(32, dtype=float).reshape(2, 4, 4)
+    p = cnn.avgpool(x, 2)
+    assert p[0, 0, 0] == (0 + 1 + 4 + 5) / 4 and p[1, 1, 1] == (26 + 27 + 30 + 31) / 4
+
+
+@pytest.mark.parametrize("arch", ["tiny", "resnet20"])
+def test_transforms_preserve_the_function(arch):
+    """Batch-norm folding (Case 2) and forward weight redistribution give the
+    same network output (Sec. 4.1-4.2: functional equivalence)."""
+    net = synth.ARCHS[arch]()
+    raw = synth.params(net)
+    t = cnn.transform(net, raw)
+    hwc = net[0]
+    for i in range(2):
+        img = synth.image(i, hwc["c"], hwc["h"], hwc["w"])
+        y0 = cnn.forward_plain(net, raw, img)
+        y1 = cnn.forward_transformed(net, t, img)
+        assert np.allclose(y0, y1, rtol=1e-9, atol=1e-12)
+
+
+def test_transform_changes_function_if_receiver_not_updated():
+    """Sanity of the previous test: dropping the receiver update breaks it."""
+    net = synth.tiny()
+    raw = synth.params(net)
+    t = cnn.transform(net, raw)
+    t[4] = dict(t[4], w=raw[4]["w"])  # dense without upsilon
+    img = synth.image(0, 3, 16, 16)
+    assert not np.allclose(cnn.forward_plain(net, raw, img), cnn.forward_transformed(net, t, img))
+
+
+def test_layout_lowering_reproduces_conv_on_plain_vectors():
+    """The diagonal lowering of a strided conv between channel-packed layouts,
+    applied to plain slot vectors with numpy rolls, equals conv2d."""
+    rng = np.random.default_rng(1)
+    n = 2048
+    Lin = cnn.packed_layout(4, 8, 8, 1, 8, 64, n)        # 32 blocks, 4 ch x 8 replicas
+    x = rng.normal(size=(4, 8, 8))
+    w = rng.normal(size=(8, 4, 3, 3))
+    Lout = cnn.packed_layout(8, 4, 4, 2, 8, 64, n)
+    diags = cnn._lower_conv(w, 2, 1, Lin, Lout, n)
+    vin = np.zeros(n)
+    for c in range(4):
+        for (ct, base) in Lin.rep[c]:
+            for h in range(8):
+                for ww in range(8):
+                    vin[Lin.slot(base, h, ww)] = x[c, h, ww]
+    out = np.zeros(n)
+    baby, groups = cnn._bsgs(diags, 64, n)
+    for o, gs in groups.items():
+        for g, terms in gs.items():
+            acc = sum(v * np.roll(vin, -b) for (_, b, v) in terms)
+            out += np.roll(acc, -g)
+    ref = cnn.conv2d(x, w, 2, 1)
+    for c in range(8):
+        for (ct, base) in Lout.rep[c]:
+            got = np.array([[out[Lout.slot(base, h, ww)] for ww in range(4)] for h in range(4)])
+            assert np.allclose(got, ref[c])
+
+
+@pytest.mark.slow
+def test_tiny_network_under_ckks_matches_float64():
+    """The whole small network homomorphically: decrypted logits within 1e-3
+    of the float64 network and the same argmax."""
+    net = synth.tiny()
+    raw = synth.params(net)
+    t = cnn.transform(net, raw)
+    prm = C.make_params(**synth.PRESETS["tiny"])
+    prog = cnn.compile_he(net, t, prm, "hw")
+    S = C.CKKS(prm)
+    keys = S.keygen(synth.SEED_KEYS, sorted(prog.rot_steps))
+    img = synth.image(0, 3, 16, 16)
+    cts = cnn.encrypt_input(S, keys, prog, img, 0, synth.enc_seed)
+    vals = cnn.run_he(S, keys, prog, cts)
+    y = cnn.decrypt_logits(S, keys, prog, vals[prog.output_tensor])
+    ref = cnn.forward_plain(net, raw, img)
+    assert np.max(np.abs(y - ref)) < 1e-3
+    assert np.argmax(y) == np.argmax(ref)
+    # three rescales (conv, activation, dense): output on q_0, q_1
+    assert prog.tensors[prog.output_tensor].level == 1
+
+
+def test_resnet20_program_levels_follow_tower_reuse():
+    """ResNet-20 compiled with Delta = 2^25, q ~ 2^50: 20 rescales along the
+    network, output at level 0 (Table 1, P2FRT = 20)."""
+    net = synth.resnet20()
+    raw = synth.params(net)
+    t = cnn.transform(net, raw)
+    pre = synth.PRESETS["resnet20"]
+    # small ring for speed; the level/scale plan depends only on the primes' sizes
+    prm = C.make_params(**dict(pre, logn=12))
+    c = cnn.Compiler(prm, "packed")
+    c.n = 1 << 15                      # slot count of N = 2^16
+    prog = c.compile(net, t)
+    n_rescale = sum(1 for s in prog.steps if s["op"] == "rescale")
+    main_path = [s for s in prog.steps if s["op"] == "rescale"]
+    assert prog.tensors[prog.output_tensor].level == 0
+    assert n_rescale >= 20
+    assert prm.L == 20
