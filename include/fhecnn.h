@@ -1,0 +1,268 @@
+/*
+ * fhecnn.h -- C ABI of the GB300 (sm_103a) library for homomorphic CNN
+ * inference under leveled RNS-CKKS with no bootstrapping.
+ *
+ * The paper (arxiv 2509.22857) states the problem as non-interactive
+ * inference (Sec. 2.1, threat model): the client holds the input and the
+ * CKKS secret key, encrypts and sends only ciphertexts; the server holds a
+ * CNN with plaintext parameters, evaluates it homomorphically under leveled
+ * FHE and returns encrypted logits that only the client decrypts.  The entry
+ * points below follow that split: client-side calls (keygen, encode,
+ * encrypt, decrypt, decode) and server-side calls (model load, convolution,
+ * quadratic activation, pooling/dense, rescale, rotation, batched inference).
+ * The scheme is RNS-CKKS as in Sec. 2.2: R_Q = Z_Q[x]/(x^N+1), Q = q_0..q_L
+ * held as 64-bit residue limbs, a special modulus P (alpha primes) for hybrid
+ * key switching.
+ *
+ * Conventions for every function:
+ *   - Return value: 0 (FHE_OK) on success, a negative FHE_E_* code on error;
+ *     fhe_last_error() then returns a thread-local message.  On error no
+ *     output handle is written and inputs are unchanged.
+ *   - Handles (fhe_ctx, fhe_sk, fhe_evk, fhe_pt, fhe_ct, fhe_model) are
+ *     opaque, created and owned by the library, released with their *_free /
+ *     *_destroy call.  A handle belongs to the context that made it and must
+ *     not outlive it.
+ *   - Host arrays passed in are owned by the caller and only read during the
+ *     call; host arrays passed out are written during the call only.
+ *   - Ciphertexts, plaintexts and keys live in device memory of the
+ *     context's GPU; they are in the NTT domain, limb-major
+ *     ([poly][limb][N] 64-bit words).  Data leaves the device only through
+ *     fhe_ct_export / fhe_decrypt + fhe_decode.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream).  Calls that take a stream are asynchronous with respect to
+ *     the host unless stated otherwise; calls without one synchronise.
+ *   - Not thread-safe per context: calls on one context must be serialised
+ *     by the caller.
+ */
+#ifndef FHECNN_H
+#define FHECNN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FHE_OK 0
+#define FHE_E_INVAL -1    /* bad argument, size or handle */
+#define FHE_E_LEVEL -2    /* no level left, or level / scale mismatch */
+#define FHE_E_NOKEY -3    /* evaluation key for a rotation step is missing */
+#define FHE_E_OOM -4      /* device or host allocation failed */
+#define FHE_E_CUDA -5     /* a CUDA call failed (message has the CUDA error) */
+#define FHE_E_TIMEOUT -6  /* a bounded device wait expired */
+
+typedef struct fhe_ctx fhe_ctx;
+typedef struct fhe_sk fhe_sk;
+typedef struct fhe_evk fhe_evk;
+typedef struct fhe_pt fhe_pt;
+typedef struct fhe_ct fhe_ct;
+typedef struct fhe_model fhe_model;
+
+/*
+ * Parameters (Table 4 and the appendix on FHE parameters: ring degree N,
+ * scale Delta, L rescale primes, output prime q_0, special modulus P).
+ * Primes are = 1 mod 2N, chosen in descending order below 2^bits: first the
+ * L primes q_1..q_L of q_bits, then q_0 of q0_bits, then the alpha special
+ * primes of p_bits, each skipping primes already taken.  alpha is also the
+ * number of consecutive primes per key-switching digit.
+ * Limits: 12 <= log_n <= 16; every prime below 2^58; 1 <= alpha <= 8;
+ * L + 1 + alpha <= 64.
+ */
+typedef struct {
+    int log_n;
+    int L;
+    int q_bits;
+    int q0_bits;
+    int p_bits;
+    int alpha;
+    double log_scale;   /* Delta = 2^log_scale */
+    int device;         /* CUDA device ordinal */
+} fhe_params;
+
+const char *fhe_last_error(void);
+
+/* Context: builds the prime chain, NTT tables and key-switching constants on
+ * the device.  fhe_ctx_destroy frees everything the context made. */
+int fhe_ctx_create(const fhe_params *params, fhe_ctx **out);
+int fhe_ctx_destroy(fhe_ctx *ctx);
+/* q_0..q_L then p_0..p_{alpha-1} into out[cap]; *n = count (test hook). */
+int fhe_ctx_primes(const fhe_ctx *ctx, uint64_t *out, size_t cap, size_t *n);
+
+/* ---------------------------------------------------------------- client */
+
+/*
+ * Key generation (client side, Sec. 2.1).  Secret key s is ternary.  The
+ * evaluation keys hold the relinearisation key (s^2 -> s) and one Galois key
+ * per distinct rotation step in rot_steps[n_steps] (slot rotation left by
+ * the step; 5^step mod 2N).  All randomness is the RFC 8439 ChaCha20 stream
+ * with key (seed mod 2^32, seed >> 32, domain, 0, 0, 0, 0, 0), nonce
+ * (id0, id1, 0) and block counter 0, 1, ...: domain 1 the secret key
+ * (coefficient k: word k, floor(3w / 2^32) - 1), domain 2 the uniform key
+ * masks (id0 = key id: 0 relinearisation, else the Galois element;
+ * id1 = 65536 * digit + limb; coefficient k: words 4k..4k+3 as a 128-bit
+ * integer mod q, drawn directly in the NTT domain), domain 3 the key errors
+ * (id1 = digit; centred binomial, popcount of the low 21 bits of word 2k
+ * minus that of word 2k+1).
+ */
+int fhe_keygen(fhe_ctx *ctx, uint64_t seed, const int32_t *rot_steps, size_t n_steps, fhe_sk **sk,
+               fhe_evk **evk);
+int fhe_sk_free(fhe_sk *sk);
+int fhe_evk_free(fhe_evk *evk);
+/* Galois elements present in the key set (test hook): out[cap], *n = count. */
+int fhe_evk_galois(const fhe_evk *evk, int32_t *out, size_t cap, size_t *n);
+
+/*
+ * Encoding (Sec. 2.2): n <= N/2 complex slots (re[i], im[i]; im may be NULL
+ * for real slots; missing slots are zero) -> round(scale * sigma^-1(z)) as a
+ * plaintext at `level` (limbs q_0..q_level).
+ */
+int fhe_encode(fhe_ctx *ctx, const double *re, const double *im, size_t n, double scale, int level,
+               fhe_pt **out);
+int fhe_pt_free(fhe_pt *pt);
+/* Secret-key encryption: c1 = a (uniform), c0 = -a*s + e + m; a is domain 4
+ * of the stream keyed by `seed` (id1 = limb), e domain 5. */
+int fhe_encrypt(fhe_ctx *ctx, const fhe_sk *sk, const fhe_pt *pt, uint64_t seed, fhe_ct **out);
+/* m = c0 + c1*s, as a plaintext at the ciphertext's level and scale. */
+int fhe_decrypt(fhe_ctx *ctx, const fhe_sk *sk, const fhe_ct *ct, fhe_pt **out);
+/* Slots of a plaintext: re[n], im[n] (im may be NULL), n <= N/2. */
+int fhe_decode(fhe_ctx *ctx, const fhe_pt *pt, double *re, double *im, size_t n);
+
+/* --------------------------------------------------------- ciphertexts */
+
+int fhe_ct_free(fhe_ct *ct);
+int fhe_ct_info(const fhe_ct *ct, int *level, int *n_poly, double *scale);
+/*
+ * Canonical export: coefficient domain, residues in [0, q_i), layout
+ * [poly][limb][N]; cap is the capacity of buf in words
+ * (needs n_poly*(level+1)*N).  Synchronous.
+ */
+int fhe_ct_export(const fhe_ct *ct, uint64_t *buf, size_t cap, int *level, double *scale, int *n_poly);
+/* Inverse of fhe_ct_export. */
+int fhe_ct_import(fhe_ctx *ctx, const uint64_t *buf, int n_poly, int level, double scale, fhe_ct **out);
+
+/* --------------------------------------------- homomorphic primitives */
+
+/* Slot rotation left by `step` (Sec. 2.2): Galois automorphism 5^step then
+ * hybrid key switching (ModUp, key inner product, ModDown) with the Galois
+ * key.  FHE_E_NOKEY if the key set lacks the step. */
+int fhe_rotate(fhe_ctx *ctx, const fhe_evk *evk, const fhe_ct *in, int step, fhe_ct **out, void *stream);
+/* Ciphertext square then relinearisation: (c0,c1)^2 = (c0^2, 2c0c1, c1^2),
+ * key-switch c1^2 with the relinearisation key.  Scale is squared. */
+int fhe_square(fhe_ctx *ctx, const fhe_evk *evk, const fhe_ct *in, fhe_ct **out, void *stream);
+/* Rescale (Sec. 2.2, Sec. 4.3): divide by the top prime q_level with
+ * rounding, drop one level, scale /= q_level.  In place on the handle.
+ * FHE_E_LEVEL at level 0. */
+int fhe_rescale(fhe_ctx *ctx, fhe_ct *ct, void *stream);
+/* out = a + b (same level; the result carries a's scale). */
+int fhe_add(fhe_ctx *ctx, const fhe_ct *a, const fhe_ct *b, fhe_ct **out, void *stream);
+/* out = a * pt (slot-wise), scale multiplies. */
+int fhe_mul_plain(fhe_ctx *ctx, const fhe_ct *a, const fhe_pt *pt, fhe_ct **out, void *stream);
+
+/* ------------------------------------------------------------- models */
+
+/* Step kinds of a compiled model program (see fhe_model_desc). */
+#define FHE_STEP_LINEAR 1   /* convolution / dense: sum of diagonals (BSGS) */
+#define FHE_STEP_RESCALE 2  /* rescale every ciphertext of a tensor */
+#define FHE_STEP_ACT 3      /* x^2 + c1 x + c0 with relinearisation */
+#define FHE_STEP_ROTSUM 4   /* x <- x + rot(x, s) for each step s (pooling) */
+#define FHE_STEP_CMUL 5     /* multiply by an integer constant (shortcut) */
+#define FHE_STEP_DROP 6     /* mod-drop to a lower level */
+#define FHE_STEP_ADD 7      /* residual add of two tensors */
+
+/*
+ * One step of a compiled network (Sec. 5.1 slot layouts, Sec. 4.3 rescale
+ * placement).  Tensors are numbered lists of ciphertexts (one per image).
+ * LINEAR: for each output ciphertext o and giant step g,
+ *     acc_{o,g} = sum_terms pt_term (.) rot(in[term_ct], term_baby)
+ *     out_o     = bias_o + sum_g rot(acc_{o,g}, g)
+ *   where term vectors (n_slots doubles each) are encoded at w_scale and the
+ *   bias vectors at bias_scale, both at the input's level.
+ * ACT: c1 and c0 are integers (given as integral doubles of any size) that
+ *   are already scaled: out = x^2 + c1*x + c0 (c0 added to poly 0).
+ * CMUL: out = value * x (value an integral double).
+ * ROTSUM: steps[n_steps] applied in order.
+ * DROP: out = x restricted to limbs 0..level.
+ * ADD: out = src + src2.
+ */
+typedef struct {
+    int kind;
+    int src, src2, dst;
+    /* LINEAR */
+    double w_scale, bias_scale;
+    int n_groups;                    /* (out ct, giant step) groups */
+    const int32_t *group_out;        /* [n_groups] */
+    const int32_t *group_giant;      /* [n_groups] rotation step g (0 = none) */
+    const int32_t *group_term_begin; /* [n_groups + 1] */
+    const int32_t *term_ct;          /* [n_terms] input ciphertext index */
+    const int32_t *term_baby;        /* [n_terms] baby rotation step b */
+    const double *term_vec;          /* [n_terms][n_slots] */
+    int n_bias;
+    const int32_t *bias_out;         /* [n_bias] output ciphertext index */
+    const double *bias_vec;          /* [n_bias][n_slots] */
+    /* ACT, CMUL */
+    double c1, c0, value;
+    /* ROTSUM */
+    int n_steps;
+    const int32_t *steps;
+    /* DROP */
+    int level;
+} fhe_step_desc;
+
+typedef struct {
+    int n_tensors;
+    const int32_t *tensor_n_ct;      /* [n_tensors] ciphertexts per image */
+    const int32_t *tensor_level;     /* [n_tensors] */
+    const double *tensor_scale;      /* [n_tensors] */
+    int input_tensor, output_tensor;
+    int n_steps;
+    const fhe_step_desc *steps;
+} fhe_model_desc;
+
+/* Encode every plaintext of the program at its level (weights stay
+ * resident in HBM) and keep the program.  The description is copied. */
+int fhe_model_load(fhe_ctx *ctx, const fhe_model_desc *desc, fhe_model **out);
+int fhe_model_free(fhe_model *model);
+
+/*
+ * Per-step evaluation of one image.  `step` is the index of a LINEAR step
+ * (fhe_eval_conv: convolutions), an ACT step (fhe_eval_quad_act, in place
+ * on io[n]), or a ROTSUM / LINEAR step (fhe_eval_pool_dense: average pool
+ * as a sum of rotations, dense layer as diagonals).  in[n_in] are the
+ * step's input ciphertexts, out[n_out] receive new handles.
+ */
+int fhe_eval_conv(fhe_ctx *ctx, const fhe_model *model, const fhe_evk *evk, int step,
+                  const fhe_ct *const *in, size_t n_in, fhe_ct **out, size_t n_out, void *stream);
+int fhe_eval_quad_act(fhe_ctx *ctx, const fhe_model *model, const fhe_evk *evk, int step, fhe_ct **io,
+                      size_t n, void *stream);
+int fhe_eval_pool_dense(fhe_ctx *ctx, const fhe_model *model, const fhe_evk *evk, int step,
+                        const fhe_ct *const *in, size_t n_in, fhe_ct **out, size_t n_out, void *stream);
+
+/*
+ * Whole-network inference of n_img images in one batched pass: in holds
+ * n_img * n_in_ct input ciphertexts (image-major), out receives
+ * n_img * n_out_ct handles.  Every kernel processes all images of a step
+ * together, so evaluation keys and weight plaintexts are read once per batch.
+ */
+int fhe_infer(fhe_ctx *ctx, const fhe_model *model, const fhe_evk *evk, const fhe_ct *const *in,
+              size_t n_img, fhe_ct **out, void *stream);
+
+/* ------------------------------------------------------ test hooks */
+
+/* Forward (inverse = 0) or inverse NTT of n_limbs device limbs in place;
+ * limb l uses prime index prime_idx[l] (0..L = q_i, L+1.. = p_j). */
+int fhe_ntt_device(fhe_ctx *ctx, uint64_t *d_limbs, size_t n_limbs, const int32_t *prime_idx, int inverse,
+                   void *stream);
+/* Copy of one key-switching key (relinearisation: galois = 0) to host:
+ * [digits][2][L+1+alpha][N] words, NTT domain. */
+int fhe_evk_export(const fhe_evk *evk, int galois, uint64_t *buf, size_t cap, size_t *n_words);
+/* Secret key (NTT domain, all L+1+alpha limbs) to host. */
+int fhe_sk_export(const fhe_sk *sk, uint64_t *buf, size_t cap);
+/* Integer coefficients of an encoding, before reduction (host encoder),
+ * as integral doubles: out[N]. */
+int fhe_encode_coeffs(fhe_ctx *ctx, const double *re, const double *im, size_t n, double scale, double *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,1010 @@
+// Context, tables, encoder and the client / primitive entry points of the C ABI.
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <string>
+
+#include "host.h"
+
+static thread_local std::string g_err;
+
+int fhe_fail(int code, const std::string &msg) {
+    g_err = msg;
+    return code;
+}
+
+extern "C" const char *fhe_last_error(void) { return g_err.c_str(); }
+
+// ================================================================ host math
+
+u64 h_powmod(u64 a, u64 e, u64 q) {
+    u64 r = 1 % q;
+    a %= q;
+    while (e) {
+        if (e & 1) r = h_mulmod(r, a, q);
+        a = h_mulmod(a, a, q);
+        e >>= 1;
+    }
+    return r;
+}
+
+bool h_is_prime(u64 n) {
+    static const u64 witnesses[] = {2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37};
+    if (n < 2) return false;
+    for (u64 p : witnesses)
+        if (n % p == 0) return n == p;
+    u64 d = n - 1;
+    int r = 0;
+    while (!(d & 1)) {
+        d >>= 1;
+        r++;
+    }
+    for (u64 a : witnesses) {
+        u64 x = h_powmod(a, d, n);
+        if (x == 1 || x == n - 1) continue;
+        bool composite = true;
+        for (int i = 1; i < r && composite; i++) {
+            x = h_mulmod(x, x, n);
+            if (x == n - 1) composite = false;
+        }
+        if (composite) return false;
+    }
+    return true;
+}
+
+std::vector<u64> h_gen_primes(int bits, int count, u64 two_n, const std::vector<u64> &taken) {
+    std::vector<u64> out;
+    const u64 top = 1ull << bits;
+    for (u64 c = top - two_n + 1; (long long)out.size() < count && c > two_n; c -= two_n) {
+        if (!h_is_prime(c)) continue;
+        bool dup = false;
+        for (u64 t : taken) dup |= (t == c);
+        for (u64 t : out) dup |= (t == c);
+        if (!dup) out.push_back(c);
+    }
+    return out;
+}
+
+u64 h_root_2n(u64 q, u64 two_n) {
+    for (u64 g = 2;; g++)
+        if (h_powmod(g, (q - 1) / 2, q) == q - 1) return h_powmod(g, (q - 1) / two_n, q);
+}
+
+u64 h_double_mod(double v, u64 q) {
+    const double av = std::fabs(v);
+    u64 r;
+    if (av < 9223372036854775808.0) {
+        r = (u64)(long long)av % q;
+    } else {
+        int e;
+        const double mant = std::frexp(av, &e);
+        const u64 mi = (u64)std::ldexp(mant, 53);
+        r = h_mulmod(mi % q, h_powmod(2, (u64)(e - 53), q), q);
+    }
+    return (v < 0 && r) ? q - r : r;
+}
+
+static uint32_t h_brv(uint32_t x, int bits) {
+    uint32_t r = 0;
+    for (int i = 0; i < bits; i++) r |= ((x >> i) & 1u) << (bits - 1 - i);
+    return r;
+}
+
+// ================================================================ encoder
+// The slot encoding m = round(scale * sigma^-1(z)) with slot j at zeta^(5^j),
+// zeta = exp(i pi / N).  Writing v_k = m_k + i m_{k+n}, v = (1/n) zeta^-k
+// DFT_n(y) with y[t_j] = z_j, t_j = (5^j mod 2N - 1)/4.  The floating-point
+// operations are done in a fixed order (this file is compiled without FMA
+// contraction): radix-2 decimation in time after a bit-reversal permutation;
+// twiddle of a length-len stage at k is (cos a, -sin a), a = 2.0*M_PI*k/len;
+// the twist multiplies by (c, -s), c + i s = exp(i M_PI k / N), then by
+// scale/n; rounding is half away from zero.
+
+void Encoder::init(int logn) {
+    logN = logn;
+    N = (size_t)1 << logn;
+    n = N / 2;
+    const int logh = logn - 1;
+    fft_off.assign(logh + 2, 0);
+    fft_re.clear();
+    fft_im.clear();
+    for (int s = 1; s <= logh; s++) {
+        const size_t len = (size_t)1 << s;
+        fft_off[s] = fft_re.size();
+        for (size_t k = 0; k < len / 2; k++) {
+            const double ang = 2.0 * M_PI * (double)k / (double)len;
+            fft_re.push_back(std::cos(ang));
+            fft_im.push_back(std::sin(ang));
+        }
+    }
+    tw_c.resize(n);
+    tw_s.resize(n);
+    for (size_t k = 0; k < n; k++) {
+        const double ang = M_PI * (double)k / (double)N;
+        tw_c[k] = std::cos(ang);
+        tw_s[k] = std::sin(ang);
+    }
+    slot_pos.resize(n);
+    u64 e = 1;
+    for (size_t j = 0; j < n; j++) {
+        slot_pos[j] = (uint32_t)((e - 1) / 4);
+        e = (e * 5) % (2 * (u64)N);
+    }
+    brv.resize(n);
+    for (size_t i = 0; i < n; i++) brv[i] = logh > 0 ? h_brv((uint32_t)i, logh) : 0;
+}
+
+void Encoder::encode(const double *re, const double *im, size_t nz, double scale, double *m) const {
+    std::vector<double> yr(n, 0.0), yi(n, 0.0), ar(n), ai(n);
+    for (size_t j = 0; j < n; j++) {
+        const double zr = j < nz ? re[j] : 0.0;
+        const double zi = (j < nz && im) ? im[j] : 0.0;
+        yr[slot_pos[j]] = zr;
+        yi[slot_pos[j]] = zi;
+    }
+    for (size_t i = 0; i < n; i++) {
+        ar[brv[i]] = yr[i];
+        ai[brv[i]] = yi[i];
+    }
+    for (int s = 1; ((size_t)1 << s) <= n; s++) {
+        const size_t len = (size_t)1 << s, half = len / 2;
+        const double *cr = &fft_re[fft_off[s]], *ci = &fft_im[fft_off[s]];
+        for (size_t st = 0; st < n; st += len) {
+            for (size_t k = 0; k < half; k++) {
+                const double wr = cr[k], wi = -ci[k];
+                const double br = ar[st + k + half], bi = ai[st + k + half];
+                const double vr = br * wr - bi * wi;
+                const double vi = br * wi + bi * wr;
+                const double ur = ar[st + k], ui = ai[st + k];
+                ar[st + k] = ur + vr;
+                ai[st + k] = ui + vi;
+                ar[st + k + half] = ur - vr;
+                ai[st + k + half] = ui - vi;
+            }
+        }
+    }
+    const double f = scale / (double)n;
+    for (size_t k = 0; k < n; k++) {
+        const double c = tw_c[k], s = tw_s[k];
+        double r = ar[k] * c + ai[k] * s;
+        double i = ai[k] * c - ar[k] * s;
+        r = r * f;
+        i = i * f;
+        m[k] = std::round(r);
+        m[k + n] = std::round(i);
+    }
+}
+
+// z_j = sum_k (v_k zeta^k) exp(+2 pi i k t_j / n), v_k = (m_k + i m_{k+n}) / scale
+void Encoder::decode(const double *m, double scale, double *re, double *im, size_t nz) const {
+    std::vector<double> xr(n), xi(n), ar(n), ai(n);
+    for (size_t k = 0; k < n; k++) {
+        const double vr = m[k] / scale, vi = m[k + n] / scale;
+        xr[k] = vr * tw_c[k] - vi * tw_s[k];
+        xi[k] = vr * tw_s[k] + vi * tw_c[k];
+    }
+    for (size_t i = 0; i < n; i++) {
+        ar[brv[i]] = xr[i];
+        ai[brv[i]] = xi[i];
+    }
+    for (int s = 1; ((size_t)1 << s) <= n; s++) {
+        const size_t len = (size_t)1 << s, half = len / 2;
+        const double *cr = &fft_re[fft_off[s]], *ci = &fft_im[fft_off[s]];
+        for (size_t st = 0; st < n; st += len) {
+            for (size_t k = 0; k < half; k++) {
+                const double wr = cr[k], wi = ci[k];
+                const double br = ar[st + k + half], bi = ai[st + k + half];
+                const double vr = br * wr - bi * wi, vi = br * wi + bi * wr;
+                const double ur = ar[st + k], ui = ai[st + k];
+                ar[st + k] = ur + vr;
+                ai[st + k] = ui + vi;
+                ar[st + k + half] = ur - vr;
+                ai[st + k + half] = ui - vi;
+            }
+        }
+    }
+    for (size_t j = 0; j < nz && j < n; j++) {
+        re[j] = ar[slot_pos[j]];
+        if (im) im[j] = ai[slot_pos[j]];
+    }
+}
+
+// ================================================================ memory
+
+int dev_alloc(fhe_ctx *ctx, void **p, size_t bytes) {
+    (void)ctx;
+    *p = nullptr;
+    if (bytes == 0) bytes = 8;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fhe_fail(FHE_E_OOM, std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+    }
+    return FHE_OK;
+}
+
+void dev_free(void *p) {
+    if (p) cudaFree(p);
+}
+
+int ws_reserve(fhe_ctx *ctx, u64 **ws, size_t *have, size_t words) {
+    if (*have >= words) return FHE_OK;
+    FHE_CU(cudaDeviceSynchronize());
+    dev_free(*ws);
+    *ws = nullptr;
+    *have = 0;
+    void *p;
+    FHE_TRY(dev_alloc(ctx, &p, words * 8));
+    *ws = (u64 *)p;
+    *have = words;
+    return FHE_OK;
+}
+
+static int upload(fhe_ctx *ctx, const void *host, size_t bytes, void **dev) {
+    FHE_TRY(dev_alloc(ctx, dev, bytes));
+    ctx->owned.push_back(*dev);
+    FHE_CU(cudaMemcpy(*dev, host, bytes, cudaMemcpyHostToDevice));
+    return FHE_OK;
+}
+
+int galois_of_step(const fhe_ctx *ctx, int step) {
+    const long long n = ctx->N / 2;
+    long long r = ((step % n) + n) % n;
+    return (int)h_powmod(5, (u64)r, 2 * (u64)ctx->N);
+}
+
+size_t key_words(const fhe_ctx *ctx) {
+    const int digits = (ctx->L + ctx->alpha) / ctx->alpha;
+    return (size_t)digits * 2 * ctx->n_primes * ctx->N;
+}
+
+// ================================================================ context
+
+static int build_tables(fhe_ctx *c) {
+    const int np = c->n_primes, L = c->L, al = c->alpha;
+    const u64 N = (u64)c->N;
+    std::vector<PrimeTab> pt(np);
+    for (int t = 0; t < np; t++) {
+        const u64 q = c->primes[t];
+        int b = 64 - __builtin_clzll(q);
+        pt[t].m.q = q;
+        pt[t].m.b = b;
+        pt[t].m.mu = (u64)(((u128)1 << (2 * b + 3)) / q);
+        const u64 psi = h_root_2n(q, 2 * N), psi_inv = h_invmod(psi, q);
+        std::vector<u64> pw(N), pwi(N);
+        pw[0] = pwi[0] = 1;
+        for (u64 e = 1; e < N; e++) {
+            pw[e] = h_mulmod(pw[e - 1], psi, q);
+            pwi[e] = h_mulmod(pwi[e - 1], psi_inv, q);
+        }
+        std::vector<ulonglong2> fw(N), iv(N);
+        for (u64 k = 0; k < N; k++) {
+            const u64 w = pw[h_brv((uint32_t)k, c->logN)], wi = pwi[h_brv((uint32_t)k, c->logN)];
+            fw[k] = make_ulonglong2(w, h_shoup(w, q));
+            iv[k] = make_ulonglong2(wi, h_shoup(wi, q));
+        }
+        void *d;
+        FHE_TRY(upload(c, fw.data(), N * sizeof(ulonglong2), &d));
+        pt[t].fwd = (const ulonglong2 *)d;
+        FHE_TRY(upload(c, iv.data(), N * sizeof(ulonglong2), &d));
+        pt[t].inv = (const ulonglong2 *)d;
+        pt[t].n_inv = h_invmod(N % q, q);
+        pt[t].n_inv_sh = h_shoup(pt[t].n_inv, q);
+    }
+    void *d;
+    FHE_TRY(upload(c, pt.data(), np * sizeof(PrimeTab), &d));
+    c->dc.primes = (const PrimeTab *)d;
+    c->dc.logN = c->logN;
+    c->dc.L = L;
+    c->dc.alpha = al;
+    c->dc.logR1 = (c->logN + 1) / 2;
+    c->dc.logR2 = c->logN / 2;
+
+    // ModDown constants: P = prod p_m
+    std::vector<ulonglong2> zs(al);
+    std::vector<u64> za(al), phat((size_t)al * (L + 1)), halfp(L + 1);
+    std::vector<ulonglong2> pinv(L + 1);
+    for (int m = 0; m < al; m++) {
+        const u64 p = c->primes[L + 1 + m];
+        u64 ph = 1;
+        for (int u = 0; u < al; u++)
+            if (u != m) ph = h_mulmod(ph, c->primes[L + 1 + u] % p, p);
+        const u64 phi = h_invmod(ph, p);
+        const u64 sc = h_mulmod(h_invmod(N % p, p), phi, p);
+        zs[m] = make_ulonglong2(sc, h_shoup(sc, p));
+        za[m] = h_mulmod((p - 1) / 2, phi, p);   // floor(P/2) = (P-1)/2 = (p-1)/2 mod p
+        for (int i = 0; i <= L; i++) {
+            const u64 q = c->primes[i];
+            u64 v = 1;
+            for (int u = 0; u < al; u++)
+                if (u != m) v = h_mulmod(v, c->primes[L + 1 + u] % q, q);
+            phat[(size_t)m * (L + 1) + i] = v;
+        }
+    }
+    for (int i = 0; i <= L; i++) {
+        const u64 q = c->primes[i];
+        u64 pm = 1;
+        for (int u = 0; u < al; u++) pm = h_mulmod(pm, c->primes[L + 1 + u] % q, q);
+        // floor(P/2) = (P-1)/2 mod q
+        halfp[i] = h_mulmod((pm + q - 1) % q, h_invmod(2, q), q);
+        const u64 inv = h_invmod(pm, q);
+        pinv[i] = make_ulonglong2(inv, h_shoup(inv, q));
+    }
+    FHE_TRY(upload(c, zs.data(), al * sizeof(ulonglong2), &d));
+    c->dc.md_z_scale = (const ulonglong2 *)d;
+    FHE_TRY(upload(c, za.data(), al * 8, &d));
+    c->dc.md_z_add = (const u64 *)d;
+    FHE_TRY(upload(c, phat.data(), phat.size() * 8, &d));
+    c->dc.md_phat = (const u64 *)d;
+    FHE_TRY(upload(c, halfp.data(), halfp.size() * 8, &d));
+    c->dc.md_halfp = (const u64 *)d;
+    FHE_TRY(upload(c, pinv.data(), pinv.size() * sizeof(ulonglong2), &d));
+    c->dc.md_pinv = (const ulonglong2 *)d;
+
+    // per-level tables
+    c->lt.resize(L + 1);
+    for (int lv = 0; lv <= L; lv++) {
+        LevelTab &T = c->lt[lv];
+        T.level = lv;
+        T.n_digits = (lv + al) / al;
+        T.ext = lv + 1 + al;
+        std::vector<ulonglong2> ys(lv + 1);
+        std::vector<u64> hat((size_t)T.n_digits * al * T.ext, 0);
+        for (int j = 0; j < T.n_digits; j++) {
+            const int lo = j * al, hi = std::min(lo + al, lv + 1);
+            for (int i = lo; i < hi; i++) {
+                const u64 q = c->primes[i];
+                u64 h = 1;
+                for (int u = lo; u < hi; u++)
+                    if (u != i) h = h_mulmod(h, c->primes[u] % q, q);
+                const u64 v = h_mulmod(h_invmod(N % q, q), h_invmod(h, q), q);
+                ys[i] = make_ulonglong2(v, h_shoup(v, q));
+                for (int t = 0; t < T.ext; t++) {
+                    const u64 pt_ = c->primes[ext_prime(t, lv, L)];
+                    u64 hh = 1;
+                    for (int u = lo; u < hi; u++)
+                        if (u != i) hh = h_mulmod(hh, c->primes[u] % pt_, pt_);
+                    hat[((size_t)j * al + (i - lo)) * T.ext + t] = hh;
+                }
+            }
+        }
+        FHE_TRY(upload(c, ys.data(), ys.size() * sizeof(ulonglong2), &d));
+        T.y_scale = (const ulonglong2 *)d;
+        FHE_TRY(upload(c, hat.data(), hat.size() * 8, &d));
+        T.modup_hat = (const u64 *)d;
+        std::vector<ulonglong2> qi(std::max(lv, 1));
+        std::vector<u64> qm(std::max(lv, 1));
+        for (int i = 0; i < lv; i++) {
+            const u64 q = c->primes[i], ql = c->primes[lv];
+            const u64 inv = h_invmod(ql % q, q);
+            qi[i] = make_ulonglong2(inv, h_shoup(inv, q));
+            qm[i] = ql % q;
+        }
+        FHE_TRY(upload(c, qi.data(), qi.size() * sizeof(ulonglong2), &d));
+        T.q_last_inv = (const ulonglong2 *)d;
+        FHE_TRY(upload(c, qm.data(), qm.size() * 8, &d));
+        T.q_last_mod = (const u64 *)d;
+    }
+    return FHE_OK;
+}
+
+extern "C" int fhe_ctx_create(const fhe_params *p, fhe_ctx **out) {
+    if (!p || !out) return fhe_fail(FHE_E_INVAL, "null argument");
+    if (p->log_n < 12 || p->log_n > 16) return fhe_fail(FHE_E_INVAL, "log_n must be in [12, 16]");
+    if (p->alpha < 1 || p->alpha > 8) return fhe_fail(FHE_E_INVAL, "alpha must be in [1, 8]");
+    if (p->L < 0 || p->L + 1 + p->alpha > FHE_MAX_LIMBS) return fhe_fail(FHE_E_INVAL, "too many primes");
+    if (p->q_bits > 58 || p->q0_bits > 58 || p->p_bits > 58 || p->q_bits < 20 || p->q0_bits < 20 ||
+        p->p_bits < 20)
+        return fhe_fail(FHE_E_INVAL, "prime sizes must be in [20, 58] bits");
+    const int digits_top = (p->L + p->alpha) / p->alpha;
+    if (digits_top > 7) return fhe_fail(FHE_E_INVAL, "more than 7 key-switching digits");
+    int ndev = 0;
+    FHE_CU(cudaGetDeviceCount(&ndev));
+    if (p->device < 0 || p->device >= ndev) return fhe_fail(FHE_E_INVAL, "no such CUDA device");
+    FHE_CU(cudaSetDevice(p->device));
+    std::unique_ptr<fhe_ctx> c(new fhe_ctx());
+    c->prm = *p;
+    c->dev = p->device;
+    c->logN = p->log_n;
+    c->N = 1ll << p->log_n;
+    c->L = p->L;
+    c->alpha = p->alpha;
+    c->n_primes = p->L + 1 + p->alpha;
+    c->scale = std::pow(2.0, p->log_scale);
+    const u64 two_n = 2 * (u64)c->N;
+    std::vector<u64> rest = p->L > 0 ? h_gen_primes(p->q_bits, p->L, two_n, {}) : std::vector<u64>();
+    if ((int)rest.size() != p->L) return fhe_fail(FHE_E_INVAL, "not enough q primes");
+    std::vector<u64> q0 = h_gen_primes(p->q0_bits, 1, two_n, rest);
+    if (q0.size() != 1) return fhe_fail(FHE_E_INVAL, "no q0 prime");
+    std::vector<u64> taken = rest;
+    taken.push_back(q0[0]);
+    std::vector<u64> sp = h_gen_primes(p->p_bits, p->alpha, two_n, taken);
+    if ((int)sp.size() != p->alpha) return fhe_fail(FHE_E_INVAL, "not enough special primes");
+    c->primes.push_back(q0[0]);
+    for (u64 x : rest) c->primes.push_back(x);
+    for (u64 x : sp) c->primes.push_back(x);
+    c->enc.init(c->logN);
+    int r = build_tables(c.get());
+    if (r != FHE_OK) {
+        for (void *q : c->owned) dev_free(q);
+        return r;
+    }
+    *out = c.release();
+    return FHE_OK;
+}
+
+extern "C" int fhe_ctx_destroy(fhe_ctx *ctx) {
+    if (!ctx) return FHE_OK;
+    cudaSetDevice(ctx->dev);
+    cudaDeviceSynchronize();
+    for (void *p : ctx->owned) dev_free(p);
+    dev_free(ctx->ks_ws);
+    dev_free(ctx->rs_ws);
+    delete ctx;
+    return FHE_OK;
+}
+
+extern "C" int fhe_ctx_primes(const fhe_ctx *ctx, uint64_t *out, size_t cap, size_t *n) {
+    if (!ctx || !n) return fhe_fail(FHE_E_INVAL, "null argument");
+    *n = ctx->primes.size();
+    if (out) {
+        if (cap < ctx->primes.size()) return fhe_fail(FHE_E_INVAL, "buffer too small");
+        for (size_t i = 0; i < ctx->primes.size(); i++) out[i] = ctx->primes[i];
+    }
+    return FHE_OK;
+}
+
+// ================================================================ core ops
+
+int op_ntt(fhe_ctx *ctx, const u64 *src, u64 *dst, long long item, int n_items, int n_limbs,
+           const unsigned char *pidx, bool inverse, cudaStream_t s) {
+    NttArgs a;
+    memset(&a, 0, sizeof(a));
+    a.src = src;
+    a.dst = dst;
+    a.src_item = a.dst_item = item;
+    a.n_items = n_items;
+    a.n_limbs = n_limbs;
+    for (int l = 0; l < n_limbs; l++) a.pidx[l] = pidx ? pidx[l] : (unsigned char)l;
+    FHE_CU(launch_ntt(ctx->dc, a, inverse, s));
+    return FHE_OK;
+}
+
+int op_keyswitch(fhe_ctx *ctx, KsArgs a, cudaStream_t s) {
+    const size_t per = ks_workspace_words(ctx->dc, a.level);
+    FHE_TRY(ws_reserve(ctx, &ctx->ks_ws, &ctx->ks_ws_words, per * (size_t)a.n_items));
+    a.ws = ctx->ks_ws;
+    a.ws_item = (long long)per;
+    FHE_CU(launch_keyswitch(ctx->dc, ctx->lt[a.level], a, s));
+    return FHE_OK;
+}
+
+int op_rescale(fhe_ctx *ctx, const u64 *in, long long in_item, u64 *out, long long out_item, int n_items,
+               int n_poly, int level, cudaStream_t s) {
+    if (level < 1) return fhe_fail(FHE_E_LEVEL, "rescale at level 0");
+    FHE_TRY(ws_reserve(ctx, &ctx->rs_ws, &ctx->rs_ws_words, (size_t)n_items * n_poly * ctx->N));
+    RescaleArgs a;
+    a.in = in;
+    a.in_item = in_item;
+    a.out = out;
+    a.out_item = out_item;
+    a.n_items = n_items;
+    a.n_poly = n_poly;
+    a.level = level;
+    a.ws = ctx->rs_ws;
+    FHE_CU(launch_rescale(ctx->dc, ctx->lt[level], a, s));
+    return FHE_OK;
+}
+
+int op_encode_to(fhe_ctx *ctx, const double *m_host, int level, u64 *dst, cudaStream_t s) {
+    double *dm;
+    FHE_CU(cudaMallocAsync((void **)&dm, ctx->N * sizeof(double), s));
+    FHE_CU(cudaMemcpyAsync(dm, m_host, ctx->N * sizeof(double), cudaMemcpyHostToDevice, s));
+    FHE_CU(launch_double_to_limbs(ctx->dc, dm, dst, level + 1, s));
+    FHE_CU(cudaFreeAsync(dm, s));
+    FHE_TRY(op_ntt(ctx, dst, dst, 0, 1, level + 1, nullptr, false, s));
+    return FHE_OK;
+}
+
+// ================================================================ keys
+
+enum { DOM_SECRET = 1, DOM_KEY_A = 2, DOM_KEY_E = 3, DOM_ENC_A = 4, DOM_ENC_E = 5 };
+
+static int make_switch_key(fhe_ctx *c, uint64_t seed, int key_id, const u64 *s_ntt, const u64 *s_new, u64 *key) {
+    const int np = c->n_primes, al = c->alpha, L = c->L;
+    const long long N = c->N;
+    const int digits = (L + al) / al;
+    std::vector<unsigned char> pidx(np);
+    for (int t = 0; t < np; t++) pidx[t] = (unsigned char)t;
+    // P mod q_t for every Q prime
+    std::vector<u64> pmod(np, 0);
+    for (int t = 0; t <= L; t++) {
+        u64 v = 1;
+        for (int u = 0; u < al; u++) v = h_mulmod(v, c->primes[L + 1 + u] % c->primes[t], c->primes[t]);
+        pmod[t] = v;
+    }
+    u64 *d_pmod;
+    FHE_TRY(dev_alloc(c, (void **)&d_pmod, np * 8));
+    long long *e;
+    FHE_TRY(dev_alloc(c, (void **)&e, N * 8));
+    FHE_CU(cudaMemcpy(d_pmod, pmod.data(), np * 8, cudaMemcpyHostToDevice));
+    for (int j = 0; j < digits; j++) {
+        u64 *b = key + (size_t)(2 * j) * np * N;
+        u64 *a = key + (size_t)(2 * j + 1) * np * N;
+        FHE_CU(launch_sample_uniform(c->dc, seed, DOM_KEY_A, (uint32_t)key_id, (uint32_t)j * 65536u, 1, a, np,
+                                     pidx.data(), 0));
+        FHE_CU(launch_sample_small(c->dc, seed, DOM_KEY_E, (uint32_t)key_id, (uint32_t)j, 1, e, 0));
+        FHE_CU(launch_signed_to_limbs(c->dc, e, b, np, pidx.data(), 0));
+        FHE_TRY(op_ntt(c, b, b, 0, 1, np, pidx.data(), false, 0));
+        // b = e - a*s
+        FHE_CU(launch_mul_limbs(c->dc, a, s_ntt, b, 1, b, np, pidx.data(), 0));
+        // + (P mod q_t) * s_new[t] on the digit's own limbs
+        const int lo = j * al, hi = std::min(lo + al, L + 1);
+        FHE_CU(launch_axpy_limbs(c->dc, s_new + (size_t)lo * N, d_pmod + lo, b + (size_t)lo * N, hi - lo,
+                                 pidx.data() + lo, 0));
+    }
+    FHE_CU(cudaDeviceSynchronize());
+    dev_free(d_pmod);
+    dev_free(e);
+    return FHE_OK;
+}
+
+extern "C" int fhe_keygen(fhe_ctx *c, uint64_t seed, const int32_t *rot_steps, size_t n_steps, fhe_sk **sk_out,
+                          fhe_evk **evk_out) {
+    if (!c || !sk_out || !evk_out || (n_steps && !rot_steps)) return fhe_fail(FHE_E_INVAL, "null argument");
+    FHE_CU(cudaSetDevice(c->dev));
+    const int np = c->n_primes;
+    const long long N = c->N;
+    std::vector<unsigned char> pidx(np);
+    for (int t = 0; t < np; t++) pidx[t] = (unsigned char)t;
+    std::unique_ptr<fhe_sk> sk(new fhe_sk());
+    sk->ctx = c;
+    FHE_TRY(dev_alloc(c, (void **)&sk->s_ntt, (size_t)np * N * 8));
+    long long *scoef;
+    FHE_TRY(dev_alloc(c, (void **)&scoef, N * 8));
+    FHE_CU(launch_sample_small(c->dc, seed, DOM_SECRET, 0, 0, 0, scoef, 0));
+    FHE_CU(launch_signed_to_limbs(c->dc, scoef, sk->s_ntt, np, pidx.data(), 0));
+    FHE_TRY(op_ntt(c, sk->s_ntt, sk->s_ntt, 0, 1, np, pidx.data(), false, 0));
+    FHE_CU(cudaDeviceSynchronize());
+    dev_free(scoef);
+
+    std::unique_ptr<fhe_evk> evk(new fhe_evk());
+    evk->ctx = c;
+    evk->digits = (c->L + c->alpha) / c->alpha;
+    const size_t kw = key_words(c);
+    u64 *s2;
+    FHE_TRY(dev_alloc(c, (void **)&s2, (size_t)np * N * 8));
+    FHE_CU(launch_mul_limbs(c->dc, sk->s_ntt, sk->s_ntt, nullptr, 0, s2, np, pidx.data(), 0));
+    FHE_TRY(dev_alloc(c, (void **)&evk->relin, kw * 8));
+    FHE_TRY(make_switch_key(c, seed, 0, sk->s_ntt, s2, evk->relin));
+    for (size_t i = 0; i < n_steps; i++) {
+        const int k = galois_of_step(c, rot_steps[i]);
+        if (k == 1 || evk->galois.count(k)) continue;
+        FHE_CU(launch_automorphism(c->dc, sk->s_ntt, s2, np, k, 0));
+        u64 *key;
+        FHE_TRY(dev_alloc(c, (void **)&key, kw * 8));
+        evk->galois[k] = key;
+        FHE_TRY(make_switch_key(c, seed, k, sk->s_ntt, s2, key));
+    }
+    FHE_CU(cudaDeviceSynchronize());
+    dev_free(s2);
+    *sk_out = sk.release();
+    *evk_out = evk.release();
+    return FHE_OK;
+}
+
+extern "C" int fhe_sk_free(fhe_sk *sk) {
+    if (!sk) return FHE_OK;
+    cudaDeviceSynchronize();
+    dev_free(sk->s_ntt);
+    delete sk;
+    return FHE_OK;
+}
+
+extern "C" int fhe_evk_free(fhe_evk *evk) {
+    if (!evk) return FHE_OK;
+    cudaDeviceSynchronize();
+    dev_free(evk->relin);
+    for (auto &kv : evk->galois) dev_free(kv.second);
+    delete evk;
+    return FHE_OK;
+}
+
+extern "C" int fhe_evk_galois(const fhe_evk *evk, int32_t *out, size_t cap, size_t *n) {
+    if (!evk || !n) return fhe_fail(FHE_E_INVAL, "null argument");
+    *n = evk->galois.size();
+    if (out) {
+        if (cap < evk->galois.size()) return fhe_fail(FHE_E_INVAL, "buffer too small");
+        size_t i = 0;
+        for (auto &kv : evk->galois) out[i++] = kv.first;
+    }
+    return FHE_OK;
+}
+
+// ================================================================ encode / encrypt
+
+extern "C" int fhe_encode(fhe_ctx *c, const double *re, const double *im, size_t n, double scale, int level,
+                          fhe_pt **out) {
+    if (!c || !out || (n && !re)) return fhe_fail(FHE_E_INVAL, "null argument");
+    if (n > (size_t)c->N / 2) return fhe_fail(FHE_E_INVAL, "more slots than N/2");
+    if (level < 0 || level > c->L) return fhe_fail(FHE_E_LEVEL, "level out of range");
+    if (!(scale > 0)) return fhe_fail(FHE_E_INVAL, "scale must be positive");
+    FHE_CU(cudaSetDevice(c->dev));
+    std::vector<double> m(c->N);
+    c->enc.encode(re, im, n, scale, m.data());
+    std::unique_ptr<fhe_pt> pt(new fhe_pt());
+    pt->ctx = c;
+    pt->level = level;
+    pt->scale = scale;
+    FHE_TRY(dev_alloc(c, (void **)&pt->d, (size_t)(level + 1) * c->N * 8));
+    FHE_TRY(op_encode_to(c, m.data(), level, pt->d, 0));
+    FHE_CU(cudaDeviceSynchronize());
+    *out = pt.release();
+    return FHE_OK;
+}
+
+extern "C" int fhe_encode_coeffs(fhe_ctx *c, const double *re, const double *im, size_t n, double scale,
+                                 double *out) {
+    if (!c || !out || (n && !re)) return fhe_fail(FHE_E_INVAL, "null argument");
+    if (n > (size_t)c->N / 2) return fhe_fail(FHE_E_INVAL, "more slots than N/2");
+    c->enc.encode(re, im, n, scale, out);
+    return FHE_OK;
+}
+
+extern "C" int fhe_pt_free(fhe_pt *pt) {
+    if (!pt) return FHE_OK;
+    cudaDeviceSynchronize();
+    dev_free(pt->d);
+    delete pt;
+    return FHE_OK;
+}
+
+extern "C" int fhe_encrypt(fhe_ctx *c, const fhe_sk *sk, const fhe_pt *pt, uint64_t seed, fhe_ct **out) {
+    if (!c || !sk || !pt || !out) return fhe_fail(FHE_E_INVAL, "null argument");
+    FHE_CU(cudaSetDevice(c->dev));
+    const int lv = pt->level, nl = lv + 1;
+    const long long N = c->N;
+    std::vector<unsigned char> pidx(nl);
+    for (int t = 0; t < nl; t++) pidx[t] = (unsigned char)t;
+    std::unique_ptr<fhe_ct> ct(new fhe_ct());
+    ct->ctx = c;
+    ct->level = lv;
+    ct->n_poly = 2;
+    ct->scale = pt->scale;
+    FHE_TRY(dev_alloc(c, (void **)&ct->d, (size_t)2 * nl * N * 8));
+    u64 *c0 = ct->d, *c1 = ct->d + (size_t)nl * N;
+    long long *e;
+    FHE_TRY(dev_alloc(c, (void **)&e, N * 8));
+    FHE_CU(launch_sample_uniform(c->dc, seed, DOM_ENC_A, 0, 0, 1, c1, nl, pidx.data(), 0));
+    FHE_CU(launch_sample_small(c->dc, seed, DOM_ENC_E, 0, 0, 1, e, 0));
+    FHE_CU(launch_signed_to_limbs(c->dc, e, c0, nl, pidx.data(), 0));
+    FHE_TRY(op_ntt(c, c0, c0, 0, 1, nl, nullptr, false, 0));
+    FHE_CU(launch_add(c->dc, c0, 0, pt->d, 0, c0, 0, 1, 1, lv, 0, 0));
+    FHE_CU(launch_mul_limbs(c->dc, c1, sk->s_ntt, c0, 1, c0, nl, pidx.data(), 0));
+    FHE_CU(cudaDeviceSynchronize());
+    dev_free(e);
+    *out = ct.release();
+    return FHE_OK;
+}
+
+extern "C" int fhe_decrypt(fhe_ctx *c, const fhe_sk *sk, const fhe_ct *ct, fhe_pt **out) {
+    if (!c || !sk || !ct || !out) return fhe_fail(FHE_E_INVAL, "null argument");
+    if (ct->n_poly != 2) return fhe_fail(FHE_E_INVAL, "decrypt needs a 2-polynomial ciphertext");
+    FHE_CU(cudaSetDevice(c->dev));
+    std::unique_ptr<fhe_pt> pt(new fhe_pt());
+    pt->ctx = c;
+    pt->level = ct->level;
+    pt->scale = ct->scale;
+    FHE_TRY(dev_alloc(c, (void **)&pt->d, (size_t)(ct->level + 1) * c->N * 8));
+    FHE_CU(launch_decrypt(c->dc, ct->d, sk->s_ntt, pt->d, ct->level, 0));
+    FHE_CU(cudaDeviceSynchronize());
+    *out = pt.release();
+    return FHE_OK;
+}
+
+// centred CRT value of residues r[0..l] as a long double (Garner's mixed radix)
+static long double crt_centered(const u64 *r, int nl, const u64 *q, const std::vector<std::vector<u64>> &inv) {
+    u64 v[FHE_MAX_LIMBS], w[FHE_MAX_LIMBS];
+    for (int pass = 0; pass < 2; pass++) {
+        u64 *d = pass == 0 ? v : w;
+        for (int k = 0; k < nl; k++) {
+            const u64 qk = q[k];
+            u64 rk = pass == 0 ? r[k] % qk : (qk - r[k] % qk) % qk;
+            u64 acc = 0;
+            for (int m = k - 1; m >= 0; m--) acc = (u64)(((u128)acc * (q[m] % qk) + d[m]) % qk);
+            d[k] = h_mulmod((rk + qk - acc) % qk, inv[k][0], qk);
+        }
+    }
+    // compare x and Q - x from the most significant digit
+    bool neg = false;
+    for (int k = nl - 1; k >= 0; k--) {
+        if (v[k] != w[k]) {
+            neg = v[k] > w[k];
+            break;
+        }
+    }
+    const u64 *d = neg ? w : v;
+    long double x = 0;
+    for (int k = nl - 1; k >= 0; k--) x = x * (long double)q[k] + (long double)d[k];
+    return neg ? -x : x;
+}
+
+extern "C" int fhe_decode(fhe_ctx *c, const fhe_pt *pt, double *re, double *im, size_t n) {
+    if (!c || !pt || (n && !re)) return fhe_fail(FHE_E_INVAL, "null argument");
+    if (n > (size_t)c->N / 2) return fhe_fail(FHE_E_INVAL, "more slots than N/2");
+    FHE_CU(cudaSetDevice(c->dev));
+    const int nl = pt->level + 1;
+    const long long N = c->N;
+    u64 *tmp;
+    FHE_TRY(dev_alloc(c, (void **)&tmp, (size_t)nl * N * 8));
+    FHE_TRY(op_ntt(c, pt->d, tmp, 0, 1, nl, nullptr, true, 0));
+    std::vector<u64> h((size_t)nl * N);
+    FHE_CU(cudaMemcpy(h.data(), tmp, h.size() * 8, cudaMemcpyDeviceToHost));
+    dev_free(tmp);
+    std::vector<std::vector<u64>> inv(nl, std::vector<u64>(1));
+    for (int k = 0; k < nl; k++) {
+        u64 p = 1;
+        for (int m = 0; m < k; m++) p = h_mulmod(p, c->primes[m] % c->primes[k], c->primes[k]);
+        inv[k][0] = h_invmod(p, c->primes[k]);
+    }
+    std::vector<double> m(N);
+    std::vector<u64> r(nl);
+    for (long long j = 0; j < N; j++) {
+        for (int k = 0; k < nl; k++) r[k] = h[(size_t)k * N + j];
+        m[j] = (double)crt_centered(r.data(), nl, c->primes.data(), inv);
+    }
+    c->enc.decode(m.data(), pt->scale, re, im, n);
+    return FHE_OK;
+}
+
+// ================================================================ ciphertexts
+
+static int new_ct(fhe_ctx *c, int level, int n_poly, double scale, fhe_ct **out) {
+    std::unique_ptr<fhe_ct> ct(new fhe_ct());
+    ct->ctx = c;
+    ct->level = level;
+    ct->n_poly = n_poly;
+    ct->scale = scale;
+    FHE_TRY(dev_alloc(c, (void **)&ct->d, (size_t)n_poly * (level + 1) * c->N * 8));
+    *out = ct.release();
+    return FHE_OK;
+}
+
+extern "C" int fhe_ct_free(fhe_ct *ct) {
+    if (!ct) return FHE_OK;
+    cudaDeviceSynchronize();
+    dev_free(ct->d);
+    delete ct;
+    return FHE_OK;
+}
+
+extern "C" int fhe_ct_info(const fhe_ct *ct, int *level, int *n_poly, double *scale) {
+    if (!ct) return fhe_fail(FHE_E_INVAL, "null argument");
+    if (level) *level = ct->level;
+    if (n_poly) *n_poly = ct->n_poly;
+    if (scale) *scale = ct->scale;
+    return FHE_OK;
+}
+
+extern "C" int fhe_ct_export(const fhe_ct *ct, uint64_t *buf, size_t cap, int *level, double *scale, int *n_poly) {
+    if (!ct || !buf) return fhe_fail(FHE_E_INVAL, "null argument");
+    fhe_ctx *c = ct->ctx;
+    FHE_CU(cudaSetDevice(c->dev));
+    const int nl = ct->level + 1;
+    const size_t words = (size_t)ct->n_poly * nl * c->N;
+    if (cap < words) return fhe_fail(FHE_E_INVAL, "buffer too small");
+    u64 *tmp;
+    FHE_TRY(dev_alloc(c, (void **)&tmp, words * 8));
+    FHE_TRY(op_ntt(c, ct->d, tmp, (long long)nl * c->N, ct->n_poly, nl, nullptr, true, 0));
+    FHE_CU(cudaMemcpy(buf, tmp, words * 8, cudaMemcpyDeviceToHost));
+    dev_free(tmp);
+    if (level) *level = ct->level;
+    if (scale) *scale = ct->scale;
+    if (n_poly) *n_poly = ct->n_poly;
+    return FHE_OK;
+}
+
+extern "C" int fhe_ct_import(fhe_ctx *c, const uint64_t *buf, int n_poly, int level, double scale, fhe_ct **out) {
+    if (!c || !buf || !out) return fhe_fail(FHE_E_INVAL, "null argument");
+    if (level < 0 || level > c->L) return fhe_fail(FHE_E_LEVEL, "level out of range");
+    if (n_poly < 1 || n_poly > 3) return fhe_fail(FHE_E_INVAL, "n_poly must be 1..3");
+    FHE_CU(cudaSetDevice(c->dev));
+    const int nl = level + 1;
+    const size_t words = (size_t)n_poly * nl * c->N;
+    for (int p = 0; p < n_poly; p++)
+        for (int l = 0; l < nl; l++) {
+            const u64 *x = (const u64 *)buf + ((size_t)p * nl + l) * c->N;
+            const u64 q = c->primes[l];
+            for (long long j = 0; j < c->N; j++)
+                if (x[j] >= q) return fhe_fail(FHE_E_INVAL, "residue out of range");
+        }
+    fhe_ct *ct;
+    FHE_TRY(new_ct(c, level, n_poly, scale, &ct));
+    cudaError_t e = cudaMemcpy(ct->d, buf, words * 8, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        fhe_ct_free(ct);
+        return fhe_fail(FHE_E_CUDA, cudaGetErrorString(e));
+    }
+    int r = op_ntt(c, ct->d, ct->d, (long long)nl * c->N, n_poly, nl, nullptr, false, 0);
+    if (r != FHE_OK) {
+        fhe_ct_free(ct);
+        return r;
+    }
+    FHE_CU(cudaDeviceSynchronize());
+    *out = ct;
+    return FHE_OK;
+}
+
+// ================================================================ primitives
+
+extern "C" int fhe_rotate(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *in, int step, fhe_ct **out, void *stream) {
+    if (!c || !evk || !in || !out) return fhe_fail(FHE_E_INVAL, "null argument");
+    if (in->n_poly != 2) return fhe_fail(FHE_E_INVAL, "rotate needs a 2-polynomial ciphertext");
+    FHE_CU(cudaSetDevice(c->dev));
+    cudaStream_t s = (cudaStream_t)stream;
+    const int k = galois_of_step(c, step);
+    const int nl = in->level + 1;
+    const long long N = c->N;
+    fhe_ct *o;
+    FHE_TRY(new_ct(c, in->level, 2, in->scale, &o));
+    if (k == 1) {
+        cudaError_t e = cudaMemcpyAsync(o->d, in->d, (size_t)2 * nl * N * 8, cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) {
+            fhe_ct_free(o);
+            return fhe_fail(FHE_E_CUDA, cudaGetErrorString(e));
+        }
+        *out = o;
+        return FHE_OK;
+    }
+    auto it = evk->galois.find(k);
+    if (it == evk->galois.end()) {
+        fhe_ct_free(o);
+        return fhe_fail(FHE_E_NOKEY, "no Galois key for rotation step " + std::to_string(step));
+    }
+    KsArgs a;
+    memset(&a, 0, sizeof(a));
+    a.d = in->d + (size_t)nl * N;
+    a.galois = k;
+    a.key = it->second;
+    a.key_digits_top = evk->digits;
+    a.add0 = in->d;
+    a.out = o->d;
+    a.n_items = 1;
+    a.level = in->level;
+    int r = op_keyswitch(c, a, s);
+    if (r != FHE_OK) {
+        fhe_ct_free(o);
+        return r;
+    }
+    *out = o;
+    return FHE_OK;
+}
+
+extern "C" int fhe_square(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *in, fhe_ct **out, void *stream) {
+    if (!c || !evk || !in || !out) return fhe_fail(FHE_E_INVAL, "null argument");
+    if (in->n_poly != 2) return fhe_fail(FHE_E_INVAL, "square needs a 2-polynomial ciphertext");
+    FHE_CU(cudaSetDevice(c->dev));
+    cudaStream_t s = (cudaStream_t)stream;
+    const int nl = in->level + 1;
+    const long long N = c->N;
+    u64 *t3;
+    FHE_CU(cudaMallocAsync((void **)&t3, (size_t)3 * nl * N * 8, s));
+    FHE_CU(launch_square_act(c->dc, in->d, 0, nullptr, nullptr, t3, 0, 1, in->level, s));
+    fhe_ct *o;
+    FHE_TRY(new_ct(c, in->level, 2, in->scale * in->scale, &o));
+    KsArgs a;
+    memset(&a, 0, sizeof(a));
+    a.d = t3 + (size_t)2 * nl * N;
+    a.galois = 1;
+    a.key = evk->relin;
+    a.key_digits_top = evk->digits;
+    a.add0 = t3;
+    a.add1 = t3 + (size_t)nl * N;
+    a.out = o->d;
+    a.n_items = 1;
+    a.level = in->level;
+    int r = op_keyswitch(c, a, s);
+    cudaFreeAsync(t3, s);
+    if (r != FHE_OK) {
+        fhe_ct_free(o);
+        return r;
+    }
+    *out = o;
+    return FHE_OK;
+}
+
+extern "C" int fhe_rescale(fhe_ctx *c, fhe_ct *ct, void *stream) {
+    if (!c || !ct) return fhe_fail(FHE_E_INVAL, "null argument");
+    if (ct->level < 1) return fhe_fail(FHE_E_LEVEL, "no level left to rescale");
+    FHE_CU(cudaSetDevice(c->dev));
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long N = c->N;
+    u64 *o;
+    FHE_TRY(dev_alloc(c, (void **)&o, (size_t)ct->n_poly * ct->level * N * 8));
+    int r = op_rescale(c, ct->d, 0, o, 0, 1, ct->n_poly, ct->level, s);
+    if (r != FHE_OK) {
+        dev_free(o);
+        return r;
+    }
+    FHE_CU(cudaStreamSynchronize(s));
+    dev_free(ct->d);
+    ct->d = o;
+    ct->scale = ct->scale / (double)c->primes[ct->level];
+    ct->level -= 1;
+    return FHE_OK;
+}
+
+extern "C" int fhe_add(fhe_ctx *c, const fhe_ct *a, const fhe_ct *b, fhe_ct **out, void *stream) {
+    if (!c || !a || !b || !out) return fhe_fail(FHE_E_INVAL, "null argument");
+    if (a->level != b->level || a->n_poly != b->n_poly) return fhe_fail(FHE_E_LEVEL, "operands differ in level");
+    FHE_CU(cudaSetDevice(c->dev));
+    fhe_ct *o;
+    FHE_TRY(new_ct(c, a->level, a->n_poly, a->scale, &o));
+    FHE_CU(launch_add(c->dc, a->d, 0, b->d, 0, o->d, 0, 1, a->n_poly, a->level, 0, (cudaStream_t)stream));
+    *out = o;
+    return FHE_OK;
+}
+
+extern "C" int fhe_mul_plain(fhe_ctx *c, const fhe_ct *a, const fhe_pt *pt, fhe_ct **out, void *stream) {
+    if (!c || !a || !pt || !out) return fhe_fail(FHE_E_INVAL, "null argument");
+    if (pt->level < a->level) return fhe_fail(FHE_E_LEVEL, "plaintext level below ciphertext level");
+    FHE_CU(cudaSetDevice(c->dev));
+    const int nl = a->level + 1;
+    std::vector<unsigned char> pidx(nl);
+    for (int t = 0; t < nl; t++) pidx[t] = (unsigned char)t;
+    fhe_ct *o;
+    FHE_TRY(new_ct(c, a->level, a->n_poly, a->scale * pt->scale, &o));
+    for (int p = 0; p < a->n_poly; p++)
+        FHE_CU(launch_mul_limbs(c->dc, a->d + (size_t)p * nl * c->N, pt->d, nullptr, 0, o->d + (size_t)p * nl * c->N,
+                                nl, pidx.data(), (cudaStream_t)stream));
+    *out = o;
+    return FHE_OK;
+}
+
+// ================================================================ test hooks
+
+extern "C" int fhe_ntt_device(fhe_ctx *c, uint64_t *d, size_t n_limbs, const int32_t *prime_idx, int inverse,
+                              void *stream) {
+    if (!c || !d || !prime_idx || n_limbs == 0) return fhe_fail(FHE_E_INVAL, "null argument");
+    FHE_CU(cudaSetDevice(c->dev));
+    std::vector<unsigned char> p(FHE_MAX_LIMBS);
+    for (size_t off = 0; off < n_limbs; off += FHE_MAX_LIMBS) {
+        const int cnt = (int)std::min<size_t>(FHE_MAX_LIMBS, n_limbs - off);
+        for (int l = 0; l < cnt; l++) {
+            if (prime_idx[off + l] < 0 || prime_idx[off + l] >= c->n_primes)
+                return fhe_fail(FHE_E_INVAL, "prime index out of range");
+            p[l] = (unsigned char)prime_idx[off + l];
+        }
+        u64 *dd = (u64 *)d + off * c->N;
+        FHE_TRY(op_ntt(c, dd, dd, 0, 1, cnt, p.data(), inverse != 0, (cudaStream_t)stream));
+    }
+    return FHE_OK;
+}
+
+extern "C" int fhe_evk_export(const fhe_evk *evk, int galois, uint64_t *buf, size_t cap, size_t *n_words) {
+    if (!evk || !n_words) return fhe_fail(FHE_E_INVAL, "null argument");
+    fhe_ctx *c = evk->ctx;
+    const u64 *k = nullptr;
+    if (galois == 0) {
+        k = evk->relin;
+    } else {
+        auto it = evk->galois.find(galois);
+        if (it == evk->galois.end()) return fhe_fail(FHE_E_NOKEY, "no such Galois key");
+        k = it->second;
+    }
+    *n_words = key_words(c);
+    if (buf) {
+        if (cap < *n_words) return fhe_fail(FHE_E_INVAL, "buffer too small");
+        FHE_CU(cudaMemcpy(buf, k, *n_words * 8, cudaMemcpyDeviceToHost));
+    }
+    return FHE_OK;
+}
+
+extern "C" int fhe_sk_export(const fhe_sk *sk, uint64_t *buf, size_t cap) {
+    if (!sk || !buf) return fhe_fail(FHE_E_INVAL, "null argument");
+    const size_t w = (size_t)sk->ctx->n_primes * sk->ctx->N;
+    if (cap < w) return fhe_fail(FHE_E_INVAL, "buffer too small");
+    FHE_CU(cudaMemcpy(buf, sk->s_ntt, w * 8, cudaMemcpyDeviceToHost));
+    return FHE_OK;
+}

@@ -1,0 +1,117 @@
+// Host-side internals shared by the library's translation units.
+#pragma once
+#include <cstdint>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/fhecnn.h"
+#include "kernels.h"
+
+typedef unsigned __int128 u128;
+
+int fhe_fail(int code, const std::string &msg);
+
+#define FHE_CU(call)                                                                           \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess) return fhe_fail(FHE_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+#define FHE_TRY(call)              \
+    do {                           \
+        int r_ = (call);           \
+        if (r_ != FHE_OK) return r_; \
+    } while (0)
+
+// ---- host modular arithmetic
+inline u64 h_mulmod(u64 a, u64 b, u64 q) { return (u64)((u128)a * b % q); }
+u64 h_powmod(u64 a, u64 e, u64 q);
+inline u64 h_invmod(u64 a, u64 q) { return h_powmod(a % q, q - 2, q); }
+inline u64 h_shoup(u64 w, u64 q) { return (u64)(((u128)w << 64) / q); }
+bool h_is_prime(u64 n);
+std::vector<u64> h_gen_primes(int bits, int count, u64 two_n, const std::vector<u64> &taken);
+u64 h_root_2n(u64 q, u64 two_n);
+
+// ---- slot encoder / decoder (host FFT)
+struct Encoder {
+    int logN = 0;
+    size_t N = 0, n = 0;
+    std::vector<double> fft_re, fft_im;   // per stage length, concatenated: len/2 entries each
+    std::vector<size_t> fft_off;          // offset of stage with length 2^s
+    std::vector<double> tw_c, tw_s;       // cos, sin(pi k / N)
+    std::vector<uint32_t> slot_pos;       // t_j = (5^j mod 2N - 1) / 4
+    std::vector<uint32_t> brv;            // bit reversal over log2(n) bits
+    void init(int logN);
+    // integral doubles m[N] = round(scale * sigma^-1(z))
+    void encode(const double *re, const double *im, size_t nz, double scale, double *m) const;
+    // slots from real coefficients (centred values) divided by scale
+    void decode(const double *m, double scale, double *re, double *im, size_t nz) const;
+};
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+struct fhe_ctx {
+    fhe_params prm;
+    int logN = 0, L = 0, alpha = 0, n_primes = 0;
+    long long N = 0;
+    double scale = 0;
+    std::vector<u64> primes;          // q_0..q_L, p_0..
+    DevCtx dc;
+    std::vector<LevelTab> lt;         // per level
+    std::vector<void *> owned;        // device allocations of the context
+    Encoder enc;
+    // growable workspaces
+    u64 *ks_ws = nullptr;
+    size_t ks_ws_words = 0;
+    u64 *rs_ws = nullptr;
+    size_t rs_ws_words = 0;
+    int dev = 0;
+};
+
+struct fhe_ct {
+    fhe_ctx *ctx;
+    u64 *d;
+    int level, n_poly;
+    double scale;
+};
+
+struct fhe_pt {
+    fhe_ctx *ctx;
+    u64 *d;       // NTT-domain limbs 0..level
+    int level;
+    double scale;
+};
+
+struct fhe_sk {
+    fhe_ctx *ctx;
+    u64 *s_ntt;   // [L+1+alpha][N]
+};
+
+struct fhe_evk {
+    fhe_ctx *ctx;
+    int digits;                   // digits at the top level
+    u64 *relin = nullptr;         // [digits][2][L+1+alpha][N]
+    std::map<int, u64 *> galois;  // Galois element -> key
+};
+
+int dev_alloc(fhe_ctx *ctx, void **p, size_t bytes);
+void dev_free(void *p);
+int ws_reserve(fhe_ctx *ctx, u64 **ws, size_t *have, size_t words);
+int galois_of_step(const fhe_ctx *ctx, int step);
+size_t key_words(const fhe_ctx *ctx);
+
+// integral double -> residue mod q (exact)
+u64 h_double_mod(double v, u64 q);
+
+// core operations on raw device buffers (batched over items)
+int op_keyswitch(fhe_ctx *ctx, KsArgs a, cudaStream_t s);
+int op_rescale(fhe_ctx *ctx, const u64 *in, long long in_item, u64 *out, long long out_item, int n_items,
+               int n_poly, int level, cudaStream_t s);
+int op_ntt(fhe_ctx *ctx, const u64 *src, u64 *dst, long long item, int n_items, int n_limbs,
+           const unsigned char *pidx, bool inverse, cudaStream_t s);
+// encode integral doubles into NTT-domain limbs 0..level (device)
+int op_encode_to(fhe_ctx *ctx, const double *m_host, int level, u64 *dst, cudaStream_t s);

@@ -1,0 +1,1126 @@
+// RNS-CKKS hot-path kernels for sm_103a.
+//
+// NTT: the negacyclic transform A[j] = a(psi^(2 brv(j) + 1)) (bit-reversed
+// evaluation order) is done in two passes over HBM.  With N = R1 * R2, the
+// first log2(R1) Cooley-Tukey stages only mix elements that are congruent
+// mod R2 ("columns" of length R1, stride R2), the remaining log2(R2) stages
+// only mix contiguous "rows" of length R2.  A pass keeps 16 elements per
+// thread in registers: four stages on elements strided by R/16 ("layout A"),
+// one exchange through shared memory, the remaining stages on 16 contiguous
+// elements ("layout B").  Butterflies are Harvey's lazy ones (values in
+// [0, 4q) forward, [0, 2q) inverse) with Shoup twiddles.  The key-switching
+// and rescale kernels are the same passes with their neighbouring
+// arithmetic (basis conversion, key inner product, P^-1 / q_l^-1 scaling,
+// Galois gathers) fused into the loads and stores.
+#include "kernels.h"
+
+#define NT 256
+
+namespace {
+
+__device__ __forceinline__ void ct_bf(u64 &X, u64 &Y, ulonglong2 w, u64 q) {
+    const u64 two_q = 2 * q;
+    u64 x = X >= two_q ? X - two_q : X;
+    u64 t = mul_shoup_lazy(Y, w.x, w.y, q);
+    X = x + t;
+    Y = x - t + two_q;
+}
+
+__device__ __forceinline__ void gs_bf(u64 &X, u64 &Y, ulonglong2 w, u64 q) {
+    const u64 two_q = 2 * q;
+    u64 s = X + Y;
+    if (s >= two_q) s -= two_q;
+    u64 t = X - Y + two_q;
+    X = s;
+    Y = mul_shoup_lazy(t, w.x, w.y, q);
+}
+
+__device__ __forceinline__ ulonglong2 twid(const ulonglong2 *__restrict__ tw, int sg, int j, int logN) {
+    return __ldg(&tw[(1 << sg) + (j >> (logN - sg))]);
+}
+
+// Galois gather in the NTT domain: sigma_k(a) at slot j is a at slot
+// brv(((2 brv(j) + 1) k mod 2N - 1) / 2).
+__device__ __forceinline__ int galois_src(int j, int k, int logN) {
+    if (k == 1) return j;
+    const unsigned mask2n = (2u << logN) - 1u;
+    unsigned e = 2u * (__brev((unsigned)j) >> (32 - logN)) + 1u;
+    unsigned ek = (unsigned)(((unsigned long long)e * (unsigned)k) & mask2n);
+    return (int)(__brev((ek - 1u) >> 1) >> (32 - logN));
+}
+
+template <int LOGR>
+struct Geo {
+    static constexpr int R = 1 << LOGR;
+    static constexpr int S = R / 16;      // threads per sub-transform
+    static constexpr int T = NT / S;      // sub-transforms per CTA
+    static constexpr int RP = R + R / 16; // padded row (row passes)
+};
+
+// ---- stages. jb + e*js is the global index of local element e.
+template <int LOGR>
+__device__ __forceinline__ void fwd_A(u64 (&x)[16], int tau, int jb, int js, int sg0, int logN,
+                                      const ulonglong2 *__restrict__ tw, u64 q) {
+    constexpr int S = Geo<LOGR>::S;
+#pragma unroll
+    for (int s = 0; s < 4; s++) {
+        const int half = 8 >> s;
+#pragma unroll
+        for (int k = 0; k < 16; k++) {
+            if (k & half) continue;
+            const int e = tau + S * k;
+            ct_bf(x[k], x[k + half], twid(tw, sg0 + s, jb + e * js, logN), q);
+        }
+    }
+}
+
+template <int LOGR>
+__device__ __forceinline__ void fwd_B(u64 (&x)[16], int tau, int jb, int js, int sg0, int logN,
+                                      const ulonglong2 *__restrict__ tw, u64 q) {
+#pragma unroll
+    for (int s = 4; s < LOGR; s++) {
+        const int half = (1 << LOGR) >> (s + 1);
+#pragma unroll
+        for (int k = 0; k < 16; k++) {
+            if (k & half) continue;
+            const int e = 16 * tau + k;
+            ct_bf(x[k], x[k + half], twid(tw, sg0 + s, jb + e * js, logN), q);
+        }
+    }
+}
+
+template <int LOGR>
+__device__ __forceinline__ void inv_B(u64 (&x)[16], int tau, int jb, int js, int sg0, int logN,
+                                      const ulonglong2 *__restrict__ tw, u64 q) {
+#pragma unroll
+    for (int s = LOGR - 1; s >= 4; s--) {
+        const int half = (1 << LOGR) >> (s + 1);
+#pragma unroll
+        for (int k = 0; k < 16; k++) {
+            if (k & half) continue;
+            const int e = 16 * tau + k;
+            gs_bf(x[k], x[k + half], twid(tw, sg0 + s, jb + e * js, logN), q);
+        }
+    }
+}
+
+template <int LOGR>
+__device__ __forceinline__ void inv_A(u64 (&x)[16], int tau, int jb, int js, int sg0, int logN,
+                                      const ulonglong2 *__restrict__ tw, u64 q) {
+    constexpr int S = Geo<LOGR>::S;
+#pragma unroll
+    for (int s = 3; s >= 0; s--) {
+        const int half = 8 >> s;
+#pragma unroll
+        for (int k = 0; k < 16; k++) {
+            if (k & half) continue;
+            const int e = tau + S * k;
+            gs_bf(x[k], x[k + half], twid(tw, sg0 + s, jb + e * js, logN), q);
+        }
+    }
+}
+
+// ---- exchanges through shared memory
+// column passes: sm[e*T + cl]
+template <int LOGR>
+__device__ __forceinline__ void xchg_col_AB(u64 (&x)[16], u64 *sm, int tau, int cl) {
+    constexpr int S = Geo<LOGR>::S, T = Geo<LOGR>::T;
+#pragma unroll
+    for (int k = 0; k < 16; k++) sm[(tau + S * k) * T + cl] = x[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 16; k++) x[k] = sm[(16 * tau + k) * T + cl];
+    __syncthreads();
+}
+template <int LOGR>
+__device__ __forceinline__ void xchg_col_BA(u64 (&x)[16], u64 *sm, int tau, int cl) {
+    constexpr int S = Geo<LOGR>::S, T = Geo<LOGR>::T;
+#pragma unroll
+    for (int k = 0; k < 16; k++) sm[(16 * tau + k) * T + cl] = x[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 16; k++) x[k] = sm[(tau + S * k) * T + cl];
+    __syncthreads();
+}
+// row passes: sm[rl*RP + e + e/16]
+template <int LOGR>
+__device__ __forceinline__ void xchg_row_AB(u64 (&x)[16], u64 *sm, int tau, int rl) {
+    constexpr int S = Geo<LOGR>::S, RP = Geo<LOGR>::RP;
+    u64 *r = sm + rl * RP;
+#pragma unroll
+    for (int k = 0; k < 16; k++) {
+        const int e = tau + S * k;
+        r[e + (e >> 4)] = x[k];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 16; k++) {
+        const int e = 16 * tau + k;
+        x[k] = r[e + (e >> 4)];
+    }
+    __syncthreads();
+}
+template <int LOGR>
+__device__ __forceinline__ void xchg_row_BA(u64 (&x)[16], u64 *sm, int tau, int rl) {
+    constexpr int S = Geo<LOGR>::S, RP = Geo<LOGR>::RP;
+    u64 *r = sm + rl * RP;
+#pragma unroll
+    for (int k = 0; k < 16; k++) {
+        const int e = 16 * tau + k;
+        r[e + (e >> 4)] = x[k];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 16; k++) {
+        const int e = tau + S * k;
+        x[k] = r[e + (e >> 4)];
+    }
+    __syncthreads();
+}
+
+constexpr int SMEM_WORDS = 4096 + 256;
+
+// ================================================================ plain NTT
+
+// forward pass 1 (columns of length 2^LOGR = 2^logR1)
+template <int LOGR>
+__global__ void __launch_bounds__(NT) k_ntt_fwd_col(DevCtx c, NttArgs a) {
+    using Gm = Geo<LOGR>;
+    __shared__ u64 sm[SMEM_WORDS];
+    const int job = blockIdx.y, item = job / a.n_limbs, limb = job % a.n_limbs;
+    const PrimeTab &P = c.primes[a.pidx[limb]];
+    const u64 q = P.m.q;
+    const int logC = c.logN - LOGR;
+    const int cl = threadIdx.x % Gm::T, tau = threadIdx.x / Gm::T;
+    const int col = blockIdx.x * Gm::T + cl;
+    const u64 *src = a.src + item * a.src_item + ((long long)limb << c.logN);
+    u64 *dst = a.dst + item * a.dst_item + ((long long)limb << c.logN);
+    u64 x[16];
+#pragma unroll
+    for (int k = 0; k < 16; k++) x[k] = src[col + ((tau + Gm::S * k) << logC)];
+    fwd_A<LOGR>(x, tau, col, 1 << logC, 0, c.logN, P.fwd, q);
+    xchg_col_AB<LOGR>(x, sm, tau, cl);
+    fwd_B<LOGR>(x, tau, col, 1 << logC, 0, c.logN, P.fwd, q);
+#pragma unroll
+    for (int k = 0; k < 16; k++) dst[col + ((16 * tau + k) << logC)] = x[k];
+}
+
+// forward pass 2 (rows of length 2^LOGR = 2^logR2), in place on dst
+template <int LOGR>
+__global__ void __launch_bounds__(NT) k_ntt_fwd_row(DevCtx c, NttArgs a) {
+    using Gm = Geo<LOGR>;
+    __shared__ u64 sm[SMEM_WORDS];
+    const int job = blockIdx.y, item = job / a.n_limbs, limb = job % a.n_limbs;
+    const PrimeTab &P = c.primes[a.pidx[limb]];
+    const u64 q = P.m.q;
+    const int tau = threadIdx.x % Gm::S, rl = threadIdx.x / Gm::S;
+    const int row = blockIdx.x * Gm::T + rl;
+    u64 *p = a.dst + item * a.dst_item + ((long long)limb << c.logN) + (row << LOGR);
+    u64 x[16];
+#pragma unroll
+    for (int k = 0; k < 16; k++) x[k] = p[tau + Gm::S * k];
+    fwd_A<LOGR>(x, tau, row << LOGR, 1, c.logR1, c.logN, P.fwd, q);
+    xchg_row_AB<LOGR>(x, sm, tau, rl);
+    fwd_B<LOGR>(x, tau, row << LOGR, 1, c.logR1, c.logN, P.fwd, q);
+    xchg_row_BA<LOGR>(x, sm, tau, rl);
+#pragma unroll
+    for (int k = 0; k < 16; k++) p[tau + Gm::S * k] = reduce_4q(x[k], q);
+}
+
+// inverse pass 1 (rows)
+template <int LOGR>
+__global__ void __launch_bounds__(NT) k_ntt_inv_row(DevCtx c, NttArgs a) {
+    using Gm = Geo<LOGR>;
+    __shared__ u64 sm[SMEM_WORDS];
+    const int job = blockIdx.y, item = job / a.n_limbs, limb = job % a.n_limbs;
+    const PrimeTab &P = c.primes[a.pidx[limb]];
+    const u64 q = P.m.q;
+    const int tau = threadIdx.x % Gm::S, rl = threadIdx.x / Gm::S;
+    const int row = blockIdx.x * Gm::T + rl;
+    const u64 *s = a.src + item * a.src_item + ((long long)limb << c.logN) + (row << LOGR);
+    u64 *d = a.dst + item * a.dst_item + ((long long)limb << c.logN) + (row << LOGR);
+    u64 x[16];
+#pragma unroll
+    for (int k = 0; k < 16; k++) x[k] = s[tau + Gm::S * k];
+    xchg_row_AB<LOGR>(x, sm, tau, rl);
+    inv_B<LOGR>(x, tau, row << LOGR, 1, c.logR1, c.logN, P.inv, q);
+    xchg_row_BA<LOGR>(x, sm, tau, rl);
+    inv_A<LOGR>(x, tau, row << LOGR, 1, c.logR1, c.logN, P.inv, q);
+#pragma unroll
+    for (int k = 0; k < 16; k++) d[tau + Gm::S * k] = x[k];
+}
+
+// inverse pass 2 (columns), times N^-1, in place on dst
+template <int LOGR>
+__global__ void __launch_bounds__(NT) k_ntt_inv_col(DevCtx c, NttArgs a) {
+    using Gm = Geo<LOGR>;
+    __shared__ u64 sm[SMEM_WORDS];
+    const int job = blockIdx.y, item = job / a.n_limbs, limb = job % a.n_limbs;
+    const PrimeTab &P = c.primes[a.pidx[limb]];
+    const u64 q = P.m.q;
+    const int logC = c.logN - LOGR;
+    const int cl = threadIdx.x % Gm::T, tau = threadIdx.x / Gm::T;
+    const int col = blockIdx.x * Gm::T + cl;
+    u64 *p = a.dst + item * a.dst_item + ((long long)limb << c.logN);
+    u64 x[16];
+#pragma unroll
+    for (int k = 0; k < 16; k++) x[k] = p[col + ((16 * tau + k) << logC)];
+    inv_B<LOGR>(x, tau, col, 1 << logC, 0, c.logN, P.inv, q);
+    xchg_col_BA<LOGR>(x, sm, tau, cl);
+    inv_A<LOGR>(x, tau, col, 1 << logC, 0, c.logN, P.inv, q);
+#pragma unroll
+    for (int k = 0; k < 16; k++) {
+        u64 v = mul_shoup_lazy(x[k], P.n_inv, P.n_inv_sh, q);
+        p[col + ((tau + Gm::S * k) << logC)] = v >= q ? v - q : v;
+    }
+}
+
+// ================================================================ key switching
+
+struct KsLayout {
+    long long y, mu, acc, z, md;   // word offsets inside one item's workspace
+};
+
+__host__ __device__ inline KsLayout ks_layout(int level, int n_digits, int alpha, int logN) {
+    const long long N = 1ll << logN;
+    const int ext = level + 1 + alpha;
+    KsLayout L;
+    L.y = 0;
+    L.mu = L.y + (level + 1) * N;
+    L.acc = L.mu + (long long)n_digits * ext * N;
+    L.z = L.acc + 2ll * ext * N;
+    L.md = L.z + 2ll * alpha * N;
+    return L;
+}
+
+// (1) iNTT rows of d (with Galois gather) -> y region
+template <int LOGR>
+__global__ void __launch_bounds__(NT) k_ks_intt_row(DevCtx c, KsArgs a, KsLayout ly) {
+    using Gm = Geo<LOGR>;
+    __shared__ u64 sm[SMEM_WORDS];
+    const int nl = a.level + 1;
+    const int job = blockIdx.y, item = job / nl, limb = job % nl;
+    const PrimeTab &P = c.primes[limb];
+    const u64 q = P.m.q;
+    const int tau = threadIdx.x % Gm::S, rl = threadIdx.x / Gm::S;
+    const int row = blockIdx.x * Gm::T + rl;
+    const u64 *s = a.d + item * a.d_item + ((long long)limb << c.logN);
+    u64 *d = a.ws + item * a.ws_item + ly.y + ((long long)limb << c.logN) + (row << LOGR);
+    u64 x[16];
+#pragma unroll
+    for (int k = 0; k < 16; k++) x[k] = s[galois_src((row << LOGR) + tau + Gm::S * k, a.galois, c.logN)];
+    xchg_row_AB<LOGR>(x, sm, tau, rl);
+    inv_B<LOGR>(x, tau, row << LOGR, 1, c.logR1, c.logN, P.inv, q);
+    xchg_row_BA<LOGR>(x, sm, tau, rl);
+    inv_A<LOGR>(x, tau, row << LOGR, 1, c.logR1, c.logN, P.inv, q);
+#pragma unroll
+    for (int k = 0; k < 16; k++) d[tau + Gm::S * k] = x[k];
+}
+
+// (2) iNTT columns, times N^-1 * Qhat_{j,i}^-1 -> y
+template <int LOGR>
+__global__ void __launch_bounds__(NT) k_ks_intt_col(DevCtx c, LevelTab lt, KsArgs a, KsLayout ly) {
+    using Gm = Geo<LOGR>;
+    __shared__ u64 sm[SMEM_WORDS];
+    const int nl = a.level + 1;
+    const int job = blockIdx.y, item = job / nl, limb = job % nl;
+    const PrimeTab &P = c.primes[limb];
+    const u64 q = P.m.q;
+    const int logC = c.logN - LOGR;
+    const int cl = threadIdx.x % Gm::T, tau = threadIdx.x / Gm::T;
+    const int col = blockIdx.x * Gm::T + cl;
+    u64 *p = a.ws + item * a.ws_item + ly.y + ((long long)limb << c.logN);
+    const ulonglong2 sc = lt.y_scale[limb];
+    u64 x[16];
+#pragma unroll
+    for (int k = 0; k < 16; k++) x[k] = p[col + ((16 * tau + k) << logC)];
+    inv_B<LOGR>(x, tau, col, 1 << logC, 0, c.logN, P.inv, q);
+    xchg_col_BA<LOGR>(x, sm, tau, cl);
+    inv_A<LOGR>(x, tau, col, 1 << logC, 0, c.logN, P.inv, q);
+#pragma unroll
+    for (int k = 0; k < 16; k++) {
+        u64 v = mul_shoup_lazy(x[k], sc.x, sc.y, q);
+        p[col + ((tau + Gm::S * k) << logC)] = v >= q ? v - q : v;
+    }
+}
+
+// (3) ModUp: basis conversion of digit j to ext limb t fused with NTT columns
+template <int LOGR>
+__global__ void __launch_bounds__(NT) k_ks_modup_col(DevCtx c, LevelTab lt, KsArgs a, KsLayout ly) {
+    using Gm = Geo<LOGR>;
+    __shared__ u64 sm[SMEM_WORDS];
+    const int ext = lt.ext, nd = lt.n_digits;
+    const int job = blockIdx.y;
+    const int item = job / (nd * ext);
+    const int j = (job / ext) % nd;
+    const int t = job % ext;
+    const int alpha = c.alpha;
+    const int d_lo = j * alpha;
+    const int d_hi = min(d_lo + alpha, a.level + 1);
+    if (t >= d_lo && t < d_hi) return;   // limb of the digit itself: no conversion
+    const PrimeTab &P = c.primes[ext_prime(t, a.level, c.L)];
+    const u64 q = P.m.q;
+    const int logC = c.logN - LOGR;
+    const int cl = threadIdx.x % Gm::T, tau = threadIdx.x / Gm::T;
+    const int col = blockIdx.x * Gm::T + cl;
+    const u64 *y = a.ws + item * a.ws_item + ly.y;
+    u64 *dst = a.ws + item * a.ws_item + ly.mu + ((long long)(j * ext + t) << c.logN);
+    const u64 *hat = lt.modup_hat + (long long)(j * alpha) * ext;
+    u64 hv[8];
+    const int nu = d_hi - d_lo;
+#pragma unroll
+    for (int u = 0; u < 8; u++) hv[u] = (u < nu) ? hat[u * ext + t] : 0;
+    u64 x[16];
+#pragma unroll
+    for (int k = 0; k < 16; k++) {
+        const int J = col + ((tau + Gm::S * k) << logC);
+        U128 acc = {0, 0};
+        for (int u = 0; u < nu; u++) mac(acc, y[((long long)(d_lo + u) << c.logN) + J], hv[u]);
+        x[k] = barrett(acc, P.m);
+    }
+    fwd_A<LOGR>(x, tau, col, 1 << logC, 0, c.logN, P.fwd, q);
+    xchg_col_AB<LOGR>(x, sm, tau, cl);
+    fwd_B<LOGR>(x, tau, col, 1 << logC, 0, c.logN, P.fwd, q);
+#pragma unroll
+    for (int k = 0; k < 16; k++) dst[col + ((16 * tau + k) << logC)] = x[k];
+}
+
+// (4) ModUp NTT rows fused with the inner product against the key:
+//     acc_k[t] = sum_j ext_j[t] * key_j[k][t]
+template <int LOGR>
+__global__ void __launch_bounds__(NT, 1) k_ks_modup_row_ip(DevCtx c, LevelTab lt, KsArgs a, KsLayout ly) {
+    using Gm = Geo<LOGR>;
+    __shared__ u64 sm[SMEM_WORDS];
+    const int ext = lt.ext, nd = lt.n_digits;
+    const int job = blockIdx.y, item = job / ext, t = job % ext;
+    const int pi = ext_prime(t, a.level, c.L);
+    const PrimeTab &P = c.primes[pi];
+    const u64 q = P.m.q;
+    const int tau = threadIdx.x % Gm::S, rl = threadIdx.x / Gm::S;
+    const int row = blockIdx.x * Gm::T + rl;
+    const int base = row << LOGR;
+    const long long N = 1ll << c.logN;
+    const long long key_limbs = c.L + 1 + c.alpha;
+    U128 acc0[16], acc1[16];
+#pragma unroll
+    for (int k = 0; k < 16; k++) acc0[k] = acc1[k] = U128{0, 0};
+    for (int j = 0; j < nd; j++) {
+        u64 x[16];
+        const int d_lo = j * c.alpha, d_hi = min(d_lo + c.alpha, a.level + 1);
+        if (t >= d_lo && t < d_hi) {
+            const u64 *s = a.d + item * a.d_item + (long long)t * N;
+#pragma unroll
+            for (int k = 0; k < 16; k++) x[k] = s[galois_src(base + tau + Gm::S * k, a.galois, c.logN)];
+        } else {
+            const u64 *s = a.ws + item * a.ws_item + ly.mu + (long long)(j * ext + t) * N + base;
+#pragma unroll
+            for (int k = 0; k < 16; k++) x[k] = s[tau + Gm::S * k];
+            fwd_A<LOGR>(x, tau, base, 1, c.logR1, c.logN, P.fwd, q);
+            xchg_row_AB<LOGR>(x, sm, tau, rl);
+            fwd_B<LOGR>(x, tau, base, 1, c.logR1, c.logN, P.fwd, q);
+            xchg_row_BA<LOGR>(x, sm, tau, rl);
+#pragma unroll
+            for (int k = 0; k < 16; k++) x[k] = reduce_4q(x[k], q);
+        }
+        const u64 *k0 = a.key + ((long long)(j * 2 + 0) * key_limbs + pi) * N + base;
+        const u64 *k1 = a.key + ((long long)(j * 2 + 1) * key_limbs + pi) * N + base;
+#pragma unroll
+        for (int k = 0; k < 16; k++) {
+            mac(acc0[k], x[k], __ldg(&k0[tau + Gm::S * k]));
+            mac(acc1[k], x[k], __ldg(&k1[tau + Gm::S * k]));
+        }
+    }
+    u64 *o0 = a.ws + item * a.ws_item + ly.acc + (long long)t * N + base;
+    u64 *o1 = o0 + (long long)ext * N;
+#pragma unroll
+    for (int k = 0; k < 16; k++) {
+        o0[tau + Gm::S * k] = barrett(acc0[k], P.m);
+        o1[tau + Gm::S * k] = barrett(acc1[k], P.m);
+    }
+}
+
+// (5) ModDown: iNTT rows of the P limbs of acc
+template <int LOGR>
+__global__ void __launch_bounds__(NT) k_ks_md_intt_row(DevCtx c, LevelTab lt, KsArgs a, KsLayout ly) {
+    using Gm = Geo<LOGR>;
+    __shared__ u64 sm[SMEM_WORDS];
+    const int al = c.alpha;
+    const int job = blockIdx.y, item = job / (2 * al), kk = (job / al) % 2, m = job % al;
+    const PrimeTab &P = c.primes[c.L + 1 + m];
+    const u64 q = P.m.q;
+    const int tau = threadIdx.x % Gm::S, rl = threadIdx.x / Gm::S;
+    const int row = blockIdx.x * Gm::T + rl;
+    const long long N = 1ll << c.logN;
+    const u64 *s = a.ws + item * a.ws_item + ly.acc + ((long long)kk * lt.ext + a.level + 1 + m) * N + (row << LOGR);
+    u64 *d = a.ws + item * a.ws_item + ly.z + ((long long)kk * al + m) * N + (row << LOGR);
+    u64 x[16];
+#pragma unroll
+    for (int k = 0; k < 16; k++) x[k] = s[tau + Gm::S * k];
+    xchg_row_AB<LOGR>(x, sm, tau, rl);
+    inv_B<LOGR>(x, tau, row << LOGR, 1, c.logR1, c.logN, P.inv, q);
+    xchg_row_BA<LOGR>(x, sm, tau, rl);
+    inv_A<LOGR>(x, tau, row << LOGR, 1, c.logR1, c.logN, P.inv, q);
+#pragma unroll
+    for (int k = 0; k < 16; k++) d[tau + Gm::S * k] = x[k];
+}
+
+// (6) ModDown: iNTT columns; z = (v + floor(P/2)) * Phat_m^-1 mod p_m
+template <int LOGR>
+__global__ void __launch_bounds__(NT) k_ks_md_intt_col(DevCtx c, LevelTab lt, KsArgs a, KsLayout ly) {
+    using Gm = Geo<LOGR>;
+    __shared__ u64 sm[SMEM_WORDS];
+    const int al = c.alpha;
+    const int job = blockIdx.y, item = job / (2 * al), kk = (job / al) % 2, m = job % al;
+    const PrimeTab &P = c.primes[c.L + 1 + m];
+    const u64 q = P.m.q;
+    const int logC = c.logN - LOGR;
+    const int cl = threadIdx.x % Gm::T, tau = threadIdx.x / Gm::T;
+    const int col = blockIdx.x * Gm::T + cl;
+    u64 *p = a.ws + item * a.ws_item + ly.z + ((long long)(kk * al + m) << c.logN);
+    const ulonglong2 sc = c.md_z_scale[m];
+    const u64 add = c.md_z_add[m];
+    u64 x[16];
+#pragma unroll
+    for (int k = 0; k < 16; k++) x[k] = p[col + ((16 * tau + k) << logC)];
+    inv_B<LOGR>(x, tau, col, 1 << logC, 0, c.logN, P.inv, q);
+    xchg_col_BA<LOGR>(x, sm, tau, cl);
+    inv_A<LOGR>(x, tau, col, 1 << logC, 0, c.logN, P.inv, q);
+#pragma unroll
+    for (int k = 0; k < 16; k++) {
+        u64 v = mul_shoup_lazy(x[k], sc.x, sc.y, q);
+        v = v >= q ? v - q : v;
+        p[col + ((tau + Gm::S * k) << logC)] = add_mod(v, add, q);
+    }
+}
+
+// (7) ModDown: basis conversion P -> q_i (minus floor(P/2)) fused with NTT columns
+template <int LOGR>
+__global__ void __launch_bounds__(NT) k_ks_md_conv_col(DevCtx c, LevelTab lt, KsArgs a, KsLayout ly) {
+    using Gm = Geo<LOGR>;
+    __shared__ u64 sm[SMEM_WORDS];
+    const int al = c.alpha;
+    const int nl = a.level + 1;
+    const int job = blockIdx.y, item = job / (2 * nl), kk = (job / nl) % 2, i = job % nl;
+    const PrimeTab &P = c.primes[i];
+    const u64 q = P.m.q;
+    const int logC = c.logN - LOGR;
+    const int cl = threadIdx.x % Gm::T, tau = threadIdx.x / Gm::T;
+    const int col = blockIdx.x * Gm::T + cl;
+    const long long N = 1ll << c.logN;
+    const u64 *z = a.ws + item * a.ws_item + ly.z + (long long)kk * al * N;
+    u64 *dst = a.ws + item * a.ws_item + ly.md + ((long long)(kk * nl + i) << c.logN);
+    u64 hv[8];
+#pragma unroll
+    for (int u = 0; u < 8; u++) hv[u] = (u < al) ? c.md_phat[u * (c.L + 1) + i] : 0;
+    const u64 halfp = c.md_halfp[i];
+    u64 x[16];
+#pragma unroll
+    for (int k = 0; k < 16; k++) {
+        const int J = col + ((tau + Gm::S * k) << logC);
+        U128 acc = {0, 0};
+        for (int u = 0; u < al; u++) mac(acc, z[(long long)u * N + J], hv[u]);
+        x[k] = sub_mod(barrett(acc, P.m), halfp, q);
+    }
+    fwd_A<LOGR>(x, tau, col, 1 << logC, 0, c.logN, P.fwd, q);
+    xchg_col_AB<LOGR>(x, sm, tau, cl);
+    fwd_B<LOGR>(x, tau, col, 1 << logC, 0, c.logN, P.fwd, q);
+#pragma unroll
+    for (int k = 0; k < 16; k++) dst[col + ((16 * tau + k) << logC)] = x[k];
+}
+
+// (8) ModDown: NTT rows, out_k = (acc_k - conv) * P^-1 (+ addend) (+= out)
+template <int LOGR>
+__global__ void __launch_bounds__(NT) k_ks_md_row_out(DevCtx c, LevelTab lt, KsArgs a, KsLayout ly) {
+    using Gm = Geo<LOGR>;
+    __shared__ u64 sm[SMEM_WORDS];
+    const int nl = a.level + 1;
+    const int job = blockIdx.y, item = job / (2 * nl), kk = (job / nl) % 2, i = job % nl;
+    const PrimeTab &P = c.primes[i];
+    const u64 q = P.m.q;
+    const int tau = threadIdx.x % Gm::S, rl = threadIdx.x / Gm::S;
+    const int row = blockIdx.x * Gm::T + rl;
+    const int base = row << LOGR;
+    const long long N = 1ll << c.logN;
+    const u64 *s = a.ws + item * a.ws_item + ly.md + (long long)(kk * nl + i) * N + base;
+    const u64 *ac = a.ws + item * a.ws_item + ly.acc + ((long long)kk * lt.ext + i) * N + base;
+    const u64 *addp = kk == 0 ? a.add0 : a.add1;
+    const ulonglong2 pinv = c.md_pinv[i];
+    u64 x[16];
+#pragma unroll
+    for (int k = 0; k < 16; k++) x[k] = s[tau + Gm::S * k];
+    fwd_A<LOGR>(x, tau, base, 1, c.logR1, c.logN, P.fwd, q);
+    xchg_row_AB<LOGR>(x, sm, tau, rl);
+    fwd_B<LOGR>(x, tau, base, 1, c.logR1, c.logN, P.fwd, q);
+    xchg_row_BA<LOGR>(x, sm, tau, rl);
+    u64 *o = a.out + item * a.out_item + ((long long)kk * nl + i) * N + base;
+#pragma unroll
+    for (int k = 0; k < 16; k++) {
+        const int e = tau + Gm::S * k;
+        u64 v = sub_mod(ac[e], reduce_4q(x[k], q), q);
+        v = mul_shoup(v, pinv.x, pinv.y, q);
+        if (addp) {
+            const u64 *ap = addp + item * a.add_item + (long long)i * N;
+            v = add_mod(v, ap[galois_src(base + e, a.galois, c.logN)], q);
+        }
+        if (a.base) v = add_mod(v, a.base[item * a.base_item + ((long long)kk * nl + i) * N + base + e], q);
+        o[e] = v;
+    }
+}
+
+// ================================================================ rescale
+
+template <int LOGR>
+__global__ void __launch_bounds__(NT) k_rs_intt_row(DevCtx c, RescaleArgs a) {
+    using Gm = Geo<LOGR>;
+    __shared__ u64 sm[SMEM_WORDS];
+    const int job = blockIdx.y, item = job / a.n_poly, poly = job % a.n_poly;
+    const int lv = a.level;
+    const PrimeTab &P = c.primes[lv];
+    const u64 q = P.m.q;
+    const int tau = threadIdx.x % Gm::S, rl = threadIdx.x / Gm::S;
+    const int row = blockIdx.x * Gm::T + rl;
+    const long long N = 1ll << c.logN;
+    const u64 *s = a.in + item * a.in_item + (long long)(poly * (lv + 1) + lv) * N + (row << LOGR);
+    u64 *d = a.ws + (long long)job * N + (row << LOGR);
+    u64 x[16];
+#pragma unroll
+    for (int k = 0; k < 16; k++) x[k] = s[tau + Gm::S * k];
+    xchg_row_AB<LOGR>(x, sm, tau, rl);
+    inv_B<LOGR>(x, tau, row << LOGR, 1, c.logR1, c.logN, P.inv, q);
+    xchg_row_BA<LOGR>(x, sm, tau, rl);
+    inv_A<LOGR>(x, tau, row << LOGR, 1, c.logR1, c.logN, P.inv, q);
+#pragma unroll
+    for (int k = 0; k < 16; k++) d[tau + Gm::S * k] = x[k];
+}
+
+template <int LOGR>
+__global__ void __launch_bounds__(NT) k_rs_intt_col(DevCtx c, RescaleArgs a) {
+    using Gm = Geo<LOGR>;
+    __shared__ u64 sm[SMEM_WORDS];
+    const int job = blockIdx.y;
+    const PrimeTab &P = c.primes[a.level];
+    const u64 q = P.m.q;
+    const int logC = c.logN - LOGR;
+    const int cl = threadIdx.x % Gm::T, tau = threadIdx.x / Gm::T;
+    const int col = blockIdx.x * Gm::T + cl;
+    u64 *p = a.ws + ((long long)job << c.logN);
+    u64 x[16];
+#pragma unroll
+    for (int k = 0; k < 16; k++) x[k] = p[col + ((16 * tau + k) << logC)];
+    inv_B<LOGR>(x, tau, col, 1 << logC, 0, c.logN, P.inv, q);
+    xchg_col_BA<LOGR>(x, sm, tau, cl);
+    inv_A<LOGR>(x, tau, col, 1 << logC, 0, c.logN, P.inv, q);
+#pragma unroll
+    for (int k = 0; k < 16; k++) {
+        u64 v = mul_shoup_lazy(x[k], P.n_inv, P.n_inv_sh, q);
+        p[col + ((tau + Gm::S * k) << logC)] = v >= q ? v - q : v;
+    }
+}
+
+// centred top limb reduced mod q_i, NTT columns; written into out limb i
+template <int LOGR>
+__global__ void __launch_bounds__(NT) k_rs_conv_col(DevCtx c, LevelTab lt, RescaleArgs a) {
+    using Gm = Geo<LOGR>;
+    __shared__ u64 sm[SMEM_WORDS];
+    const int lv = a.level;
+    const int job = blockIdx.y, item = job / (a.n_poly * lv), poly = (job / lv) % a.n_poly, i = job % lv;
+    const PrimeTab &P = c.primes[i];
+    const u64 q = P.m.q;
+    const u64 ql = c.primes[lv].m.q;
+    const u64 qlmod = lt.q_last_mod[i];
+    const int logC = c.logN - LOGR;
+    const int cl = threadIdx.x % Gm::T, tau = threadIdx.x / Gm::T;
+    const int col = blockIdx.x * Gm::T + cl;
+    const u64 *v = a.ws + ((long long)(item * a.n_poly + poly) << c.logN);
+    u64 *dst = a.out + item * a.out_item + ((long long)(poly * lv + i) << c.logN);
+    u64 x[16];
+#pragma unroll
+    for (int k = 0; k < 16; k++) {
+        const u64 t = v[col + ((tau + Gm::S * k) << logC)];
+        u64 r = barrett(U128{t, 0}, P.m);
+        if (t > (ql - 1) / 2) r = sub_mod(r, qlmod, q);
+        x[k] = r;
+    }
+    fwd_A<LOGR>(x, tau, col, 1 << logC, 0, c.logN, P.fwd, q);
+    xchg_col_AB<LOGR>(x, sm, tau, cl);
+    fwd_B<LOGR>(x, tau, col, 1 << logC, 0, c.logN, P.fwd, q);
+#pragma unroll
+    for (int k = 0; k < 16; k++) dst[col + ((16 * tau + k) << logC)] = x[k];
+}
+
+template <int LOGR>
+__global__ void __launch_bounds__(NT) k_rs_row_out(DevCtx c, LevelTab lt, RescaleArgs a) {
+    using Gm = Geo<LOGR>;
+    __shared__ u64 sm[SMEM_WORDS];
+    const int lv = a.level;
+    const int job = blockIdx.y, item = job / (a.n_poly * lv), poly = (job / lv) % a.n_poly, i = job % lv;
+    const PrimeTab &P = c.primes[i];
+    const u64 q = P.m.q;
+    const int tau = threadIdx.x % Gm::S, rl = threadIdx.x / Gm::S;
+    const int row = blockIdx.x * Gm::T + rl;
+    const int base = row << LOGR;
+    const long long N = 1ll << c.logN;
+    u64 *o = a.out + item * a.out_item + (long long)(poly * lv + i) * N + base;
+    const u64 *src = a.in + item * a.in_item + (long long)(poly * (lv + 1) + i) * N + base;
+    const ulonglong2 inv = lt.q_last_inv[i];
+    u64 x[16];
+#pragma unroll
+    for (int k = 0; k < 16; k++) x[k] = o[tau + Gm::S * k];
+    fwd_A<LOGR>(x, tau, base, 1, c.logR1, c.logN, P.fwd, q);
+    xchg_row_AB<LOGR>(x, sm, tau, rl);
+    fwd_B<LOGR>(x, tau, base, 1, c.logR1, c.logN, P.fwd, q);
+    xchg_row_BA<LOGR>(x, sm, tau, rl);
+#pragma unroll
+    for (int k = 0; k < 16; k++) {
+        const int e = tau + Gm::S * k;
+        u64 v = sub_mod(src[e], reduce_4q(x[k], q), q);
+        o[e] = mul_shoup(v, inv.x, inv.y, q);
+    }
+}
+
+// ================================================================ elementwise
+
+__global__ void k_add(DevCtx c, const u64 *a, long long a_item, const u64 *b, long long b_item, u64 *out,
+                      long long out_item, int n_poly, int level, int subtract) {
+    const long long N = 1ll << c.logN;
+    const int item = blockIdx.z;
+    const int pl = blockIdx.y;  // poly * (level+1) + limb
+    const int limb = pl % (level + 1);
+    const u64 q = c.primes[limb].m.q;
+    const long long off = (long long)pl * N;
+    for (long long j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += (long long)gridDim.x * blockDim.x) {
+        u64 x = a[item * a_item + off + j], y = b[item * b_item + off + j];
+        out[item * out_item + off + j] = subtract ? sub_mod(x, y, q) : add_mod(x, y, q);
+    }
+}
+
+__global__ void k_mul_const(DevCtx c, const u64 *a, long long a_item, const u64 *cst, u64 *out,
+                            long long out_item, int level) {
+    const long long N = 1ll << c.logN;
+    const int item = blockIdx.z;
+    const int pl = blockIdx.y;
+    const int limb = pl % (level + 1);
+    const ModQ m = c.primes[limb].m;
+    const u64 w = cst[limb];
+    const long long off = (long long)pl * N;
+    for (long long j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += (long long)gridDim.x * blockDim.x)
+        out[item * out_item + off + j] = mulmod(a[item * a_item + off + j], w, m);
+}
+
+__global__ void k_add_const(DevCtx c, const u64 *a, long long a_item, const u64 *cst, u64 *out,
+                            long long out_item, int level) {
+    const long long N = 1ll << c.logN;
+    const int item = blockIdx.z;
+    const int pl = blockIdx.y;  // 2*(level+1)
+    const int limb = pl % (level + 1);
+    const u64 q = c.primes[limb].m.q;
+    const u64 w = pl < level + 1 ? cst[limb] : 0;
+    const long long off = (long long)pl * N;
+    for (long long j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += (long long)gridDim.x * blockDim.x)
+        out[item * out_item + off + j] = add_mod(a[item * a_item + off + j], w, q);
+}
+
+__global__ void k_square_act(DevCtx c, const u64 *in, long long in_item, const u64 *c1, const u64 *c0,
+                             u64 *out, long long out_item, int level) {
+    const long long N = 1ll << c.logN;
+    const int item = blockIdx.z;
+    const int limb = blockIdx.y;
+    const ModQ m = c.primes[limb].m;
+    const long long P = (long long)(level + 1) * N;
+    const u64 w1 = c1 ? c1[limb] : 0, w0 = c0 ? c0[limb] : 0;
+    const u64 *x = in + item * in_item + (long long)limb * N;
+    u64 *o = out + item * out_item + (long long)limb * N;
+    for (long long j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += (long long)gridDim.x * blockDim.x) {
+        const u64 a = x[j], b = x[P + j];
+        U128 t0 = mul_wide(a, a);
+        mac(t0, w1, a);
+        u64 d0 = add_mod(barrett(t0, m), w0, m.q);
+        U128 t1 = mul_wide(a, b);
+        add_to(t1, t1);
+        mac(t1, w1, b);
+        o[j] = d0;
+        o[P + j] = barrett(t1, m);
+        o[2 * P + j] = mulmod(b, b, m);
+    }
+}
+
+__global__ void k_drop(DevCtx c, const u64 *in, long long in_item, int in_level, u64 *out, long long out_item,
+                       int new_level) {
+    const long long N = 1ll << c.logN;
+    const int item = blockIdx.z;
+    const int pl = blockIdx.y;
+    const int poly = pl / (new_level + 1), limb = pl % (new_level + 1);
+    const u64 *s = in + item * in_item + ((long long)poly * (in_level + 1) + limb) * N;
+    u64 *d = out + item * out_item + (long long)pl * N;
+    for (long long j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += (long long)gridDim.x * blockDim.x)
+        d[j] = s[j];
+}
+
+__global__ void k_decrypt(DevCtx c, const u64 *ct, const u64 *s, u64 *m, int level) {
+    const long long N = 1ll << c.logN;
+    const int limb = blockIdx.y;
+    const ModQ md = c.primes[limb].m;
+    const long long off = (long long)limb * N, P = (long long)(level + 1) * N;
+    for (long long j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += (long long)gridDim.x * blockDim.x) {
+        U128 t = mul_wide(ct[P + off + j], s[off + j]);
+        add_to(t, U128{ct[off + j], 0});
+        m[off + j] = barrett(t, md);
+    }
+}
+
+// ---- pt-MAC: one CTA = one output group x 256 coefficients x one limb, all images
+#define MAC_IMG 4
+__global__ void __launch_bounds__(256) k_mac(DevCtx c, MacArgs a) {
+    const MacGroup g = a.groups[blockIdx.x];
+    const int limb = blockIdx.z;
+    const ModQ m = c.primes[limb].m;
+    const long long N = 1ll << c.logN;
+    const long long off = (long long)limb * N + blockIdx.y * blockDim.x + threadIdx.x;
+    const long long P = (long long)(a.level + 1) * N;
+    for (int i0 = 0; i0 < a.n_items; i0 += MAC_IMG) {
+        const int ni = min(MAC_IMG, a.n_items - i0);
+        U128 acc[MAC_IMG][2];
+#pragma unroll
+        for (int u = 0; u < MAC_IMG; u++) acc[u][0] = acc[u][1] = U128{0, 0};
+        int cnt = 0;
+        for (int t = g.term_begin; t < g.term_end; t++) {
+            const MacTerm tm = a.terms[t];
+            const u64 p = __ldg(&tm.pt[off]);
+#pragma unroll
+            for (int u = 0; u < MAC_IMG; u++) {
+                if (u < ni) {
+                    const u64 *s = tm.src + (long long)(i0 + u) * tm.src_item + off;
+                    mac(acc[u][0], p, s[0]);
+                    mac(acc[u][1], p, s[P]);
+                }
+            }
+            if (++cnt == 7) {
+#pragma unroll
+                for (int u = 0; u < MAC_IMG; u++) {
+                    acc[u][0] = U128{barrett(acc[u][0], m), 0};
+                    acc[u][1] = U128{barrett(acc[u][1], m), 0};
+                }
+                cnt = 0;
+            }
+        }
+        const u64 b = g.bias ? __ldg(&g.bias[off]) : 0;
+#pragma unroll
+        for (int u = 0; u < MAC_IMG; u++) {
+            if (u < ni) {
+                u64 *o = g.out + (long long)(i0 + u) * g.out_item + off;
+                o[0] = add_mod(barrett(acc[u][0], m), b, m.q);
+                o[P] = barrett(acc[u][1], m);
+            }
+        }
+    }
+}
+
+// ---- ChaCha20 (RFC 8439 block function)
+__device__ __forceinline__ unsigned rotl(unsigned x, int r) { return (x << r) | (x >> (32 - r)); }
+#define CQR(a, b, c, d)               \
+    a += b; d ^= a; d = rotl(d, 16);  \
+    c += d; b ^= c; b = rotl(b, 12);  \
+    a += b; d ^= a; d = rotl(d, 8);   \
+    c += d; b ^= c; b = rotl(b, 7);
+
+__device__ void chacha_block(uint64_t seed, uint32_t domain, uint32_t id0, uint32_t id1, uint32_t ctr,
+                             unsigned out[16]) {
+    unsigned s[16] = {0x61707865u, 0x3320646eu, 0x79622d32u, 0x6b206574u,
+                      (unsigned)seed, (unsigned)(seed >> 32), domain, 0u, 0u, 0u, 0u, 0u,
+                      ctr, id0, id1, 0u};
+    unsigned x[16];
+#pragma unroll
+    for (int i = 0; i < 16; i++) x[i] = s[i];
+#pragma unroll
+    for (int i = 0; i < 10; i++) {
+        CQR(x[0], x[4], x[8], x[12]);
+        CQR(x[1], x[5], x[9], x[13]);
+        CQR(x[2], x[6], x[10], x[14]);
+        CQR(x[3], x[7], x[11], x[15]);
+        CQR(x[0], x[5], x[10], x[15]);
+        CQR(x[1], x[6], x[11], x[12]);
+        CQR(x[2], x[7], x[8], x[13]);
+        CQR(x[3], x[4], x[9], x[14]);
+    }
+#pragma unroll
+    for (int i = 0; i < 16; i++) out[i] = x[i] + s[i];
+}
+
+struct PidxArr {
+    unsigned char p[FHE_MAX_LIMBS];
+};
+
+// each thread: one block = 4 coefficients of one limb
+__global__ void k_sample_uniform(DevCtx c, uint64_t seed, uint32_t domain, uint32_t id0, uint32_t id1_base,
+                                 uint32_t id1_step, u64 *out, PidxArr pidx) {
+    const long long N = 1ll << c.logN;
+    const int limb = blockIdx.y;
+    const ModQ m = c.primes[pidx.p[limb]].m;
+    const u64 r64 = barrett(U128{0, 1}, m);   // 2^64 mod q
+    for (long long b = blockIdx.x * blockDim.x + threadIdx.x; b < N / 4; b += (long long)gridDim.x * blockDim.x) {
+        unsigned w[16];
+        chacha_block(seed, domain, id0, id1_base + (uint32_t)limb * id1_step, (uint32_t)b, w);
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const u64 lo = (u64)w[4 * u] | ((u64)w[4 * u + 1] << 32);
+            const u64 hi = (u64)w[4 * u + 2] | ((u64)w[4 * u + 3] << 32);
+            const u64 h = barrett(U128{hi, 0}, m);
+            U128 t = mul_wide(h, r64);
+            add_to(t, U128{barrett(U128{lo, 0}, m), 0});
+            out[(long long)limb * N + 4 * b + u] = barrett(t, m);
+        }
+    }
+}
+
+// kind 0: ternary (16 coefficients per block), kind 1: CBD eta=21 (8 per block)
+__global__ void k_sample_small(DevCtx c, uint64_t seed, uint32_t domain, uint32_t id0, uint32_t id1, int kind,
+                               long long *out) {
+    const long long N = 1ll << c.logN;
+    const int per = kind == 0 ? 16 : 8;
+    for (long long b = blockIdx.x * blockDim.x + threadIdx.x; b < N / per; b += (long long)gridDim.x * blockDim.x) {
+        unsigned w[16];
+        chacha_block(seed, domain, id0, id1, (uint32_t)b, w);
+        if (kind == 0) {
+#pragma unroll
+            for (int u = 0; u < 16; u++) out[16 * b + u] = (long long)(((u64)w[u] * 3) >> 32) - 1;
+        } else {
+#pragma unroll
+            for (int u = 0; u < 8; u++)
+                out[8 * b + u] = (long long)__popc(w[2 * u] & 0x1FFFFFu) - (long long)__popc(w[2 * u + 1] & 0x1FFFFFu);
+        }
+    }
+}
+
+__global__ void k_signed_to_limbs(DevCtx c, const long long *v, u64 *out, PidxArr pidx) {
+    const long long N = 1ll << c.logN;
+    const int limb = blockIdx.y;
+    const u64 q = c.primes[pidx.p[limb]].m.q;
+    for (long long j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += (long long)gridDim.x * blockDim.x) {
+        const long long x = v[j];
+        u64 r = x >= 0 ? (u64)x % q : (q - ((u64)(-x) % q)) % q;
+        out[(long long)limb * N + j] = r;
+    }
+}
+
+__global__ void k_mul_limbs(DevCtx c, const u64 *a, const u64 *b, const u64 *add, int negate, u64 *out,
+                            PidxArr pidx) {
+    const long long N = 1ll << c.logN;
+    const int limb = blockIdx.y;
+    const ModQ m = c.primes[pidx.p[limb]].m;
+    const long long off = (long long)limb * N;
+    for (long long j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += (long long)gridDim.x * blockDim.x) {
+        u64 p = mulmod(a[off + j], b[off + j], m);
+        if (negate) p = p ? m.q - p : 0;
+        if (add) p = add_mod(p, add[off + j], m.q);
+        out[off + j] = p;
+    }
+}
+
+__global__ void k_automorphism(DevCtx c, const u64 *in, u64 *out, int galois) {
+    const long long N = 1ll << c.logN;
+    const long long off = (long long)blockIdx.y * N;
+    for (long long j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += (long long)gridDim.x * blockDim.x)
+        out[off + j] = in[off + galois_src((int)j, galois, c.logN)];
+}
+
+__global__ void k_axpy_limbs(DevCtx c, const u64 *x, const u64 *cst, u64 *out, PidxArr pidx) {
+    const long long N = 1ll << c.logN;
+    const int limb = blockIdx.y;
+    const ModQ m = c.primes[pidx.p[limb]].m;
+    const u64 w = cst[limb];
+    const long long off = (long long)limb * N;
+    for (long long j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += (long long)gridDim.x * blockDim.x)
+        out[off + j] = add_mod(out[off + j], mulmod(x[off + j], w, m), m.q);
+}
+
+__device__ u64 pow2_mod(int e, const ModQ &m) {
+    u64 r = 1, b = 2 % m.q;
+    while (e) {
+        if (e & 1) r = mulmod(r, b, m);
+        b = mulmod(b, b, m);
+        e >>= 1;
+    }
+    return r;
+}
+
+// exact residue of an integral double: |v| < 2^63 through int64, else as a
+// 53-bit integer mantissa times 2^shift
+__global__ void k_double_to_limbs(DevCtx c, const double *v, u64 *out) {
+    const long long N = 1ll << c.logN;
+    const int limb = blockIdx.y;
+    const ModQ m = c.primes[limb].m;
+    for (long long j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += (long long)gridDim.x * blockDim.x) {
+        const double x = v[j];
+        const double ax = fabs(x);
+        u64 r;
+        if (ax < 9223372036854775808.0) {
+            r = (u64)(long long)ax % m.q;
+        } else {
+            int e;
+            const double mant = frexp(ax, &e);
+            const u64 mi = (u64)ldexp(mant, 53);
+            r = mulmod(mi % m.q, pow2_mod(e - 53, m), m);
+        }
+        out[(long long)limb * N + j] = (x < 0 && r) ? m.q - r : r;
+    }
+}
+
+}  // namespace
+
+// ================================================================ launchers
+
+#define DISPATCH_LOGR(logr, KERNEL, GRID, ...)                                      \
+    do {                                                                            \
+        switch (logr) {                                                             \
+        case 4: KERNEL<4><<<GRID, NT, 0, s>>>(__VA_ARGS__); break;                  \
+        case 5: KERNEL<5><<<GRID, NT, 0, s>>>(__VA_ARGS__); break;                  \
+        case 6: KERNEL<6><<<GRID, NT, 0, s>>>(__VA_ARGS__); break;                  \
+        case 7: KERNEL<7><<<GRID, NT, 0, s>>>(__VA_ARGS__); break;                  \
+        case 8: KERNEL<8><<<GRID, NT, 0, s>>>(__VA_ARGS__); break;                  \
+        default: return cudaErrorInvalidValue;                                      \
+        }                                                                           \
+    } while (0)
+
+static inline int tiles_col(const DevCtx &c) { return 1 << (c.logN - 12); }  // CTAs per limb
+
+size_t ks_workspace_words(const DevCtx &c, int level) {
+    const int nd = (level + c.alpha) / c.alpha;
+    KsLayout L = ks_layout(level, nd, c.alpha, c.logN);
+    return (size_t)(L.md + 2ll * (level + 1) * (1ll << c.logN));
+}
+
+cudaError_t launch_ntt(const DevCtx &c, const NttArgs &a, bool inverse, cudaStream_t s) {
+    dim3 g(tiles_col(c), a.n_items * a.n_limbs);
+    if (!inverse) {
+        DISPATCH_LOGR(c.logR1, k_ntt_fwd_col, g, c, a);
+        DISPATCH_LOGR(c.logR2, k_ntt_fwd_row, g, c, a);
+    } else {
+        DISPATCH_LOGR(c.logR2, k_ntt_inv_row, g, c, a);
+        DISPATCH_LOGR(c.logR1, k_ntt_inv_col, g, c, a);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_keyswitch(const DevCtx &c, const LevelTab &lt, const KsArgs &a, cudaStream_t s) {
+    const int nl = a.level + 1, ext = lt.ext, nd = lt.n_digits, B = a.n_items;
+    if (nd > 7) return cudaErrorInvalidValue;   // inner-product accumulator bound
+    KsLayout ly = ks_layout(a.level, nd, c.alpha, c.logN);
+    const int tc = tiles_col(c);
+    DISPATCH_LOGR(c.logR2, k_ks_intt_row, dim3(tc, B * nl), c, a, ly);
+    DISPATCH_LOGR(c.logR1, k_ks_intt_col, dim3(tc, B * nl), c, lt, a, ly);
+    DISPATCH_LOGR(c.logR1, k_ks_modup_col, dim3(tc, B * nd * ext), c, lt, a, ly);
+    DISPATCH_LOGR(c.logR2, k_ks_modup_row_ip, dim3(tc, B * ext), c, lt, a, ly);
+    DISPATCH_LOGR(c.logR2, k_ks_md_intt_row, dim3(tc, B * 2 * c.alpha), c, lt, a, ly);
+    DISPATCH_LOGR(c.logR1, k_ks_md_intt_col, dim3(tc, B * 2 * c.alpha), c, lt, a, ly);
+    DISPATCH_LOGR(c.logR1, k_ks_md_conv_col, dim3(tc, B * 2 * nl), c, lt, a, ly);
+    DISPATCH_LOGR(c.logR2, k_ks_md_row_out, dim3(tc, B * 2 * nl), c, lt, a, ly);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rescale(const DevCtx &c, const LevelTab &lt, const RescaleArgs &a, cudaStream_t s) {
+    const int tc = tiles_col(c), B = a.n_items, lv = a.level;
+    if (lv < 1) return cudaErrorInvalidValue;
+    DISPATCH_LOGR(c.logR2, k_rs_intt_row, dim3(tc, B * a.n_poly), c, a);
+    DISPATCH_LOGR(c.logR1, k_rs_intt_col, dim3(tc, B * a.n_poly), c, a);
+    DISPATCH_LOGR(c.logR1, k_rs_conv_col, dim3(tc, B * a.n_poly * lv), c, lt, a);
+    DISPATCH_LOGR(c.logR2, k_rs_row_out, dim3(tc, B * a.n_poly * lv), c, lt, a);
+    return cudaGetLastError();
+}
+
+static dim3 ew_grid(const DevCtx &c, int y, int z) {
+    int x = (int)((1ll << c.logN) / 256);
+    if (x > 64) x = 64;
+    return dim3(x, y, z);
+}
+
+cudaError_t launch_add(const DevCtx &c, const u64 *a, long long a_item, const u64 *b, long long b_item, u64 *out,
+                       long long out_item, int n_items, int n_poly, int level, int subtract, cudaStream_t s) {
+    k_add<<<ew_grid(c, n_poly * (level + 1), n_items), 256, 0, s>>>(c, a, a_item, b, b_item, out, out_item, n_poly,
+                                                                     level, subtract);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mul_const(const DevCtx &c, const u64 *a, long long a_item, const u64 *cst, u64 *out,
+                             long long out_item, int n_items, int n_poly, int level, cudaStream_t s) {
+    k_mul_const<<<ew_grid(c, n_poly * (level + 1), n_items), 256, 0, s>>>(c, a, a_item, cst, out, out_item, level);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_add_const(const DevCtx &c, const u64 *a, long long a_item, const u64 *cst, u64 *out,
+                             long long out_item, int n_items, int level, cudaStream_t s) {
+    k_add_const<<<ew_grid(c, 2 * (level + 1), n_items), 256, 0, s>>>(c, a, a_item, cst, out, out_item, level);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_square_act(const DevCtx &c, const u64 *in, long long in_item, const u64 *c1, const u64 *c0,
+                              u64 *out, long long out_item, int n_items, int level, cudaStream_t s) {
+    k_square_act<<<ew_grid(c, level + 1, n_items), 256, 0, s>>>(c, in, in_item, c1, c0, out, out_item, level);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_drop(const DevCtx &c, const u64 *in, long long in_item, int in_level, u64 *out,
+                        long long out_item, int new_level, int n_items, int n_poly, cudaStream_t s) {
+    k_drop<<<ew_grid(c, n_poly * (new_level + 1), n_items), 256, 0, s>>>(c, in, in_item, in_level, out, out_item,
+                                                                          new_level);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_decrypt(const DevCtx &c, const u64 *ct, const u64 *s_ntt, u64 *m, int level, cudaStream_t s) {
+    k_decrypt<<<ew_grid(c, level + 1, 1), 256, 0, s>>>(c, ct, s_ntt, m, level);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mac(const DevCtx &c, const MacArgs &a, cudaStream_t s) {
+    if (a.n_groups == 0) return cudaSuccess;
+    dim3 g(a.n_groups, (unsigned)((1ll << c.logN) / 256), a.level + 1);
+    k_mac<<<g, 256, 0, s>>>(c, a);
+    return cudaGetLastError();
+}
+
+static PidxArr to_pidx(const unsigned char *p, int n) {
+    PidxArr r;
+    for (int i = 0; i < FHE_MAX_LIMBS; i++) r.p[i] = i < n ? p[i] : 0;
+    return r;
+}
+
+cudaError_t launch_sample_uniform(const DevCtx &c, uint64_t seed, uint32_t domain, uint32_t id0, uint32_t id1_base,
+                                  uint32_t id1_step, u64 *out, int n_limbs, const unsigned char *pidx,
+                                  cudaStream_t s) {
+    k_sample_uniform<<<ew_grid(c, n_limbs, 1), 256, 0, s>>>(c, seed, domain, id0, id1_base, id1_step, out,
+                                                             to_pidx(pidx, n_limbs));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sample_small(const DevCtx &c, uint64_t seed, uint32_t domain, uint32_t id0, uint32_t id1, int kind,
+                                long long *out, cudaStream_t s) {
+    k_sample_small<<<ew_grid(c, 1, 1), 256, 0, s>>>(c, seed, domain, id0, id1, kind, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_signed_to_limbs(const DevCtx &c, const long long *v, u64 *out, int n_limbs,
+                                   const unsigned char *pidx, cudaStream_t s) {
+    k_signed_to_limbs<<<ew_grid(c, n_limbs, 1), 256, 0, s>>>(c, v, out, to_pidx(pidx, n_limbs));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mul_limbs(const DevCtx &c, const u64 *a, const u64 *b, const u64 *add, int negate, u64 *out,
+                             int n_limbs, const unsigned char *pidx, cudaStream_t s) {
+    k_mul_limbs<<<ew_grid(c, n_limbs, 1), 256, 0, s>>>(c, a, b, add, negate, out, to_pidx(pidx, n_limbs));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_axpy_limbs(const DevCtx &c, const u64 *x, const u64 *cst, u64 *out, int n_limbs,
+                              const unsigned char *pidx, cudaStream_t s) {
+    k_axpy_limbs<<<ew_grid(c, n_limbs, 1), 256, 0, s>>>(c, x, cst, out, to_pidx(pidx, n_limbs));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_double_to_limbs(const DevCtx &c, const double *v, u64 *out, int n_limbs, cudaStream_t s) {
+    k_double_to_limbs<<<ew_grid(c, n_limbs, 1), 256, 0, s>>>(c, v, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_automorphism(const DevCtx &c, const u64 *in, u64 *out, int n_limbs, int galois, cudaStream_t s) {
+    k_automorphism<<<ew_grid(c, n_limbs, 1), 256, 0, s>>>(c, in, out, galois);
+    return cudaGetLastError();
+}

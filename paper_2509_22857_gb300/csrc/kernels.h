@@ -1,0 +1,174 @@
+// Device-side tables and kernel launchers of the RNS-CKKS hot path.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "modarith.cuh"
+
+#define FHE_MAX_LIMBS 64
+
+// One prime of the chain q_0..q_L, p_0..p_{alpha-1}.
+struct PrimeTab {
+    ModQ m;
+    u64 n_inv, n_inv_sh;            // N^-1 mod q and its Shoup companion
+    const ulonglong2 *fwd;          // [N] (psi^brv(k), Shoup)
+    const ulonglong2 *inv;          // [N] (psi^-brv(k), Shoup)
+};
+
+// Per-level constants of hybrid key switching and rescale (device pointers).
+struct LevelTab {
+    int level, n_digits, ext;       // ext = level + 1 + alpha
+    // iNTT epilogue of ModUp: N^-1 * (Qhat_{j,i})^-1 mod q_i, Shoup pair, [level+1]
+    const ulonglong2 *y_scale;
+    // (Qhat_{j,i} mod prime of ext limb t), [n_digits][alpha][ext]
+    const u64 *modup_hat;
+    // rescale by q_level: q_level^-1 mod q_i, Shoup pair, [level]
+    const ulonglong2 *q_last_inv;
+    // q_level mod q_i, [level]
+    const u64 *q_last_mod;
+};
+
+// Context passed by value to kernels.
+struct DevCtx {
+    const PrimeTab *primes;         // [L+1+alpha]
+    int logN, L, alpha;
+    int logR1, logR2;               // NTT split: columns of 2^logR1, rows of 2^logR2
+    // ModDown constants (level independent)
+    const ulonglong2 *md_z_scale;   // [alpha] N^-1 * Phat_m^-1 mod p_m (Shoup)
+    const u64 *md_z_add;            // [alpha] floor(P/2) * Phat_m^-1 mod p_m
+    const u64 *md_phat;             // [alpha][L+1] Phat_m mod q_i
+    const u64 *md_halfp;            // [L+1] floor(P/2) mod q_i
+    const ulonglong2 *md_pinv;      // [L+1] P^-1 mod q_i (Shoup)
+};
+
+__host__ __device__ inline int ext_prime(int l, int level, int L) {
+    // extended basis Q_level u P: limbs 0..level are q_0..q_level, then p_*
+    return l <= level ? l : L + 1 + (l - level - 1);
+}
+
+// A set of limbs: item i, limb l at base + i*item + l*N (in words).
+struct LimbSet {
+    u64 *base;
+    long long item;
+    int n_items;
+    int n_limbs;
+};
+
+// Rotation / relinearisation key switch of a batch of ciphertexts at one level.
+struct KsArgs {
+    const u64 *d;           // poly to switch, NTT domain: d + i*d_item, limbs 0..level
+    long long d_item;
+    int galois;             // Galois element applied to d (and to add0) on load; 1 = none
+    const u64 *key;         // [n_digits_top][2][L+1+alpha][N]
+    int key_digits_top;     // digits of the key at the top level
+    const u64 *add0;        // addend of output poly 0 (nullable), limbs 0..level, + i*add_item
+    const u64 *add1;        // addend of output poly 1 (nullable)
+    long long add_item;
+    const u64 *base;        // added to both output polys without gather (nullable; may alias out)
+    long long base_item;
+    u64 *out;               // [item][2][level+1][N]
+    long long out_item;
+    int n_items;
+    int level;
+    // workspace (item-major): y [level+1], mu [digits][ext], acc [2][ext],
+    // z [2][alpha], md [2][level+1] limbs; sized by the caller
+    u64 *ws;
+    long long ws_item;      // words per item
+};
+
+size_t ks_workspace_words(const DevCtx &c, int level);
+cudaError_t launch_keyswitch(const DevCtx &c, const LevelTab &lt, const KsArgs &a, cudaStream_t s);
+
+// Rescale: out[i] = q_l^-1 (in[i] - [in[l]]_centred) mod q_i for i < level, both polys.
+struct RescaleArgs {
+    const u64 *in;
+    long long in_item;      // item stride; poly stride is (level+1)*N
+    u64 *out;
+    long long out_item;     // poly stride is level*N
+    int n_items;
+    int n_poly;
+    int level;              // input level (>= 1)
+    u64 *ws;                // [n_items*n_poly][N]
+};
+cudaError_t launch_rescale(const DevCtx &c, const LevelTab &lt, const RescaleArgs &a, cudaStream_t s);
+
+// Plain forward/inverse NTT of limbs; limb l of item i uses prime pidx[l].
+struct NttArgs {
+    const u64 *src;
+    u64 *dst;
+    long long src_item, dst_item;
+    int n_items, n_limbs;
+    unsigned char pidx[FHE_MAX_LIMBS];
+};
+cudaError_t launch_ntt(const DevCtx &c, const NttArgs &a, bool inverse, cudaStream_t s);
+
+// Elementwise ops over ciphertext limbs (limb l uses prime l).
+cudaError_t launch_add(const DevCtx &c, const u64 *a, long long a_item, const u64 *b, long long b_item,
+                       u64 *out, long long out_item, int n_items, int n_poly, int level, int subtract,
+                       cudaStream_t s);
+// out[p][l] = a[p][l] * (const[l]) for every poly p
+cudaError_t launch_mul_const(const DevCtx &c, const u64 *a, long long a_item, const u64 *cst,
+                             u64 *out, long long out_item, int n_items, int n_poly, int level,
+                             cudaStream_t s);
+// out[0][l] = a[0][l] + cst[l] (constant polynomial), out[1] = a[1]
+cudaError_t launch_add_const(const DevCtx &c, const u64 *a, long long a_item, const u64 *cst,
+                             u64 *out, long long out_item, int n_items, int level, cudaStream_t s);
+// Tensor square with the activation's lower terms folded in:
+//   d0 = c0^2 + C1 c0 + C0, d1 = 2 c0 c1 + C1 c1, d2 = c1^2
+cudaError_t launch_square_act(const DevCtx &c, const u64 *in, long long in_item, const u64 *c1,
+                              const u64 *c0, u64 *out, long long out_item, int n_items, int level,
+                              cudaStream_t s);
+// copy limbs 0..new_level of every poly (mod-drop)
+cudaError_t launch_drop(const DevCtx &c, const u64 *in, long long in_item, int in_level, u64 *out,
+                        long long out_item, int new_level, int n_items, int n_poly, cudaStream_t s);
+// m = c0 + c1*s (NTT domain), limbs 0..level
+cudaError_t launch_decrypt(const DevCtx &c, const u64 *ct, const u64 *s_ntt, u64 *m, int level,
+                           cudaStream_t s);
+
+// Plaintext-ciphertext multiply-accumulate of a linear layer.  Output group
+// g (one accumulator ciphertext per image) is
+//   out_g = sum_{t in terms(g)} pt_t (.) src_t   (+ bias_g on poly 0)
+// where src_t is a ciphertext tensor (per image at src_t + img*src_item_t).
+struct MacTerm {
+    const u64 *src;       // image 0's ciphertext (2 polys x (level+1) limbs)
+    long long src_item;   // per-image stride of src
+    const u64 *pt;        // plaintext limbs (level+1) x N
+};
+struct MacGroup {
+    u64 *out;             // image 0's output ciphertext
+    long long out_item;   // per-image stride of out
+    const u64 *bias;      // plaintext added to poly 0 (nullable)
+    int term_begin, term_end;
+};
+struct MacArgs {
+    const MacGroup *groups;   // device array
+    const MacTerm *terms;     // device array
+    int n_groups;
+    int n_items;
+    int level;
+};
+cudaError_t launch_mac(const DevCtx &c, const MacArgs &a, cudaStream_t s);
+
+// ChaCha20-based samplers (the stream of one (seed, domain, id0, id1)).
+// uniform residues written directly as NTT-domain limbs
+cudaError_t launch_sample_uniform(const DevCtx &c, uint64_t seed, uint32_t domain, uint32_t id0,
+                                  uint32_t id1_base, uint32_t id1_step, u64 *out, int n_limbs,
+                                  const unsigned char *pidx, cudaStream_t s);
+// small signed samples (ternary or CBD-21) as int64 coefficients
+cudaError_t launch_sample_small(const DevCtx &c, uint64_t seed, uint32_t domain, uint32_t id0,
+                                uint32_t id1, int kind, long long *out, cudaStream_t s);
+// signed int64 coefficients -> residues for limbs with primes pidx[l]
+cudaError_t launch_signed_to_limbs(const DevCtx &c, const long long *v, u64 *out, int n_limbs,
+                                   const unsigned char *pidx, cudaStream_t s);
+// out[l] = a[l] (.) b[l] (+ c[l]) mod pidx[l]; sub: out = c - a*b
+cudaError_t launch_mul_limbs(const DevCtx &c, const u64 *a, const u64 *b, const u64 *add, int negate,
+                             u64 *out, int n_limbs, const unsigned char *pidx, cudaStream_t s);
+// out[l] += cst[l] * x[l] mod pidx[l]
+cudaError_t launch_axpy_limbs(const DevCtx &c, const u64 *x, const u64 *cst, u64 *out, int n_limbs,
+                              const unsigned char *pidx, cudaStream_t s);
+// integral doubles (any magnitude) -> residues of limbs 0..n_limbs-1 (prime l)
+cudaError_t launch_double_to_limbs(const DevCtx &c, const double *v, u64 *out, int n_limbs, cudaStream_t s);
+// NTT-domain automorphism of limbs (gather): out[j] = in[pi_k(j)]
+cudaError_t launch_automorphism(const DevCtx &c, const u64 *in, u64 *out, int n_limbs, int galois,
+                                cudaStream_t s);

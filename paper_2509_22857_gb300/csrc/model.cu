@@ -1,0 +1,583 @@
+// Compiled CNN programs: weight plaintexts resident in HBM, and a batched
+// executor that runs every step for all images of a batch in the same
+// kernels (so each evaluation key and each weight plaintext is read once per
+// batch rather than once per image).
+#include <algorithm>
+#include <cstring>
+#include <memory>
+#include <set>
+
+#include "host.h"
+
+namespace {
+
+struct MTensor {
+    int n_ct, level;
+    double scale;
+};
+
+struct MLinear {
+    int level = 0;
+    std::vector<int> baby_ct, baby_step;           // distinct (ct, b != 0)
+    std::vector<int> g_out, g_giant, g_tb, g_te;   // groups
+    std::vector<int> t_ct, t_baby;
+    std::vector<u64 *> t_pt;
+    std::vector<u64 *> bias_pt;                    // per output ct (nullable)
+};
+
+struct MStep {
+    int kind = 0, src = -1, src2 = -1, dst = -1;
+    MLinear lin;
+    u64 *c1 = nullptr, *c0 = nullptr, *cval = nullptr;   // per-limb residues
+    std::vector<int> rot;
+    int level = 0;
+};
+
+}  // namespace
+
+struct fhe_model {
+    fhe_ctx *ctx;
+    std::vector<MTensor> tensors;
+    std::vector<MStep> steps;
+    std::vector<int> last_use;
+    int input = 0, output = 0;
+    std::vector<void *> owned;
+    size_t pt_bytes = 0;
+};
+
+static int residues_of(fhe_model *m, double v, int level, u64 **out) {
+    fhe_ctx *c = m->ctx;
+    std::vector<u64> r(level + 1);
+    for (int l = 0; l <= level; l++) r[l] = h_double_mod(v, c->primes[l]);
+    void *d;
+    FHE_TRY(dev_alloc(c, &d, r.size() * 8));
+    m->owned.push_back(d);
+    FHE_CU(cudaMemcpy(d, r.data(), r.size() * 8, cudaMemcpyHostToDevice));
+    *out = (u64 *)d;
+    return FHE_OK;
+}
+
+static int encode_vec(fhe_model *m, const double *vec, double scale, int level, u64 **out) {
+    fhe_ctx *c = m->ctx;
+    std::vector<double> coef(c->N);
+    c->enc.encode(vec, nullptr, (size_t)c->N / 2, scale, coef.data());
+    void *d;
+    const size_t bytes = (size_t)(level + 1) * c->N * 8;
+    FHE_TRY(dev_alloc(c, &d, bytes));
+    m->owned.push_back(d);
+    m->pt_bytes += bytes;
+    FHE_TRY(op_encode_to(c, coef.data(), level, (u64 *)d, 0));
+    *out = (u64 *)d;
+    return FHE_OK;
+}
+
+static int load_linear(fhe_model *m, const fhe_step_desc &sd, MStep &st) {
+    fhe_ctx *c = m->ctx;
+    MLinear &L = st.lin;
+    const MTensor &tin = m->tensors[st.src], &tout = m->tensors[st.dst];
+    L.level = tin.level;
+    if (tout.level != tin.level) return fhe_fail(FHE_E_LEVEL, "linear step changes level");
+    const size_t ns = (size_t)c->N / 2;
+    if (sd.n_groups < 0 || (sd.n_groups > 0 && (!sd.group_out || !sd.group_giant || !sd.group_term_begin)))
+        return fhe_fail(FHE_E_INVAL, "linear step: missing group arrays");
+    const int n_terms = sd.n_groups > 0 ? sd.group_term_begin[sd.n_groups] : 0;
+    if (n_terms > 0 && (!sd.term_ct || !sd.term_baby || !sd.term_vec))
+        return fhe_fail(FHE_E_INVAL, "linear step: missing term arrays");
+    std::set<std::pair<int, int>> baby;
+    std::vector<int> has_zero(tout.n_ct, 0);
+    for (int g = 0; g < sd.n_groups; g++) {
+        const int o = sd.group_out[g];
+        if (o < 0 || o >= tout.n_ct) return fhe_fail(FHE_E_INVAL, "linear step: output index");
+        if (sd.group_giant[g] == 0) has_zero[o] = 1;
+        L.g_out.push_back(o);
+        L.g_giant.push_back(sd.group_giant[g]);
+        L.g_tb.push_back(sd.group_term_begin[g]);
+        L.g_te.push_back(sd.group_term_begin[g + 1]);
+        if (sd.group_term_begin[g + 1] < sd.group_term_begin[g]) return fhe_fail(FHE_E_INVAL, "term ranges");
+    }
+    for (int o = 0; o < tout.n_ct; o++)
+        if (!has_zero[o]) {
+            L.g_out.push_back(o);
+            L.g_giant.push_back(0);
+            L.g_tb.push_back(n_terms);
+            L.g_te.push_back(n_terms);
+        }
+    for (int t = 0; t < n_terms; t++) {
+        const int ct = sd.term_ct[t], b = sd.term_baby[t];
+        if (ct < 0 || ct >= tin.n_ct) return fhe_fail(FHE_E_INVAL, "linear step: input index");
+        L.t_ct.push_back(ct);
+        L.t_baby.push_back(b);
+        if (galois_of_step(c, b) != 1) baby.insert({ct, b});
+        u64 *pt;
+        FHE_TRY(encode_vec(m, sd.term_vec + (size_t)t * ns, sd.w_scale, L.level, &pt));
+        L.t_pt.push_back(pt);
+    }
+    for (auto &p : baby) {
+        L.baby_ct.push_back(p.first);
+        L.baby_step.push_back(p.second);
+    }
+    L.bias_pt.assign(tout.n_ct, nullptr);
+    for (int b = 0; b < sd.n_bias; b++) {
+        const int o = sd.bias_out[b];
+        if (o < 0 || o >= tout.n_ct) return fhe_fail(FHE_E_INVAL, "bias index");
+        FHE_TRY(encode_vec(m, sd.bias_vec + (size_t)b * ns, sd.bias_scale, L.level, &L.bias_pt[o]));
+    }
+    return FHE_OK;
+}
+
+extern "C" int fhe_model_load(fhe_ctx *c, const fhe_model_desc *d, fhe_model **out) {
+    if (!c || !d || !out) return fhe_fail(FHE_E_INVAL, "null argument");
+    if (d->n_tensors <= 0 || !d->tensor_n_ct || !d->tensor_level || !d->tensor_scale)
+        return fhe_fail(FHE_E_INVAL, "model without tensors");
+    FHE_CU(cudaSetDevice(c->dev));
+    std::unique_ptr<fhe_model> m(new fhe_model());
+    m->ctx = c;
+    for (int t = 0; t < d->n_tensors; t++) {
+        if (d->tensor_level[t] < 0 || d->tensor_level[t] > c->L) return fhe_fail(FHE_E_LEVEL, "tensor level");
+        if (d->tensor_n_ct[t] <= 0) return fhe_fail(FHE_E_INVAL, "tensor size");
+        m->tensors.push_back({d->tensor_n_ct[t], d->tensor_level[t], d->tensor_scale[t]});
+    }
+    if (d->input_tensor < 0 || d->input_tensor >= d->n_tensors || d->output_tensor < 0 ||
+        d->output_tensor >= d->n_tensors)
+        return fhe_fail(FHE_E_INVAL, "input / output tensor");
+    m->input = d->input_tensor;
+    m->output = d->output_tensor;
+    auto check_t = [&](int t) { return t >= 0 && t < d->n_tensors; };
+    int rc = FHE_OK;
+    for (int i = 0; i < d->n_steps && rc == FHE_OK; i++) {
+        const fhe_step_desc &sd = d->steps[i];
+        MStep st;
+        st.kind = sd.kind;
+        st.src = sd.src;
+        st.src2 = sd.src2;
+        st.dst = sd.dst;
+        if (!check_t(sd.src) || !check_t(sd.dst) || (sd.kind == FHE_STEP_ADD && !check_t(sd.src2))) {
+            rc = fhe_fail(FHE_E_INVAL, "step " + std::to_string(i) + ": tensor index");
+            break;
+        }
+        const MTensor &ti = m->tensors[sd.src], &to = m->tensors[sd.dst];
+        switch (sd.kind) {
+        case FHE_STEP_LINEAR:
+            rc = load_linear(m.get(), sd, st);
+            break;
+        case FHE_STEP_RESCALE:
+            if (to.level != ti.level - 1 || ti.level < 1 || to.n_ct != ti.n_ct)
+                rc = fhe_fail(FHE_E_LEVEL, "rescale step levels");
+            break;
+        case FHE_STEP_ACT:
+            if (to.level != ti.level || to.n_ct != ti.n_ct) rc = fhe_fail(FHE_E_LEVEL, "act step levels");
+            if (rc == FHE_OK) rc = residues_of(m.get(), sd.c1, ti.level, &st.c1);
+            if (rc == FHE_OK) rc = residues_of(m.get(), sd.c0, ti.level, &st.c0);
+            break;
+        case FHE_STEP_CMUL:
+            if (to.level != ti.level || to.n_ct != ti.n_ct) rc = fhe_fail(FHE_E_LEVEL, "cmul step levels");
+            if (rc == FHE_OK) rc = residues_of(m.get(), sd.value, ti.level, &st.cval);
+            break;
+        case FHE_STEP_ROTSUM:
+            if (to.level != ti.level || to.n_ct != ti.n_ct) rc = fhe_fail(FHE_E_LEVEL, "rotsum step levels");
+            for (int k = 0; k < sd.n_steps; k++) st.rot.push_back(sd.steps[k]);
+            break;
+        case FHE_STEP_DROP:
+            if (to.level != sd.level || sd.level > ti.level || to.n_ct != ti.n_ct)
+                rc = fhe_fail(FHE_E_LEVEL, "drop step levels");
+            st.level = sd.level;
+            break;
+        case FHE_STEP_ADD: {
+            const MTensor &t2 = m->tensors[sd.src2];
+            if (t2.level != ti.level || to.level != ti.level || t2.n_ct != ti.n_ct || to.n_ct != ti.n_ct)
+                rc = fhe_fail(FHE_E_LEVEL, "add step levels");
+            break;
+        }
+        default:
+            rc = fhe_fail(FHE_E_INVAL, "unknown step kind");
+        }
+        m->steps.push_back(std::move(st));
+    }
+    if (rc != FHE_OK) {
+        cudaDeviceSynchronize();
+        for (void *p : m->owned) dev_free(p);
+        return rc;
+    }
+    m->last_use.assign(m->tensors.size(), -1);
+    for (int i = 0; i < (int)m->steps.size(); i++) {
+        m->last_use[m->steps[i].src] = i;
+        if (m->steps[i].src2 >= 0) m->last_use[m->steps[i].src2] = i;
+    }
+    FHE_CU(cudaDeviceSynchronize());
+    *out = m.release();
+    return FHE_OK;
+}
+
+extern "C" int fhe_model_free(fhe_model *m) {
+    if (!m) return FHE_OK;
+    cudaDeviceSynchronize();
+    for (void *p : m->owned) dev_free(p);
+    delete m;
+    return FHE_OK;
+}
+
+// ================================================================ executor
+
+namespace {
+
+struct Exec {
+    fhe_model *m;
+    const fhe_evk *evk;
+    int B;
+    cudaStream_t s;
+    std::vector<u64 *> buf;               // per tensor: [B][n_ct][2][level+1][N]
+    std::vector<std::vector<char>> host_stage;
+
+    long long ctst(int t) const { return 2ll * (m->tensors[t].level + 1) * m->ctx->N; }
+    long long item(int t) const { return (long long)m->tensors[t].n_ct * ctst(t); }
+
+    int alloc_t(int t) {
+        if (buf[t]) return FHE_OK;
+        const size_t bytes = (size_t)B * item(t) * 8;
+        FHE_CU(cudaMallocAsync((void **)&buf[t], bytes, s));
+        return FHE_OK;
+    }
+    void release(int t) {
+        if (buf[t] && t != m->output) {
+            cudaFreeAsync(buf[t], s);
+            buf[t] = nullptr;
+        }
+    }
+    const u64 *key_for(int step, int *err) {
+        const int k = galois_of_step(m->ctx, step);
+        auto it = evk->galois.find(k);
+        if (it == evk->galois.end()) {
+            *err = fhe_fail(FHE_E_NOKEY, "no Galois key for rotation step " + std::to_string(step));
+            return nullptr;
+        }
+        *err = FHE_OK;
+        return it->second;
+    }
+
+    // out = base + rot(x, step) for n items of one tensor-like layout
+    int rotate_items(const u64 *x, long long x_item, int step, const u64 *base, long long base_item, u64 *out,
+                     long long out_item, int n, int level) {
+        int err;
+        const u64 *key = key_for(step, &err);
+        if (!key) return err;
+        KsArgs a;
+        memset(&a, 0, sizeof(a));
+        const long long nlN = (long long)(level + 1) * m->ctx->N;
+        a.d = x + nlN;
+        a.d_item = x_item;
+        a.galois = galois_of_step(m->ctx, step);
+        a.key = key;
+        a.key_digits_top = evk->digits;
+        a.add0 = x;
+        a.add_item = x_item;
+        a.base = base;
+        a.base_item = base_item;
+        a.out = out;
+        a.out_item = out_item;
+        a.n_items = n;
+        a.level = level;
+        return op_keyswitch(m->ctx, a, s);
+    }
+
+    int linear(const MStep &st) {
+        const MLinear &L = st.lin;
+        fhe_ctx *c = m->ctx;
+        const int lv = L.level;
+        const long long cs = ctst(st.src);
+        const u64 *in = buf[st.src];
+        u64 *out = buf[st.dst];
+        const long long in_item = item(st.src), out_item = item(st.dst);
+        // baby-step rotations of the inputs
+        std::vector<u64 *> rb(L.baby_ct.size(), nullptr);
+        for (size_t k = 0; k < L.baby_ct.size(); k++) {
+            FHE_CU(cudaMallocAsync((void **)&rb[k], (size_t)B * cs * 8, s));
+            FHE_TRY(rotate_items(in + L.baby_ct[k] * cs, in_item, L.baby_step[k], nullptr, 0, rb[k], cs, B, lv));
+        }
+        auto src_of = [&](int ct, int b, long long *it) -> const u64 * {
+            if (galois_of_step(c, b) == 1) {
+                *it = in_item;
+                return in + ct * cs;
+            }
+            for (size_t k = 0; k < L.baby_ct.size(); k++)
+                if (L.baby_ct[k] == ct && L.baby_step[k] == b) {
+                    *it = cs;
+                    return rb[k];
+                }
+            return nullptr;
+        };
+        // accumulators of the giant steps (g != 0); g == 0 goes straight to out
+        const int ng = (int)L.g_out.size();
+        std::vector<u64 *> acc(ng, nullptr);
+        std::vector<MacGroup> hg(ng);
+        std::vector<MacTerm> ht;
+        for (int g = 0; g < ng; g++) {
+            const int o = L.g_out[g];
+            MacGroup &G = hg[g];
+            if (galois_of_step(c, L.g_giant[g]) == 1) {
+                G.out = out + o * cs;
+                G.out_item = out_item;
+                G.bias = L.bias_pt[o];
+            } else {
+                FHE_CU(cudaMallocAsync((void **)&acc[g], (size_t)B * cs * 8, s));
+                G.out = acc[g];
+                G.out_item = cs;
+                G.bias = nullptr;
+            }
+            G.term_begin = (int)ht.size();
+            for (int t = L.g_tb[g]; t < L.g_te[g]; t++) {
+                MacTerm T;
+                T.src = src_of(L.t_ct[t], L.t_baby[t], &T.src_item);
+                if (!T.src) return fhe_fail(FHE_E_INVAL, "internal: missing baby rotation");
+                T.pt = L.t_pt[t];
+                ht.push_back(T);
+            }
+            G.term_end = (int)ht.size();
+        }
+        // stage the work lists through pinned host memory
+        const size_t gb = hg.size() * sizeof(MacGroup), tb = ht.size() * sizeof(MacTerm);
+        host_stage.emplace_back(gb + tb + 16);
+        char *hs = host_stage.back().data();
+        memcpy(hs, hg.data(), gb);
+        if (tb) memcpy(hs + gb, ht.data(), tb);
+        char *dw;
+        FHE_CU(cudaMallocAsync((void **)&dw, gb + tb + 16, s));
+        FHE_CU(cudaMemcpyAsync(dw, hs, gb + tb, cudaMemcpyHostToDevice, s));
+        MacArgs ma;
+        ma.groups = (const MacGroup *)dw;
+        ma.terms = (const MacTerm *)(dw + gb);
+        ma.n_groups = ng;
+        ma.n_items = B;
+        ma.level = lv;
+        FHE_CU(launch_mac(c->dc, ma, s));
+        // giant steps: out_o += rot(acc_{o,g}, g)
+        for (int g = 0; g < ng; g++) {
+            if (!acc[g]) continue;
+            u64 *o = out + L.g_out[g] * cs;
+            FHE_TRY(rotate_items(acc[g], cs, L.g_giant[g], o, out_item, o, out_item, B, lv));
+        }
+        for (auto p : rb) cudaFreeAsync(p, s);
+        for (auto p : acc)
+            if (p) cudaFreeAsync(p, s);
+        cudaFreeAsync(dw, s);
+        return FHE_OK;
+    }
+
+    int act(const MStep &st) {
+        fhe_ctx *c = m->ctx;
+        const int lv = m->tensors[st.src].level;
+        const long long nlN = (long long)(lv + 1) * c->N;
+        const int n = B * m->tensors[st.src].n_ct;
+        u64 *t3;
+        FHE_CU(cudaMallocAsync((void **)&t3, (size_t)n * 3 * nlN * 8, s));
+        FHE_CU(launch_square_act(c->dc, buf[st.src], 2 * nlN, st.c1, st.c0, t3, 3 * nlN, n, lv, s));
+        KsArgs a;
+        memset(&a, 0, sizeof(a));
+        a.d = t3 + 2 * nlN;
+        a.d_item = 3 * nlN;
+        a.galois = 1;
+        a.key = evk->relin;
+        a.key_digits_top = evk->digits;
+        a.add0 = t3;
+        a.add1 = t3 + nlN;
+        a.add_item = 3 * nlN;
+        a.out = buf[st.dst];
+        a.out_item = 2 * nlN;
+        a.n_items = n;
+        a.level = lv;
+        FHE_TRY(op_keyswitch(c, a, s));
+        cudaFreeAsync(t3, s);
+        return FHE_OK;
+    }
+
+    int rotsum(const MStep &st) {
+        const int lv = m->tensors[st.src].level;
+        const long long cs = ctst(st.src);
+        const int n = B * m->tensors[st.src].n_ct;
+        const u64 *cur = buf[st.src];
+        u64 *tmp = nullptr;
+        if (st.rot.empty()) {
+            FHE_CU(cudaMemcpyAsync(buf[st.dst], cur, (size_t)n * cs * 8, cudaMemcpyDeviceToDevice, s));
+            return FHE_OK;
+        }
+        for (size_t k = 0; k < st.rot.size(); k++) {
+            u64 *nxt;
+            if (k + 1 == st.rot.size()) {
+                nxt = buf[st.dst];
+            } else {
+                FHE_CU(cudaMallocAsync((void **)&nxt, (size_t)n * cs * 8, s));
+            }
+            FHE_TRY(rotate_items(cur, cs, st.rot[k], cur, cs, nxt, cs, n, lv));
+            if (tmp) cudaFreeAsync(tmp, s);
+            tmp = (k + 1 == st.rot.size()) ? nullptr : nxt;
+            cur = nxt;
+        }
+        return FHE_OK;
+    }
+
+    int step(int i) {
+        const MStep &st = m->steps[i];
+        fhe_ctx *c = m->ctx;
+        FHE_TRY(alloc_t(st.dst));
+        const MTensor &ti = m->tensors[st.src];
+        const int n = B * ti.n_ct;
+        switch (st.kind) {
+        case FHE_STEP_LINEAR:
+            FHE_TRY(linear(st));
+            break;
+        case FHE_STEP_RESCALE:
+            FHE_TRY(op_rescale(c, buf[st.src], ctst(st.src), buf[st.dst], ctst(st.dst), n, 2, ti.level, s));
+            break;
+        case FHE_STEP_ACT:
+            FHE_TRY(act(st));
+            break;
+        case FHE_STEP_ROTSUM:
+            FHE_TRY(rotsum(st));
+            break;
+        case FHE_STEP_CMUL:
+            FHE_CU(launch_mul_const(c->dc, buf[st.src], ctst(st.src), st.cval, buf[st.dst], ctst(st.dst), n, 2,
+                                    ti.level, s));
+            break;
+        case FHE_STEP_DROP:
+            FHE_CU(launch_drop(c->dc, buf[st.src], ctst(st.src), ti.level, buf[st.dst], ctst(st.dst), st.level, n, 2,
+                               s));
+            break;
+        case FHE_STEP_ADD:
+            FHE_CU(launch_add(c->dc, buf[st.src], ctst(st.src), buf[st.src2], ctst(st.src2), buf[st.dst],
+                              ctst(st.dst), n, 2, ti.level, 0, s));
+            break;
+        }
+        if (m->last_use[st.src] == i) release(st.src);
+        if (st.src2 >= 0 && m->last_use[st.src2] == i) release(st.src2);
+        return FHE_OK;
+    }
+};
+
+int run_steps(Exec &e, int first, int last) {
+    for (int i = first; i < last; i++) FHE_TRY(e.step(i));
+    return FHE_OK;
+}
+
+}  // namespace
+
+extern "C" int fhe_infer(fhe_ctx *c, const fhe_model *mc, const fhe_evk *evk, const fhe_ct *const *in, size_t n_img,
+                         fhe_ct **out, void *stream) {
+    if (!c || !mc || !evk || !in || !out || n_img == 0) return fhe_fail(FHE_E_INVAL, "null argument");
+    fhe_model *m = const_cast<fhe_model *>(mc);
+    FHE_CU(cudaSetDevice(c->dev));
+    Exec e;
+    e.m = m;
+    e.evk = evk;
+    e.B = (int)n_img;
+    e.s = (cudaStream_t)stream;
+    e.buf.assign(m->tensors.size(), nullptr);
+    const MTensor &ti = m->tensors[m->input];
+    for (size_t k = 0; k < n_img * ti.n_ct; k++) {
+        if (!in[k] || in[k]->level != ti.level || in[k]->n_poly != 2)
+            return fhe_fail(FHE_E_LEVEL, "input ciphertext level / shape does not match the model");
+    }
+    FHE_TRY(e.alloc_t(m->input));
+    const long long cs = e.ctst(m->input);
+    for (size_t k = 0; k < n_img * ti.n_ct; k++)
+        FHE_CU(cudaMemcpyAsync(e.buf[m->input] + k * cs, in[k]->d, cs * 8, cudaMemcpyDeviceToDevice, e.s));
+    int rc = run_steps(e, 0, (int)m->steps.size());
+    if (rc != FHE_OK) {
+        cudaStreamSynchronize(e.s);
+        for (auto p : e.buf)
+            if (p) cudaFree(p);
+        return rc;
+    }
+    const MTensor &to = m->tensors[m->output];
+    const long long cso = e.ctst(m->output);
+    std::vector<fhe_ct *> made;
+    for (size_t k = 0; k < n_img * to.n_ct; k++) {
+        fhe_ct *o = new fhe_ct();
+        o->ctx = c;
+        o->level = to.level;
+        o->n_poly = 2;
+        o->scale = to.scale;
+        if (dev_alloc(c, (void **)&o->d, cso * 8) != FHE_OK) {
+            delete o;
+            for (auto p : made) fhe_ct_free(p);
+            return FHE_E_OOM;
+        }
+        cudaMemcpyAsync(o->d, e.buf[m->output] + k * cso, cso * 8, cudaMemcpyDeviceToDevice, e.s);
+        made.push_back(o);
+    }
+    cudaFreeAsync(e.buf[m->output], e.s);
+    FHE_CU(cudaStreamSynchronize(e.s));
+    for (size_t k = 0; k < made.size(); k++) out[k] = made[k];
+    return FHE_OK;
+}
+
+// ---- per-step entry points (one image)
+
+static int run_single(fhe_ctx *c, const fhe_model *mc, const fhe_evk *evk, int step, const fhe_ct *const *in,
+                      size_t n_in, fhe_ct **out, size_t n_out, void *stream, int kind_a, int kind_b) {
+    if (!c || !mc || !evk || !in || !out) return fhe_fail(FHE_E_INVAL, "null argument");
+    fhe_model *m = const_cast<fhe_model *>(mc);
+    if (step < 0 || step >= (int)m->steps.size()) return fhe_fail(FHE_E_INVAL, "step index");
+    const MStep &st = m->steps[step];
+    if (st.kind != kind_a && st.kind != kind_b) return fhe_fail(FHE_E_INVAL, "step has another kind");
+    const MTensor &ti = m->tensors[st.src], &to = m->tensors[st.dst];
+    if ((int)n_in != ti.n_ct || (int)n_out != to.n_ct) return fhe_fail(FHE_E_INVAL, "ciphertext count");
+    for (size_t k = 0; k < n_in; k++)
+        if (!in[k] || in[k]->level != ti.level || in[k]->n_poly != 2)
+            return fhe_fail(FHE_E_LEVEL, "input level does not match the step");
+    FHE_CU(cudaSetDevice(c->dev));
+    Exec e;
+    e.m = m;
+    e.evk = evk;
+    e.B = 1;
+    e.s = (cudaStream_t)stream;
+    e.buf.assign(m->tensors.size(), nullptr);
+    FHE_TRY(e.alloc_t(st.src));
+    const long long cs = e.ctst(st.src);
+    for (size_t k = 0; k < n_in; k++)
+        FHE_CU(cudaMemcpyAsync(e.buf[st.src] + k * cs, in[k]->d, cs * 8, cudaMemcpyDeviceToDevice, e.s));
+    FHE_TRY(e.alloc_t(st.dst));
+    int rc = FHE_OK;
+    switch (st.kind) {
+    case FHE_STEP_LINEAR: rc = e.linear(st); break;
+    case FHE_STEP_ACT: rc = e.act(st); break;
+    case FHE_STEP_ROTSUM: rc = e.rotsum(st); break;
+    }
+    if (rc != FHE_OK) return rc;
+    const long long cso = e.ctst(st.dst);
+    for (size_t k = 0; k < n_out; k++) {
+        fhe_ct *o = new fhe_ct();
+        o->ctx = c;
+        o->level = to.level;
+        o->n_poly = 2;
+        o->scale = to.scale;
+        FHE_TRY(dev_alloc(c, (void **)&o->d, cso * 8));
+        FHE_CU(cudaMemcpyAsync(o->d, e.buf[st.dst] + k * cso, cso * 8, cudaMemcpyDeviceToDevice, e.s));
+        out[k] = o;
+    }
+    FHE_CU(cudaStreamSynchronize(e.s));
+    cudaFree(e.buf[st.src]);
+    cudaFree(e.buf[st.dst]);
+    return FHE_OK;
+}
+
+extern "C" int fhe_eval_conv(fhe_ctx *c, const fhe_model *m, const fhe_evk *evk, int step, const fhe_ct *const *in,
+                             size_t n_in, fhe_ct **out, size_t n_out, void *stream) {
+    return run_single(c, m, evk, step, in, n_in, out, n_out, stream, FHE_STEP_LINEAR, FHE_STEP_LINEAR);
+}
+
+extern "C" int fhe_eval_pool_dense(fhe_ctx *c, const fhe_model *m, const fhe_evk *evk, int step,
+                                   const fhe_ct *const *in, size_t n_in, fhe_ct **out, size_t n_out, void *stream) {
+    return run_single(c, m, evk, step, in, n_in, out, n_out, stream, FHE_STEP_ROTSUM, FHE_STEP_LINEAR);
+}
+
+extern "C" int fhe_eval_quad_act(fhe_ctx *c, const fhe_model *m, const fhe_evk *evk, int step, fhe_ct **io, size_t n,
+                                 void *stream) {
+    std::vector<fhe_ct *> res(n, nullptr);
+    FHE_TRY(run_single(c, m, evk, step, (const fhe_ct *const *)io, n, res.data(), n, stream, FHE_STEP_ACT,
+                       FHE_STEP_ACT));
+    for (size_t k = 0; k < n; k++) {
+        std::swap(io[k]->d, res[k]->d);
+        io[k]->scale = res[k]->scale;
+        fhe_ct_free(res[k]);
+    }
+    return FHE_OK;
+}

@@ -127,5 +127,5 @@ def enc_seed(image_index: int, ct_index: int) -> int:
 # hybrid key switching); default scale Delta = 2^log_scale.
 PRESETS = {
     "tiny": dict(logn=13, L=4, q_bits=40, q0_bits=40, p_bits=40, alpha=1, log_scale=40),
-    "resnet20": dict(logn=16, L=20, q_bits=50, q0_bits=40, p_bits=60, alpha=3, log_scale=25),
+    "resnet20": dict(logn=16, L=20, q_bits=50, q0_bits=40, p_bits=58, alpha=3, log_scale=25),
 }
