@@ -1,0 +1,417 @@
+"""Benchmark: encrypted ResNet-20 inference under leveled RNS-CKKS on GB300.
+
+One step = one batched homomorphic inference of a batch of encrypted
+32x32x3 images through the whole ResNet-20-shaped network (every
+convolution, activation, rescale, shortcut, pool and dense layer: all the
+hot-path operations), N = 2^16, 21 moduli of the ciphertext chain + 3
+special primes.  Inputs are seeded synthetic images and random weights.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B]
+  python bench.py --impl reference ...   (the CPU oracle on a bounded sample)
+
+Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank runs an
+independent replica on its own GPU; the work shards by image and needs no
+exchange between ranks.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+METRIC = "batched vs single encrypted img/s (ResNet-20 shape, N=2^16, bit-exact); % HBM"
+PRESET = "resnet20"
+KS_KERNELS = ["modup_intt_rows", "modup_intt_cols", "modup_conv_ntt_cols", "modup_ntt_rows_key_ip",
+              "moddown_intt_rows", "moddown_intt_cols", "moddown_conv_ntt_cols", "moddown_ntt_rows_out"]
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device),
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def ks_weight(level, alpha):
+    """limb transforms in one hybrid key switch at `level` (the dominant cost)"""
+    nl = level + 1
+    nd = (level + alpha) // alpha
+    return nl + (nd * (nl + alpha) - nl) + 2 * alpha + 2 * nl
+
+
+def program_ledger(prog, alpha):
+    """key switches of one image and their weighted count (in top-level units)"""
+    n_ks, w = 0, 0.0
+    for st in prog.steps:
+        t_in = prog.tensors[st["src"]]
+        lv = t_in.level
+        if st["kind"] == 1:
+            babies = {(i, b) for terms in st["groups"].values() for (i, b, _) in terms if b}
+            giants = [k for k in st["groups"] if k[1]]
+            k = len(babies) + len(giants)
+        elif st["kind"] == 3:
+            k = t_in.layout.n_ct
+        elif st["kind"] == 4:
+            k = t_in.layout.n_ct * len(st["steps"])
+        else:
+            k = 0
+        n_ks += k
+        w += k * ks_weight(lv, alpha)
+    return n_ks, w
+
+
+def plaintext_bytes(prog, N):
+    total = 0
+    for st in prog.steps:
+        if st["kind"] == 1:
+            n_pt = sum(len(t) for t in st["groups"].values()) + len(st["bias"])
+            total += n_pt * (prog.tensors[st["src"]].level + 1) * N * 8
+    return total
+
+
+def oracle_ledger(prog, alpha):
+    """the same count on the oracle's program format"""
+    w = 0.0
+    for st in prog.steps:
+        src = st["src"][0] if isinstance(st["src"], list) else st["src"]
+        t_in = prog.tensors[src]
+        if st["op"] == "linear":
+            k = len(st["baby"]) + sum(1 for gs in st["groups"].values() for g in gs if g)
+        elif st["op"] == "act":
+            k = t_in.layout.n_ct
+        elif st["op"] == "rotsum":
+            k = t_in.layout.n_ct * len(st["steps"])
+        else:
+            k = 0
+        w += k * ks_weight(t_in.level, alpha)
+    return w
+
+
+# ===================================================================== ours
+
+def run_ours(args, rank, world):
+    import torch
+    from paper_2509_22857_gb300 import _lib as F
+    from paper_2509_22857_gb300 import model as M
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    pre = synth.PRESETS[PRESET]
+    N = 1 << pre["logn"]
+    t0 = time.time()
+    ctx = F.fhe_ctx_create(pre["logn"], pre["L"], pre["q_bits"], pre["q0_bits"], pre["p_bits"], pre["alpha"],
+                           pre["log_scale"], dev)
+    net = synth.resnet20()
+    raw = synth.params(net)
+    prog = M.compile_network(net, raw, F.fhe_ctx_primes(ctx)[: pre["L"] + 1], pre["logn"], pre["log_scale"],
+                             "packed")
+    sk, evk = F.fhe_keygen(ctx, synth.SEED_KEYS, sorted(prog.rotations))
+    desc = M.ModelDesc(prog, N // 2)
+    model = F.fhe_model_load(ctx, desc.desc)
+    t_setup = time.time() - t0
+    n_in = prog.tensors[prog.input].layout.n_ct
+    n_out = prog.tensors[prog.output].layout.n_ct
+    B = args.batch
+
+    # client side: encrypt B images (image index offset by rank: replicas see different images)
+    cts = []
+    for i in range(B):
+        img = synth.image(rank * B + i, 3, 32, 32)
+        for k, v in enumerate(M.input_slots(prog, img, N // 2)):
+            pt = F.fhe_encode(ctx, v, 2.0 ** pre["log_scale"], pre["L"])
+            cts.append(F.fhe_encrypt(ctx, sk, pt, synth.enc_seed(rank * B + i, k)))
+            F.fhe_pt_free(pt)
+
+    def infer(handles, n):
+        outs = F.fhe_infer(ctx, model, evk, handles, n, n_out, stream)
+        for h in outs:
+            F.fhe_ct_free(h)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def timed(fn, k):
+        torch.cuda.synchronize()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms = e0.elapsed_time(e1) / k
+        if world > 1:
+            t = torch.tensor([ms], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    # single-image baseline (one image per launch sequence)
+    for _ in range(max(1, args.warmup)):
+        infer(cts[:n_in], 1)
+    ms_single = timed(lambda: infer(cts[:n_in], 1), args.steps)
+
+    # batched
+    for _ in range(args.warmup):
+        infer(cts, B)
+    clk = Clocks(dev)
+    clk.start()
+    l0 = F.fhe_kernel_launches()
+    torch.cuda.nvtx.range_push("bench_timed")
+    ms_batch = timed(lambda: infer(cts, B), args.steps)
+    torch.cuda.nvtx.range_pop()
+    launches = (F.fhe_kernel_launches() - l0) // args.steps
+    clocks = clk.stop()
+
+    # end to end through the public API with host buffers: import (H2D + NTT),
+    # infer, export (inverse NTT + D2H) every step
+    host_in = [F.fhe_ct_export(h, N)[0] for h in cts]
+    lvl_in, sc_in = pre["L"], 2.0 ** pre["log_scale"]
+
+    def e2e_step():
+        hs = [F.fhe_ct_import(ctx, b, lvl_in, sc_in) for b in host_in]
+        outs = F.fhe_infer(ctx, model, evk, hs, B, n_out, stream)
+        for h in outs:
+            F.fhe_ct_export(h, N)
+            F.fhe_ct_free(h)
+        for h in hs:
+            F.fhe_ct_free(h)
+
+    e2e_step()
+    ms_e2e = timed(e2e_step, max(1, args.steps))
+    out_level = prog.tensors[prog.output].level
+    h2d = sum(b.nbytes for b in host_in)
+    d2h = B * n_out * 2 * (out_level + 1) * N * 8
+
+    # key-switch roofline at the top level, batch of B (the pipeline that
+    # dominates the step): algorithmic bytes per switched polynomial =
+    # (l+1)W in + 2*beta*(l+1+alpha)W key / B + 2(l+1)W out, W = N*8
+    lv = pre["L"]
+    ks_ms = F.fhe_profile_keyswitch(ctx, evk, lv, B, 3, stream)
+    alpha = pre["alpha"]
+    beta = (lv + alpha) // alpha
+    W = N * 8
+    ks_bytes = B * ((lv + 1) * W + 2 * (lv + 1) * W) + 2 * beta * (lv + 1 + alpha) * W
+    ks_total = sum(ks_ms) / 1e3
+    peak, peak_kind = _peaks()
+    achieved = ks_bytes / ks_total / 1e9
+    img_s_batch = B * world / (ms_batch / 1e3)
+    img_s_single = 1 * world / (ms_single / 1e3)
+    n_ks, wks = program_ledger(prog, alpha)
+
+    res = {
+        "metric": METRIC,
+        "value": round(img_s_batch, 4),
+        "unit": "img/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms_batch, 3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u64",
+        "data": "synthetic",
+        "config": {
+            "workload": "ResNet-20 (16/32/64, 3x3 blocks, 1x1 stride-2 shortcuts), 32x32x3 seeded uniform "
+                        "images, 10 classes; CKKS N=2^16, Delta=2^25, q0 40-bit + 20 x 50-bit, 3 x 58-bit "
+                        "special primes, digit width 3; channel-packed layout",
+            "batch": B,
+            "mixed_levels": False,
+            "single_img_s": round(img_s_single, 4),
+            "single_ms_per_img": round(ms_single, 3),
+            "batched_over_single": round(img_s_batch / img_s_single, 4),
+            "keyswitches_per_img": n_ks,
+            "l2": "inputs larger than L2: every step streams %.1f GB of resident weight plaintexts "
+                  "(L2 is 0.13 GB)" % (plaintext_bytes(prog, N) / 1e9),
+            "setup_s": round(t_setup, 1),
+            "parallelism": "replicas" if world > 1 else "single",
+        },
+        "clocks": clocks,
+        "e2e": {"value": round(B * world / (ms_e2e / 1e3), 4), "unit": "img/s",
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "hbm", "kernel": "hybrid key switch (8 fused kernels), level %d, %d items" % (lv, B),
+                     "achieved": round(achieved, 1), "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": None,
+                     "algorithmic_bytes": int(ks_bytes),
+                     "kernel_ms": {k: round(v, 4) for k, v in zip(KS_KERNELS, ks_ms)}},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        res["cpu_baseline"] = cpu_baseline(prog, wks, pre)
+    F.fhe_model_free(model)
+    for h in cts:
+        F.fhe_ct_free(h)
+    F.fhe_evk_free(evk)
+    F.fhe_sk_free(sk)
+    F.fhe_ctx_destroy(ctx)
+    return res
+
+
+# ===================================================================== oracle
+
+def oracle_rotation_seconds(pre, level):
+    """the CPU oracle, as it stands: one rotation of a fresh ciphertext at `level`"""
+    from oracle import ckks as O
+    prm = O.make_params(**pre)
+    S = O.CKKS(prm)
+    keys = S.keygen(synth.SEED_KEYS, [1])
+    z = np.random.default_rng(0).uniform(-1, 1, prm.N // 2)
+    ct = S.encrypt(keys, S.encode(z, prm.scale, level), 5)
+    t0 = time.perf_counter()
+    S.rotate(ct, 1, keys)
+    return time.perf_counter() - t0, S, keys, ct
+
+
+def cpu_baseline(prog, weighted_ks, pre):
+    secs = oracle_rotation_seconds(pre, pre["L"])[0]
+    per_img = secs * weighted_ks / ks_weight(pre["L"], pre["alpha"])
+    return {"value": round(1.0 / per_img, 8), "unit": "img/s", "cores": 1, "kind": "oracle",
+            "sample": "one hybrid-key-switch rotation at the top level (N=2^16, 21+3 primes) timed on the CPU "
+                      "oracle (%.1f s), scaled by the image's key switches weighted by limb transforms "
+                      "(%.0f top-level equivalents); plaintext products and additions not counted" %
+                      (secs, weighted_ks / ks_weight(pre["L"], pre["alpha"]))}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    from oracle import ckks as O
+    from oracle import cnn
+    pre = synth.PRESETS[PRESET]
+    prm = O.make_params(**dict(pre, logn=12))      # the plan depends on the primes' sizes only
+    net = synth.resnet20()
+    comp = cnn.Compiler(prm, "packed")
+    comp.n = 1 << (pre["logn"] - 1)
+    prog = comp.compile(net, cnn.transform(net, synth.params(net)))
+    unit = oracle_ledger(prog, pre["alpha"]) / ks_weight(pre["L"], pre["alpha"])
+    _, S, keys, ct = oracle_rotation_seconds(pre, pre["L"])
+    for _ in range(args.warmup):
+        S.rotate(ct, 1, keys)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        S.rotate(ct, 1, keys)
+    secs = (time.perf_counter() - t0) / args.steps
+    v = 1.0 / (secs * unit)
+    return {"impl": "reference", "metric": METRIC, "value": round(v, 8), "unit": "img/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(secs * 1e3, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic",
+            "config": {"workload": "ResNet-20, N=2^16 (as the GPU arm); each step one top-level rotation of the "
+                                   "CPU oracle, scaled to img/s by the image's weighted key-switch count"},
+            "cpu_baseline": {"value": round(v, 8), "unit": "img/s", "cores": 1, "kind": "oracle",
+                             "sample": "one top-level rotation per step"},
+            "e2e": {"value": round(v, 8), "unit": "img/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def run_ks_only(args):
+    """Only the hybrid key switch at the top level for `batch` items (small
+    device footprint: the relinearisation key and the workspace); used for
+    detailed profiles of the key-switching kernels."""
+    import torch
+    from paper_2509_22857_gb300 import _lib as F
+    pre = synth.PRESETS[PRESET]
+    ctx = F.fhe_ctx_create(pre["logn"], pre["L"], pre["q_bits"], pre["q0_bits"], pre["p_bits"], pre["alpha"],
+                           pre["log_scale"], 0)
+    sk, evk = F.fhe_keygen(ctx, synth.SEED_KEYS, [])
+    level = pre["L"] if args.ks_level is None else args.ks_level
+    ms = F.fhe_profile_keyswitch(ctx, evk, level, args.batch, max(1, args.steps), torch.cuda.current_stream())
+    print(json.dumps({"level": level, "items": args.batch, "kernel_ms": dict(zip(KS_KERNELS, ms)),
+                      "total_ms": sum(ms), "us_per_item": sum(ms) / args.batch * 1e3}))
+    F.fhe_evk_free(evk)
+    F.fhe_sk_free(sk)
+    F.fhe_ctx_destroy(ctx)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ks-only", action="store_true", help="time only the top-level key switch")
+    ap.add_argument("--ks-level", type=int, default=None)
+    args = ap.parse_args()
+    if args.ks_only:
+        run_ks_only(args)
+        return
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        res = run_reference(args, rank, world)
+        if res is not None:
+            print(json.dumps(res), flush=True)
+        return
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    res = run_ours(args, rank, world)
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -66,7 +66,7 @@ typedef struct fhe_model fhe_model;
  * L primes q_1..q_L of q_bits, then q_0 of q0_bits, then the alpha special
  * primes of p_bits, each skipping primes already taken.  alpha is also the
  * number of consecutive primes per key-switching digit.
- * Limits: 12 <= log_n <= 16; every prime below 2^58; 1 <= alpha <= 8;
+ * Limits: 12 <= log_n <= 16; prime sizes 31..58 bits; 1 <= alpha <= 8;
  * L + 1 + alpha <= 64.
  */
 typedef struct {
@@ -81,6 +81,9 @@ typedef struct {
 } fhe_params;
 
 const char *fhe_last_error(void);
+/* Number of CUDA kernels this library has launched in the process so far
+ * (all contexts); a monotonic counter for launch accounting. */
+uint64_t fhe_kernel_launches(void);
 
 /* Context: builds the prime chain, NTT tables and key-switching constants on
  * the device.  fhe_ctx_destroy frees everything the context made. */
@@ -256,6 +259,18 @@ int fhe_ntt_device(fhe_ctx *ctx, uint64_t *d_limbs, size_t n_limbs, const int32_
 /* Copy of one key-switching key (relinearisation: galois = 0) to host:
  * [digits][2][L+1+alpha][N] words, NTT domain. */
 int fhe_evk_export(const fhe_evk *evk, int galois, uint64_t *buf, size_t cap, size_t *n_words);
+/*
+ * Timing hook: `iters` hybrid key switches (relinearisation key) of n_items
+ * pseudo-random polynomials at `level`, after one warm-up, on `stream`, with
+ * CUDA events recorded on that stream around each kernel of the pipeline.
+ * ms_out[8] receives the mean duration of each kernel: ModUp inverse NTT
+ * rows, inverse NTT columns (times Qhat^-1), basis conversion + NTT columns,
+ * NTT rows + key inner product, ModDown inverse NTT rows, inverse NTT
+ * columns, basis conversion + NTT columns, NTT rows + P^-1 output.
+ * Synchronises with the stream.
+ */
+int fhe_profile_keyswitch(fhe_ctx *ctx, const fhe_evk *evk, int level, int n_items, int iters, float *ms_out,
+                          void *stream);
 /* Secret key (NTT domain, all L+1+alpha limbs) to host. */
 int fhe_sk_export(const fhe_sk *sk, uint64_t *buf, size_t cap);
 /* Integer coefficients of an encoding, before reduction (host encoder),

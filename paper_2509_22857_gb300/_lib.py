@@ -66,6 +66,7 @@ def lib() -> ctypes.CDLL:
         V = c_void
         sigs = {
             "fhe_last_error": (ctypes.c_char_p, []),
+            "fhe_kernel_launches": (ctypes.c_uint64, []),
             "fhe_ctx_create": (c_int, [ctypes.POINTER(FheParams), PP]),
             "fhe_ctx_destroy": (c_int, [V]),
             "fhe_ctx_primes": (c_int, [V, P_U64, c_size, ctypes.POINTER(c_size)]),
@@ -96,6 +97,7 @@ def lib() -> ctypes.CDLL:
             "fhe_ntt_device": (c_int, [V, V, c_size, P_I32, c_int, V]),
             "fhe_evk_export": (c_int, [V, c_int, P_U64, c_size, ctypes.POINTER(c_size)]),
             "fhe_sk_export": (c_int, [V, P_U64, c_size]),
+            "fhe_profile_keyswitch": (c_int, [V, V, c_int, c_int, c_int, ctypes.POINTER(ctypes.c_float), V]),
             "fhe_encode_coeffs": (c_int, [V, P_DBL, P_DBL, c_size, c_double, P_DBL]),
         }
         for name, (res, args) in sigs.items():
@@ -125,6 +127,10 @@ def _stream(stream) -> Optional[int]:
 
 
 # ------------------------------------------------------------------ context
+
+def fhe_kernel_launches() -> int:
+    return int(lib().fhe_kernel_launches())
+
 
 def fhe_ctx_create(log_n, L, q_bits, q0_bits, p_bits, alpha, log_scale, device=0) -> int:
     p = FheParams(log_n, L, q_bits, q0_bits, p_bits, alpha, float(log_scale), device)
@@ -326,15 +332,22 @@ def fhe_evk_export(evk, galois: int) -> np.ndarray:
     return out
 
 
+def fhe_profile_keyswitch(ctx, evk, level: int, n_items: int, iters: int, stream=None) -> List[float]:
+    ms = (ctypes.c_float * 8)()
+    _check(lib().fhe_profile_keyswitch(ctx, evk, level, n_items, iters, ms, _stream(stream)))
+    return [float(x) for x in ms]
+
+
 def fhe_sk_export(sk, n_words: int) -> np.ndarray:
     out = np.zeros(n_words, dtype=np.uint64)
     _check(lib().fhe_sk_export(sk, _ptr(out, P_U64), n_words))
     return out
 
 
-EXPORTED = ["fhe_last_error", "fhe_ctx_create", "fhe_ctx_destroy", "fhe_ctx_primes", "fhe_keygen",
+EXPORTED = ["fhe_last_error", "fhe_kernel_launches", "fhe_ctx_create", "fhe_ctx_destroy", "fhe_ctx_primes", "fhe_keygen",
             "fhe_sk_free", "fhe_evk_free", "fhe_evk_galois", "fhe_encode", "fhe_pt_free", "fhe_encrypt",
             "fhe_decrypt", "fhe_decode", "fhe_ct_free", "fhe_ct_info", "fhe_ct_export", "fhe_ct_import",
             "fhe_rotate", "fhe_square", "fhe_rescale", "fhe_add", "fhe_mul_plain", "fhe_model_load",
             "fhe_model_free", "fhe_eval_conv", "fhe_eval_quad_act", "fhe_eval_pool_dense", "fhe_infer",
-            "fhe_ntt_device", "fhe_evk_export", "fhe_sk_export", "fhe_encode_coeffs"]
+            "fhe_ntt_device", "fhe_evk_export", "fhe_sk_export", "fhe_encode_coeffs",
+            "fhe_profile_keyswitch"]

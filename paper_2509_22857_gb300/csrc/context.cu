@@ -15,6 +15,8 @@ int fhe_fail(int code, const std::string &msg) {
 
 extern "C" const char *fhe_last_error(void) { return g_err.c_str(); }
 
+extern "C" uint64_t fhe_kernel_launches(void) { return (uint64_t)fhe_launch_counter(); }
+
 // ================================================================ host math
 
 u64 h_powmod(u64 a, u64 e, u64 q) {
@@ -394,9 +396,11 @@ extern "C" int fhe_ctx_create(const fhe_params *p, fhe_ctx **out) {
     if (p->log_n < 12 || p->log_n > 16) return fhe_fail(FHE_E_INVAL, "log_n must be in [12, 16]");
     if (p->alpha < 1 || p->alpha > 8) return fhe_fail(FHE_E_INVAL, "alpha must be in [1, 8]");
     if (p->L < 0 || p->L + 1 + p->alpha > FHE_MAX_LIMBS) return fhe_fail(FHE_E_INVAL, "too many primes");
-    if (p->q_bits > 58 || p->q0_bits > 58 || p->p_bits > 58 || p->q_bits < 20 || p->q0_bits < 20 ||
-        p->p_bits < 20)
-        return fhe_fail(FHE_E_INVAL, "prime sizes must be in [20, 58] bits");
+    // 58: lazy NTT values stay below 2^61 and Barrett's constants fit 64 bits;
+    // 31: a 64-bit word (sampling) or a 58-bit residue reduces in one Barrett step
+    if (p->q_bits > 58 || p->q0_bits > 58 || p->p_bits > 58 || p->q_bits < 31 || p->q0_bits < 31 ||
+        p->p_bits < 31)
+        return fhe_fail(FHE_E_INVAL, "prime sizes must be in [31, 58] bits");
     const int digits_top = (p->L + p->alpha) / p->alpha;
     if (digits_top > 7) return fhe_fail(FHE_E_INVAL, "more than 7 key-switching digits");
     int ndev = 0;
@@ -998,6 +1002,55 @@ extern "C" int fhe_evk_export(const fhe_evk *evk, int galois, uint64_t *buf, siz
         if (cap < *n_words) return fhe_fail(FHE_E_INVAL, "buffer too small");
         FHE_CU(cudaMemcpy(buf, k, *n_words * 8, cudaMemcpyDeviceToHost));
     }
+    return FHE_OK;
+}
+
+extern "C" int fhe_profile_keyswitch(fhe_ctx *c, const fhe_evk *evk, int level, int n_items, int iters,
+                                     float *ms_out, void *stream) {
+    if (!c || !evk || !ms_out || n_items < 1 || iters < 1) return fhe_fail(FHE_E_INVAL, "bad argument");
+    if (level < 0 || level > c->L) return fhe_fail(FHE_E_LEVEL, "level out of range");
+    FHE_CU(cudaSetDevice(c->dev));
+    cudaStream_t s = (cudaStream_t)stream;
+    const int nl = level + 1;
+    const long long N = c->N;
+    const size_t item = (size_t)3 * nl * N;   // d, then 2 output polys
+    u64 *buf;
+    FHE_TRY(dev_alloc(c, (void **)&buf, item * n_items * 8));
+    std::vector<unsigned char> pidx(nl);
+    for (int t = 0; t < nl; t++) pidx[t] = (unsigned char)t;
+    for (int i = 0; i < n_items; i++)
+        FHE_CU(launch_sample_uniform(c->dc, 99, 9, (uint32_t)i, 0, 1, buf + i * item, nl, pidx.data(), s));
+    KsArgs a;
+    memset(&a, 0, sizeof(a));
+    a.d = buf;
+    a.d_item = (long long)item;
+    a.galois = 1;
+    a.key = evk->relin;
+    a.key_digits_top = evk->digits;
+    a.out = buf + (size_t)nl * N;
+    a.out_item = (long long)item;
+    a.n_items = n_items;
+    a.level = level;
+    const size_t per = ks_workspace_words(c->dc, level);
+    FHE_TRY(ws_reserve(c, &c->ks_ws, &c->ks_ws_words, per * (size_t)n_items));
+    a.ws = c->ks_ws;
+    a.ws_item = (long long)per;
+    cudaEvent_t ev[9];
+    for (auto &e : ev) FHE_CU(cudaEventCreate(&e));
+    double acc[8] = {0};
+    FHE_CU(launch_keyswitch(c->dc, c->lt[level], a, s, nullptr));   // warm-up
+    for (int it = 0; it < iters; it++) {
+        FHE_CU(launch_keyswitch(c->dc, c->lt[level], a, s, ev));
+        FHE_CU(cudaEventSynchronize(ev[8]));
+        for (int k = 0; k < 8; k++) {
+            float ms;
+            FHE_CU(cudaEventElapsedTime(&ms, ev[k], ev[k + 1]));
+            acc[k] += ms;
+        }
+    }
+    for (int k = 0; k < 8; k++) ms_out[k] = (float)(acc[k] / iters);
+    for (auto &e : ev) cudaEventDestroy(e);
+    dev_free(buf);
     return FHE_OK;
 }
 

@@ -14,7 +14,14 @@
 // Galois gathers) fused into the loads and stores.
 #include "kernels.h"
 
+#include <atomic>
+
 #define NT 256
+
+// number of kernel launches issued by this library (for launch accounting)
+static std::atomic<unsigned long long> g_launches{0};
+unsigned long long fhe_launch_counter() { return g_launches.load(); }
+#define COUNT_LAUNCH() g_launches.fetch_add(1, std::memory_order_relaxed)
 
 namespace {
 
@@ -368,14 +375,24 @@ __global__ void __launch_bounds__(NT) k_ks_modup_col(DevCtx c, LevelTab lt, KsAr
     const u64 *hat = lt.modup_hat + (long long)(j * alpha) * ext;
     u64 hv[8];
     const int nu = d_hi - d_lo;
+    // a residue of a wider source prime is first reduced mod the target, so
+    // that every product stays below t^2 (the Barrett precondition)
+    unsigned wide = 0;
 #pragma unroll
-    for (int u = 0; u < 8; u++) hv[u] = (u < nu) ? hat[u * ext + t] : 0;
+    for (int u = 0; u < 8; u++) {
+        hv[u] = (u < nu) ? hat[u * ext + t] : 0;
+        if (u < nu && c.primes[d_lo + u].m.b > P.m.b) wide |= 1u << u;
+    }
     u64 x[16];
 #pragma unroll
     for (int k = 0; k < 16; k++) {
         const int J = col + ((tau + Gm::S * k) << logC);
         U128 acc = {0, 0};
-        for (int u = 0; u < nu; u++) mac(acc, y[((long long)(d_lo + u) << c.logN) + J], hv[u]);
+        for (int u = 0; u < nu; u++) {
+            u64 v = y[((long long)(d_lo + u) << c.logN) + J];
+            if (wide & (1u << u)) v = barrett(U128{v, 0}, P.m);
+            mac(acc, v, hv[u]);
+        }
         x[k] = barrett(acc, P.m);
     }
     fwd_A<LOGR>(x, tau, col, 1 << logC, 0, c.logN, P.fwd, q);
@@ -510,15 +527,23 @@ __global__ void __launch_bounds__(NT) k_ks_md_conv_col(DevCtx c, LevelTab lt, Ks
     const u64 *z = a.ws + item * a.ws_item + ly.z + (long long)kk * al * N;
     u64 *dst = a.ws + item * a.ws_item + ly.md + ((long long)(kk * nl + i) << c.logN);
     u64 hv[8];
+    unsigned wide = 0;
 #pragma unroll
-    for (int u = 0; u < 8; u++) hv[u] = (u < al) ? c.md_phat[u * (c.L + 1) + i] : 0;
+    for (int u = 0; u < 8; u++) {
+        hv[u] = (u < al) ? c.md_phat[u * (c.L + 1) + i] : 0;
+        if (u < al && c.primes[c.L + 1 + u].m.b > P.m.b) wide |= 1u << u;
+    }
     const u64 halfp = c.md_halfp[i];
     u64 x[16];
 #pragma unroll
     for (int k = 0; k < 16; k++) {
         const int J = col + ((tau + Gm::S * k) << logC);
         U128 acc = {0, 0};
-        for (int u = 0; u < al; u++) mac(acc, z[(long long)u * N + J], hv[u]);
+        for (int u = 0; u < al; u++) {
+            u64 v = z[(long long)u * N + J];
+            if (wide & (1u << u)) v = barrett(U128{v, 0}, P.m);
+            mac(acc, v, hv[u]);
+        }
         x[k] = sub_mod(barrett(acc, P.m), halfp, q);
     }
     fwd_A<LOGR>(x, tau, col, 1 << logC, 0, c.logN, P.fwd, q);
@@ -971,6 +996,7 @@ __global__ void k_double_to_limbs(DevCtx c, const double *v, u64 *out) {
 
 #define DISPATCH_LOGR(logr, KERNEL, GRID, ...)                                      \
     do {                                                                            \
+        COUNT_LAUNCH();                                                             \
         switch (logr) {                                                             \
         case 4: KERNEL<4><<<GRID, NT, 0, s>>>(__VA_ARGS__); break;                  \
         case 5: KERNEL<5><<<GRID, NT, 0, s>>>(__VA_ARGS__); break;                  \
@@ -1001,19 +1027,32 @@ cudaError_t launch_ntt(const DevCtx &c, const NttArgs &a, bool inverse, cudaStre
     return cudaGetLastError();
 }
 
-cudaError_t launch_keyswitch(const DevCtx &c, const LevelTab &lt, const KsArgs &a, cudaStream_t s) {
+cudaError_t launch_keyswitch(const DevCtx &c, const LevelTab &lt, const KsArgs &a, cudaStream_t s,
+                             cudaEvent_t *ev) {
     const int nl = a.level + 1, ext = lt.ext, nd = lt.n_digits, B = a.n_items;
     if (nd > 7) return cudaErrorInvalidValue;   // inner-product accumulator bound
     KsLayout ly = ks_layout(a.level, nd, c.alpha, c.logN);
     const int tc = tiles_col(c);
+#define KS_EV(i) \
+    if (ev) cudaEventRecord(ev[i], s)
+    KS_EV(0);
     DISPATCH_LOGR(c.logR2, k_ks_intt_row, dim3(tc, B * nl), c, a, ly);
+    KS_EV(1);
     DISPATCH_LOGR(c.logR1, k_ks_intt_col, dim3(tc, B * nl), c, lt, a, ly);
+    KS_EV(2);
     DISPATCH_LOGR(c.logR1, k_ks_modup_col, dim3(tc, B * nd * ext), c, lt, a, ly);
+    KS_EV(3);
     DISPATCH_LOGR(c.logR2, k_ks_modup_row_ip, dim3(tc, B * ext), c, lt, a, ly);
+    KS_EV(4);
     DISPATCH_LOGR(c.logR2, k_ks_md_intt_row, dim3(tc, B * 2 * c.alpha), c, lt, a, ly);
+    KS_EV(5);
     DISPATCH_LOGR(c.logR1, k_ks_md_intt_col, dim3(tc, B * 2 * c.alpha), c, lt, a, ly);
+    KS_EV(6);
     DISPATCH_LOGR(c.logR1, k_ks_md_conv_col, dim3(tc, B * 2 * nl), c, lt, a, ly);
+    KS_EV(7);
     DISPATCH_LOGR(c.logR2, k_ks_md_row_out, dim3(tc, B * 2 * nl), c, lt, a, ly);
+    KS_EV(8);
+#undef KS_EV
     return cudaGetLastError();
 }
 
@@ -1035,6 +1074,7 @@ static dim3 ew_grid(const DevCtx &c, int y, int z) {
 
 cudaError_t launch_add(const DevCtx &c, const u64 *a, long long a_item, const u64 *b, long long b_item, u64 *out,
                        long long out_item, int n_items, int n_poly, int level, int subtract, cudaStream_t s) {
+    COUNT_LAUNCH();
     k_add<<<ew_grid(c, n_poly * (level + 1), n_items), 256, 0, s>>>(c, a, a_item, b, b_item, out, out_item, n_poly,
                                                                      level, subtract);
     return cudaGetLastError();
@@ -1042,30 +1082,35 @@ cudaError_t launch_add(const DevCtx &c, const u64 *a, long long a_item, const u6
 
 cudaError_t launch_mul_const(const DevCtx &c, const u64 *a, long long a_item, const u64 *cst, u64 *out,
                              long long out_item, int n_items, int n_poly, int level, cudaStream_t s) {
+    COUNT_LAUNCH();
     k_mul_const<<<ew_grid(c, n_poly * (level + 1), n_items), 256, 0, s>>>(c, a, a_item, cst, out, out_item, level);
     return cudaGetLastError();
 }
 
 cudaError_t launch_add_const(const DevCtx &c, const u64 *a, long long a_item, const u64 *cst, u64 *out,
                              long long out_item, int n_items, int level, cudaStream_t s) {
+    COUNT_LAUNCH();
     k_add_const<<<ew_grid(c, 2 * (level + 1), n_items), 256, 0, s>>>(c, a, a_item, cst, out, out_item, level);
     return cudaGetLastError();
 }
 
 cudaError_t launch_square_act(const DevCtx &c, const u64 *in, long long in_item, const u64 *c1, const u64 *c0,
                               u64 *out, long long out_item, int n_items, int level, cudaStream_t s) {
+    COUNT_LAUNCH();
     k_square_act<<<ew_grid(c, level + 1, n_items), 256, 0, s>>>(c, in, in_item, c1, c0, out, out_item, level);
     return cudaGetLastError();
 }
 
 cudaError_t launch_drop(const DevCtx &c, const u64 *in, long long in_item, int in_level, u64 *out,
                         long long out_item, int new_level, int n_items, int n_poly, cudaStream_t s) {
+    COUNT_LAUNCH();
     k_drop<<<ew_grid(c, n_poly * (new_level + 1), n_items), 256, 0, s>>>(c, in, in_item, in_level, out, out_item,
                                                                           new_level);
     return cudaGetLastError();
 }
 
 cudaError_t launch_decrypt(const DevCtx &c, const u64 *ct, const u64 *s_ntt, u64 *m, int level, cudaStream_t s) {
+    COUNT_LAUNCH();
     k_decrypt<<<ew_grid(c, level + 1, 1), 256, 0, s>>>(c, ct, s_ntt, m, level);
     return cudaGetLastError();
 }
@@ -1073,6 +1118,7 @@ cudaError_t launch_decrypt(const DevCtx &c, const u64 *ct, const u64 *s_ntt, u64
 cudaError_t launch_mac(const DevCtx &c, const MacArgs &a, cudaStream_t s) {
     if (a.n_groups == 0) return cudaSuccess;
     dim3 g(a.n_groups, (unsigned)((1ll << c.logN) / 256), a.level + 1);
+    COUNT_LAUNCH();
     k_mac<<<g, 256, 0, s>>>(c, a);
     return cudaGetLastError();
 }
@@ -1086,6 +1132,7 @@ static PidxArr to_pidx(const unsigned char *p, int n) {
 cudaError_t launch_sample_uniform(const DevCtx &c, uint64_t seed, uint32_t domain, uint32_t id0, uint32_t id1_base,
                                   uint32_t id1_step, u64 *out, int n_limbs, const unsigned char *pidx,
                                   cudaStream_t s) {
+    COUNT_LAUNCH();
     k_sample_uniform<<<ew_grid(c, n_limbs, 1), 256, 0, s>>>(c, seed, domain, id0, id1_base, id1_step, out,
                                                              to_pidx(pidx, n_limbs));
     return cudaGetLastError();
@@ -1093,34 +1140,40 @@ cudaError_t launch_sample_uniform(const DevCtx &c, uint64_t seed, uint32_t domai
 
 cudaError_t launch_sample_small(const DevCtx &c, uint64_t seed, uint32_t domain, uint32_t id0, uint32_t id1, int kind,
                                 long long *out, cudaStream_t s) {
+    COUNT_LAUNCH();
     k_sample_small<<<ew_grid(c, 1, 1), 256, 0, s>>>(c, seed, domain, id0, id1, kind, out);
     return cudaGetLastError();
 }
 
 cudaError_t launch_signed_to_limbs(const DevCtx &c, const long long *v, u64 *out, int n_limbs,
                                    const unsigned char *pidx, cudaStream_t s) {
+    COUNT_LAUNCH();
     k_signed_to_limbs<<<ew_grid(c, n_limbs, 1), 256, 0, s>>>(c, v, out, to_pidx(pidx, n_limbs));
     return cudaGetLastError();
 }
 
 cudaError_t launch_mul_limbs(const DevCtx &c, const u64 *a, const u64 *b, const u64 *add, int negate, u64 *out,
                              int n_limbs, const unsigned char *pidx, cudaStream_t s) {
+    COUNT_LAUNCH();
     k_mul_limbs<<<ew_grid(c, n_limbs, 1), 256, 0, s>>>(c, a, b, add, negate, out, to_pidx(pidx, n_limbs));
     return cudaGetLastError();
 }
 
 cudaError_t launch_axpy_limbs(const DevCtx &c, const u64 *x, const u64 *cst, u64 *out, int n_limbs,
                               const unsigned char *pidx, cudaStream_t s) {
+    COUNT_LAUNCH();
     k_axpy_limbs<<<ew_grid(c, n_limbs, 1), 256, 0, s>>>(c, x, cst, out, to_pidx(pidx, n_limbs));
     return cudaGetLastError();
 }
 
 cudaError_t launch_double_to_limbs(const DevCtx &c, const double *v, u64 *out, int n_limbs, cudaStream_t s) {
+    COUNT_LAUNCH();
     k_double_to_limbs<<<ew_grid(c, n_limbs, 1), 256, 0, s>>>(c, v, out);
     return cudaGetLastError();
 }
 
 cudaError_t launch_automorphism(const DevCtx &c, const u64 *in, u64 *out, int n_limbs, int galois, cudaStream_t s) {
+    COUNT_LAUNCH();
     k_automorphism<<<ew_grid(c, n_limbs, 1), 256, 0, s>>>(c, in, out, galois);
     return cudaGetLastError();
 }

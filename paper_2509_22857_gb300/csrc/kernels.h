@@ -8,6 +8,9 @@
 
 #define FHE_MAX_LIMBS 64
 
+// kernel launches issued so far by this library (all launchers count)
+unsigned long long fhe_launch_counter();
+
 // One prime of the chain q_0..q_L, p_0..p_{alpha-1}.
 struct PrimeTab {
     ModQ m;
@@ -78,7 +81,9 @@ struct KsArgs {
 };
 
 size_t ks_workspace_words(const DevCtx &c, int level);
-cudaError_t launch_keyswitch(const DevCtx &c, const LevelTab &lt, const KsArgs &a, cudaStream_t s);
+// ev (nullable): 9 events recorded on s before each of the 8 kernels and after the last
+cudaError_t launch_keyswitch(const DevCtx &c, const LevelTab &lt, const KsArgs &a, cudaStream_t s,
+                             cudaEvent_t *ev = nullptr);
 
 // Rescale: out[i] = q_l^-1 (in[i] - [in[l]]_centred) mod q_i for i < level, both polys.
 struct RescaleArgs {

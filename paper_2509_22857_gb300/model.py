@@ -1,0 +1,460 @@
+"""Host-side lowering of a quadratic-activation CNN to the library's program.
+
+Offline model preparation (run once per model, before inference):
+
+* parameter transforms -- batch norm folded into the preceding convolution
+  (node fusing Case 2, Sec. 4.1) and forward weight redistribution (Sec. 4.2):
+  each activation a x^2 + b x + c becomes monic x^2 + (b/a) x + (c/a), the
+  average pool a plain sum, and the receivers absorb the updates;
+* slot layouts (Sec. 5.1): the HW layout (a channel per ciphertext, its
+  spatial values replicated into every free block of slots) or a
+  channel-packed layout (one block of slots per channel); strided layers keep
+  the gaps they leave (adaptive mapping);
+* every linear layer as diagonals in baby-step / giant-step form:
+  out = sum_g rot_g( sum_(i,b) d'_(i,g,b) (.) rot_b(in_i) ), with
+  d'_(g,b) the diagonal of rotation g+b pre-rotated by -g;
+* levels, scales and rescale points by the tower-reuse rule of Sec. 4.3
+  (rescale when round(log_Delta scale) exceeds round(log_Delta q_level)).
+
+The result is handed to ``fhe_model_load``; the homomorphic evaluation itself
+runs in the CUDA library.  Expressions that decide encoded integers (folded
+weights, plaintext scales, activation constants) use a fixed floating-point
+operation order, documented at each.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+from dataclasses import dataclass, field
+from typing import Dict, List, Optional, Sequence, Tuple
+
+import numpy as np
+
+from . import _lib as F
+
+
+# =========================================================== transforms
+
+def prepare_params(net: List[Dict], raw: Dict) -> Dict[int, Dict]:
+    """Folded, redistributed parameters per node.  Operation order:
+    b1 = gamma/sigma; b0 = beta - b1*mu; w' = (w*b1[o])*u_in;
+    bias' = bias*b1 + b0; activation c1 = b/a, c0 = c/a (u = a);
+    pool u = u_in/float(k*k); dense w' = w*u_in; identity shortcut times u."""
+    u: Dict[int, float] = {}
+    out: Dict[int, Dict] = {}
+    for idx, node in enumerate(net):
+        kind = node["op"]
+        if kind == "input":
+            u[idx] = 1.0
+            continue
+        if kind == "conv":
+            p = raw[idx]
+            b1 = p["gamma"] / p["sigma"]
+            b0 = p["beta"] - b1 * p["mu"]
+            out[idx] = dict(w=(p["w"] * b1.reshape(-1, 1, 1, 1)) * u[node["src"]], bias=p["bias"] * b1 + b0)
+            u[idx] = 1.0
+        elif kind == "act":
+            p = raw[idx]
+            out[idx] = dict(c1=p["b"] / p["a"], c0=p["c"] / p["a"])
+            u[idx] = p["a"]
+        elif kind == "pool":
+            u[idx] = u[node["src"]] / float(node["k"] * node["k"])
+        elif kind == "dense":
+            p = raw[idx]
+            out[idx] = dict(w=p["w"] * u[node["src"]], bias=p["bias"])
+            u[idx] = 1.0
+        elif kind == "add":
+            sc = node["src"][1]
+            out[idx] = dict(shortcut=None if net[sc]["op"] == "conv" else u[sc])
+            u[idx] = 1.0
+    return out
+
+
+# =========================================================== layouts
+
+@dataclass
+class SlotMap:
+    """Channel c has copies at (ciphertext, base slot) pairs copies[c]; its
+    logical position (h, w) is at base + h*st*row + w*st."""
+    n_ct: int
+    copies: List[List[Tuple[int, int]]]
+    H: int
+    W: int
+    st: int
+    row: int
+    block: int
+
+    def offsets(self) -> np.ndarray:
+        h = np.arange(self.H).reshape(-1, 1)
+        w = np.arange(self.W).reshape(1, -1)
+        return (h * self.st * self.row + w * self.st).reshape(-1)
+
+
+def map_hw(c, H, W, n_slots) -> SlotMap:
+    blk = H * W
+    bases = [b * blk for b in range(n_slots // blk)]
+    return SlotMap(c, [[(ch, base) for base in bases] for ch in range(c)], H, W, 1, W, blk)
+
+
+def map_packed(c, H, W, st, row, blk, n_slots) -> SlotMap:
+    nb = n_slots // blk
+    if c <= nb:
+        used = c * (nb // c)
+        copies = [[(0, b * blk) for b in range(ch, used, c)] for ch in range(c)]
+        return SlotMap(1, copies, H, W, st, row, blk)
+    if c % nb:
+        raise ValueError("channel count must be a multiple of the blocks per ciphertext")
+    return SlotMap(c // nb, [[(ch // nb, (ch % nb) * blk)] for ch in range(c)], H, W, st, row, blk)
+
+
+def map_single(c, blk, n_slots) -> SlotMap:
+    nb = n_slots // blk
+    return SlotMap(-(-c // nb), [[(k // nb, (k % nb) * blk)] for k in range(c)], 1, 1, 1, 1, blk)
+
+
+def _pick_copy(copies, out_base, n_slots):
+    best = None
+    for ct, base in copies:
+        key = ((base - out_base) % n_slots, ct)
+        if best is None or key < best[0]:
+            best = (key, ct, base)
+    return best[1], best[2]
+
+
+def diagonals(w: np.ndarray, stride: int, pad: int, src: SlotMap, dst: SlotMap, n_slots: int):
+    """{(out ct, in ct, r): vector} such that out[s] = sum_r vec[s]*in[s + r]."""
+    cout, cin, k, _ = w.shape
+    oh = np.repeat(np.arange(dst.H), dst.W)
+    ow = np.tile(np.arange(dst.W), dst.H)
+    rows = {"oc": [], "ic": [], "r": [], "so": [], "v": []}
+    for o in range(cout):
+        for oct_, obase in dst.copies[o]:
+            so = obase + oh * dst.st * dst.row + ow * dst.st
+            for i in range(cin):
+                ict, ibase = _pick_copy(src.copies[i], obase, n_slots)
+                for dh in range(k):
+                    ih = oh * stride + dh - pad
+                    for dw in range(k):
+                        iw = ow * stride + dw - pad
+                        ok = (ih >= 0) & (ih < src.H) & (iw >= 0) & (iw < src.W)
+                        if not ok.any():
+                            continue
+                        si = ibase + ih[ok] * src.st * src.row + iw[ok] * src.st
+                        rows["oc"].append(np.full(ok.sum(), oct_))
+                        rows["ic"].append(np.full(ok.sum(), ict))
+                        rows["r"].append((si - so[ok]) % n_slots)
+                        rows["so"].append(so[ok])
+                        rows["v"].append(np.full(ok.sum(), w[o, i, dh, dw]))
+    oc = np.concatenate(rows["oc"])
+    ic = np.concatenate(rows["ic"])
+    r = np.concatenate(rows["r"])
+    so = np.concatenate(rows["so"])
+    v = np.concatenate(rows["v"])
+    order = np.lexsort((so, r, ic, oc))
+    oc, ic, r, so, v = oc[order], ic[order], r[order], so[order], v[order]
+    key = np.stack([oc, ic, r], axis=1)
+    cut = np.flatnonzero(np.any(key[1:] != key[:-1], axis=1)) + 1
+    out = {}
+    for lo, hi in zip(np.concatenate([[0], cut]), np.concatenate([cut, [len(oc)]])):
+        seg_so = so[lo:hi]
+        if np.any(seg_so[1:] == seg_so[:-1]):
+            raise ValueError("two weights land on one diagonal slot")
+        vec = np.zeros(n_slots)
+        vec[seg_so] = v[lo:hi]
+        out[(int(oc[lo]), int(ic[lo]), int(r[lo]))] = vec
+    return out
+
+
+# =========================================================== program
+
+@dataclass
+class TInfo:
+    layout: SlotMap
+    level: int
+    scale: float
+
+
+@dataclass
+class Program:
+    tensors: List[TInfo] = field(default_factory=list)
+    steps: List[Dict] = field(default_factory=list)
+    rotations: set = field(default_factory=set)
+    input: int = 0
+    output: int = 0
+
+
+def _lam(x: float, log_delta: float) -> int:
+    return int(math.floor(math.log2(x) / log_delta + 0.5))
+
+
+def _round_int(v: float) -> float:
+    """round half away from zero, as an integral double"""
+    if abs(v) >= 2.0 ** 52:
+        return float(v)
+    return math.copysign(math.floor(abs(v) + 0.5), v)
+
+
+class Planner:
+    def __init__(self, primes_q: Sequence[int], log_n: int, log_scale: float, layout: str):
+        self.q = list(primes_q)
+        self.L = len(self.q) - 1
+        self.n = 1 << (log_n - 1)
+        self.delta = 2.0 ** log_scale
+        self.logd = math.log2(self.delta)
+        self.layout = layout
+        self.p = Program()
+
+    # ---- bookkeeping
+    def _t(self, layout, level, scale) -> int:
+        self.p.tensors.append(TInfo(layout, level, scale))
+        return len(self.p.tensors) - 1
+
+    def _emit(self, **st) -> int:
+        self.p.steps.append(st)
+        return st["dst"]
+
+    def _rule(self, t: int) -> int:
+        """tower reuse: rescale when lambda(x) > lambda(q_level)"""
+        info = self.p.tensors[t]
+        ql = self.q[info.level]
+        if info.level >= 1 and _lam(info.scale, self.logd) > _lam(ql, self.logd):
+            return self._emit(kind=F.STEP_RESCALE, src=t, dst=self._t(info.layout, info.level - 1, info.scale / ql))
+        return t
+
+    def _bsgs_step(self, src: int, diag: Dict, giant: int, dst_layout: SlotMap, w_scale: float,
+                   bias: Optional[np.ndarray], bias_layout: SlotMap) -> int:
+        info = self.p.tensors[src]
+        prod = info.scale * w_scale
+        dst = self._t(dst_layout, info.level, prod)
+        groups: Dict[Tuple[int, int], List] = {}
+        for (o, i, r), vec in diag.items():
+            b = r % giant
+            g = r - b
+            groups.setdefault((o, g), []).append((i, b, np.roll(vec, g)))
+            if b:
+                self.p.rotations.add(b)
+            if g:
+                self.p.rotations.add(g)
+        bias_vecs = {}
+        if bias is not None:
+            offs = bias_layout.offsets()
+            for ch, val in enumerate(bias):
+                for ct, base in bias_layout.copies[ch]:
+                    bias_vecs.setdefault(ct, np.zeros(self.n))[base + offs] = val
+        return self._emit(kind=F.STEP_LINEAR, src=src, dst=dst, w_scale=w_scale, bias_scale=prod,
+                          groups=groups, bias=bias_vecs)
+
+    def _shortcut_scale(self, info: TInfo, target: TInfo) -> float:
+        ql = self.q[info.level]
+        ws = target.scale * ql / info.scale
+        if info.level >= 1 and _lam(info.scale * ws, self.logd) > _lam(ql, self.logd):
+            return ws
+        return target.scale / info.scale
+
+    def _land_on(self, t: int, target: TInfo) -> int:
+        info = self.p.tensors[t]
+        if info.level < target.level:
+            raise ValueError("shortcut arrives below the main branch's level")
+        if info.level > target.level:
+            return self._emit(kind=F.STEP_DROP, src=t, level=target.level,
+                              dst=self._t(info.layout, target.level, target.scale))
+        info.scale = target.scale
+        return t
+
+    # ---- layers
+    def conv(self, src: int, node: Dict, prm: Dict, target: Optional[TInfo] = None) -> int:
+        info = self.p.tensors[src]
+        lin = info.layout
+        ho = (lin.H + 2 * node["pad"] - node["k"]) // node["stride"] + 1
+        wo = (lin.W + 2 * node["pad"] - node["k"]) // node["stride"] + 1
+        st = lin.st * node["stride"]
+        if self.layout == "hw":
+            lout = SlotMap(node["cout"], [[(o, base) for (_, base) in lin.copies[0]] for o in range(node["cout"])],
+                           ho, wo, st, lin.row, lin.block)
+            giant = self.n
+        else:
+            lout = map_packed(node["cout"], ho, wo, st, lin.row, lin.block, self.n)
+            giant = lin.block
+        diag = diagonals(prm["w"], node["stride"], node["pad"], lin, lout, self.n)
+        ws = self.delta if target is None else self._shortcut_scale(info, target)
+        t = self._bsgs_step(src, diag, giant, lout, ws, prm["bias"], lout)
+        t = self._rule(t)
+        return t if target is None else self._land_on(t, target)
+
+    def act(self, src: int, prm: Dict) -> int:
+        info = self.p.tensors[src]
+        s = info.scale
+        s2 = s * s
+        dst = self._t(info.layout, info.level, s2)
+        self._emit(kind=F.STEP_ACT, src=src, dst=dst, c1=_round_int(prm["c1"] * s), c0=_round_int(prm["c0"] * s2))
+        return self._rule(dst)
+
+    def pool(self, src: int, k: int) -> int:
+        info = self.p.tensors[src]
+        L = info.layout
+        lg = int(math.log2(k))
+        steps = [L.st << m for m in range(lg)] + [(L.st * L.row) << m for m in range(lg)]
+        lp = SlotMap(L.n_ct, L.copies, L.H // k, L.W // k, L.st * k, L.row, L.block)
+        self.p.rotations.update(steps)
+        return self._emit(kind=F.STEP_ROTSUM, src=src, dst=self._t(lp, info.level, info.scale), steps=steps)
+
+    def shortcut_identity(self, src: int, value: float, target: TInfo) -> int:
+        info = self.p.tensors[src]
+        ws = self._shortcut_scale(info, target)
+        dst = self._t(info.layout, info.level, info.scale * ws)
+        self._emit(kind=F.STEP_CMUL, src=src, dst=dst, value=_round_int(value * ws))
+        return self._land_on(self._rule(dst), target)
+
+    def add(self, a: int, b: int) -> int:
+        ia = self.p.tensors[a]
+        return self._emit(kind=F.STEP_ADD, src=a, src2=b, dst=self._t(ia.layout, ia.level, ia.scale))
+
+    def dense(self, src: int, node: Dict, prm: Dict) -> int:
+        info = self.p.tensors[src]
+        lin = info.layout
+        w = prm["w"]
+        cout = node["cout"]
+        if self.layout == "hw":
+            # products in block k of ciphertext 0, then a sum over the block
+            offs = lin.offsets()
+            diag = {}
+            for c in range(len(lin.copies)):
+                vec = diag.setdefault((0, lin.copies[c][0][0], 0), np.zeros(self.n))
+                for k in range(cout):
+                    ct, base = _pick_copy(lin.copies[c], k * lin.block, self.n)
+                    vec[base + offs] = w[k, c * len(offs):(c + 1) * len(offs)]
+            part = SlotMap(1, [[(0, k * lin.block)] for k in range(cout)], 1, 1, 1, 1, lin.block)
+            t = self._bsgs_step(src, diag, self.n, part, self.delta, prm["bias"], part)
+            t = self._rule(t)
+            ti = self.p.tensors[t]
+            steps = [lin.st << m for m in range(int(math.log2(lin.W)))] + \
+                    [(lin.st * lin.row) << m for m in range(int(math.log2(lin.H)))]
+            self.p.rotations.update(steps)
+            return self._emit(kind=F.STEP_ROTSUM, src=t, steps=steps,
+                              dst=self._t(map_single(cout, lin.block, self.n), ti.level, ti.scale))
+        lout = map_single(cout, lin.block, self.n)
+        diag = diagonals(w.reshape(cout, -1, 1, 1), 1, 0, lin, lout, self.n)
+        t = self._bsgs_step(src, diag, 8 * lin.block, lout, self.delta, prm["bias"], lout)
+        return self._rule(t)
+
+    def compile(self, net: List[Dict], prm: Dict) -> Program:
+        node_t: Dict[int, int] = {}
+        later = {n["src"][1] for n in net if n["op"] == "add" and net[n["src"][1]]["op"] == "conv"}
+        for idx, node in enumerate(net):
+            kind = node["op"]
+            if kind == "input":
+                if self.layout == "hw":
+                    lay = map_hw(node["c"], node["h"], node["w"], self.n)
+                else:
+                    lay = map_packed(node["c"], node["h"], node["w"], 1, node["w"], node["h"] * node["w"], self.n)
+                node_t[idx] = self.p.input = self._t(lay, self.L, self.delta)
+            elif kind == "conv":
+                if idx not in later:
+                    node_t[idx] = self.conv(node_t[node["src"]], node, prm[idx])
+            elif kind == "act":
+                node_t[idx] = self.act(node_t[node["src"]], prm[idx])
+            elif kind == "pool":
+                node_t[idx] = self.pool(node_t[node["src"]], node["k"])
+            elif kind == "add":
+                a, b = node["src"]
+                main = self.p.tensors[node_t[a]]
+                if net[b]["op"] == "conv":
+                    sc = self.conv(node_t[net[b]["src"]], net[b], prm[b], target=main)
+                else:
+                    sc = self.shortcut_identity(node_t[b], prm[idx]["shortcut"], main)
+                node_t[idx] = self.add(node_t[a], sc)
+            elif kind == "dense":
+                node_t[idx] = self.dense(node_t[node["src"]], node, prm[idx])
+        self.p.output = node_t[len(net) - 1]
+        return self.p
+
+
+def compile_network(net, raw, primes_q, log_n, log_scale, layout) -> Program:
+    return Planner(primes_q, log_n, log_scale, layout).compile(net, prepare_params(net, raw))
+
+
+# =========================================================== to the C ABI
+
+class ModelDesc:
+    """Owns the arrays behind an FheModelDesc."""
+
+    def __init__(self, prog: Program, n_slots: int):
+        keep = []
+
+        def arr(x, dt):
+            a = np.ascontiguousarray(np.asarray(x, dtype=dt))
+            keep.append(a)
+            return a
+
+        def p32(a):
+            return a.ctypes.data_as(F.P_I32)
+
+        def pd(a):
+            return a.ctypes.data_as(F.P_DBL)
+
+        T = prog.tensors
+        n_ct = arr([t.layout.n_ct for t in T], np.int32)
+        lev = arr([t.level for t in T], np.int32)
+        sc = arr([t.scale for t in T], np.float64)
+        steps = (F.FheStepDesc * max(len(prog.steps), 1))()
+        for i, st in enumerate(prog.steps):
+            d = steps[i]
+            d.kind = st["kind"]
+            d.src = st["src"]
+            d.src2 = st.get("src2", -1)
+            d.dst = st["dst"]
+            if st["kind"] == F.STEP_LINEAR:
+                g_out, g_g, g_tb, t_ct, t_b, vecs = [], [], [0], [], [], []
+                for (o, g), terms in sorted(st["groups"].items()):
+                    g_out.append(o)
+                    g_g.append(g)
+                    for (ct, b, v) in terms:
+                        t_ct.append(ct)
+                        t_b.append(b)
+                        vecs.append(v)
+                    g_tb.append(len(t_ct))
+                d.w_scale = st["w_scale"]
+                d.bias_scale = st["bias_scale"]
+                d.n_groups = len(g_out)
+                d.group_out = p32(arr(g_out, np.int32))
+                d.group_giant = p32(arr(g_g, np.int32))
+                d.group_term_begin = p32(arr(g_tb, np.int32))
+                d.term_ct = p32(arr(t_ct or [0], np.int32))
+                d.term_baby = p32(arr(t_b or [0], np.int32))
+                d.term_vec = pd(arr(np.stack(vecs) if vecs else np.zeros((1, n_slots)), np.float64))
+                bo = sorted(st["bias"])
+                d.n_bias = len(bo)
+                d.bias_out = p32(arr(bo or [0], np.int32))
+                d.bias_vec = pd(arr(np.stack([st["bias"][o] for o in bo]) if bo else np.zeros((1, n_slots)),
+                                    np.float64))
+            elif st["kind"] == F.STEP_ACT:
+                d.c1 = st["c1"]
+                d.c0 = st["c0"]
+            elif st["kind"] == F.STEP_CMUL:
+                d.value = st["value"]
+            elif st["kind"] == F.STEP_ROTSUM:
+                d.n_steps = len(st["steps"])
+                d.steps = p32(arr(st["steps"], np.int32))
+            elif st["kind"] == F.STEP_DROP:
+                d.level = st["level"]
+        self.desc = F.FheModelDesc(len(T), p32(n_ct), p32(lev), pd(sc), prog.input, prog.output, len(prog.steps),
+                                   steps)
+        self._keep = keep
+        self._steps = steps
+
+
+def input_slots(prog: Program, img: np.ndarray, n_slots: int) -> List[np.ndarray]:
+    """The client's slot vectors of an image in the program's input layout."""
+    lay = prog.tensors[prog.input].layout
+    offs = lay.offsets()
+    out = [np.zeros(n_slots) for _ in range(lay.n_ct)]
+    for c, copies in enumerate(lay.copies):
+        flat = img[c].reshape(-1)
+        for ct, base in copies:
+            out[ct][base + offs] = flat
+    return out
+
+
+def logit_slots(prog: Program) -> List[Tuple[int, int]]:
+    lay = prog.tensors[prog.output].layout
+    return [cp[0] for cp in lay.copies]

@@ -51,24 +51,27 @@ def tiny() -> List[Dict]:
     return net
 
 
-def resnet20(num_classes: int = 10) -> List[Dict]:
-    """ResNet-20 for 32x32x3: conv 3->16, three stages of three basic blocks
-    (16/32/64 channels; the first block of stages 2 and 3 has stride 2 and a
-    1x1 stride-2 convolution on the shortcut, the others identity shortcuts),
-    global 8x8 average pool, dense 64->num_classes.  Every convolution is
-    followed by batch norm; every block ends with add then activation."""
-    net = [{"op": "input", "c": 3, "h": 32, "w": 32}]
+def resnet(widths=(16, 32, 64), blocks=3, in_hw=32, num_classes=10) -> List[Dict]:
+    """CIFAR-style ResNet: conv 3->widths[0], len(widths) stages of `blocks`
+    basic blocks (the first block of every later stage has stride 2 and a
+    1x1 stride-2 convolution on the shortcut, the others identity
+    shortcuts), global average pool, dense -> num_classes.  Every
+    convolution is followed by batch norm; every block ends with add then
+    activation."""
+    net = [{"op": "input", "c": 3, "h": in_hw, "w": in_hw}]
 
     def add(node):
         net.append(node)
         return len(net) - 1
 
-    x = add(_conv(0, 3, 16, 3, 1, 1, "conv1"))
+    x = add(_conv(0, 3, widths[0], 3, 1, 1, "conv1"))
     x = add({"op": "act", "src": x})
-    cin = 16
-    for s, cout in enumerate((16, 32, 64)):
-        for b in range(3):
+    cin = widths[0]
+    hw = in_hw
+    for s, cout in enumerate(widths):
+        for b in range(blocks):
             stride = 2 if (s > 0 and b == 0) else 1
+            hw //= stride
             a = add(_conv(x, cin, cout, 3, stride, 1, "s%db%da" % (s + 1, b + 1)))
             a = add({"op": "act", "src": a})
             m = add(_conv(a, cout, cout, 3, 1, 1, "s%db%db" % (s + 1, b + 1)))
@@ -79,12 +82,24 @@ def resnet20(num_classes: int = 10) -> List[Dict]:
             y = add({"op": "add", "src": [m, sc]})
             x = add({"op": "act", "src": y})
             cin = cout
-    p = add({"op": "pool", "src": x, "k": 8})
-    add({"op": "dense", "src": p, "cin": 64, "cout": num_classes, "name": "fc"})
+    p = add({"op": "pool", "src": x, "k": hw})
+    add({"op": "dense", "src": p, "cin": cin, "cout": num_classes, "name": "fc"})
     return net
 
 
-ARCHS = {"tiny": tiny, "resnet20": resnet20}
+def resnet20(num_classes: int = 10) -> List[Dict]:
+    """ResNet-20 for 32x32x3: three stages of three basic blocks with
+    16/32/64 channels, global 8x8 average pool, dense 64->num_classes."""
+    return resnet((16, 32, 64), 3, 32, num_classes)
+
+
+def resnet_mini() -> List[Dict]:
+    """A ResNet with the same structure at a small size (8x8x3 input,
+    4/8/16 channels, one block per stage) for full-network parity tests."""
+    return resnet((4, 8, 16), 1, 8, 10)
+
+
+ARCHS = {"tiny": tiny, "resnet20": resnet20, "resnet_mini": resnet_mini}
 
 
 # ------------------------------------------------------------- parameters
@@ -127,5 +142,6 @@ def enc_seed(image_index: int, ct_index: int) -> int:
 # hybrid key switching); default scale Delta = 2^log_scale.
 PRESETS = {
     "tiny": dict(logn=13, L=4, q_bits=40, q0_bits=40, p_bits=40, alpha=1, log_scale=40),
+    "resnet_mini": dict(logn=12, L=8, q_bits=50, q0_bits=40, p_bits=58, alpha=3, log_scale=25),
     "resnet20": dict(logn=16, L=20, q_bits=50, q0_bits=40, p_bits=58, alpha=3, log_scale=25),
 }

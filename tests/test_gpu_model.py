@@ -1,0 +1,147 @@
+"""Whole networks on the GPU through the C ABI: output ciphertexts bit-equal
+to the oracle's, decrypted logits within 1e-3 of the float64 network with
+the same argmax, batching and per-layer entry points consistent."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import ckks as O
+from oracle import cnn
+
+pytestmark = pytest.mark.gpu
+
+CASES = {"tiny": ("tiny", "tiny", "hw"), "mini": ("resnet_mini", "resnet_mini", "packed")}
+
+
+class Setup:
+    def __init__(self, case):
+        from paper_2509_22857_gb300 import _lib as F
+        from paper_2509_22857_gb300 import model as M
+        arch, preset, layout = CASES[case]
+        self.F, self.M = F, M
+        self.net = synth.ARCHS[arch]()
+        self.raw = synth.params(self.net)
+        pre = synth.PRESETS[preset]
+        self.pre = pre
+        self.prm = O.make_params(**pre)
+        self.S = O.CKKS(self.prm)
+        self.po = cnn.compile_he(self.net, cnn.transform(self.net, self.raw), self.prm, layout)
+        self.keys = self.S.keygen(synth.SEED_KEYS, sorted(self.po.rot_steps))
+        self.ctx = F.fhe_ctx_create(pre["logn"], pre["L"], pre["q_bits"], pre["q0_bits"], pre["p_bits"],
+                                    pre["alpha"], pre["log_scale"])
+        self.pm = M.compile_network(self.net, self.raw, F.fhe_ctx_primes(self.ctx)[: pre["L"] + 1], pre["logn"],
+                                    pre["log_scale"], layout)
+        self.sk, self.evk = F.fhe_keygen(self.ctx, synth.SEED_KEYS, sorted(self.pm.rotations))
+        self.desc = M.ModelDesc(self.pm, self.prm.N // 2)
+        self.model = F.fhe_model_load(self.ctx, self.desc.desc)
+        self.inp = self.net[0]
+
+    def encrypt(self, i):
+        F, M = self.F, self.M
+        img = synth.image(i, self.inp["c"], self.inp["h"], self.inp["w"])
+        out = []
+        for k, v in enumerate(M.input_slots(self.pm, img, self.prm.N // 2)):
+            pt = F.fhe_encode(self.ctx, v, self.prm.scale, self.prm.L)
+            out.append(F.fhe_encrypt(self.ctx, self.sk, pt, synth.enc_seed(i, k)))
+            F.fhe_pt_free(pt)
+        return img, out
+
+    def oracle_outputs(self, i):
+        img = synth.image(i, self.inp["c"], self.inp["h"], self.inp["w"])
+        cts = cnn.encrypt_input(self.S, self.keys, self.po, img, i, synth.enc_seed)
+        return cnn.run_he(self.S, self.keys, self.po, cts)
+
+    def coef(self, ct):
+        prm = self.prm
+        return np.stack([np.stack([O.intt(ct.c[r, t], prm.primes[t], prm.psi[t]) for t in range(ct.level + 1)])
+                         for r in range(ct.c.shape[0])])
+
+    def logits(self, handles):
+        F = self.F
+        vals = []
+        for ct, slot in self.M.logit_slots(self.pm):
+            pt = F.fhe_decrypt(self.ctx, self.sk, handles[ct])
+            z = F.fhe_decode(self.ctx, pt, self.prm.N // 2)
+            F.fhe_pt_free(pt)
+            vals.append(z[slot].real)
+        return np.array(vals)
+
+    def close(self):
+        F = self.F
+        F.fhe_model_free(self.model)
+        F.fhe_evk_free(self.evk)
+        F.fhe_sk_free(self.sk)
+        F.fhe_ctx_destroy(self.ctx)
+
+
+@pytest.fixture(scope="module", params=list(CASES))
+def setup(request):
+    s = Setup(request.param)
+    yield s
+    s.close()
+
+
+def test_network_bit_exact_and_logits(setup):
+    s = setup
+    F = s.F
+    img, cts = s.encrypt(0)
+    n_out = s.pm.tensors[s.pm.output].layout.n_ct
+    outs = F.fhe_infer(s.ctx, s.model, s.evk, cts, 1, n_out)
+    ref = s.oracle_outputs(0)[s.po.output_tensor]
+    for h, r in zip(outs, ref):
+        buf, lv, sc = F.fhe_ct_export(h, s.prm.N)
+        assert lv == r.level and sc == r.scale
+        assert np.array_equal(buf, s.coef(r))
+    y = s.logits(outs)
+    want = cnn.forward_plain(s.net, s.raw, img)
+    assert np.max(np.abs(y - want)) < 1e-3
+    assert np.argmax(y) == np.argmax(want)
+    for h in outs + cts:
+        F.fhe_ct_free(h)
+
+
+def test_batched_equals_one_at_a_time(setup):
+    s = setup
+    F = s.F
+    n_out = s.pm.tensors[s.pm.output].layout.n_ct
+    imgs = [s.encrypt(i)[1] for i in range(3)]
+    flat = [h for cts in imgs for h in cts]
+    batched = F.fhe_infer(s.ctx, s.model, s.evk, flat, 3, n_out)
+    for i in range(3):
+        single = F.fhe_infer(s.ctx, s.model, s.evk, imgs[i], 1, n_out)
+        for a, b in zip(single, batched[i * n_out:(i + 1) * n_out]):
+            assert np.array_equal(F.fhe_ct_export(a, s.prm.N)[0], F.fhe_ct_export(b, s.prm.N)[0])
+            F.fhe_ct_free(a)
+    for h in batched + flat:
+        F.fhe_ct_free(h)
+
+
+def test_per_layer_entry_points(setup):
+    """fhe_eval_conv / fhe_eval_quad_act / fhe_eval_pool_dense on one image
+    reproduce the oracle's tensors of those steps."""
+    s = setup
+    F = s.F
+    ref = s.oracle_outputs(1)
+    kinds = [st["kind"] for st in s.pm.steps]
+    # first linear step (a convolution), the first activation, the first rotsum
+    for kind, call in ((1, "conv"), (3, "act"), (4, "pool")):
+        i = kinds.index(kind)
+        st = s.pm.steps[i]
+        so = s.po.steps[i]
+        ins = ref[so["src"]]
+        handles = []
+        for ct in ins:
+            handles.append(F.fhe_ct_import(s.ctx, s.coef(ct), ct.level, ct.scale))
+        n_out = s.pm.tensors[st["dst"]].layout.n_ct
+        if call == "conv":
+            outs = F.fhe_eval_conv(s.ctx, s.model, s.evk, i, handles, n_out)
+        elif call == "pool":
+            outs = F.fhe_eval_pool_dense(s.ctx, s.model, s.evk, i, handles, n_out)
+        else:
+            F.fhe_eval_quad_act(s.ctx, s.model, s.evk, i, handles)
+            outs, handles = handles, []
+        for h, r in zip(outs, ref[so["dst"]]):
+            assert np.array_equal(F.fhe_ct_export(h, s.prm.N)[0], s.coef(r)), (call, i)
+            F.fhe_ct_free(h)
+        for h in handles:
+            F.fhe_ct_free(h)

@@ -1,0 +1,69 @@
+"""The package's host-side model lowering (parameter transforms, slot layouts,
+diagonals, levels, scales, constants) produces exactly the oracle's program:
+same steps, same rotation set, bit-identical diagonal and bias vectors."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import ckks as O
+from oracle import cnn
+from paper_2509_22857_gb300 import model as M
+
+NAMES = {1: "linear", 2: "rescale", 3: "act", 4: "rotsum", 5: "cmul", 6: "drop", 7: "add"}
+
+
+def _both(arch, preset, layout):
+    net = synth.ARCHS[arch]()
+    raw = synth.params(net)
+    pre = synth.PRESETS[preset]
+    prm = O.make_params(**dict(pre, logn=min(pre["logn"], 12)))   # primes' sizes fix the plan
+    c = cnn.Compiler(prm, layout)
+    c.n = 1 << (pre["logn"] - 1)
+    po = c.compile(net, cnn.transform(net, raw))
+    pm = M.compile_network(net, raw, prm.q, pre["logn"], pre["log_scale"], layout)
+    return po, pm
+
+
+def _check(po, pm):
+    assert sorted(po.rot_steps) == sorted(pm.rotations)
+    ko = [(s["op"], po.tensors[s["dst"]].level, po.tensors[s["dst"]].scale) for s in po.steps]
+    km = [(NAMES[s["kind"]], pm.tensors[s["dst"]].level, pm.tensors[s["dst"]].scale) for s in pm.steps]
+    assert ko == km
+    lo = [s for s in po.steps if s["op"] == "linear"]
+    lm = [s for s in pm.steps if s["kind"] == 1]
+    for a, b in zip(lo, lm):
+        ga = {(o, g): sorted((i, bb, v.tobytes()) for (i, bb, v) in terms)
+              for o, gs in a["groups"].items() for g, terms in gs.items()}
+        gb = {k: sorted((i, bb, v.tobytes()) for (i, bb, v) in terms) for k, terms in b["groups"].items()}
+        assert ga == gb
+        assert a["w_scale"] == b["w_scale"] and a["bias_scale"] == b["bias_scale"]
+        assert {k: v.tobytes() for k, v in a["bias"].items()} == {k: v.tobytes() for k, v in b["bias"].items()}
+    co = [float(s[k]) for s in po.steps if s["op"] in ("act", "cmul") for k in ("c1", "c0", "value") if k in s]
+    cm = [s[k] for s in pm.steps if s["kind"] in (3, 5) for k in ("c1", "c0", "value") if k in s]
+    assert co == cm
+    assert [s["steps"] for s in po.steps if s["op"] == "rotsum"] == \
+        [s["steps"] for s in pm.steps if s["kind"] == 4]
+
+
+def test_tiny_hw_program_matches_oracle():
+    _check(*_both("tiny", "tiny", "hw"))
+
+
+def test_mini_resnet_program_matches_oracle():
+    _check(*_both("resnet_mini", "resnet_mini", "packed"))
+
+
+@pytest.mark.slow
+def test_resnet20_program_matches_oracle():
+    po, pm = _both("resnet20", "resnet20", "packed")
+    _check(po, pm)
+    # 20 levels consumed along the main path: output at level 0 (Table 1, P2FRT)
+    assert pm.tensors[pm.output].level == 0
+
+
+def test_input_slots_match_oracle():
+    po, pm = _both("resnet_mini", "resnet_mini", "packed")
+    img = synth.image(3, 3, 8, 8)
+    a = cnn.input_vectors(po, img, 2048)
+    b = M.input_slots(pm, img, 2048)
+    assert len(a) == len(b) and all(np.array_equal(x, y) for x, y in zip(a, b))
