@@ -271,6 +271,23 @@ int fhe_evk_export(const fhe_evk *evk, int galois, uint64_t *buf, size_t cap, si
  */
 int fhe_profile_keyswitch(fhe_ctx *ctx, const fhe_evk *evk, int level, int n_items, int iters, float *ms_out,
                           void *stream);
+/*
+ * Rescale that allocates nothing (the paper has no counterpart: this is for
+ * callers that cannot let the library call cudaMalloc -- their device memory
+ * belongs to their own pool or to a fixed budget, or they cannot afford the
+ * synchronisation an allocation brings).  Same result as fhe_rescale: in is
+ * one ciphertext's [n_poly][level+1][N] NTT-domain limbs in device memory,
+ * out receives [n_poly][level][N]; both are caller-owned and must not
+ * overlap; the scale bookkeeping (scale / q_level) is the caller's.  The
+ * scratch is a fixed 1 MiB device array inside the library (n_poly * N <=
+ * 131072 words, i.e. two polynomials at N = 2^16), held by every GPU that
+ * loads the library until the process exits; larger sizes are rejected with
+ * FHE_E_INVAL.  The first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress): make it before any stream capture.  All
+ * calls share the array, so calls that overlap on the GPU (other streams,
+ * other threads) race; serialise them.  Asynchronous on `stream`.
+ */
+int fhe_rescale_noalloc(fhe_ctx *ctx, const uint64_t *in, uint64_t *out, int n_poly, int level, void *stream);
 /* Secret key (NTT domain, all L+1+alpha limbs) to host. */
 int fhe_sk_export(const fhe_sk *sk, uint64_t *buf, size_t cap);
 /* Integer coefficients of an encoding, before reduction (host encoder),

@@ -86,6 +86,7 @@ def lib() -> ctypes.CDLL:
             "fhe_rotate": (c_int, [V, V, V, c_int, PP, V]),
             "fhe_square": (c_int, [V, V, V, PP, V]),
             "fhe_rescale": (c_int, [V, V, V]),
+            "fhe_rescale_noalloc": (c_int, [V, V, V, c_int, c_int, V]),
             "fhe_add": (c_int, [V, V, V, PP, V]),
             "fhe_mul_plain": (c_int, [V, V, V, PP, V]),
             "fhe_model_load": (c_int, [V, ctypes.POINTER(FheModelDesc), PP]),
@@ -265,6 +266,10 @@ def fhe_rescale(ctx, ct, stream=None):
     _check(lib().fhe_rescale(ctx, ct, _stream(stream)))
 
 
+def fhe_rescale_noalloc(ctx, in_dev_ptr: int, out_dev_ptr: int, n_poly: int, level: int, stream=None):
+    _check(lib().fhe_rescale_noalloc(ctx, in_dev_ptr, out_dev_ptr, n_poly, level, _stream(stream)))
+
+
 def fhe_add(ctx, a, b, stream=None) -> int:
     h = c_void()
     _check(lib().fhe_add(ctx, a, b, ctypes.byref(h), _stream(stream)))
@@ -350,4 +355,4 @@ EXPORTED = ["fhe_last_error", "fhe_kernel_launches", "fhe_ctx_create", "fhe_ctx_
             "fhe_rotate", "fhe_square", "fhe_rescale", "fhe_add", "fhe_mul_plain", "fhe_model_load",
             "fhe_model_free", "fhe_eval_conv", "fhe_eval_quad_act", "fhe_eval_pool_dense", "fhe_infer",
             "fhe_ntt_device", "fhe_evk_export", "fhe_sk_export", "fhe_encode_coeffs",
-            "fhe_profile_keyswitch"]
+            "fhe_profile_keyswitch", "fhe_rescale_noalloc"]
