@@ -272,7 +272,7 @@ static int build_tables(fhe_ctx *c) {
         int b = 64 - __builtin_clzll(q);
         pt[t].m.q = q;
         pt[t].m.b = b;
-        pt[t].m.mu = (u64)(((u128)1 << (2 * b + 3)) / q);
+        pt[t].m.mu = (u64)(((u128)1 << (b + 62)) / q);
         const u64 psi = h_root_2n(q, 2 * N), psi_inv = h_invmod(psi, q);
         std::vector<u64> pw(N), pwi(N);
         pw[0] = pwi[0] = 1;

@@ -42,9 +42,6 @@ __device__ __forceinline__ void gs_bf(u64 &X, u64 &Y, ulonglong2 w, u64 q) {
     Y = mul_shoup_lazy(t, w.x, w.y, q);
 }
 
-__device__ __forceinline__ ulonglong2 twid(const ulonglong2 *__restrict__ tw, int sg, int j, int logN) {
-    return __ldg(&tw[(1 << sg) + (j >> (logN - sg))]);
-}
 
 // Galois gather in the NTT domain: sigma_k(a) at slot j is a at slot
 // brv(((2 brv(j) + 1) k mod 2N - 1) / 2).
@@ -64,67 +61,88 @@ struct Geo {
     static constexpr int RP = R + R / 16; // padded row (row passes)
 };
 
-// ---- stages. jb + e*js is the global index of local element e.
-template <int LOGR>
-__device__ __forceinline__ void fwd_A(u64 (&x)[16], int tau, int jb, int js, int sg0, int logN,
-                                      const ulonglong2 *__restrict__ tw, u64 q) {
+// ---- twiddle sources: entry (1 << sg) + (j >> (logN - sg)) of a table
+struct TwGlobal {
+    const ulonglong2 *__restrict__ t;
+    int logN;
+    __device__ __forceinline__ ulonglong2 operator()(int sg, int j) const {
+        return __ldg(&t[(1 << sg) + (j >> (logN - sg))]);
+    }
+};
+// column passes only touch entries below 2^logR1: staged in shared memory
+struct TwShared {
+    const ulonglong2 *t;
+    int logN;
+    __device__ __forceinline__ ulonglong2 operator()(int sg, int j) const { return t[(1 << sg) + (j >> (logN - sg))]; }
+};
+
+// ---- stages.  jb + e*js is the global index of local element e.  In every
+// stage the butterflies of a group of 2*half consecutive registers share one
+// twiddle, which is loaded once per group.
+template <int LOGR, class TW>
+__device__ __forceinline__ void fwd_A(u64 (&x)[16], int tau, int jb, int js, int sg0, TW tw, u64 q) {
     constexpr int S = Geo<LOGR>::S;
 #pragma unroll
     for (int s = 0; s < 4; s++) {
         const int half = 8 >> s;
 #pragma unroll
-        for (int k = 0; k < 16; k++) {
-            if (k & half) continue;
-            const int e = tau + S * k;
-            ct_bf(x[k], x[k + half], twid(tw, sg0 + s, jb + e * js, logN), q);
+        for (int k0 = 0; k0 < 16; k0 += 2 * half) {
+            const ulonglong2 w = tw(sg0 + s, jb + (tau + S * k0) * js);
+#pragma unroll
+            for (int u = 0; u < half; u++) ct_bf(x[k0 + u], x[k0 + u + half], w, q);
         }
     }
 }
 
-template <int LOGR>
-__device__ __forceinline__ void fwd_B(u64 (&x)[16], int tau, int jb, int js, int sg0, int logN,
-                                      const ulonglong2 *__restrict__ tw, u64 q) {
+template <int LOGR, class TW>
+__device__ __forceinline__ void fwd_B(u64 (&x)[16], int tau, int jb, int js, int sg0, TW tw, u64 q) {
 #pragma unroll
     for (int s = 4; s < LOGR; s++) {
         const int half = (1 << LOGR) >> (s + 1);
 #pragma unroll
-        for (int k = 0; k < 16; k++) {
-            if (k & half) continue;
-            const int e = 16 * tau + k;
-            ct_bf(x[k], x[k + half], twid(tw, sg0 + s, jb + e * js, logN), q);
+        for (int k0 = 0; k0 < 16; k0 += 2 * half) {
+            const ulonglong2 w = tw(sg0 + s, jb + (16 * tau + k0) * js);
+#pragma unroll
+            for (int u = 0; u < half; u++) ct_bf(x[k0 + u], x[k0 + u + half], w, q);
         }
     }
 }
 
-template <int LOGR>
-__device__ __forceinline__ void inv_B(u64 (&x)[16], int tau, int jb, int js, int sg0, int logN,
-                                      const ulonglong2 *__restrict__ tw, u64 q) {
+template <int LOGR, class TW>
+__device__ __forceinline__ void inv_B(u64 (&x)[16], int tau, int jb, int js, int sg0, TW tw, u64 q) {
 #pragma unroll
     for (int s = LOGR - 1; s >= 4; s--) {
         const int half = (1 << LOGR) >> (s + 1);
 #pragma unroll
-        for (int k = 0; k < 16; k++) {
-            if (k & half) continue;
-            const int e = 16 * tau + k;
-            gs_bf(x[k], x[k + half], twid(tw, sg0 + s, jb + e * js, logN), q);
+        for (int k0 = 0; k0 < 16; k0 += 2 * half) {
+            const ulonglong2 w = tw(sg0 + s, jb + (16 * tau + k0) * js);
+#pragma unroll
+            for (int u = 0; u < half; u++) gs_bf(x[k0 + u], x[k0 + u + half], w, q);
         }
     }
 }
 
-template <int LOGR>
-__device__ __forceinline__ void inv_A(u64 (&x)[16], int tau, int jb, int js, int sg0, int logN,
-                                      const ulonglong2 *__restrict__ tw, u64 q) {
+template <int LOGR, class TW>
+__device__ __forceinline__ void inv_A(u64 (&x)[16], int tau, int jb, int js, int sg0, TW tw, u64 q) {
     constexpr int S = Geo<LOGR>::S;
 #pragma unroll
     for (int s = 3; s >= 0; s--) {
         const int half = 8 >> s;
 #pragma unroll
-        for (int k = 0; k < 16; k++) {
-            if (k & half) continue;
-            const int e = tau + S * k;
-            gs_bf(x[k], x[k + half], twid(tw, sg0 + s, jb + e * js, logN), q);
+        for (int k0 = 0; k0 < 16; k0 += 2 * half) {
+            const ulonglong2 w = tw(sg0 + s, jb + (tau + S * k0) * js);
+#pragma unroll
+            for (int u = 0; u < half; u++) gs_bf(x[k0 + u], x[k0 + u + half], w, q);
         }
     }
+}
+
+// stage the first 2^LOGR twiddles (all a column pass uses) in shared memory
+template <int LOGR>
+__device__ __forceinline__ TwShared stage_twiddles(ulonglong2 *sm_tw, const ulonglong2 *__restrict__ tab, int logN) {
+    for (int i = threadIdx.x; i < (1 << LOGR); i += NT) sm_tw[i] = __ldg(&tab[i]);
+    __syncthreads();
+    return TwShared{sm_tw, logN};
 }
 
 // ---- exchanges through shared memory
@@ -197,6 +215,8 @@ __global__ void __launch_bounds__(NT) k_ntt_fwd_col(DevCtx c, NttArgs a) {
     const int job = blockIdx.y, item = job / a.n_limbs, limb = job % a.n_limbs;
     const PrimeTab &P = c.primes[a.pidx[limb]];
     const u64 q = P.m.q;
+    __shared__ ulonglong2 sm_tw[256];
+    const TwShared tws = stage_twiddles<LOGR>(sm_tw, P.fwd, c.logN);
     const int logC = c.logN - LOGR;
     const int cl = threadIdx.x % Gm::T, tau = threadIdx.x / Gm::T;
     const int col = blockIdx.x * Gm::T + cl;
@@ -205,9 +225,9 @@ __global__ void __launch_bounds__(NT) k_ntt_fwd_col(DevCtx c, NttArgs a) {
     u64 x[16];
 #pragma unroll
     for (int k = 0; k < 16; k++) x[k] = src[col + ((tau + Gm::S * k) << logC)];
-    fwd_A<LOGR>(x, tau, col, 1 << logC, 0, c.logN, P.fwd, q);
+    fwd_A<LOGR>(x, tau, col, 1 << logC, 0, tws, q);
     xchg_col_AB<LOGR>(x, sm, tau, cl);
-    fwd_B<LOGR>(x, tau, col, 1 << logC, 0, c.logN, P.fwd, q);
+    fwd_B<LOGR>(x, tau, col, 1 << logC, 0, tws, q);
 #pragma unroll
     for (int k = 0; k < 16; k++) dst[col + ((16 * tau + k) << logC)] = x[k];
 }
@@ -226,9 +246,9 @@ __global__ void __launch_bounds__(NT) k_ntt_fwd_row(DevCtx c, NttArgs a) {
     u64 x[16];
 #pragma unroll
     for (int k = 0; k < 16; k++) x[k] = p[tau + Gm::S * k];
-    fwd_A<LOGR>(x, tau, row << LOGR, 1, c.logR1, c.logN, P.fwd, q);
+    fwd_A<LOGR>(x, tau, row << LOGR, 1, c.logR1, TwGlobal{P.fwd, c.logN}, q);
     xchg_row_AB<LOGR>(x, sm, tau, rl);
-    fwd_B<LOGR>(x, tau, row << LOGR, 1, c.logR1, c.logN, P.fwd, q);
+    fwd_B<LOGR>(x, tau, row << LOGR, 1, c.logR1, TwGlobal{P.fwd, c.logN}, q);
     xchg_row_BA<LOGR>(x, sm, tau, rl);
 #pragma unroll
     for (int k = 0; k < 16; k++) p[tau + Gm::S * k] = reduce_4q(x[k], q);
@@ -250,9 +270,9 @@ __global__ void __launch_bounds__(NT) k_ntt_inv_row(DevCtx c, NttArgs a) {
 #pragma unroll
     for (int k = 0; k < 16; k++) x[k] = s[tau + Gm::S * k];
     xchg_row_AB<LOGR>(x, sm, tau, rl);
-    inv_B<LOGR>(x, tau, row << LOGR, 1, c.logR1, c.logN, P.inv, q);
+    inv_B<LOGR>(x, tau, row << LOGR, 1, c.logR1, TwGlobal{P.inv, c.logN}, q);
     xchg_row_BA<LOGR>(x, sm, tau, rl);
-    inv_A<LOGR>(x, tau, row << LOGR, 1, c.logR1, c.logN, P.inv, q);
+    inv_A<LOGR>(x, tau, row << LOGR, 1, c.logR1, TwGlobal{P.inv, c.logN}, q);
 #pragma unroll
     for (int k = 0; k < 16; k++) d[tau + Gm::S * k] = x[k];
 }
@@ -265,6 +285,8 @@ __global__ void __launch_bounds__(NT) k_ntt_inv_col(DevCtx c, NttArgs a) {
     const int job = blockIdx.y, item = job / a.n_limbs, limb = job % a.n_limbs;
     const PrimeTab &P = c.primes[a.pidx[limb]];
     const u64 q = P.m.q;
+    __shared__ ulonglong2 sm_tw[256];
+    const TwShared tws = stage_twiddles<LOGR>(sm_tw, P.inv, c.logN);
     const int logC = c.logN - LOGR;
     const int cl = threadIdx.x % Gm::T, tau = threadIdx.x / Gm::T;
     const int col = blockIdx.x * Gm::T + cl;
@@ -272,9 +294,9 @@ __global__ void __launch_bounds__(NT) k_ntt_inv_col(DevCtx c, NttArgs a) {
     u64 x[16];
 #pragma unroll
     for (int k = 0; k < 16; k++) x[k] = p[col + ((16 * tau + k) << logC)];
-    inv_B<LOGR>(x, tau, col, 1 << logC, 0, c.logN, P.inv, q);
+    inv_B<LOGR>(x, tau, col, 1 << logC, 0, tws, q);
     xchg_col_BA<LOGR>(x, sm, tau, cl);
-    inv_A<LOGR>(x, tau, col, 1 << logC, 0, c.logN, P.inv, q);
+    inv_A<LOGR>(x, tau, col, 1 << logC, 0, tws, q);
 #pragma unroll
     for (int k = 0; k < 16; k++) {
         u64 v = mul_shoup_lazy(x[k], P.n_inv, P.n_inv_sh, q);
@@ -317,9 +339,9 @@ __global__ void __launch_bounds__(NT) k_ks_intt_row(DevCtx c, KsArgs a, KsLayout
 #pragma unroll
     for (int k = 0; k < 16; k++) x[k] = s[galois_src((row << LOGR) + tau + Gm::S * k, a.galois, c.logN)];
     xchg_row_AB<LOGR>(x, sm, tau, rl);
-    inv_B<LOGR>(x, tau, row << LOGR, 1, c.logR1, c.logN, P.inv, q);
+    inv_B<LOGR>(x, tau, row << LOGR, 1, c.logR1, TwGlobal{P.inv, c.logN}, q);
     xchg_row_BA<LOGR>(x, sm, tau, rl);
-    inv_A<LOGR>(x, tau, row << LOGR, 1, c.logR1, c.logN, P.inv, q);
+    inv_A<LOGR>(x, tau, row << LOGR, 1, c.logR1, TwGlobal{P.inv, c.logN}, q);
 #pragma unroll
     for (int k = 0; k < 16; k++) d[tau + Gm::S * k] = x[k];
 }
@@ -333,6 +355,8 @@ __global__ void __launch_bounds__(NT) k_ks_intt_col(DevCtx c, LevelTab lt, KsArg
     const int job = blockIdx.y, item = job / nl, limb = job % nl;
     const PrimeTab &P = c.primes[limb];
     const u64 q = P.m.q;
+    __shared__ ulonglong2 sm_tw[256];
+    const TwShared tws = stage_twiddles<LOGR>(sm_tw, P.inv, c.logN);
     const int logC = c.logN - LOGR;
     const int cl = threadIdx.x % Gm::T, tau = threadIdx.x / Gm::T;
     const int col = blockIdx.x * Gm::T + cl;
@@ -341,9 +365,9 @@ __global__ void __launch_bounds__(NT) k_ks_intt_col(DevCtx c, LevelTab lt, KsArg
     u64 x[16];
 #pragma unroll
     for (int k = 0; k < 16; k++) x[k] = p[col + ((16 * tau + k) << logC)];
-    inv_B<LOGR>(x, tau, col, 1 << logC, 0, c.logN, P.inv, q);
+    inv_B<LOGR>(x, tau, col, 1 << logC, 0, tws, q);
     xchg_col_BA<LOGR>(x, sm, tau, cl);
-    inv_A<LOGR>(x, tau, col, 1 << logC, 0, c.logN, P.inv, q);
+    inv_A<LOGR>(x, tau, col, 1 << logC, 0, tws, q);
 #pragma unroll
     for (int k = 0; k < 16; k++) {
         u64 v = mul_shoup_lazy(x[k], sc.x, sc.y, q);
@@ -367,6 +391,8 @@ __global__ void __launch_bounds__(NT) k_ks_modup_col(DevCtx c, LevelTab lt, KsAr
     if (t >= d_lo && t < d_hi) return;   // limb of the digit itself: no conversion
     const PrimeTab &P = c.primes[ext_prime(t, a.level, c.L)];
     const u64 q = P.m.q;
+    __shared__ ulonglong2 sm_tw[256];
+    const TwShared tws = stage_twiddles<LOGR>(sm_tw, P.fwd, c.logN);
     const int logC = c.logN - LOGR;
     const int cl = threadIdx.x % Gm::T, tau = threadIdx.x / Gm::T;
     const int col = blockIdx.x * Gm::T + cl;
@@ -375,84 +401,77 @@ __global__ void __launch_bounds__(NT) k_ks_modup_col(DevCtx c, LevelTab lt, KsAr
     const u64 *hat = lt.modup_hat + (long long)(j * alpha) * ext;
     u64 hv[8];
     const int nu = d_hi - d_lo;
-    // a residue of a wider source prime is first reduced mod the target, so
-    // that every product stays below t^2 (the Barrett precondition)
-    unsigned wide = 0;
 #pragma unroll
-    for (int u = 0; u < 8; u++) {
-        hv[u] = (u < nu) ? hat[u * ext + t] : 0;
-        if (u < nu && c.primes[d_lo + u].m.b > P.m.b) wide |= 1u << u;
-    }
+    for (int u = 0; u < 8; u++) hv[u] = (u < nu) ? hat[u * ext + t] : 0;
     u64 x[16];
 #pragma unroll
     for (int k = 0; k < 16; k++) {
         const int J = col + ((tau + Gm::S * k) << logC);
         U128 acc = {0, 0};
-        for (int u = 0; u < nu; u++) {
-            u64 v = y[((long long)(d_lo + u) << c.logN) + J];
-            if (wide & (1u << u)) v = barrett(U128{v, 0}, P.m);
-            mac(acc, v, hv[u]);
-        }
+        for (int u = 0; u < nu; u++) mac(acc, y[((long long)(d_lo + u) << c.logN) + J], hv[u]);
         x[k] = barrett(acc, P.m);
     }
-    fwd_A<LOGR>(x, tau, col, 1 << logC, 0, c.logN, P.fwd, q);
+    fwd_A<LOGR>(x, tau, col, 1 << logC, 0, tws, q);
     xchg_col_AB<LOGR>(x, sm, tau, cl);
-    fwd_B<LOGR>(x, tau, col, 1 << logC, 0, c.logN, P.fwd, q);
+    fwd_B<LOGR>(x, tau, col, 1 << logC, 0, tws, q);
 #pragma unroll
     for (int k = 0; k < 16; k++) dst[col + ((16 * tau + k) << logC)] = x[k];
 }
 
-// (4) ModUp NTT rows fused with the inner product against the key:
-//     acc_k[t] = sum_j ext_j[t] * key_j[k][t]
+// (4) ModUp: NTT rows of every converted limb, in place
 template <int LOGR>
-__global__ void __launch_bounds__(NT, 1) k_ks_modup_row_ip(DevCtx c, LevelTab lt, KsArgs a, KsLayout ly) {
+__global__ void __launch_bounds__(NT) k_ks_modup_row(DevCtx c, LevelTab lt, KsArgs a, KsLayout ly) {
     using Gm = Geo<LOGR>;
     __shared__ u64 sm[SMEM_WORDS];
     const int ext = lt.ext, nd = lt.n_digits;
-    const int job = blockIdx.y, item = job / ext, t = job % ext;
-    const int pi = ext_prime(t, a.level, c.L);
-    const PrimeTab &P = c.primes[pi];
+    const int job = blockIdx.y;
+    const int item = job / (nd * ext);
+    const int j = (job / ext) % nd;
+    const int t = job % ext;
+    const int d_lo = j * c.alpha, d_hi = min(d_lo + c.alpha, a.level + 1);
+    if (t >= d_lo && t < d_hi) return;
+    const PrimeTab &P = c.primes[ext_prime(t, a.level, c.L)];
     const u64 q = P.m.q;
     const int tau = threadIdx.x % Gm::S, rl = threadIdx.x / Gm::S;
     const int row = blockIdx.x * Gm::T + rl;
     const int base = row << LOGR;
+    u64 *p = a.ws + item * a.ws_item + ly.mu + ((long long)(j * ext + t) << c.logN) + base;
+    u64 x[16];
+#pragma unroll
+    for (int k = 0; k < 16; k++) x[k] = p[tau + Gm::S * k];
+    fwd_A<LOGR>(x, tau, base, 1, c.logR1, TwGlobal{P.fwd, c.logN}, q);
+    xchg_row_AB<LOGR>(x, sm, tau, rl);
+    fwd_B<LOGR>(x, tau, base, 1, c.logR1, TwGlobal{P.fwd, c.logN}, q);
+    xchg_row_BA<LOGR>(x, sm, tau, rl);
+#pragma unroll
+    for (int k = 0; k < 16; k++) p[tau + Gm::S * k] = reduce_4q(x[k], q);
+}
+
+// (4b) inner product with the key, acc_k[t] = sum_j ext_j[t] * key_j[k][t].
+// One thread per coefficient; the items of the batch are looped inside so
+// each key coefficient is fetched from HBM once per batch.
+__global__ void __launch_bounds__(256) k_ks_ip(DevCtx c, LevelTab lt, KsArgs a, KsLayout ly) {
+    const int ext = lt.ext, nd = lt.n_digits;
+    const int t = blockIdx.y;
+    const int pi = ext_prime(t, a.level, c.L);
+    const ModQ m = c.primes[pi].m;
     const long long N = 1ll << c.logN;
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
     const long long key_limbs = c.L + 1 + c.alpha;
-    U128 acc0[16], acc1[16];
-#pragma unroll
-    for (int k = 0; k < 16; k++) acc0[k] = acc1[k] = U128{0, 0};
-    for (int j = 0; j < nd; j++) {
-        u64 x[16];
-        const int d_lo = j * c.alpha, d_hi = min(d_lo + c.alpha, a.level + 1);
-        if (t >= d_lo && t < d_hi) {
-            const u64 *s = a.d + item * a.d_item + (long long)t * N;
-#pragma unroll
-            for (int k = 0; k < 16; k++) x[k] = s[galois_src(base + tau + Gm::S * k, a.galois, c.logN)];
-        } else {
-            const u64 *s = a.ws + item * a.ws_item + ly.mu + (long long)(j * ext + t) * N + base;
-#pragma unroll
-            for (int k = 0; k < 16; k++) x[k] = s[tau + Gm::S * k];
-            fwd_A<LOGR>(x, tau, base, 1, c.logR1, c.logN, P.fwd, q);
-            xchg_row_AB<LOGR>(x, sm, tau, rl);
-            fwd_B<LOGR>(x, tau, base, 1, c.logR1, c.logN, P.fwd, q);
-            xchg_row_BA<LOGR>(x, sm, tau, rl);
-#pragma unroll
-            for (int k = 0; k < 16; k++) x[k] = reduce_4q(x[k], q);
+    const int jt = t <= a.level ? t / c.alpha : -1;   // digit that holds limb t itself
+    const int src_col = jt >= 0 ? galois_src(col, a.galois, c.logN) : col;
+    for (int item = 0; item < a.n_items; item++) {
+        U128 acc0 = {0, 0}, acc1 = {0, 0};
+        const u64 *mu = a.ws + item * a.ws_item + ly.mu + (long long)t * N + col;
+        for (int j = 0; j < nd; j++) {
+            const u64 x = (j == jt) ? a.d[item * a.d_item + (long long)t * N + src_col] : mu[(long long)j * ext * N];
+            const u64 *kb = a.key + ((long long)(j * 2) * key_limbs + pi) * N + col;
+            mac(acc0, x, __ldg(kb));
+            mac(acc1, x, __ldg(kb + key_limbs * N));
         }
-        const u64 *k0 = a.key + ((long long)(j * 2 + 0) * key_limbs + pi) * N + base;
-        const u64 *k1 = a.key + ((long long)(j * 2 + 1) * key_limbs + pi) * N + base;
-#pragma unroll
-        for (int k = 0; k < 16; k++) {
-            mac(acc0[k], x[k], __ldg(&k0[tau + Gm::S * k]));
-            mac(acc1[k], x[k], __ldg(&k1[tau + Gm::S * k]));
-        }
-    }
-    u64 *o0 = a.ws + item * a.ws_item + ly.acc + (long long)t * N + base;
-    u64 *o1 = o0 + (long long)ext * N;
-#pragma unroll
-    for (int k = 0; k < 16; k++) {
-        o0[tau + Gm::S * k] = barrett(acc0[k], P.m);
-        o1[tau + Gm::S * k] = barrett(acc1[k], P.m);
+        u64 *o0 = a.ws + item * a.ws_item + ly.acc + (long long)t * N + col;
+        o0[0] = barrett(acc0, m);
+        o0[(long long)ext * N] = barrett(acc1, m);
     }
 }
 
@@ -474,9 +493,9 @@ __global__ void __launch_bounds__(NT) k_ks_md_intt_row(DevCtx c, LevelTab lt, Ks
 #pragma unroll
     for (int k = 0; k < 16; k++) x[k] = s[tau + Gm::S * k];
     xchg_row_AB<LOGR>(x, sm, tau, rl);
-    inv_B<LOGR>(x, tau, row << LOGR, 1, c.logR1, c.logN, P.inv, q);
+    inv_B<LOGR>(x, tau, row << LOGR, 1, c.logR1, TwGlobal{P.inv, c.logN}, q);
     xchg_row_BA<LOGR>(x, sm, tau, rl);
-    inv_A<LOGR>(x, tau, row << LOGR, 1, c.logR1, c.logN, P.inv, q);
+    inv_A<LOGR>(x, tau, row << LOGR, 1, c.logR1, TwGlobal{P.inv, c.logN}, q);
 #pragma unroll
     for (int k = 0; k < 16; k++) d[tau + Gm::S * k] = x[k];
 }
@@ -490,6 +509,8 @@ __global__ void __launch_bounds__(NT) k_ks_md_intt_col(DevCtx c, LevelTab lt, Ks
     const int job = blockIdx.y, item = job / (2 * al), kk = (job / al) % 2, m = job % al;
     const PrimeTab &P = c.primes[c.L + 1 + m];
     const u64 q = P.m.q;
+    __shared__ ulonglong2 sm_tw[256];
+    const TwShared tws = stage_twiddles<LOGR>(sm_tw, P.inv, c.logN);
     const int logC = c.logN - LOGR;
     const int cl = threadIdx.x % Gm::T, tau = threadIdx.x / Gm::T;
     const int col = blockIdx.x * Gm::T + cl;
@@ -499,9 +520,9 @@ __global__ void __launch_bounds__(NT) k_ks_md_intt_col(DevCtx c, LevelTab lt, Ks
     u64 x[16];
 #pragma unroll
     for (int k = 0; k < 16; k++) x[k] = p[col + ((16 * tau + k) << logC)];
-    inv_B<LOGR>(x, tau, col, 1 << logC, 0, c.logN, P.inv, q);
+    inv_B<LOGR>(x, tau, col, 1 << logC, 0, tws, q);
     xchg_col_BA<LOGR>(x, sm, tau, cl);
-    inv_A<LOGR>(x, tau, col, 1 << logC, 0, c.logN, P.inv, q);
+    inv_A<LOGR>(x, tau, col, 1 << logC, 0, tws, q);
 #pragma unroll
     for (int k = 0; k < 16; k++) {
         u64 v = mul_shoup_lazy(x[k], sc.x, sc.y, q);
@@ -520,6 +541,8 @@ __global__ void __launch_bounds__(NT) k_ks_md_conv_col(DevCtx c, LevelTab lt, Ks
     const int job = blockIdx.y, item = job / (2 * nl), kk = (job / nl) % 2, i = job % nl;
     const PrimeTab &P = c.primes[i];
     const u64 q = P.m.q;
+    __shared__ ulonglong2 sm_tw[256];
+    const TwShared tws = stage_twiddles<LOGR>(sm_tw, P.fwd, c.logN);
     const int logC = c.logN - LOGR;
     const int cl = threadIdx.x % Gm::T, tau = threadIdx.x / Gm::T;
     const int col = blockIdx.x * Gm::T + cl;
@@ -527,28 +550,20 @@ __global__ void __launch_bounds__(NT) k_ks_md_conv_col(DevCtx c, LevelTab lt, Ks
     const u64 *z = a.ws + item * a.ws_item + ly.z + (long long)kk * al * N;
     u64 *dst = a.ws + item * a.ws_item + ly.md + ((long long)(kk * nl + i) << c.logN);
     u64 hv[8];
-    unsigned wide = 0;
 #pragma unroll
-    for (int u = 0; u < 8; u++) {
-        hv[u] = (u < al) ? c.md_phat[u * (c.L + 1) + i] : 0;
-        if (u < al && c.primes[c.L + 1 + u].m.b > P.m.b) wide |= 1u << u;
-    }
+    for (int u = 0; u < 8; u++) hv[u] = (u < al) ? c.md_phat[u * (c.L + 1) + i] : 0;
     const u64 halfp = c.md_halfp[i];
     u64 x[16];
 #pragma unroll
     for (int k = 0; k < 16; k++) {
         const int J = col + ((tau + Gm::S * k) << logC);
         U128 acc = {0, 0};
-        for (int u = 0; u < al; u++) {
-            u64 v = z[(long long)u * N + J];
-            if (wide & (1u << u)) v = barrett(U128{v, 0}, P.m);
-            mac(acc, v, hv[u]);
-        }
+        for (int u = 0; u < al; u++) mac(acc, z[(long long)u * N + J], hv[u]);
         x[k] = sub_mod(barrett(acc, P.m), halfp, q);
     }
-    fwd_A<LOGR>(x, tau, col, 1 << logC, 0, c.logN, P.fwd, q);
+    fwd_A<LOGR>(x, tau, col, 1 << logC, 0, tws, q);
     xchg_col_AB<LOGR>(x, sm, tau, cl);
-    fwd_B<LOGR>(x, tau, col, 1 << logC, 0, c.logN, P.fwd, q);
+    fwd_B<LOGR>(x, tau, col, 1 << logC, 0, tws, q);
 #pragma unroll
     for (int k = 0; k < 16; k++) dst[col + ((16 * tau + k) << logC)] = x[k];
 }
@@ -573,9 +588,9 @@ __global__ void __launch_bounds__(NT) k_ks_md_row_out(DevCtx c, LevelTab lt, KsA
     u64 x[16];
 #pragma unroll
     for (int k = 0; k < 16; k++) x[k] = s[tau + Gm::S * k];
-    fwd_A<LOGR>(x, tau, base, 1, c.logR1, c.logN, P.fwd, q);
+    fwd_A<LOGR>(x, tau, base, 1, c.logR1, TwGlobal{P.fwd, c.logN}, q);
     xchg_row_AB<LOGR>(x, sm, tau, rl);
-    fwd_B<LOGR>(x, tau, base, 1, c.logR1, c.logN, P.fwd, q);
+    fwd_B<LOGR>(x, tau, base, 1, c.logR1, TwGlobal{P.fwd, c.logN}, q);
     xchg_row_BA<LOGR>(x, sm, tau, rl);
     u64 *o = a.out + item * a.out_item + ((long long)kk * nl + i) * N + base;
 #pragma unroll
@@ -611,9 +626,9 @@ __global__ void __launch_bounds__(NT) k_rs_intt_row(DevCtx c, RescaleArgs a) {
 #pragma unroll
     for (int k = 0; k < 16; k++) x[k] = s[tau + Gm::S * k];
     xchg_row_AB<LOGR>(x, sm, tau, rl);
-    inv_B<LOGR>(x, tau, row << LOGR, 1, c.logR1, c.logN, P.inv, q);
+    inv_B<LOGR>(x, tau, row << LOGR, 1, c.logR1, TwGlobal{P.inv, c.logN}, q);
     xchg_row_BA<LOGR>(x, sm, tau, rl);
-    inv_A<LOGR>(x, tau, row << LOGR, 1, c.logR1, c.logN, P.inv, q);
+    inv_A<LOGR>(x, tau, row << LOGR, 1, c.logR1, TwGlobal{P.inv, c.logN}, q);
 #pragma unroll
     for (int k = 0; k < 16; k++) d[tau + Gm::S * k] = x[k];
 }
@@ -625,6 +640,8 @@ __global__ void __launch_bounds__(NT) k_rs_intt_col(DevCtx c, RescaleArgs a) {
     const int job = blockIdx.y;
     const PrimeTab &P = c.primes[a.level];
     const u64 q = P.m.q;
+    __shared__ ulonglong2 sm_tw[256];
+    const TwShared tws = stage_twiddles<LOGR>(sm_tw, P.inv, c.logN);
     const int logC = c.logN - LOGR;
     const int cl = threadIdx.x % Gm::T, tau = threadIdx.x / Gm::T;
     const int col = blockIdx.x * Gm::T + cl;
@@ -632,9 +649,9 @@ __global__ void __launch_bounds__(NT) k_rs_intt_col(DevCtx c, RescaleArgs a) {
     u64 x[16];
 #pragma unroll
     for (int k = 0; k < 16; k++) x[k] = p[col + ((16 * tau + k) << logC)];
-    inv_B<LOGR>(x, tau, col, 1 << logC, 0, c.logN, P.inv, q);
+    inv_B<LOGR>(x, tau, col, 1 << logC, 0, tws, q);
     xchg_col_BA<LOGR>(x, sm, tau, cl);
-    inv_A<LOGR>(x, tau, col, 1 << logC, 0, c.logN, P.inv, q);
+    inv_A<LOGR>(x, tau, col, 1 << logC, 0, tws, q);
 #pragma unroll
     for (int k = 0; k < 16; k++) {
         u64 v = mul_shoup_lazy(x[k], P.n_inv, P.n_inv_sh, q);
@@ -651,6 +668,8 @@ __global__ void __launch_bounds__(NT) k_rs_conv_col(DevCtx c, LevelTab lt, Resca
     const int job = blockIdx.y, item = job / (a.n_poly * lv), poly = (job / lv) % a.n_poly, i = job % lv;
     const PrimeTab &P = c.primes[i];
     const u64 q = P.m.q;
+    __shared__ ulonglong2 sm_tw[256];
+    const TwShared tws = stage_twiddles<LOGR>(sm_tw, P.fwd, c.logN);
     const u64 ql = c.primes[lv].m.q;
     const u64 qlmod = lt.q_last_mod[i];
     const int logC = c.logN - LOGR;
@@ -666,9 +685,9 @@ __global__ void __launch_bounds__(NT) k_rs_conv_col(DevCtx c, LevelTab lt, Resca
         if (t > (ql - 1) / 2) r = sub_mod(r, qlmod, q);
         x[k] = r;
     }
-    fwd_A<LOGR>(x, tau, col, 1 << logC, 0, c.logN, P.fwd, q);
+    fwd_A<LOGR>(x, tau, col, 1 << logC, 0, tws, q);
     xchg_col_AB<LOGR>(x, sm, tau, cl);
-    fwd_B<LOGR>(x, tau, col, 1 << logC, 0, c.logN, P.fwd, q);
+    fwd_B<LOGR>(x, tau, col, 1 << logC, 0, tws, q);
 #pragma unroll
     for (int k = 0; k < 16; k++) dst[col + ((16 * tau + k) << logC)] = x[k];
 }
@@ -691,9 +710,9 @@ __global__ void __launch_bounds__(NT) k_rs_row_out(DevCtx c, LevelTab lt, Rescal
     u64 x[16];
 #pragma unroll
     for (int k = 0; k < 16; k++) x[k] = o[tau + Gm::S * k];
-    fwd_A<LOGR>(x, tau, base, 1, c.logR1, c.logN, P.fwd, q);
+    fwd_A<LOGR>(x, tau, base, 1, c.logR1, TwGlobal{P.fwd, c.logN}, q);
     xchg_row_AB<LOGR>(x, sm, tau, rl);
-    fwd_B<LOGR>(x, tau, base, 1, c.logR1, c.logN, P.fwd, q);
+    fwd_B<LOGR>(x, tau, base, 1, c.logR1, TwGlobal{P.fwd, c.logN}, q);
     xchg_row_BA<LOGR>(x, sm, tau, rl);
 #pragma unroll
     for (int k = 0; k < 16; k++) {
@@ -793,50 +812,43 @@ __global__ void k_decrypt(DevCtx c, const u64 *ct, const u64 *s, u64 *m, int lev
     }
 }
 
-// ---- pt-MAC: one CTA = one output group x 256 coefficients x one limb, all images
-#define MAC_IMG 4
+// ---- pt-MAC.  A CTA owns 32 consecutive coefficients of one limb for 8
+// images (thread = coefficient x image) and computes every output group of
+// the step: the rotated inputs it reads stay in L1 across groups, and the
+// CTAs of the image tiles of one coefficient tile run back to back so each
+// plaintext tile is fetched from HBM once per batch.
+#define MAC_TC 32
+#define MAC_IB 8
 __global__ void __launch_bounds__(256) k_mac(DevCtx c, MacArgs a) {
-    const MacGroup g = a.groups[blockIdx.x];
     const int limb = blockIdx.z;
     const ModQ m = c.primes[limb].m;
     const long long N = 1ll << c.logN;
-    const long long off = (long long)limb * N + blockIdx.y * blockDim.x + threadIdx.x;
+    const int cl = threadIdx.x % MAC_TC, il = threadIdx.x / MAC_TC;
+    const int img = blockIdx.x * MAC_IB + il;
+    if (img >= a.n_items) return;
+    const long long off = (long long)limb * N + blockIdx.y * MAC_TC + cl;
     const long long P = (long long)(a.level + 1) * N;
-    for (int i0 = 0; i0 < a.n_items; i0 += MAC_IMG) {
-        const int ni = min(MAC_IMG, a.n_items - i0);
-        U128 acc[MAC_IMG][2];
-#pragma unroll
-        for (int u = 0; u < MAC_IMG; u++) acc[u][0] = acc[u][1] = U128{0, 0};
+    for (int g = 0; g < a.n_groups; g++) {
+        const MacGroup G = a.groups[g];
+        U128 acc0 = {0, 0}, acc1 = {0, 0};
         int cnt = 0;
-        for (int t = g.term_begin; t < g.term_end; t++) {
-            const MacTerm tm = a.terms[t];
-            const u64 p = __ldg(&tm.pt[off]);
-#pragma unroll
-            for (int u = 0; u < MAC_IMG; u++) {
-                if (u < ni) {
-                    const u64 *s = tm.src + (long long)(i0 + u) * tm.src_item + off;
-                    mac(acc[u][0], p, s[0]);
-                    mac(acc[u][1], p, s[P]);
-                }
-            }
+        for (int t = G.term_begin; t < G.term_end; t++) {
+            const MacTerm T = a.terms[t];
+            const MacSrc S = a.srcs[T.src];
+            const u64 p = __ldg(&T.pt[off]);
+            const u64 *sp = S.base + (long long)img * S.item + off;
+            mac(acc0, p, sp[0]);
+            mac(acc1, p, sp[P]);
             if (++cnt == 7) {
-#pragma unroll
-                for (int u = 0; u < MAC_IMG; u++) {
-                    acc[u][0] = U128{barrett(acc[u][0], m), 0};
-                    acc[u][1] = U128{barrett(acc[u][1], m), 0};
-                }
+                acc0 = U128{barrett(acc0, m), 0};
+                acc1 = U128{barrett(acc1, m), 0};
                 cnt = 0;
             }
         }
-        const u64 b = g.bias ? __ldg(&g.bias[off]) : 0;
-#pragma unroll
-        for (int u = 0; u < MAC_IMG; u++) {
-            if (u < ni) {
-                u64 *o = g.out + (long long)(i0 + u) * g.out_item + off;
-                o[0] = add_mod(barrett(acc[u][0], m), b, m.q);
-                o[P] = barrett(acc[u][1], m);
-            }
-        }
+        u64 *o = G.out + (long long)img * G.out_item + off;
+        const u64 b = G.bias ? __ldg(&G.bias[off]) : 0;
+        o[0] = add_mod(barrett(acc0, m), b, m.q);
+        o[P] = barrett(acc1, m);
     }
 }
 
@@ -1042,7 +1054,9 @@ cudaError_t launch_keyswitch(const DevCtx &c, const LevelTab &lt, const KsArgs &
     KS_EV(2);
     DISPATCH_LOGR(c.logR1, k_ks_modup_col, dim3(tc, B * nd * ext), c, lt, a, ly);
     KS_EV(3);
-    DISPATCH_LOGR(c.logR2, k_ks_modup_row_ip, dim3(tc, B * ext), c, lt, a, ly);
+    DISPATCH_LOGR(c.logR2, k_ks_modup_row, dim3(tc, B * nd * ext), c, lt, a, ly);
+    COUNT_LAUNCH();
+    k_ks_ip<<<dim3((unsigned)((1ll << c.logN) / 256), ext), 256, 0, s>>>(c, lt, a, ly);
     KS_EV(4);
     DISPATCH_LOGR(c.logR2, k_ks_md_intt_row, dim3(tc, B * 2 * c.alpha), c, lt, a, ly);
     KS_EV(5);
@@ -1117,7 +1131,7 @@ cudaError_t launch_decrypt(const DevCtx &c, const u64 *ct, const u64 *s_ntt, u64
 
 cudaError_t launch_mac(const DevCtx &c, const MacArgs &a, cudaStream_t s) {
     if (a.n_groups == 0) return cudaSuccess;
-    dim3 g(a.n_groups, (unsigned)((1ll << c.logN) / 256), a.level + 1);
+    dim3 g((a.n_items + MAC_IB - 1) / MAC_IB, (unsigned)((1ll << c.logN) / MAC_TC), a.level + 1);
     COUNT_LAUNCH();
     k_mac<<<g, 256, 0, s>>>(c, a);
     return cudaGetLastError();

@@ -133,11 +133,15 @@ cudaError_t launch_decrypt(const DevCtx &c, const u64 *ct, const u64 *s_ntt, u64
 
 // Plaintext-ciphertext multiply-accumulate of a linear layer.  Output group
 // g (one accumulator ciphertext per image) is
-//   out_g = sum_{t in terms(g)} pt_t (.) src_t   (+ bias_g on poly 0)
-// where src_t is a ciphertext tensor (per image at src_t + img*src_item_t).
+//   out_g = sum_{t in terms(g)} pt_t (.) srcs[src_t]   (+ bias_g on poly 0)
+// where a source is a ciphertext tensor (image i at base + i*item).
+struct MacSrc {
+    const u64 *base;      // image 0's ciphertext (2 polys x (level+1) limbs)
+    long long item;       // per-image stride
+};
 struct MacTerm {
-    const u64 *src;       // image 0's ciphertext (2 polys x (level+1) limbs)
-    long long src_item;   // per-image stride of src
+    int src;              // index into srcs
+    int pad_;
     const u64 *pt;        // plaintext limbs (level+1) x N
 };
 struct MacGroup {
@@ -147,8 +151,9 @@ struct MacGroup {
     int term_begin, term_end;
 };
 struct MacArgs {
-    const MacGroup *groups;   // device array
-    const MacTerm *terms;     // device array
+    const MacGroup *groups;   // device arrays
+    const MacTerm *terms;
+    const MacSrc *srcs;
     int n_groups;
     int n_items;
     int level;

@@ -2,14 +2,14 @@
 //
 // * Shoup multiplication by a precomputed constant w (w' = floor(w 2^64 / q)):
 //   one high and two low 64-bit products, result in [0, 2q).
-// * Barrett reduction of a 128-bit accumulator x < 2^(2b+3), b = bitlen(q):
-//   with A = b-2 and mu = floor(2^(2b+3) / q), the estimate
-//   floor(floor(x / 2^A) * mu / 2^(b+5)) is at most 2 below floor(x / q)
-//   (its error is below x/2^(2b+3) + 2^A/q + 1 < 2.5), so x - estimate*q lies
-//   in [0, 3q) and two conditional subtractions finish.
-//   (x / 2^A < 2^(b+5) and mu < 2^(b+4) fit 64 bits, and the shift b+5 stays
-//   below 64, for b <= 58.)
-//   Up to eight products of residues can be summed before one reduction.
+// * Barrett reduction of a 128-bit accumulator x < 2^(b+62), b = bitlen(q):
+//   with A = b-2 and mu = floor(2^(b+62) / q) (< 2^63), the estimate
+//   floor(floor(x / 2^A) * mu / 2^64) -- one high product -- is at most 2
+//   below floor(x / q): its error is below x/2^(b+62) + 2^A/q + 1 < 2.5.
+//   So x - estimate*q lies in [0, 3q) and two conditional subtractions
+//   finish.  floor(x / 2^A) < 2^64 holds because x < 2^(b+62).  For b <= 58
+//   this admits any 64-bit word, eight products of residues of q, or sums of
+//   up to eight products of a 58-bit residue and a residue of q.
 #pragma once
 #include <cstdint>
 
@@ -31,7 +31,7 @@ FHE_HD u64 umulhi64(u64 a, u64 b) {
 
 struct ModQ {
     u64 q;
-    u64 mu;      // floor(2^(2b+3) / q)
+    u64 mu;      // floor(2^(b+62) / q)
     int b;       // bit length of q
     int pad_;
 };
@@ -57,12 +57,8 @@ FHE_HD void mac(U128 &acc, u64 a, u64 b) { add_to(acc, mul_wide(a, b)); }
 
 FHE_HD u64 barrett(U128 x, const ModQ &m) {
     const int A = m.b - 2;
-    // x >> A (x < 2^(2b+3) so the result fits 64 bits)
-    u64 x1 = (x.lo >> A) | (x.hi << (64 - A));
-    u64 plo = x1 * m.mu;
-    u64 phi = umulhi64(x1, m.mu);
-    const int S = m.b + 5;  // (2b+3) - A
-    u64 est = (plo >> S) | (phi << (64 - S));
+    const u64 x1 = (x.lo >> A) | (x.hi << (64 - A));
+    const u64 est = umulhi64(x1, m.mu);
     u64 r = x.lo - est * m.q;
     if (r >= m.q) r -= m.q;
     if (r >= m.q) r -= m.q;

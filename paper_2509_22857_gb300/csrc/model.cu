@@ -293,17 +293,16 @@ struct Exec {
             FHE_CU(cudaMallocAsync((void **)&rb[k], (size_t)B * cs * 8, s));
             FHE_TRY(rotate_items(in + L.baby_ct[k] * cs, in_item, L.baby_step[k], nullptr, 0, rb[k], cs, B, lv));
         }
-        auto src_of = [&](int ct, int b, long long *it) -> const u64 * {
-            if (galois_of_step(c, b) == 1) {
-                *it = in_item;
-                return in + ct * cs;
-            }
+        // sources: the input ciphertexts, then the baby-step rotations
+        const int n_in = m->tensors[st.src].n_ct;
+        std::vector<MacSrc> hs;
+        for (int ct = 0; ct < n_in; ct++) hs.push_back(MacSrc{in + ct * cs, in_item});
+        for (size_t k = 0; k < rb.size(); k++) hs.push_back(MacSrc{rb[k], cs});
+        auto src_of = [&](int ct, int b) -> int {
+            if (galois_of_step(c, b) == 1) return ct;
             for (size_t k = 0; k < L.baby_ct.size(); k++)
-                if (L.baby_ct[k] == ct && L.baby_step[k] == b) {
-                    *it = cs;
-                    return rb[k];
-                }
-            return nullptr;
+                if (L.baby_ct[k] == ct && L.baby_step[k] == b) return n_in + (int)k;
+            return -1;
         };
         // accumulators of the giant steps (g != 0); g == 0 goes straight to out
         const int ng = (int)L.g_out.size();
@@ -326,25 +325,29 @@ struct Exec {
             G.term_begin = (int)ht.size();
             for (int t = L.g_tb[g]; t < L.g_te[g]; t++) {
                 MacTerm T;
-                T.src = src_of(L.t_ct[t], L.t_baby[t], &T.src_item);
-                if (!T.src) return fhe_fail(FHE_E_INVAL, "internal: missing baby rotation");
+                T.src = src_of(L.t_ct[t], L.t_baby[t]);
+                T.pad_ = 0;
+                if (T.src < 0) return fhe_fail(FHE_E_INVAL, "internal: missing baby rotation");
                 T.pt = L.t_pt[t];
                 ht.push_back(T);
             }
             G.term_end = (int)ht.size();
         }
-        // stage the work lists through pinned host memory
-        const size_t gb = hg.size() * sizeof(MacGroup), tb = ht.size() * sizeof(MacTerm);
-        host_stage.emplace_back(gb + tb + 16);
-        char *hs = host_stage.back().data();
-        memcpy(hs, hg.data(), gb);
-        if (tb) memcpy(hs + gb, ht.data(), tb);
+        // stage the work lists through host memory
+        const size_t gb = hg.size() * sizeof(MacGroup), tb = ht.size() * sizeof(MacTerm),
+                     sb = hs.size() * sizeof(MacSrc);
+        host_stage.emplace_back(gb + tb + sb + 16);
+        char *hsb = host_stage.back().data();
+        memcpy(hsb, hg.data(), gb);
+        if (tb) memcpy(hsb + gb, ht.data(), tb);
+        memcpy(hsb + gb + tb, hs.data(), sb);
         char *dw;
-        FHE_CU(cudaMallocAsync((void **)&dw, gb + tb + 16, s));
-        FHE_CU(cudaMemcpyAsync(dw, hs, gb + tb, cudaMemcpyHostToDevice, s));
+        FHE_CU(cudaMallocAsync((void **)&dw, gb + tb + sb + 16, s));
+        FHE_CU(cudaMemcpyAsync(dw, hsb, gb + tb + sb, cudaMemcpyHostToDevice, s));
         MacArgs ma;
         ma.groups = (const MacGroup *)dw;
         ma.terms = (const MacTerm *)(dw + gb);
+        ma.srcs = (const MacSrc *)(dw + gb + tb);
         ma.n_groups = ng;
         ma.n_items = B;
         ma.level = lv;

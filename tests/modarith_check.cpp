@@ -36,7 +36,7 @@ int main() {
             ModQ m;
             m.q = q;
             m.b = 64 - __builtin_clzll(q);
-            m.mu = (u64)(((u128)1 << (2 * m.b + 3)) / q);
+            m.mu = (u64)(((u128)1 << (m.b + 62)) / q);
             for (int it = 0; it < 20000; it++) {
                 int terms = 1 + (int)(g() % 8);
                 U128 acc = {0, 0};
@@ -51,10 +51,16 @@ int main() {
                 u64 w = g() % q, wp = (u64)(((u128)w << 64) / q), a = g();
                 u64 s = mul_shoup(a % (4 * q > q ? 4 * q : q), w, wp, q);
                 if (s != (u64)((u128)(a % (4 * q > q ? 4 * q : q)) * w % q)) { printf("shoup fail\n"); return 1; }
-                // a residue of a wider prime (< 2^58), and a full 64-bit word
-                u64 wide = g() >> 6;
-                u64 v = barrett(U128{wide, 0}, m);
-                if (v != wide % q) { printf("pre-reduction fail\n"); return 1; }
+                // sums of up to eight products of a residue of a 58-bit prime
+                // and a residue of q (basis conversions), and a 64-bit word
+                U128 acc2 = {0, 0};
+                u128 ref2 = 0;
+                for (int t = 0; t < terms; t++) {
+                    u64 a = g() >> 6, b = g() % q;
+                    mac(acc2, a, b);
+                    ref2 += (u128)a * b;
+                }
+                if (barrett(acc2, m) != (u64)(ref2 % q)) { printf("wide-sum fail q=%llu\n", q); return 1; }
                 u64 word = g();
                 if (barrett(U128{word, 0}, m) != word % q) { printf("word reduction fail\n"); return 1; }
             }
