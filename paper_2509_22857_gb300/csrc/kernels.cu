@@ -377,7 +377,7 @@ __global__ void __launch_bounds__(NT) k_ks_intt_col(DevCtx c, LevelTab lt, KsArg
 
 // (3) ModUp: basis conversion of digit j to ext limb t fused with NTT columns
 template <int LOGR>
-__global__ void __launch_bounds__(NT) k_ks_modup_col(DevCtx c, LevelTab lt, KsArgs a, KsLayout ly) {
+__global__ void __launch_bounds__(NT, 3) k_ks_modup_col(DevCtx c, LevelTab lt, KsArgs a, KsLayout ly) {
     using Gm = Geo<LOGR>;
     __shared__ u64 sm[SMEM_WORDS];
     const int ext = lt.ext, nd = lt.n_digits;
@@ -399,17 +399,26 @@ __global__ void __launch_bounds__(NT) k_ks_modup_col(DevCtx c, LevelTab lt, KsAr
     const u64 *y = a.ws + item * a.ws_item + ly.y;
     u64 *dst = a.ws + item * a.ws_item + ly.mu + ((long long)(j * ext + t) << c.logN);
     const u64 *hat = lt.modup_hat + (long long)(j * alpha) * ext;
-    u64 hv[8];
     const int nu = d_hi - d_lo;
-#pragma unroll
-    for (int u = 0; u < 8; u++) hv[u] = (u < nu) ? hat[u * ext + t] : 0;
+    // sum over the digit's primes: runtime loop outside, 8 elements inside
+    const long long sc = (long long)Gm::S << logC;
     u64 x[16];
 #pragma unroll
-    for (int k = 0; k < 16; k++) {
-        const int J = col + ((tau + Gm::S * k) << logC);
-        U128 acc = {0, 0};
-        for (int u = 0; u < nu; u++) mac(acc, y[((long long)(d_lo + u) << c.logN) + J], hv[u]);
-        x[k] = barrett(acc, P.m);
+    for (int h8 = 0; h8 < 16; h8 += 8) {
+        U128 acc[8];
+#pragma unroll
+        for (int k = 0; k < 8; k++) acc[k] = U128{0, 0};
+        for (int u = 0; u < nu; u++) {
+            const u64 h = hat[u * ext + t];
+            const u64 *yp = y + ((long long)(d_lo + u) << c.logN) + col + ((long long)tau << logC) + h8 * sc;
+            u64 v[8];
+#pragma unroll
+            for (int k = 0; k < 8; k++) v[k] = yp[k * sc];
+#pragma unroll
+            for (int k = 0; k < 8; k++) mac(acc[k], v[k], h);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; k++) x[h8 + k] = barrett(acc[k], P.m);
     }
     fwd_A<LOGR>(x, tau, col, 1 << logC, 0, tws, q);
     xchg_col_AB<LOGR>(x, sm, tau, cl);
@@ -460,14 +469,29 @@ __global__ void __launch_bounds__(256) k_ks_ip(DevCtx c, LevelTab lt, KsArgs a, 
     const long long key_limbs = c.L + 1 + c.alpha;
     const int jt = t <= a.level ? t / c.alpha : -1;   // digit that holds limb t itself
     const int src_col = jt >= 0 ? galois_src(col, a.galois, c.logN) : col;
-    for (int item = 0; item < a.n_items; item++) {
-        U128 acc0 = {0, 0}, acc1 = {0, 0};
-        const u64 *mu = a.ws + item * a.ws_item + ly.mu + (long long)t * N + col;
-        for (int j = 0; j < nd; j++) {
-            const u64 x = (j == jt) ? a.d[item * a.d_item + (long long)t * N + src_col] : mu[(long long)j * ext * N];
+    // the key of this limb for every digit, kept in registers across the batch
+    u64 k0[7], k1[7];
+#pragma unroll
+    for (int j = 0; j < 7; j++) {
+        if (j < nd) {
             const u64 *kb = a.key + ((long long)(j * 2) * key_limbs + pi) * N + col;
-            mac(acc0, x, __ldg(kb));
-            mac(acc1, x, __ldg(kb + key_limbs * N));
+            k0[j] = __ldg(kb);
+            k1[j] = __ldg(kb + key_limbs * N);
+        }
+    }
+    for (int item = 0; item < a.n_items; item++) {
+        const u64 *mu = a.ws + item * a.ws_item + ly.mu + (long long)t * N + col;
+        u64 x[7];
+#pragma unroll
+        for (int j = 0; j < 7; j++)
+            if (j < nd) x[j] = (j == jt) ? a.d[item * a.d_item + (long long)t * N + src_col] : mu[(long long)j * ext * N];
+        U128 acc0 = {0, 0}, acc1 = {0, 0};
+#pragma unroll
+        for (int j = 0; j < 7; j++) {
+            if (j < nd) {
+                mac(acc0, x[j], k0[j]);
+                mac(acc1, x[j], k1[j]);
+            }
         }
         u64 *o0 = a.ws + item * a.ws_item + ly.acc + (long long)t * N + col;
         o0[0] = barrett(acc0, m);
@@ -533,7 +557,7 @@ __global__ void __launch_bounds__(NT) k_ks_md_intt_col(DevCtx c, LevelTab lt, Ks
 
 // (7) ModDown: basis conversion P -> q_i (minus floor(P/2)) fused with NTT columns
 template <int LOGR>
-__global__ void __launch_bounds__(NT) k_ks_md_conv_col(DevCtx c, LevelTab lt, KsArgs a, KsLayout ly) {
+__global__ void __launch_bounds__(NT, 3) k_ks_md_conv_col(DevCtx c, LevelTab lt, KsArgs a, KsLayout ly) {
     using Gm = Geo<LOGR>;
     __shared__ u64 sm[SMEM_WORDS];
     const int al = c.alpha;
@@ -549,17 +573,25 @@ __global__ void __launch_bounds__(NT) k_ks_md_conv_col(DevCtx c, LevelTab lt, Ks
     const long long N = 1ll << c.logN;
     const u64 *z = a.ws + item * a.ws_item + ly.z + (long long)kk * al * N;
     u64 *dst = a.ws + item * a.ws_item + ly.md + ((long long)(kk * nl + i) << c.logN);
-    u64 hv[8];
-#pragma unroll
-    for (int u = 0; u < 8; u++) hv[u] = (u < al) ? c.md_phat[u * (c.L + 1) + i] : 0;
     const u64 halfp = c.md_halfp[i];
+    const long long sc = (long long)Gm::S << logC;
     u64 x[16];
 #pragma unroll
-    for (int k = 0; k < 16; k++) {
-        const int J = col + ((tau + Gm::S * k) << logC);
-        U128 acc = {0, 0};
-        for (int u = 0; u < al; u++) mac(acc, z[(long long)u * N + J], hv[u]);
-        x[k] = sub_mod(barrett(acc, P.m), halfp, q);
+    for (int h8 = 0; h8 < 16; h8 += 8) {
+        U128 acc[8];
+#pragma unroll
+        for (int k = 0; k < 8; k++) acc[k] = U128{0, 0};
+        for (int u = 0; u < al; u++) {
+            const u64 h = c.md_phat[u * (c.L + 1) + i];
+            const u64 *zp = z + (long long)u * N + col + ((long long)tau << logC) + h8 * sc;
+            u64 v[8];
+#pragma unroll
+            for (int k = 0; k < 8; k++) v[k] = zp[k * sc];
+#pragma unroll
+            for (int k = 0; k < 8; k++) mac(acc[k], v[k], h);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; k++) x[h8 + k] = sub_mod(barrett(acc[k], P.m), halfp, q);
     }
     fwd_A<LOGR>(x, tau, col, 1 << logC, 0, tws, q);
     xchg_col_AB<LOGR>(x, sm, tau, cl);
