@@ -58,6 +58,7 @@ typedef struct fhe_evk fhe_evk;
 typedef struct fhe_pt fhe_pt;
 typedef struct fhe_ct fhe_ct;
 typedef struct fhe_model fhe_model;
+typedef struct fhe_pipeline fhe_pipeline;
 
 /*
  * Parameters (Table 4 and the appendix on FHE parameters: ring degree N,
@@ -249,6 +250,30 @@ int fhe_eval_pool_dense(fhe_ctx *ctx, const fhe_model *model, const fhe_evk *evk
  */
 int fhe_infer(fhe_ctx *ctx, const fhe_model *model, const fhe_evk *evk, const fhe_ct *const *in,
               size_t n_img, fhe_ct **out, void *stream);
+
+/*
+ * Continuous batching with images at mixed levels.  The program is cut after
+ * every activation (and its rescale) into S segments; a group of up to
+ * `group` images enters per tick and leaves S-1 ticks later, so up to
+ * S*group images at S different levels are in flight at once.  All segments
+ * of a tick run concurrently (one stream each); with use_graphs, each tick's
+ * launches are captured into a CUDA graph (one per buffer parity, from the
+ * third tick on) and replayed.  Evaluation keys and weight plaintexts are
+ * shared by all groups.  Results are bit-identical to fhe_infer.
+ */
+int fhe_pipeline_create(fhe_ctx *ctx, const fhe_model *model, const fhe_evk *evk, int group, int use_graphs,
+                        fhe_pipeline **out);
+int fhe_pipeline_info(const fhe_pipeline *pipe, int *n_segments, int *group, int *n_in_ct, int *n_out_ct);
+/*
+ * One tick: in holds n_in (<= group) images' input ciphertexts (image-major,
+ * n_in_ct each; n_in may be 0).  out (capacity group * n_out_ct) receives the
+ * output ciphertexts of the group that leaves this tick, *n_out its image
+ * count (0 while the pipeline fills) and *out_tag the tick at which that
+ * group entered (-1 if none).  Synchronous.
+ */
+int fhe_pipeline_tick(fhe_pipeline *pipe, const fhe_ct *const *in, size_t n_in, fhe_ct **out, size_t *n_out,
+                      int64_t *out_tag);
+int fhe_pipeline_free(fhe_pipeline *pipe);
 
 /* ------------------------------------------------------ test hooks */
 

@@ -95,6 +95,12 @@ def lib() -> ctypes.CDLL:
             "fhe_eval_quad_act": (c_int, [V, V, V, c_int, PP, c_size, V]),
             "fhe_eval_pool_dense": (c_int, [V, V, V, c_int, PP, c_size, PP, c_size, V]),
             "fhe_infer": (c_int, [V, V, V, PP, c_size, PP, V]),
+            "fhe_pipeline_create": (c_int, [V, V, V, c_int, c_int, PP]),
+            "fhe_pipeline_info": (c_int, [V, ctypes.POINTER(c_int), ctypes.POINTER(c_int), ctypes.POINTER(c_int),
+                                          ctypes.POINTER(c_int)]),
+            "fhe_pipeline_tick": (c_int, [V, PP, c_size, PP, ctypes.POINTER(c_size),
+                                          ctypes.POINTER(ctypes.c_int64)]),
+            "fhe_pipeline_free": (c_int, [V]),
             "fhe_ntt_device": (c_int, [V, V, c_size, P_I32, c_int, V]),
             "fhe_evk_export": (c_int, [V, c_int, P_U64, c_size, ctypes.POINTER(c_size)]),
             "fhe_sk_export": (c_int, [V, P_U64, c_size]),
@@ -322,6 +328,31 @@ def fhe_infer(ctx, model, evk, cts, n_img: int, n_out_per_img: int, stream=None)
     return [out[i] for i in range(n_img * n_out_per_img)]
 
 
+def fhe_pipeline_create(ctx, model, evk, group: int, use_graphs: bool = True) -> int:
+    h = c_void()
+    _check(lib().fhe_pipeline_create(ctx, model, evk, group, int(use_graphs), ctypes.byref(h)))
+    return h.value
+
+
+def fhe_pipeline_info(pipe) -> Tuple[int, int, int, int]:
+    a, b, c_, d = c_int(), c_int(), c_int(), c_int()
+    _check(lib().fhe_pipeline_info(pipe, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c_), ctypes.byref(d)))
+    return a.value, b.value, c_.value, d.value
+
+
+def fhe_pipeline_tick(pipe, cts, n_in: int, out_capacity: int) -> Tuple[List[int], int, int]:
+    """returns (output handles, images completed, entry tick of that group or -1)"""
+    out = (c_void * max(out_capacity, 1))()
+    n_out, tag = c_size(), ctypes.c_int64()
+    _check(lib().fhe_pipeline_tick(pipe, _handles(cts), n_in, out, ctypes.byref(n_out), ctypes.byref(tag)))
+    n_ct_out = fhe_pipeline_info(pipe)[3]
+    return [out[i] for i in range(n_out.value * n_ct_out)], n_out.value, tag.value
+
+
+def fhe_pipeline_free(pipe):
+    _check(lib().fhe_pipeline_free(pipe))
+
+
 # ------------------------------------------------------------------ test hooks
 
 def fhe_ntt_device(ctx, dev_ptr: int, prime_idx: Sequence[int], inverse: bool, stream=None):
@@ -355,4 +386,5 @@ EXPORTED = ["fhe_last_error", "fhe_kernel_launches", "fhe_ctx_create", "fhe_ctx_
             "fhe_rotate", "fhe_square", "fhe_rescale", "fhe_add", "fhe_mul_plain", "fhe_model_load",
             "fhe_model_free", "fhe_eval_conv", "fhe_eval_quad_act", "fhe_eval_pool_dense", "fhe_infer",
             "fhe_ntt_device", "fhe_evk_export", "fhe_sk_export", "fhe_encode_coeffs",
-            "fhe_profile_keyswitch", "fhe_rescale_noalloc"]
+            "fhe_profile_keyswitch", "fhe_rescale_noalloc", "fhe_pipeline_create", "fhe_pipeline_info",
+            "fhe_pipeline_tick", "fhe_pipeline_free"]

@@ -475,19 +475,25 @@ int op_ntt(fhe_ctx *ctx, const u64 *src, u64 *dst, long long item, int n_items, 
     return FHE_OK;
 }
 
-int op_keyswitch(fhe_ctx *ctx, KsArgs a, cudaStream_t s) {
+int op_keyswitch(fhe_ctx *ctx, KsArgs a, cudaStream_t s, u64 *ws) {
     const size_t per = ks_workspace_words(ctx->dc, a.level);
-    FHE_TRY(ws_reserve(ctx, &ctx->ks_ws, &ctx->ks_ws_words, per * (size_t)a.n_items));
-    a.ws = ctx->ks_ws;
+    if (!ws) {
+        FHE_TRY(ws_reserve(ctx, &ctx->ks_ws, &ctx->ks_ws_words, per * (size_t)a.n_items));
+        ws = ctx->ks_ws;
+    }
+    a.ws = ws;
     a.ws_item = (long long)per;
     FHE_CU(launch_keyswitch(ctx->dc, ctx->lt[a.level], a, s));
     return FHE_OK;
 }
 
 int op_rescale(fhe_ctx *ctx, const u64 *in, long long in_item, u64 *out, long long out_item, int n_items,
-               int n_poly, int level, cudaStream_t s) {
+               int n_poly, int level, cudaStream_t s, u64 *ws) {
     if (level < 1) return fhe_fail(FHE_E_LEVEL, "rescale at level 0");
-    FHE_TRY(ws_reserve(ctx, &ctx->rs_ws, &ctx->rs_ws_words, (size_t)n_items * n_poly * ctx->N));
+    if (!ws) {
+        FHE_TRY(ws_reserve(ctx, &ctx->rs_ws, &ctx->rs_ws_words, (size_t)n_items * n_poly * ctx->N));
+        ws = ctx->rs_ws;
+    }
     RescaleArgs a;
     a.in = in;
     a.in_item = in_item;
@@ -496,7 +502,7 @@ int op_rescale(fhe_ctx *ctx, const u64 *in, long long in_item, u64 *out, long lo
     a.n_items = n_items;
     a.n_poly = n_poly;
     a.level = level;
-    a.ws = ctx->rs_ws;
+    a.ws = ws;
     FHE_CU(launch_rescale(ctx->dc, ctx->lt[level], a, s));
     return FHE_OK;
 }

@@ -108,9 +108,10 @@ size_t key_words(const fhe_ctx *ctx);
 u64 h_double_mod(double v, u64 q);
 
 // core operations on raw device buffers (batched over items)
-int op_keyswitch(fhe_ctx *ctx, KsArgs a, cudaStream_t s);
+// ws: caller-sized workspace, or nullptr for the context's growable one
+int op_keyswitch(fhe_ctx *ctx, KsArgs a, cudaStream_t s, u64 *ws = nullptr);
 int op_rescale(fhe_ctx *ctx, const u64 *in, long long in_item, u64 *out, long long out_item, int n_items,
-               int n_poly, int level, cudaStream_t s);
+               int n_poly, int level, cudaStream_t s, u64 *ws = nullptr);
 int op_ntt(fhe_ctx *ctx, const u64 *src, u64 *dst, long long item, int n_items, int n_limbs,
            const unsigned char *pidx, bool inverse, cudaStream_t s);
 // encode integral doubles into NTT-domain limbs 0..level (device)

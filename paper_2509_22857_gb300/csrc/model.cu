@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cstring>
 #include <memory>
+#include <map>
 #include <set>
 
 #include "host.h"
@@ -220,6 +221,23 @@ extern "C" int fhe_model_free(fhe_model *m) {
 
 namespace {
 
+// Buffers that persist across executions (pipeline mode): every temporary of
+// a step and every device work list is allocated on first use and reused, so
+// later executions of the same steps issue kernels only (and can be captured
+// in a CUDA graph).
+struct Persist {
+    std::map<std::pair<int, int>, u64 *> tmp;      // (step, index) -> device buffer
+    std::map<std::pair<int, int>, char *> lists;   // (variant, step) -> device work list
+    std::vector<void *> owned;
+    int variant = 0;                               // which set of work lists (pipeline parity)
+    u64 *ks_ws = nullptr;                          // this executor's key-switch workspace
+    u64 *rs_ws = nullptr;                          // and rescale workspace
+
+    ~Persist() {
+        for (void *p : owned) cudaFree(p);
+    }
+};
+
 struct Exec {
     fhe_model *m;
     const fhe_evk *evk;
@@ -227,21 +245,65 @@ struct Exec {
     cudaStream_t s;
     std::vector<u64 *> buf;               // per tensor: [B][n_ct][2][level+1][N]
     std::vector<std::vector<char>> host_stage;
+    Persist *pers = nullptr;              // non-null: pipeline mode
+    int cur_step = -1;
 
     long long ctst(int t) const { return 2ll * (m->tensors[t].level + 1) * m->ctx->N; }
     long long item(int t) const { return (long long)m->tensors[t].n_ct * ctst(t); }
 
     int alloc_t(int t) {
         if (buf[t]) return FHE_OK;
+        if (pers) return fhe_fail(FHE_E_INVAL, "internal: tensor without a buffer in pipeline mode");
         const size_t bytes = (size_t)B * item(t) * 8;
         FHE_CU(cudaMallocAsync((void **)&buf[t], bytes, s));
         return FHE_OK;
     }
     void release(int t) {
+        if (pers) return;
         if (buf[t] && t != m->output) {
             cudaFreeAsync(buf[t], s);
             buf[t] = nullptr;
         }
+    }
+    // a temporary of the current step (index idx): stream-ordered, or persistent
+    int tmp(int idx, size_t bytes, u64 **out) {
+        if (!pers) {
+            FHE_CU(cudaMallocAsync((void **)out, bytes, s));
+            return FHE_OK;
+        }
+        auto key = std::make_pair(cur_step, idx);
+        auto it = pers->tmp.find(key);
+        if (it == pers->tmp.end()) {
+            void *p;
+            FHE_TRY(dev_alloc(m->ctx, &p, bytes));
+            pers->owned.push_back(p);
+            it = pers->tmp.emplace(key, (u64 *)p).first;
+        }
+        *out = it->second;
+        return FHE_OK;
+    }
+    void tmp_free(void *p) {
+        if (!pers && p) cudaFreeAsync(p, s);
+    }
+    // a work list in device memory with the given host content
+    int work_list(const char *host, size_t bytes, char **out) {
+        if (!pers) {
+            host_stage.emplace_back(host, host + bytes);
+            FHE_CU(cudaMallocAsync((void **)out, bytes + 16, s));
+            FHE_CU(cudaMemcpyAsync(*out, host_stage.back().data(), bytes, cudaMemcpyHostToDevice, s));
+            return FHE_OK;
+        }
+        auto key = std::make_pair(pers->variant, cur_step);
+        auto it = pers->lists.find(key);
+        if (it == pers->lists.end()) {
+            void *p;
+            FHE_TRY(dev_alloc(m->ctx, &p, bytes + 16));
+            pers->owned.push_back(p);
+            FHE_CU(cudaMemcpy(p, host, bytes, cudaMemcpyHostToDevice));
+            it = pers->lists.emplace(key, (char *)p).first;
+        }
+        *out = it->second;
+        return FHE_OK;
     }
     const u64 *key_for(int step, int *err) {
         const int k = galois_of_step(m->ctx, step);
@@ -253,6 +315,7 @@ struct Exec {
         *err = FHE_OK;
         return it->second;
     }
+    int keyswitch(const KsArgs &a) { return op_keyswitch(m->ctx, a, s, pers ? pers->ks_ws : nullptr); }
 
     // out = base + rot(x, step) for n items of one tensor-like layout
     int rotate_items(const u64 *x, long long x_item, int step, const u64 *base, long long base_item, u64 *out,
@@ -276,7 +339,7 @@ struct Exec {
         a.out_item = out_item;
         a.n_items = n;
         a.level = level;
-        return op_keyswitch(m->ctx, a, s);
+        return keyswitch(a);
     }
 
     int linear(const MStep &st) {
@@ -287,10 +350,11 @@ struct Exec {
         const u64 *in = buf[st.src];
         u64 *out = buf[st.dst];
         const long long in_item = item(st.src), out_item = item(st.dst);
+        int ti = 0;
         // baby-step rotations of the inputs
         std::vector<u64 *> rb(L.baby_ct.size(), nullptr);
         for (size_t k = 0; k < L.baby_ct.size(); k++) {
-            FHE_CU(cudaMallocAsync((void **)&rb[k], (size_t)B * cs * 8, s));
+            FHE_TRY(tmp(ti++, (size_t)B * cs * 8, &rb[k]));
             FHE_TRY(rotate_items(in + L.baby_ct[k] * cs, in_item, L.baby_step[k], nullptr, 0, rb[k], cs, B, lv));
         }
         // sources: the input ciphertexts, then the baby-step rotations
@@ -317,7 +381,7 @@ struct Exec {
                 G.out_item = out_item;
                 G.bias = L.bias_pt[o];
             } else {
-                FHE_CU(cudaMallocAsync((void **)&acc[g], (size_t)B * cs * 8, s));
+                FHE_TRY(tmp(ti++, (size_t)B * cs * 8, &acc[g]));
                 G.out = acc[g];
                 G.out_item = cs;
                 G.bias = nullptr;
@@ -333,17 +397,14 @@ struct Exec {
             }
             G.term_end = (int)ht.size();
         }
-        // stage the work lists through host memory
         const size_t gb = hg.size() * sizeof(MacGroup), tb = ht.size() * sizeof(MacTerm),
                      sb = hs.size() * sizeof(MacSrc);
-        host_stage.emplace_back(gb + tb + sb + 16);
-        char *hsb = host_stage.back().data();
-        memcpy(hsb, hg.data(), gb);
-        if (tb) memcpy(hsb + gb, ht.data(), tb);
-        memcpy(hsb + gb + tb, hs.data(), sb);
+        std::vector<char> lst(gb + tb + sb);
+        memcpy(lst.data(), hg.data(), gb);
+        if (tb) memcpy(lst.data() + gb, ht.data(), tb);
+        memcpy(lst.data() + gb + tb, hs.data(), sb);
         char *dw;
-        FHE_CU(cudaMallocAsync((void **)&dw, gb + tb + sb + 16, s));
-        FHE_CU(cudaMemcpyAsync(dw, hsb, gb + tb + sb, cudaMemcpyHostToDevice, s));
+        FHE_TRY(work_list(lst.data(), lst.size(), &dw));
         MacArgs ma;
         ma.groups = (const MacGroup *)dw;
         ma.terms = (const MacTerm *)(dw + gb);
@@ -358,10 +419,9 @@ struct Exec {
             u64 *o = out + L.g_out[g] * cs;
             FHE_TRY(rotate_items(acc[g], cs, L.g_giant[g], o, out_item, o, out_item, B, lv));
         }
-        for (auto p : rb) cudaFreeAsync(p, s);
-        for (auto p : acc)
-            if (p) cudaFreeAsync(p, s);
-        cudaFreeAsync(dw, s);
+        for (auto p : rb) tmp_free(p);
+        for (auto p : acc) tmp_free(p);
+        if (!pers) cudaFreeAsync(dw, s);
         return FHE_OK;
     }
 
@@ -371,7 +431,7 @@ struct Exec {
         const long long nlN = (long long)(lv + 1) * c->N;
         const int n = B * m->tensors[st.src].n_ct;
         u64 *t3;
-        FHE_CU(cudaMallocAsync((void **)&t3, (size_t)n * 3 * nlN * 8, s));
+        FHE_TRY(tmp(0, (size_t)n * 3 * nlN * 8, &t3));
         FHE_CU(launch_square_act(c->dc, buf[st.src], 2 * nlN, st.c1, st.c0, t3, 3 * nlN, n, lv, s));
         KsArgs a;
         memset(&a, 0, sizeof(a));
@@ -387,8 +447,8 @@ struct Exec {
         a.out_item = 2 * nlN;
         a.n_items = n;
         a.level = lv;
-        FHE_TRY(op_keyswitch(c, a, s));
-        cudaFreeAsync(t3, s);
+        FHE_TRY(keyswitch(a));
+        tmp_free(t3);
         return FHE_OK;
     }
 
@@ -397,7 +457,7 @@ struct Exec {
         const long long cs = ctst(st.src);
         const int n = B * m->tensors[st.src].n_ct;
         const u64 *cur = buf[st.src];
-        u64 *tmp = nullptr;
+        u64 *prev_tmp = nullptr;
         if (st.rot.empty()) {
             FHE_CU(cudaMemcpyAsync(buf[st.dst], cur, (size_t)n * cs * 8, cudaMemcpyDeviceToDevice, s));
             return FHE_OK;
@@ -407,11 +467,11 @@ struct Exec {
             if (k + 1 == st.rot.size()) {
                 nxt = buf[st.dst];
             } else {
-                FHE_CU(cudaMallocAsync((void **)&nxt, (size_t)n * cs * 8, s));
+                FHE_TRY(tmp((int)(k & 1), (size_t)n * cs * 8, &nxt));
             }
             FHE_TRY(rotate_items(cur, cs, st.rot[k], cur, cs, nxt, cs, n, lv));
-            if (tmp) cudaFreeAsync(tmp, s);
-            tmp = (k + 1 == st.rot.size()) ? nullptr : nxt;
+            if (prev_tmp) tmp_free(prev_tmp);
+            prev_tmp = (k + 1 == st.rot.size()) ? nullptr : nxt;
             cur = nxt;
         }
         return FHE_OK;
@@ -420,6 +480,7 @@ struct Exec {
     int step(int i) {
         const MStep &st = m->steps[i];
         fhe_ctx *c = m->ctx;
+        cur_step = i;
         FHE_TRY(alloc_t(st.dst));
         const MTensor &ti = m->tensors[st.src];
         const int n = B * ti.n_ct;
@@ -428,7 +489,8 @@ struct Exec {
             FHE_TRY(linear(st));
             break;
         case FHE_STEP_RESCALE:
-            FHE_TRY(op_rescale(c, buf[st.src], ctst(st.src), buf[st.dst], ctst(st.dst), n, 2, ti.level, s));
+            FHE_TRY(op_rescale(c, buf[st.src], ctst(st.src), buf[st.dst], ctst(st.dst), n, 2, ti.level, s,
+                               pers ? pers->rs_ws : nullptr));
             break;
         case FHE_STEP_ACT:
             FHE_TRY(act(st));
@@ -582,5 +644,279 @@ extern "C" int fhe_eval_quad_act(fhe_ctx *c, const fhe_model *m, const fhe_evk *
         io[k]->scale = res[k]->scale;
         fhe_ct_free(res[k]);
     }
+    return FHE_OK;
+}
+
+// ================================================================ pipeline
+//
+// Continuous, mixed-level batching.  The program is cut after every
+// activation (and the rescale that follows it) into S segments.  Groups of
+// `group` images flow through the segments: at each tick every segment k
+// processes the group that entered k ticks earlier, so up to S * group images
+// at S different levels are in flight, and a new group can enter every tick
+// while earlier ones are still on the GPU.  The segments of a tick run
+// concurrently on their own streams; each tick's launches are captured once
+// per buffer parity into a CUDA graph and replayed.  Tensors live across a cut
+// are double-buffered by parity: at tick T segment k reads cut k's buffers
+// [T % 2] and writes cut k+1's buffers [(T + 1) % 2].
+
+namespace {
+
+struct Segment {
+    int s0 = 0, s1 = 0;
+    std::vector<int> ins, outs, pass, internal;
+    cudaStream_t st = nullptr;
+    cudaEvent_t done = nullptr;
+    Persist pers;
+    std::map<int, u64 *> ibuf;
+};
+
+}  // namespace
+
+struct fhe_pipeline {
+    fhe_ctx *ctx = nullptr;
+    fhe_model *m = nullptr;
+    const fhe_evk *evk = nullptr;
+    int g = 1;
+    int S = 0;
+    bool graphs = true;
+    std::vector<int> cuts;
+    std::vector<std::map<int, u64 *>> cutbuf[2];
+    std::vector<std::unique_ptr<Segment>> seg;
+    cudaStream_t main = nullptr;
+    cudaEvent_t fork = nullptr;
+    cudaGraphExec_t exec[2] = {nullptr, nullptr};
+    long long tick = 0;
+    std::vector<int> entered;   // images entered at each tick
+    std::vector<void *> owned;
+
+    ~fhe_pipeline() {
+        if (main) cudaStreamSynchronize(main);
+        for (auto &e : exec)
+            if (e) cudaGraphExecDestroy(e);
+        for (auto &sg : seg) {
+            if (sg->st) cudaStreamDestroy(sg->st);
+            if (sg->done) cudaEventDestroy(sg->done);
+        }
+        seg.clear();
+        if (fork) cudaEventDestroy(fork);
+        if (main) cudaStreamDestroy(main);
+        for (void *p : owned) cudaFree(p);
+    }
+};
+
+namespace {
+
+int pipe_alloc(fhe_pipeline *p, size_t bytes, u64 **out) {
+    void *d;
+    FHE_TRY(dev_alloc(p->ctx, &d, bytes));
+    p->owned.push_back(d);
+    FHE_CU(cudaMemset(d, 0, bytes));
+    *out = (u64 *)d;
+    return FHE_OK;
+}
+
+int run_segment(fhe_pipeline *p, int k, int parity) {
+    Segment &sg = *p->seg[k];
+    fhe_model *m = p->m;
+    Exec e;
+    e.m = m;
+    e.evk = p->evk;
+    e.B = p->g;
+    e.s = sg.st;
+    e.buf.assign(m->tensors.size(), nullptr);
+    e.pers = &sg.pers;
+    sg.pers.variant = parity;
+    for (int t : sg.ins) e.buf[t] = p->cutbuf[parity][k].at(t);
+    for (int t : sg.outs) e.buf[t] = p->cutbuf[1 - parity][k + 1].at(t);
+    for (auto &kv : sg.ibuf) e.buf[kv.first] = kv.second;
+    for (int i = sg.s0; i < sg.s1; i++) FHE_TRY(e.step(i));
+    for (int t : sg.pass) {
+        const size_t bytes = (size_t)p->g * e.item(t) * 8;
+        FHE_CU(cudaMemcpyAsync(p->cutbuf[1 - parity][k + 1].at(t), p->cutbuf[parity][k].at(t), bytes,
+                               cudaMemcpyDeviceToDevice, sg.st));
+    }
+    return FHE_OK;
+}
+
+// all segments of one tick: fork from the main stream, join back into it
+int run_tick(fhe_pipeline *p, int parity) {
+    FHE_CU(cudaEventRecord(p->fork, p->main));
+    for (int k = 0; k < p->S; k++) {
+        FHE_CU(cudaStreamWaitEvent(p->seg[k]->st, p->fork, 0));
+        FHE_TRY(run_segment(p, k, parity));
+        FHE_CU(cudaEventRecord(p->seg[k]->done, p->seg[k]->st));
+    }
+    for (int k = 0; k < p->S; k++) FHE_CU(cudaStreamWaitEvent(p->main, p->seg[k]->done, 0));
+    return FHE_OK;
+}
+
+}  // namespace
+
+extern "C" int fhe_pipeline_create(fhe_ctx *c, const fhe_model *mc, const fhe_evk *evk, int group, int use_graphs,
+                                   fhe_pipeline **out) {
+    if (!c || !mc || !evk || !out || group < 1) return fhe_fail(FHE_E_INVAL, "bad argument");
+    fhe_model *m = const_cast<fhe_model *>(mc);
+    FHE_CU(cudaSetDevice(c->dev));
+    std::unique_ptr<fhe_pipeline> p(new fhe_pipeline());
+    p->ctx = c;
+    p->m = m;
+    p->evk = evk;
+    p->g = group;
+    p->graphs = use_graphs != 0;
+    const int n = (int)m->steps.size();
+    // cuts after each activation (after its rescale, when one follows)
+    p->cuts.push_back(0);
+    for (int i = 0; i < n; i++) {
+        if (m->steps[i].kind != FHE_STEP_ACT) continue;
+        int c_at = i + 1;
+        if (c_at < n && m->steps[c_at].kind == FHE_STEP_RESCALE && m->steps[c_at].src == m->steps[i].dst) c_at++;
+        if (c_at < n && c_at > p->cuts.back()) p->cuts.push_back(c_at);
+    }
+    p->cuts.push_back(n);
+    p->S = (int)p->cuts.size() - 1;
+    // definition and last use of every tensor
+    const int nt = (int)m->tensors.size();
+    std::vector<int> def(nt, -2), last(nt, -1);
+    def[m->input] = -1;
+    for (int i = 0; i < n; i++) {
+        def[m->steps[i].dst] = i;
+        last[m->steps[i].src] = std::max(last[m->steps[i].src], i);
+        if (m->steps[i].src2 >= 0) last[m->steps[i].src2] = std::max(last[m->steps[i].src2], i);
+    }
+    last[m->output] = n;
+    auto live = [&](int cpos) {
+        std::vector<int> r;
+        for (int t = 0; t < nt; t++)
+            if (def[t] >= -1 && def[t] < cpos && last[t] >= cpos) r.push_back(t);
+        return r;
+    };
+    for (int par = 0; par < 2; par++) p->cutbuf[par].resize(p->S + 1);
+    for (int ci = 0; ci <= p->S; ci++)
+        for (int t : live(p->cuts[ci]))
+            for (int par = 0; par < 2; par++) {
+                u64 *b;
+                FHE_TRY(pipe_alloc(p.get(), (size_t)group * m->tensors[t].n_ct * 2 * (m->tensors[t].level + 1) *
+                                                c->N * 8, &b));
+                p->cutbuf[par][ci][t] = b;
+            }
+    FHE_CU(cudaStreamCreateWithFlags(&p->main, cudaStreamNonBlocking));
+    FHE_CU(cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming));
+    for (int k = 0; k < p->S; k++) {
+        std::unique_ptr<Segment> sg(new Segment());
+        sg->s0 = p->cuts[k];
+        sg->s1 = p->cuts[k + 1];
+        sg->ins = live(sg->s0);
+        std::vector<int> lo = live(sg->s1);
+        for (int t : lo) {
+            if (def[t] >= sg->s0 && def[t] < sg->s1) sg->outs.push_back(t);
+            else sg->pass.push_back(t);
+        }
+        size_t ks_words = 0, rs_words = 0;
+        for (int i = sg->s0; i < sg->s1; i++) {
+            const MStep &st = m->steps[i];
+            const MTensor &ti = m->tensors[st.src];
+            const int t = st.dst;
+            if (std::find(lo.begin(), lo.end(), t) == lo.end()) {
+                sg->internal.push_back(t);
+                u64 *b;
+                FHE_TRY(pipe_alloc(p.get(), (size_t)group * m->tensors[t].n_ct * 2 * (m->tensors[t].level + 1) *
+                                                c->N * 8, &b));
+                sg->ibuf[t] = b;
+            }
+            int items = 0;
+            if (st.kind == FHE_STEP_LINEAR) items = group;
+            if (st.kind == FHE_STEP_ACT || st.kind == FHE_STEP_ROTSUM) items = group * ti.n_ct;
+            ks_words = std::max(ks_words, (size_t)items * ks_workspace_words(c->dc, ti.level));
+            if (st.kind == FHE_STEP_RESCALE) rs_words = std::max(rs_words, (size_t)group * ti.n_ct * 2 * (size_t)c->N);
+        }
+        if (ks_words) FHE_TRY(pipe_alloc(p.get(), ks_words * 8, &sg->pers.ks_ws));
+        if (rs_words) FHE_TRY(pipe_alloc(p.get(), rs_words * 8, &sg->pers.rs_ws));
+        FHE_CU(cudaStreamCreateWithFlags(&sg->st, cudaStreamNonBlocking));
+        FHE_CU(cudaEventCreateWithFlags(&sg->done, cudaEventDisableTiming));
+        p->seg.push_back(std::move(sg));
+    }
+    FHE_CU(cudaDeviceSynchronize());
+    *out = p.release();
+    return FHE_OK;
+}
+
+extern "C" int fhe_pipeline_info(const fhe_pipeline *p, int *n_segments, int *group, int *n_in_ct, int *n_out_ct) {
+    if (!p) return fhe_fail(FHE_E_INVAL, "null argument");
+    if (n_segments) *n_segments = p->S;
+    if (group) *group = p->g;
+    if (n_in_ct) *n_in_ct = p->m->tensors[p->m->input].n_ct;
+    if (n_out_ct) *n_out_ct = p->m->tensors[p->m->output].n_ct;
+    return FHE_OK;
+}
+
+extern "C" int fhe_pipeline_tick(fhe_pipeline *p, const fhe_ct *const *in, size_t n_in, fhe_ct **out, size_t *n_out,
+                                 int64_t *out_tag) {
+    if (!p || !n_out || !out_tag || (n_in && !in) || n_in > (size_t)p->g) return fhe_fail(FHE_E_INVAL, "bad argument");
+    fhe_ctx *c = p->ctx;
+    fhe_model *m = p->m;
+    FHE_CU(cudaSetDevice(c->dev));
+    const int par = (int)(p->tick & 1);
+    const MTensor &ti = m->tensors[m->input];
+    const long long cs_in = 2ll * (ti.level + 1) * c->N;
+    for (size_t k = 0; k < n_in * ti.n_ct; k++) {
+        if (!in[k] || in[k]->level != ti.level || in[k]->n_poly != 2)
+            return fhe_fail(FHE_E_LEVEL, "input ciphertext level / shape does not match the model");
+    }
+    for (size_t k = 0; k < n_in * ti.n_ct; k++)
+        FHE_CU(cudaMemcpyAsync(p->cutbuf[par][0].at(m->input) + k * cs_in, in[k]->d, cs_in * 8,
+                               cudaMemcpyDeviceToDevice, p->main));
+    p->entered.push_back((int)n_in);
+    if (p->graphs && p->tick >= 2) {
+        if (!p->exec[par]) {
+            cudaGraph_t g;
+            FHE_CU(cudaStreamBeginCapture(p->main, cudaStreamCaptureModeRelaxed));
+            int rc = run_tick(p, par);
+            cudaError_t ce = cudaStreamEndCapture(p->main, &g);
+            if (rc != FHE_OK) return rc;
+            if (ce != cudaSuccess) return fhe_fail(FHE_E_CUDA, std::string("capture: ") + cudaGetErrorString(ce));
+            ce = cudaGraphInstantiate(&p->exec[par], g, 0);
+            cudaGraphDestroy(g);
+            if (ce != cudaSuccess) return fhe_fail(FHE_E_CUDA, std::string("instantiate: ") + cudaGetErrorString(ce));
+        }
+        FHE_CU(cudaGraphLaunch(p->exec[par], p->main));
+    } else {
+        FHE_TRY(run_tick(p, par));
+    }
+    // the group that entered S-1 ticks ago leaves now
+    *n_out = 0;
+    *out_tag = -1;
+    const long long entry = p->tick - (p->S - 1);
+    if (entry >= 0 && p->entered[entry] > 0) {
+        const MTensor &to = m->tensors[m->output];
+        const long long cs = 2ll * (to.level + 1) * c->N;
+        const u64 *src = p->cutbuf[1 - par][p->S].at(m->output);
+        const size_t cnt = (size_t)p->entered[entry] * to.n_ct;
+        for (size_t k = 0; k < cnt; k++) {
+            fhe_ct *o = new fhe_ct();
+            o->ctx = c;
+            o->level = to.level;
+            o->n_poly = 2;
+            o->scale = to.scale;
+            if (dev_alloc(c, (void **)&o->d, cs * 8) != FHE_OK) {
+                delete o;
+                for (size_t r = 0; r < k; r++) fhe_ct_free(out[r]);
+                return FHE_E_OOM;
+            }
+            FHE_CU(cudaMemcpyAsync(o->d, src + k * cs, cs * 8, cudaMemcpyDeviceToDevice, p->main));
+            out[k] = o;
+        }
+        *n_out = (size_t)p->entered[entry];
+        *out_tag = entry;
+    }
+    FHE_CU(cudaStreamSynchronize(p->main));
+    p->tick++;
+    return FHE_OK;
+}
+
+extern "C" int fhe_pipeline_free(fhe_pipeline *p) {
+    if (!p) return FHE_OK;
+    cudaSetDevice(p->ctx->dev);
+    delete p;
     return FHE_OK;
 }
