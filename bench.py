@@ -209,51 +209,83 @@ def run_ours(args, rank, world):
         infer(cts[:n_in], 1)
     ms_single = timed(lambda: infer(cts[:n_in], 1), args.steps)
 
-    # batched
+    # uniform batch: B images through the whole network together
     for _ in range(args.warmup):
         infer(cts, B)
+    ms_uniform = timed(lambda: infer(cts, B), args.steps)
+
+    # mixed levels: a pipeline of S segments with a group of g images entering
+    # every tick, about B images in flight at S different levels; one step is
+    # S ticks (as many images finish as one uniform pass of S*g images)
+    probe = F.fhe_pipeline_create(ctx, model, evk, 1, False)
+    S = F.fhe_pipeline_info(probe)[0]
+    F.fhe_pipeline_free(probe)
+    g = max(1, -(-B // S))
+    pipe = F.fhe_pipeline_create(ctx, model, evk, g, True)
+    state = {"next": 0}
+
+    def tick(handles_of):
+        i0 = state["next"] % B
+        grp = [h for i in range(g) for h in handles_of((i0 + i) % B)]
+        state["next"] += g
+        outs, n_done, _ = F.fhe_pipeline_tick(pipe, grp, g, g * n_out)
+        for h in outs:
+            F.fhe_ct_free(h)
+
+    def pipe_step():
+        for _ in range(S):
+            tick(lambda i: cts[i * n_in:(i + 1) * n_in])
+
+    for _ in range(max(1, args.warmup)):
+        pipe_step()
     clk = Clocks(dev)
     clk.start()
     l0 = F.fhe_kernel_launches()
     torch.cuda.nvtx.range_push("bench_timed")
-    ms_batch = timed(lambda: infer(cts, B), args.steps)
+    ms_batch = timed(pipe_step, args.steps)
     torch.cuda.nvtx.range_pop()
     launches = (F.fhe_kernel_launches() - l0) // args.steps
     clocks = clk.stop()
 
-    # end to end through the public API with host buffers: import (H2D + NTT),
-    # infer, export (inverse NTT + D2H) every step
+    # end to end through the public API with host buffers: every tick imports
+    # its group (H2D + NTT), runs, and exports the finished group (inverse
+    # NTT + D2H)
     host_in = [F.fhe_ct_export(h, N)[0] for h in cts]
     lvl_in, sc_in = pre["L"], 2.0 ** pre["log_scale"]
 
     def e2e_step():
-        hs = [F.fhe_ct_import(ctx, b, lvl_in, sc_in) for b in host_in]
-        outs = F.fhe_infer(ctx, model, evk, hs, B, n_out, stream)
-        for h in outs:
-            F.fhe_ct_export(h, N)
-            F.fhe_ct_free(h)
-        for h in hs:
-            F.fhe_ct_free(h)
+        for _ in range(S):
+            i0 = state["next"] % B
+            hs = [F.fhe_ct_import(ctx, host_in[((i0 + i) % B) * n_in + k], lvl_in, sc_in)
+                  for i in range(g) for k in range(n_in)]
+            state["next"] += g
+            outs, n_done, _ = F.fhe_pipeline_tick(pipe, hs, g, g * n_out)
+            for h in outs:
+                F.fhe_ct_export(h, N)
+                F.fhe_ct_free(h)
+            for h in hs:
+                F.fhe_ct_free(h)
 
-    e2e_step()
     ms_e2e = timed(e2e_step, max(1, args.steps))
+    F.fhe_pipeline_free(pipe)
     out_level = prog.tensors[prog.output].level
-    h2d = sum(b.nbytes for b in host_in)
-    d2h = B * n_out * 2 * (out_level + 1) * N * 8
+    h2d = S * g * n_in * 2 * (pre["L"] + 1) * N * 8
+    d2h = S * g * n_out * 2 * (out_level + 1) * N * 8
 
     # key-switch roofline at the top level, batch of B (the pipeline that
     # dominates the step): algorithmic bytes per switched polynomial =
     # (l+1)W in + 2*beta*(l+1+alpha)W key / B + 2(l+1)W out, W = N*8
     lv = pre["L"]
-    ks_ms = F.fhe_profile_keyswitch(ctx, evk, lv, B, 3, stream)
+    ks_ms = F.fhe_profile_keyswitch(ctx, evk, lv, g, 3, stream)
     alpha = pre["alpha"]
     beta = (lv + alpha) // alpha
     W = N * 8
-    ks_bytes = B * ((lv + 1) * W + 2 * (lv + 1) * W) + 2 * beta * (lv + 1 + alpha) * W
+    ks_bytes = g * ((lv + 1) * W + 2 * (lv + 1) * W) + 2 * beta * (lv + 1 + alpha) * W
     ks_total = sum(ks_ms) / 1e3
     peak, peak_kind = _peaks()
     achieved = ks_bytes / ks_total / 1e9
-    img_s_batch = B * world / (ms_batch / 1e3)
+    img_s_batch = S * g * world / (ms_batch / 1e3)
+    img_s_uniform = B * world / (ms_uniform / 1e3)
     img_s_single = 1 * world / (ms_single / 1e3)
     n_ks, wks = program_ledger(prog, alpha)
 
@@ -274,8 +306,12 @@ def run_ours(args, rank, world):
             "workload": "ResNet-20 (16/32/64, 3x3 blocks, 1x1 stride-2 shortcuts), 32x32x3 seeded uniform "
                         "images, 10 classes; CKKS N=2^16, Delta=2^25, q0 40-bit + 20 x 50-bit, 3 x 58-bit "
                         "special primes, digit width 3; channel-packed layout",
-            "batch": B,
-            "mixed_levels": False,
+            "batch": S * g,
+            "mixed_levels": True,
+            "pipeline": "%d segments (cut after each activation), a group of %d images enters per tick; "
+                        "segments run on concurrent streams, each tick replayed from a CUDA graph" % (S, g),
+            "uniform_batch": B,
+            "uniform_batch_img_s": round(img_s_uniform, 4),
             "single_img_s": round(img_s_single, 4),
             "single_ms_per_img": round(ms_single, 3),
             "batched_over_single": round(img_s_batch / img_s_single, 4),
@@ -286,10 +322,10 @@ def run_ours(args, rank, world):
             "parallelism": "replicas" if world > 1 else "single",
         },
         "clocks": clocks,
-        "e2e": {"value": round(B * world / (ms_e2e / 1e3), 4), "unit": "img/s",
+        "e2e": {"value": round(S * g * world / (ms_e2e / 1e3), 4), "unit": "img/s",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
-        "roofline": {"bound": "hbm", "kernel": "hybrid key switch (8 fused kernels), level %d, %d items" % (lv, B),
+        "roofline": {"bound": "hbm", "kernel": "hybrid key switch (9 kernels), level %d, %d items (one group)" % (lv, g),
                      "achieved": round(achieved, 1), "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": None,
                      "algorithmic_bytes": int(ks_bytes),

@@ -21,6 +21,7 @@
 // number of kernel launches issued by this library (for launch accounting)
 static std::atomic<unsigned long long> g_launches{0};
 unsigned long long fhe_launch_counter() { return g_launches.load(); }
+void fhe_launch_counter_add(long long n) { g_launches.fetch_add((unsigned long long)n); }
 #define COUNT_LAUNCH() g_launches.fetch_add(1, std::memory_order_relaxed)
 
 namespace {

@@ -10,6 +10,8 @@
 
 // kernel launches issued so far by this library (all launchers count)
 unsigned long long fhe_launch_counter();
+// graph replays add the kernels they launch (captured launches are not run)
+void fhe_launch_counter_add(long long n);
 
 // One prime of the chain q_0..q_L, p_0..p_{alpha-1}.
 struct PrimeTab {

@@ -686,6 +686,7 @@ struct fhe_pipeline {
     cudaStream_t main = nullptr;
     cudaEvent_t fork = nullptr;
     cudaGraphExec_t exec[2] = {nullptr, nullptr};
+    long long captured[2] = {0, 0};   // kernel launches in each graph
     long long tick = 0;
     std::vector<int> entered;   // images entered at each tick
     std::vector<void *> owned;
@@ -870,9 +871,12 @@ extern "C" int fhe_pipeline_tick(fhe_pipeline *p, const fhe_ct *const *in, size_
     if (p->graphs && p->tick >= 2) {
         if (!p->exec[par]) {
             cudaGraph_t g;
+            const unsigned long long l0 = fhe_launch_counter();
             FHE_CU(cudaStreamBeginCapture(p->main, cudaStreamCaptureModeRelaxed));
             int rc = run_tick(p, par);
             cudaError_t ce = cudaStreamEndCapture(p->main, &g);
+            p->captured[par] = (long long)(fhe_launch_counter() - l0);
+            fhe_launch_counter_add(-p->captured[par]);
             if (rc != FHE_OK) return rc;
             if (ce != cudaSuccess) return fhe_fail(FHE_E_CUDA, std::string("capture: ") + cudaGetErrorString(ce));
             ce = cudaGraphInstantiate(&p->exec[par], g, 0);
@@ -880,6 +884,7 @@ extern "C" int fhe_pipeline_tick(fhe_pipeline *p, const fhe_ct *const *in, size_
             if (ce != cudaSuccess) return fhe_fail(FHE_E_CUDA, std::string("instantiate: ") + cudaGetErrorString(ce));
         }
         FHE_CU(cudaGraphLaunch(p->exec[par], p->main));
+        fhe_launch_counter_add(p->captured[par]);
     } else {
         FHE_TRY(run_tick(p, par));
     }
