@@ -59,6 +59,7 @@ typedef struct fhe_pt fhe_pt;
 typedef struct fhe_ct fhe_ct;
 typedef struct fhe_model fhe_model;
 typedef struct fhe_pipeline fhe_pipeline;
+typedef struct fhe_server fhe_server;
 
 /*
  * Parameters (Table 4 and the appendix on FHE parameters: ring degree N,
@@ -274,6 +275,31 @@ int fhe_pipeline_info(const fhe_pipeline *pipe, int *n_segments, int *group, int
 int fhe_pipeline_tick(fhe_pipeline *pipe, const fhe_ct *const *in, size_t n_in, fhe_ct **out, size_t *n_out,
                       int64_t *out_tag);
 int fhe_pipeline_free(fhe_pipeline *pipe);
+
+/*
+ * Serving (continuous batching): one server per context and key set.  Each
+ * added model gets its own pipeline (above) and worker thread; requests are
+ * queued per model and admitted into the next tick of their model's pipeline
+ * while earlier requests are still inside it, and the workers of different
+ * models tick concurrently.  fhe_server_add_model admits a model only if
+ * cudaMemGetInfo reports at least reserve_bytes free (0: no check) and its
+ * pipeline can be allocated (else FHE_E_OOM).  Weight plaintexts and
+ * evaluation keys stay resident.
+ * fhe_server_submit takes ownership of the model's n_in_ct input ciphertexts
+ * of one image (they are freed once admitted) and returns a ticket.
+ * fhe_server_poll returns the request's n_out_ct output ciphertexts (new
+ * handles owned by the caller) once done (*n_out = 0 before; wait != 0
+ * blocks until done) and its latency from submit to completion.
+ * fhe_server_stats: completed requests and the p50 / p99 of their latency.
+ */
+int fhe_server_create(fhe_ctx *ctx, const fhe_evk *evk, fhe_server **out);
+int fhe_server_add_model(fhe_server *server, const fhe_model *model, int group, size_t reserve_bytes,
+                         int *model_id);
+int fhe_server_submit(fhe_server *server, int model_id, fhe_ct *const *in, uint64_t *ticket);
+int fhe_server_poll(fhe_server *server, uint64_t ticket, int wait, fhe_ct **out, size_t cap, size_t *n_out,
+                    double *latency_ms);
+int fhe_server_stats(fhe_server *server, uint64_t *completed, double *p50_ms, double *p99_ms);
+int fhe_server_destroy(fhe_server *server);
 
 /* ------------------------------------------------------ test hooks */
 

@@ -101,6 +101,12 @@ def lib() -> ctypes.CDLL:
             "fhe_pipeline_tick": (c_int, [V, PP, c_size, PP, ctypes.POINTER(c_size),
                                           ctypes.POINTER(ctypes.c_int64)]),
             "fhe_pipeline_free": (c_int, [V]),
+            "fhe_server_create": (c_int, [V, V, PP]),
+            "fhe_server_add_model": (c_int, [V, V, c_int, c_size, ctypes.POINTER(c_int)]),
+            "fhe_server_submit": (c_int, [V, c_int, PP, ctypes.POINTER(c_u64)]),
+            "fhe_server_poll": (c_int, [V, c_u64, c_int, PP, c_size, ctypes.POINTER(c_size), P_DBL]),
+            "fhe_server_stats": (c_int, [V, ctypes.POINTER(c_u64), P_DBL, P_DBL]),
+            "fhe_server_destroy": (c_int, [V]),
             "fhe_ntt_device": (c_int, [V, V, c_size, P_I32, c_int, V]),
             "fhe_evk_export": (c_int, [V, c_int, P_U64, c_size, ctypes.POINTER(c_size)]),
             "fhe_sk_export": (c_int, [V, P_U64, c_size]),
@@ -353,6 +359,42 @@ def fhe_pipeline_free(pipe):
     _check(lib().fhe_pipeline_free(pipe))
 
 
+def fhe_server_create(ctx, evk) -> int:
+    h = c_void()
+    _check(lib().fhe_server_create(ctx, evk, ctypes.byref(h)))
+    return h.value
+
+
+def fhe_server_add_model(server, model, group: int, reserve_bytes: int = 0) -> int:
+    mid = c_int()
+    _check(lib().fhe_server_add_model(server, model, group, reserve_bytes, ctypes.byref(mid)))
+    return mid.value
+
+
+def fhe_server_submit(server, model_id: int, cts) -> int:
+    t = c_u64()
+    _check(lib().fhe_server_submit(server, model_id, _handles(cts), ctypes.byref(t)))
+    return t.value
+
+
+def fhe_server_poll(server, ticket: int, wait: bool, cap: int) -> Tuple[List[int], float]:
+    """returns (output handles, latency ms); no handles while pending"""
+    out = (c_void * max(cap, 1))()
+    n, lat = c_size(), c_double()
+    _check(lib().fhe_server_poll(server, ticket, int(wait), out, cap, ctypes.byref(n), ctypes.byref(lat)))
+    return [out[i] for i in range(n.value)], lat.value
+
+
+def fhe_server_stats(server) -> Tuple[int, float, float]:
+    n, p50, p99 = c_u64(), c_double(), c_double()
+    _check(lib().fhe_server_stats(server, ctypes.byref(n), ctypes.byref(p50), ctypes.byref(p99)))
+    return n.value, p50.value, p99.value
+
+
+def fhe_server_destroy(server):
+    _check(lib().fhe_server_destroy(server))
+
+
 # ------------------------------------------------------------------ test hooks
 
 def fhe_ntt_device(ctx, dev_ptr: int, prime_idx: Sequence[int], inverse: bool, stream=None):
@@ -387,4 +429,5 @@ EXPORTED = ["fhe_last_error", "fhe_kernel_launches", "fhe_ctx_create", "fhe_ctx_
             "fhe_model_free", "fhe_eval_conv", "fhe_eval_quad_act", "fhe_eval_pool_dense", "fhe_infer",
             "fhe_ntt_device", "fhe_evk_export", "fhe_sk_export", "fhe_encode_coeffs",
             "fhe_profile_keyswitch", "fhe_rescale_noalloc", "fhe_pipeline_create", "fhe_pipeline_info",
-            "fhe_pipeline_tick", "fhe_pipeline_free"]
+            "fhe_pipeline_tick", "fhe_pipeline_free", "fhe_server_create", "fhe_server_add_model",
+            "fhe_server_submit", "fhe_server_poll", "fhe_server_stats", "fhe_server_destroy"]

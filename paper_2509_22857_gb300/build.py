@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libfhecnn.so")
-SOURCES = ["kernels.cu", "context.cu", "model.cu", "noalloc.cu"]
+SOURCES = ["kernels.cu", "context.cu", "model.cu", "noalloc.cu", "server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

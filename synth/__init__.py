@@ -99,7 +99,47 @@ def resnet_mini() -> List[Dict]:
     return resnet((4, 8, 16), 1, 8, 10)
 
 
-ARCHS = {"tiny": tiny, "resnet20": resnet20, "resnet_mini": resnet_mini}
+def vgg(cfg=(64, "M", 128, "M", 256, 256, "M", 512, 512, "M", 512, 512, "M"), in_hw=32,
+        fc=(512, 512), num_classes=10) -> List[Dict]:
+    """VGG-style network: 3x3 convolutions (+BN, activation) with 2x2 average
+    pools ("M"), then dense layers with activations, then the classifier."""
+    net = [{"op": "input", "c": 3, "h": in_hw, "w": in_hw}]
+
+    def add(node):
+        net.append(node)
+        return len(net) - 1
+
+    x, cin, hw = 0, 3, in_hw
+    for i, v in enumerate(cfg):
+        if v == "M":
+            x = add({"op": "pool", "src": x, "k": 2})
+            hw //= 2
+        else:
+            x = add(_conv(x, cin, v, 3, 1, 1, "conv%d" % (i + 1)))
+            x = add({"op": "act", "src": x})
+            cin = v
+    feat = cin * hw * hw
+    for j, f in enumerate(fc):
+        x = add({"op": "dense", "src": x, "cin": feat, "cout": f, "name": "fc%d" % (j + 1)})
+        x = add({"op": "act", "src": x})
+        feat = f
+    add({"op": "dense", "src": x, "cin": feat, "cout": num_classes, "name": "fc%d" % (len(fc) + 1)})
+    return net
+
+
+def vgg11(num_classes: int = 10) -> List[Dict]:
+    """VGG-11 (configuration A: 8 convolutions 64-128-256-256-512-512-512-512,
+    5 average pools, dense 512-512-num_classes) for 32x32x3."""
+    return vgg()
+
+
+def vgg_mini() -> List[Dict]:
+    """A VGG with the same structure at a small size (8x8x3, 4/8 channels,
+    3 pools, dense 8-8-10) for full-network parity tests."""
+    return vgg(cfg=(4, "M", 8, "M", "M"), in_hw=8, fc=(8,), num_classes=10)
+
+
+ARCHS = {"tiny": tiny, "resnet20": resnet20, "resnet_mini": resnet_mini, "vgg11": vgg11, "vgg_mini": vgg_mini}
 
 
 # ------------------------------------------------------------- parameters
@@ -143,5 +183,6 @@ def enc_seed(image_index: int, ct_index: int) -> int:
 PRESETS = {
     "tiny": dict(logn=13, L=4, q_bits=40, q0_bits=40, p_bits=40, alpha=1, log_scale=40),
     "resnet_mini": dict(logn=12, L=8, q_bits=50, q0_bits=40, p_bits=58, alpha=3, log_scale=25),
+    "vgg11": dict(logn=16, L=11, q_bits=50, q0_bits=40, p_bits=58, alpha=3, log_scale=25),
     "resnet20": dict(logn=16, L=20, q_bits=50, q0_bits=40, p_bits=58, alpha=3, log_scale=25),
 }

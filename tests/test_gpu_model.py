@@ -10,7 +10,8 @@ from oracle import cnn
 
 pytestmark = pytest.mark.gpu
 
-CASES = {"tiny": ("tiny", "tiny", "hw"), "mini": ("resnet_mini", "resnet_mini", "packed")}
+CASES = {"tiny": ("tiny", "tiny", "hw"), "mini": ("resnet_mini", "resnet_mini", "packed"),
+         "vgg_mini": ("vgg_mini", "resnet_mini", "packed")}
 
 
 class Setup:

@@ -53,6 +53,10 @@ def test_mini_resnet_program_matches_oracle():
     _check(*_both("resnet_mini", "resnet_mini", "packed"))
 
 
+def test_mini_vgg_program_matches_oracle():
+    _check(*_both("vgg_mini", "resnet_mini", "packed"))
+
+
 @pytest.mark.slow
 def test_resnet20_program_matches_oracle():
     po, pm = _both("resnet20", "resnet20", "packed")
