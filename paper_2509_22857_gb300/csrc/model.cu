@@ -838,6 +838,17 @@ extern "C" int fhe_pipeline_create(fhe_ctx *c, const fhe_model *mc, const fhe_ev
         p->seg.push_back(std::move(sg));
     }
     FHE_CU(cudaDeviceSynchronize());
+    if (p->graphs) {
+        // capture both parities' graphs now, on an empty pipeline, so that no
+        // capture happens later while other threads use the device
+        for (int k = 0; k < 4; k++) {
+            size_t n_done = 0;
+            int64_t tag = -1;
+            FHE_TRY(fhe_pipeline_tick(p.get(), nullptr, 0, nullptr, &n_done, &tag));
+        }
+        p->tick = 0;
+        p->entered.clear();
+    }
     *out = p.release();
     return FHE_OK;
 }
@@ -868,7 +879,7 @@ extern "C" int fhe_pipeline_tick(fhe_pipeline *p, const fhe_ct *const *in, size_
         FHE_CU(cudaMemcpyAsync(p->cutbuf[par][0].at(m->input) + k * cs_in, in[k]->d, cs_in * 8,
                                cudaMemcpyDeviceToDevice, p->main));
     p->entered.push_back((int)n_in);
-    if (p->graphs && p->tick >= 2) {
+    if (p->graphs && (p->exec[par] || p->tick >= 2)) {
         if (!p->exec[par]) {
             cudaGraph_t g;
             const unsigned long long l0 = fhe_launch_counter();

@@ -41,6 +41,18 @@ def test_server_results_equal_alone():
         return cts
 
     server = F.fhe_server_create(ctx, evk)
+    try:
+        _serve(F, ctx, evk, server, models, progs, encrypt, N)
+    finally:
+        F.fhe_server_destroy(server)
+        for m in models:
+            F.fhe_model_free(m)
+        F.fhe_evk_free(evk)
+        F.fhe_sk_free(sk)
+        F.fhe_ctx_destroy(ctx)
+
+
+def _serve(F, ctx, evk, server, models, progs, encrypt, N):
     mids = [F.fhe_server_add_model(server, m, 2) for m in models]
     # a stream of requests: model picked round robin with a 2:1 mix, small
     # random gaps so later requests arrive while earlier ones are in flight
@@ -65,9 +77,3 @@ def test_server_results_equal_alone():
     # an unknown ticket is an error, not a hang
     with pytest.raises(F.FheError):
         F.fhe_server_poll(server, 10 ** 9, False, 1)
-    F.fhe_server_destroy(server)
-    for m in models:
-        F.fhe_model_free(m)
-    F.fhe_evk_free(evk)
-    F.fhe_sk_free(sk)
-    F.fhe_ctx_destroy(ctx)
