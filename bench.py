@@ -86,6 +86,22 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(ms: float, world: int, device: str = "cuda") -> float:
+    """slowest rank's time: every rank contributes its own, all get the max"""
+    if world <= 1:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_throughput(units_per_rank: int, world: int, ms_max: float) -> float:
+    """whole-job throughput: the units all ranks processed over the slowest
+    rank's time (replicas, weak scaling)"""
+    return units_per_rank * world / (ms_max / 1e3)
+
+
 def ks_weight(level, alpha):
     """limb transforms in one hybrid key switch at `level` (the dominant cost)"""
     nl = level + 1
@@ -197,12 +213,7 @@ def run_ours(args, rank, world):
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
-        ms = e0.elapsed_time(e1) / k
-        if world > 1:
-            t = torch.tensor([ms], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms
+        return max_over_ranks(e0.elapsed_time(e1) / k, world)
 
     # single-image baseline (one image per launch sequence)
     for _ in range(max(1, args.warmup)):
@@ -284,9 +295,9 @@ def run_ours(args, rank, world):
     ks_total = sum(ks_ms) / 1e3
     peak, peak_kind = _peaks()
     achieved = ks_bytes / ks_total / 1e9
-    img_s_batch = S * g * world / (ms_batch / 1e3)
-    img_s_uniform = B * world / (ms_uniform / 1e3)
-    img_s_single = 1 * world / (ms_single / 1e3)
+    img_s_batch = aggregate_throughput(S * g, world, ms_batch)
+    img_s_uniform = aggregate_throughput(B, world, ms_uniform)
+    img_s_single = aggregate_throughput(1, world, ms_single)
     n_ks, wks = program_ledger(prog, alpha)
 
     res = {
@@ -322,7 +333,7 @@ def run_ours(args, rank, world):
             "parallelism": "replicas" if world > 1 else "single",
         },
         "clocks": clocks,
-        "e2e": {"value": round(S * g * world / (ms_e2e / 1e3), 4), "unit": "img/s",
+        "e2e": {"value": round(aggregate_throughput(S * g, world, ms_e2e), 4), "unit": "img/s",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "kernel": "hybrid key switch (9 kernels), level %d, %d items (one group)" % (lv, g),
