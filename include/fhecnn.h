@@ -181,6 +181,10 @@ int fhe_mul_plain(fhe_ctx *ctx, const fhe_ct *a, const fhe_pt *pt, fhe_ct **out,
  * LINEAR: for each output ciphertext o and giant step g,
  *     acc_{o,g} = sum_terms pt_term (.) rot(in[term_ct], term_baby)
  *     out_o     = bias_o + sum_g rot(acc_{o,g}, g)
+ *   The baby-step rotations of one input share one ModUp (the Galois
+ *   automorphism is applied to the extended limbs), and the giant-step
+ *   rotations of one output share one ModDown (their inner products are summed
+ *   in the extended basis Q_l u P first).
  *   where term vectors (n_slots doubles each) are encoded at w_scale and the
  *   bias vectors at bias_scale, both at the input's level.
  * ACT: c1 and c0 are integers (given as integral doubles of any size) that

@@ -575,28 +575,61 @@ class CKKS:
         return Ciphertext(a.c[:, : level + 1].copy(), level, a.scale)
 
     # -- key switching
-    def key_switch(self, d: np.ndarray, level: int, key: SwitchKey) -> np.ndarray:
-        """Hybrid key switch of one polynomial d (NTT domain, limbs 0..level).
-        Returns [2][level+1][N]."""
+    def ext_primes(self, level: int) -> List[int]:
+        """indices of the extended basis Q_level u P"""
+        prm = self.prm
+        return list(range(level + 1)) + list(range(prm.L + 1, prm.L + 1 + prm.alpha))
+
+    def modup(self, d: np.ndarray, level: int) -> List[np.ndarray]:
+        """ModUp of one polynomial (NTT domain, limbs 0..level): for every
+        digit j, the digit's residues extended to Q_level u P by the fast
+        basis conversion, NTT domain.  Returns [digit][ext limb][N]."""
         prm = self.prm
         Qidx = list(range(level + 1))
-        Pidx = list(range(prm.L + 1, prm.L + 1 + prm.alpha))
-        ext = Qidx + Pidx
-        # ModUp: each digit extended to Q_l * P
+        ext = self.ext_primes(level)
         d_coef = self.from_ntt(d, Qidx)
-        acc = np.zeros((2, len(ext), prm.N), dtype=np.uint64)
-        for j, dj in enumerate(prm.digits(level)):
+        out = []
+        for dj in prm.digits(level):
             qd = [prm.primes[i] for i in dj]
+            limbs = np.empty((len(ext), prm.N), dtype=np.uint64)
             for k, t in enumerate(ext):
                 qt = prm.primes[t]
                 if t in dj:
-                    x = d[t]
+                    limbs[k] = d[t]
                 else:
-                    x = ntt(basis_convert(d_coef[dj], qd, qt), qt, prm.psi[t])
-                # inner product with the key of digit j
+                    limbs[k] = ntt(basis_convert(d_coef[dj], qd, qt), qt, prm.psi[t])
+            out.append(limbs)
+        return out
+
+    def galois_ext(self, limbs: np.ndarray, level: int, k: int) -> np.ndarray:
+        """sigma_k applied to NTT-domain limbs of the extended basis, through
+        the coefficient-domain definition on each limb."""
+        prm = self.prm
+        ext = self.ext_primes(level)
+        out = np.empty_like(limbs)
+        for r, t in enumerate(ext):
+            qt = prm.primes[t]
+            coef = intt(limbs[r], qt, prm.psi[t])
+            out[r] = ntt(automorphism_coeff(coef, k, qt), qt, prm.psi[t])
+        return out
+
+    def inner_product(self, ext_digits: List[np.ndarray], level: int, key: SwitchKey) -> np.ndarray:
+        """sum_j ext_j * key_j over Q_level u P: [2][ext][N]"""
+        prm = self.prm
+        ext = self.ext_primes(level)
+        acc = np.zeros((2, len(ext), prm.N), dtype=np.uint64)
+        for j, x in enumerate(ext_digits):
+            for k, t in enumerate(ext):
+                qt = prm.primes[t]
                 for r in range(2):
-                    acc[r, k] = vadd(acc[r, k], vmul(x, key.digits[j][r, t], qt), qt)
-        # ModDown: (acc - [acc]_P centred) * P^-1 over Q_l
+                    acc[r, k] = vadd(acc[r, k], vmul(x[k], key.digits[j][r, t], qt), qt)
+        return acc
+
+    def moddown(self, acc: np.ndarray, level: int) -> np.ndarray:
+        """(acc - [acc]_P centred) * P^-1 over Q_level: [2][level+1][N]"""
+        prm = self.prm
+        Qidx = list(range(level + 1))
+        Pidx = list(range(prm.L + 1, prm.L + 1 + prm.alpha))
         pq = [prm.primes[t] for t in Pidx]
         half_p = prm.P // 2
         out = np.empty((2, level + 1, prm.N), dtype=np.uint64)
@@ -610,6 +643,65 @@ class CKKS:
                 conv = ntt(conv, qi, prm.psi[i])
                 out[r, i] = vmul_scalar(vsub(acc[r, i], conv, qi), invmod(prm.P % qi, qi), qi)
         return out
+
+    def key_switch(self, d: np.ndarray, level: int, key: SwitchKey) -> np.ndarray:
+        """Hybrid key switch of one polynomial d (NTT domain, limbs 0..level):
+        ModUp, inner product with the key, ModDown.  Returns [2][level+1][N]."""
+        return self.moddown(self.inner_product(self.modup(d, level), level, key), level)
+
+    def _galois_key(self, step: int, keys: Keys):
+        k = galois_elt(step, self.prm.N)
+        if k not in keys.galois:
+            raise KeyError("no Galois key for step %d" % step)
+        return k, keys.galois[k]
+
+    def rotate_hoisted(self, ct: Ciphertext, steps: Sequence[int], keys: Keys) -> Dict[int, Ciphertext]:
+        """Rotations of one ciphertext by several steps sharing one ModUp:
+        ModUp(c1) once; for each step, sigma applied to the extended limbs,
+        inner product with that step's key, ModDown, plus sigma(c0)."""
+        prm = self.prm
+        lv = ct.level
+        ext = self.modup(ct.c[1], lv)
+        out = {}
+        for step in steps:
+            k, key = self._galois_key(step, keys)
+            rot_ext = [self.galois_ext(x, lv, k) for x in ext]
+            ks = self.moddown(self.inner_product(rot_ext, lv, key), lv)
+            g0 = self.galois_ext(np.concatenate([ct.c[0], np.zeros((prm.alpha, prm.N), dtype=np.uint64)]), lv, k)
+            c = np.empty_like(ct.c)
+            for t in range(lv + 1):
+                c[0, t] = vadd(g0[t], ks[0, t], prm.primes[t])
+                c[1, t] = ks[1, t]
+            out[step] = Ciphertext(c, lv, ct.scale)
+        return out
+
+    def rotate_sum_lazy(self, terms: Sequence, keys: Keys, base: Ciphertext) -> Ciphertext:
+        """base + sum_g rot(ct_g, g) with one ModDown: each term's ModUp and
+        inner product (sigma_g on the extended limbs) are summed over Q_l u P,
+        the sigma_g(c0) parts over Q_l, then a single ModDown."""
+        prm = self.prm
+        lv = base.level
+        ext_n = len(self.ext_primes(lv))
+        acc = np.zeros((2, ext_n, prm.N), dtype=np.uint64)
+        c0 = np.zeros((lv + 1, prm.N), dtype=np.uint64)
+        for ct, step in terms:
+            k, key = self._galois_key(step, keys)
+            rot_ext = [self.galois_ext(x, lv, k) for x in self.modup(ct.c[1], lv)]
+            ip = self.inner_product(rot_ext, lv, key)
+            ext = self.ext_primes(lv)
+            for r in range(2):
+                for q in range(ext_n):
+                    acc[r, q] = vadd(acc[r, q], ip[r, q], prm.primes[ext[q]])
+            g0 = self.galois_ext(np.concatenate([ct.c[0], np.zeros((prm.alpha, prm.N), dtype=np.uint64)]), lv, k)
+            for t in range(lv + 1):
+                c0[t] = vadd(c0[t], g0[t], prm.primes[t])
+        ks = self.moddown(acc, lv)
+        c = np.empty_like(base.c)
+        for t in range(lv + 1):
+            qt = prm.primes[t]
+            c[0, t] = vadd(vadd(base.c[0, t], c0[t], qt), ks[0, t], qt)
+            c[1, t] = vadd(base.c[1, t], ks[1, t], qt)
+        return Ciphertext(c, lv, base.scale)
 
     def relinearize(self, ct: Ciphertext, keys: Keys) -> Ciphertext:
         assert ct.c.shape[0] == 3

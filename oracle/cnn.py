@@ -20,8 +20,11 @@ Three pieces, each written as plainly as possible:
    leave gaps that later layers follow (adaptive / lazy mapping).  A linear
    layer is written as sum over diagonals: out = sum_r d_r (.) rot(in, r),
    split into baby steps b = r mod G (rotations of the input) and giant steps
-   g = r - b (rotations of partial sums), with d_r pre-rotated by -g.
-   Rescales follow the tower-reuse rule of Sec. 4.3.
+   g = r - b (rotations of partial sums), with d_r pre-rotated by -g.  The
+   baby-step rotations of one input share one ModUp and the giant-step
+   rotations of one output share one ModDown (``rotate_hoisted`` and
+   ``rotate_sum_lazy`` in ckks.py).  Rescales follow the tower-reuse rule of
+   Sec. 4.3.
 
 Floating-point expressions that feed integers (weights after folding, the
 scales of encoded plaintexts and constants) are written out once here, in a
@@ -532,28 +535,34 @@ def run_he(S: C.CKKS, keys: C.Keys, prog: Program, cts: List[C.Ciphertext],
         op = st["op"]
         dst_info = prog.tensors[st["dst"]]
         if op == "linear":
+            # baby steps: the rotations of one input share its ModUp; giant
+            # steps: the rotated partial sums of one output share a ModDown
             xs = vals[st["src"]]
             level = xs[0].level
             rot = {}
             for i in range(len(xs)):
                 rot[(i, 0)] = xs[i]
-            for (i, b) in st["baby"]:
-                rot[(i, b)] = S.rotate(xs[i], b, keys)
+                steps_i = [b for (ii, b) in st["baby"] if ii == i]
+                if steps_i:
+                    for b, r in S.rotate_hoisted(xs[i], steps_i, keys).items():
+                        rot[(i, b)] = r
             outs = []
             for o in range(st["n_out"]):
-                total = None
+                partial = {}
                 for g in sorted(st["groups"].get(o, {})):
                     acc = None
                     for (i, b, vec) in st["groups"][o][g]:
                         pt = S.encode(vec, st["w_scale"], level)
                         term = S.mul_plain(rot[(i, b)], pt)
                         acc = term if acc is None else S.add(acc, term)
-                    if g:
-                        acc = S.rotate(acc, g, keys)
-                    total = acc if total is None else S.add(total, acc)
+                    partial[g] = acc
+                base = partial.get(0)
+                if base is None:
+                    base = C.Ciphertext(np.zeros((2, level + 1, prm.N), dtype=np.uint64), level, 1.0)
                 if o in st["bias"]:
-                    pt = S.encode(st["bias"][o], st["bias_scale"], level)
-                    total = S.add_plain(total, pt)
+                    base = S.add_plain(base, S.encode(st["bias"][o], st["bias_scale"], level))
+                giants = [(partial[g], g) for g in sorted(partial) if g]
+                total = S.rotate_sum_lazy(giants, keys, base) if giants else base
                 total.scale = dst_info.scale
                 outs.append(total)
             vals[st["dst"]] = outs

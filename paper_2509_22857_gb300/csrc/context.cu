@@ -475,7 +475,7 @@ int op_ntt(fhe_ctx *ctx, const u64 *src, u64 *dst, long long item, int n_items, 
     return FHE_OK;
 }
 
-int op_keyswitch(fhe_ctx *ctx, KsArgs a, cudaStream_t s, u64 *ws) {
+int op_keyswitch(fhe_ctx *ctx, KsArgs a, cudaStream_t s, u64 *ws, int phases) {
     const size_t per = ks_workspace_words(ctx->dc, a.level);
     if (!ws) {
         FHE_TRY(ws_reserve(ctx, &ctx->ks_ws, &ctx->ks_ws_words, per * (size_t)a.n_items));
@@ -483,7 +483,7 @@ int op_keyswitch(fhe_ctx *ctx, KsArgs a, cudaStream_t s, u64 *ws) {
     }
     a.ws = ws;
     a.ws_item = (long long)per;
-    FHE_CU(launch_keyswitch(ctx->dc, ctx->lt[a.level], a, s));
+    FHE_CU(launch_keyswitch(ctx->dc, ctx->lt[a.level], a, s, nullptr, phases));
     return FHE_OK;
 }
 

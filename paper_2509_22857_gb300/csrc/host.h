@@ -109,7 +109,8 @@ u64 h_double_mod(double v, u64 q);
 
 // core operations on raw device buffers (batched over items)
 // ws: caller-sized workspace, or nullptr for the context's growable one
-int op_keyswitch(fhe_ctx *ctx, KsArgs a, cudaStream_t s, u64 *ws = nullptr);
+// phases: KS_MODUP | KS_IP | KS_MODDOWN (the workspace carries state between them)
+int op_keyswitch(fhe_ctx *ctx, KsArgs a, cudaStream_t s, u64 *ws = nullptr, int phases = KS_ALL);
 int op_rescale(fhe_ctx *ctx, const u64 *in, long long in_item, u64 *out, long long out_item, int n_items,
                int n_poly, int level, cudaStream_t s, u64 *ws = nullptr);
 int op_ntt(fhe_ctx *ctx, const u64 *src, u64 *dst, long long item, int n_items, int n_limbs,

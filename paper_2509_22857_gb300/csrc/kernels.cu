@@ -47,7 +47,7 @@ __device__ __forceinline__ void gs_bf(u64 &X, u64 &Y, ulonglong2 w, u64 q) {
 // Galois gather in the NTT domain: sigma_k(a) at slot j is a at slot
 // brv(((2 brv(j) + 1) k mod 2N - 1) / 2).
 __device__ __forceinline__ int galois_src(int j, int k, int logN) {
-    if (k == 1) return j;
+    if (k <= 1) return j;
     const unsigned mask2n = (2u << logN) - 1u;
     unsigned e = 2u * (__brev((unsigned)j) >> (32 - logN)) + 1u;
     unsigned ek = (unsigned)(((unsigned long long)e * (unsigned)k) & mask2n);
@@ -469,7 +469,9 @@ __global__ void __launch_bounds__(256) k_ks_ip(DevCtx c, LevelTab lt, KsArgs a, 
     const int col = blockIdx.x * blockDim.x + threadIdx.x;
     const long long key_limbs = c.L + 1 + c.alpha;
     const int jt = t <= a.level ? t / c.alpha : -1;   // digit that holds limb t itself
-    const int src_col = jt >= 0 ? galois_src(col, a.galois, c.logN) : col;
+    // hoisted rotation: sigma acts on every extended limb (NTT-domain gather)
+    const int ip_col = galois_src(col, a.ip_galois, c.logN);
+    const int src_col = jt >= 0 ? galois_src(ip_col, a.galois, c.logN) : ip_col;
     // the key of this limb for every digit, kept in registers across the batch
     u64 k0[7], k1[7];
 #pragma unroll
@@ -481,7 +483,7 @@ __global__ void __launch_bounds__(256) k_ks_ip(DevCtx c, LevelTab lt, KsArgs a, 
         }
     }
     for (int item = 0; item < a.n_items; item++) {
-        const u64 *mu = a.ws + item * a.ws_item + ly.mu + (long long)t * N + col;
+        const u64 *mu = a.ws + item * a.ws_item + ly.mu + (long long)t * N + ip_col;
         u64 x[7];
 #pragma unroll
         for (int j = 0; j < 7; j++)
@@ -495,8 +497,29 @@ __global__ void __launch_bounds__(256) k_ks_ip(DevCtx c, LevelTab lt, KsArgs a, 
             }
         }
         u64 *o0 = a.ws + item * a.ws_item + ly.acc + (long long)t * N + col;
-        o0[0] = barrett(acc0, m);
-        o0[(long long)ext * N] = barrett(acc1, m);
+        u64 r0 = barrett(acc0, m), r1 = barrett(acc1, m);
+        if (a.ip_accumulate) {
+            r0 = add_mod(r0, o0[0], m.q);
+            r1 = add_mod(r1, o0[(long long)ext * N], m.q);
+        }
+        o0[0] = r0;
+        o0[(long long)ext * N] = r1;
+    }
+}
+
+// out[i][t] (+)= in[i][t] gathered by sigma_galois, limbs 0..level
+__global__ void k_gather_acc(DevCtx c, const u64 *in, long long in_item, u64 *out, long long out_item, int level,
+                             int galois, int accumulate) {
+    const long long N = 1ll << c.logN;
+    const int item = blockIdx.z;
+    const int limb = blockIdx.y;
+    const u64 q = c.primes[limb].m.q;
+    const u64 *src = in + item * in_item + (long long)limb * N;
+    u64 *dst = out + item * out_item + (long long)limb * N;
+    for (long long j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += (long long)gridDim.x * blockDim.x) {
+        u64 v = src[galois_src((int)j, galois, c.logN)];
+        if (accumulate) v = add_mod(v, dst[j], q);
+        dst[j] = v;
     }
 }
 
@@ -633,7 +656,7 @@ __global__ void __launch_bounds__(NT) k_ks_md_row_out(DevCtx c, LevelTab lt, KsA
         v = mul_shoup(v, pinv.x, pinv.y, q);
         if (addp) {
             const u64 *ap = addp + item * a.add_item + (long long)i * N;
-            v = add_mod(v, ap[galois_src(base + e, a.galois, c.logN)], q);
+            v = add_mod(v, ap[galois_src(base + e, a.add_galois, c.logN)], q);
         }
         if (a.base) v = add_mod(v, a.base[item * a.base_item + ((long long)kk * nl + i) * N + base + e], q);
         o[e] = v;
@@ -1072,8 +1095,11 @@ cudaError_t launch_ntt(const DevCtx &c, const NttArgs &a, bool inverse, cudaStre
     return cudaGetLastError();
 }
 
-cudaError_t launch_keyswitch(const DevCtx &c, const LevelTab &lt, const KsArgs &a, cudaStream_t s,
-                             cudaEvent_t *ev) {
+cudaError_t launch_keyswitch(const DevCtx &c, const LevelTab &lt, const KsArgs &args, cudaStream_t s,
+                             cudaEvent_t *ev, int phases) {
+    KsArgs a = args;
+    if (a.ip_galois == 0) a.ip_galois = 1;
+    if (a.add_galois == 0) a.add_galois = a.galois;
     const int nl = a.level + 1, ext = lt.ext, nd = lt.n_digits, B = a.n_items;
     if (nd > 7) return cudaErrorInvalidValue;   // inner-product accumulator bound
     KsLayout ly = ks_layout(a.level, nd, c.alpha, c.logN);
@@ -1081,23 +1107,25 @@ cudaError_t launch_keyswitch(const DevCtx &c, const LevelTab &lt, const KsArgs &
 #define KS_EV(i) \
     if (ev) cudaEventRecord(ev[i], s)
     KS_EV(0);
-    DISPATCH_LOGR(c.logR2, k_ks_intt_row, dim3(tc, B * nl), c, a, ly);
+    if (phases & KS_MODUP) DISPATCH_LOGR(c.logR2, k_ks_intt_row, dim3(tc, B * nl), c, a, ly);
     KS_EV(1);
-    DISPATCH_LOGR(c.logR1, k_ks_intt_col, dim3(tc, B * nl), c, lt, a, ly);
+    if (phases & KS_MODUP) DISPATCH_LOGR(c.logR1, k_ks_intt_col, dim3(tc, B * nl), c, lt, a, ly);
     KS_EV(2);
-    DISPATCH_LOGR(c.logR1, k_ks_modup_col, dim3(tc, B * nd * ext), c, lt, a, ly);
+    if (phases & KS_MODUP) DISPATCH_LOGR(c.logR1, k_ks_modup_col, dim3(tc, B * nd * ext), c, lt, a, ly);
     KS_EV(3);
-    DISPATCH_LOGR(c.logR2, k_ks_modup_row, dim3(tc, B * nd * ext), c, lt, a, ly);
-    COUNT_LAUNCH();
-    k_ks_ip<<<dim3((unsigned)((1ll << c.logN) / 256), ext), 256, 0, s>>>(c, lt, a, ly);
+    if (phases & KS_MODUP) DISPATCH_LOGR(c.logR2, k_ks_modup_row, dim3(tc, B * nd * ext), c, lt, a, ly);
+    if (phases & KS_IP) {
+        COUNT_LAUNCH();
+        k_ks_ip<<<dim3((unsigned)((1ll << c.logN) / 256), ext), 256, 0, s>>>(c, lt, a, ly);
+    }
     KS_EV(4);
-    DISPATCH_LOGR(c.logR2, k_ks_md_intt_row, dim3(tc, B * 2 * c.alpha), c, lt, a, ly);
+    if (phases & KS_MODDOWN) DISPATCH_LOGR(c.logR2, k_ks_md_intt_row, dim3(tc, B * 2 * c.alpha), c, lt, a, ly);
     KS_EV(5);
-    DISPATCH_LOGR(c.logR1, k_ks_md_intt_col, dim3(tc, B * 2 * c.alpha), c, lt, a, ly);
+    if (phases & KS_MODDOWN) DISPATCH_LOGR(c.logR1, k_ks_md_intt_col, dim3(tc, B * 2 * c.alpha), c, lt, a, ly);
     KS_EV(6);
-    DISPATCH_LOGR(c.logR1, k_ks_md_conv_col, dim3(tc, B * 2 * nl), c, lt, a, ly);
+    if (phases & KS_MODDOWN) DISPATCH_LOGR(c.logR1, k_ks_md_conv_col, dim3(tc, B * 2 * nl), c, lt, a, ly);
     KS_EV(7);
-    DISPATCH_LOGR(c.logR2, k_ks_md_row_out, dim3(tc, B * 2 * nl), c, lt, a, ly);
+    if (phases & KS_MODDOWN) DISPATCH_LOGR(c.logR2, k_ks_md_row_out, dim3(tc, B * 2 * nl), c, lt, a, ly);
     KS_EV(8);
 #undef KS_EV
     return cudaGetLastError();
@@ -1117,6 +1145,14 @@ static dim3 ew_grid(const DevCtx &c, int y, int z) {
     int x = (int)((1ll << c.logN) / 256);
     if (x > 64) x = 64;
     return dim3(x, y, z);
+}
+
+cudaError_t launch_gather_acc(const DevCtx &c, const u64 *in, long long in_item, u64 *out, long long out_item,
+                              int n_items, int level, int galois, int accumulate, cudaStream_t s) {
+    COUNT_LAUNCH();
+    k_gather_acc<<<ew_grid(c, level + 1, n_items), 256, 0, s>>>(c, in, in_item, out, out_item, level, galois,
+                                                                 accumulate);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_add(const DevCtx &c, const u64 *a, long long a_item, const u64 *b, long long b_item, u64 *out,

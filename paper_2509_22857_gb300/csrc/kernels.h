@@ -70,6 +70,9 @@ struct KsArgs {
     const u64 *add0;        // addend of output poly 0 (nullable), limbs 0..level, + i*add_item
     const u64 *add1;        // addend of output poly 1 (nullable)
     long long add_item;
+    int ip_galois;          // Galois gather applied to every limb entering the inner product (0/1: none)
+    int ip_accumulate;      // inner product adds into the accumulator instead of overwriting it
+    int add_galois;         // Galois gather of add0 in the output (0: same as galois)
     const u64 *base;        // added to both output polys without gather (nullable; may alias out)
     long long base_item;
     u64 *out;               // [item][2][level+1][N]
@@ -83,9 +86,18 @@ struct KsArgs {
 };
 
 size_t ks_workspace_words(const DevCtx &c, int level);
-// ev (nullable): 9 events recorded on s before each of the 8 kernels and after the last
+// ev (nullable): 9 events recorded on s before each of the 8 kernels and after the last.
+// phases: KS_MODUP (inverse NTT, basis conversion, NTT), KS_IP (key inner
+// product), KS_MODDOWN (back to Q, output); a plain key switch runs all three.
+#define KS_MODUP 1
+#define KS_IP 2
+#define KS_MODDOWN 4
+#define KS_ALL 7
 cudaError_t launch_keyswitch(const DevCtx &c, const LevelTab &lt, const KsArgs &a, cudaStream_t s,
-                             cudaEvent_t *ev = nullptr);
+                             cudaEvent_t *ev = nullptr, int phases = KS_ALL);
+// out[i][t] = (accumulate ? out[i][t] : 0) + sigma_galois(in[i][t]) for limbs t <= level (one poly)
+cudaError_t launch_gather_acc(const DevCtx &c, const u64 *in, long long in_item, u64 *out, long long out_item,
+                              int n_items, int level, int galois, int accumulate, cudaStream_t s);
 
 // Rescale: out[i] = q_l^-1 (in[i] - [in[l]]_centred) mod q_i for i < level, both polys.
 struct RescaleArgs {

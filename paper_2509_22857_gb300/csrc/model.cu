@@ -315,7 +315,9 @@ struct Exec {
         *err = FHE_OK;
         return it->second;
     }
-    int keyswitch(const KsArgs &a) { return op_keyswitch(m->ctx, a, s, pers ? pers->ks_ws : nullptr); }
+    int keyswitch(const KsArgs &a, int phases = KS_ALL) {
+        return op_keyswitch(m->ctx, a, s, pers ? pers->ks_ws : nullptr, phases);
+    }
 
     // out = base + rot(x, step) for n items of one tensor-like layout
     int rotate_items(const u64 *x, long long x_item, int step, const u64 *base, long long base_item, u64 *out,
@@ -351,11 +353,37 @@ struct Exec {
         u64 *out = buf[st.dst];
         const long long in_item = item(st.src), out_item = item(st.dst);
         int ti = 0;
-        // baby-step rotations of the inputs
+        // baby-step rotations of the inputs: the rotations of one input share
+        // its ModUp (hoisting); each then needs an inner product and a ModDown
         std::vector<u64 *> rb(L.baby_ct.size(), nullptr);
+        for (size_t k = 0; k < L.baby_ct.size(); k++) FHE_TRY(tmp(ti++, (size_t)B * cs * 8, &rb[k]));
+        const long long nlN = (long long)(lv + 1) * c->N;
         for (size_t k = 0; k < L.baby_ct.size(); k++) {
-            FHE_TRY(tmp(ti++, (size_t)B * cs * 8, &rb[k]));
-            FHE_TRY(rotate_items(in + L.baby_ct[k] * cs, in_item, L.baby_step[k], nullptr, 0, rb[k], cs, B, lv));
+            if (k > 0 && L.baby_ct[k] == L.baby_ct[k - 1]) continue;   // ModUp done for this input
+            const u64 *x = in + L.baby_ct[k] * cs;
+            KsArgs a;
+            memset(&a, 0, sizeof(a));
+            a.d = x + nlN;
+            a.d_item = in_item;
+            a.galois = 1;
+            a.n_items = B;
+            a.level = lv;
+            FHE_TRY(keyswitch(a, KS_MODUP));
+            for (size_t kk = k; kk < L.baby_ct.size() && L.baby_ct[kk] == L.baby_ct[k]; kk++) {
+                int err;
+                const u64 *key = key_for(L.baby_step[kk], &err);
+                if (!key) return err;
+                const int gal = galois_of_step(c, L.baby_step[kk]);
+                a.key = key;
+                a.key_digits_top = evk->digits;
+                a.ip_galois = gal;
+                a.add0 = x;
+                a.add_item = in_item;
+                a.add_galois = gal;
+                a.out = rb[kk];
+                a.out_item = cs;
+                FHE_TRY(keyswitch(a, KS_IP | KS_MODDOWN));
+            }
         }
         // sources: the input ciphertexts, then the baby-step rotations
         const int n_in = m->tensors[st.src].n_ct;
@@ -413,12 +441,47 @@ struct Exec {
         ma.n_items = B;
         ma.level = lv;
         FHE_CU(launch_mac(c->dc, ma, s));
-        // giant steps: out_o += rot(acc_{o,g}, g)
-        for (int g = 0; g < ng; g++) {
-            if (!acc[g]) continue;
-            u64 *o = out + L.g_out[g] * cs;
-            FHE_TRY(rotate_items(acc[g], cs, L.g_giant[g], o, out_item, o, out_item, B, lv));
+        // giant steps: out_o += sum_g rot(acc_{o,g}, g) with one ModDown per
+        // output: each term's ModUp and inner product accumulate in the
+        // extended basis, the rotated c0 parts over Q
+        u64 *c0acc = nullptr;
+        for (int o = 0; o < m->tensors[st.dst].n_ct; o++) {
+            bool first = true;
+            KsArgs a;
+            memset(&a, 0, sizeof(a));
+            for (int g = 0; g < ng; g++) {
+                if (!acc[g] || L.g_out[g] != o) continue;
+                if (!c0acc) FHE_TRY(tmp(ti++, (size_t)B * nlN * 8, &c0acc));
+                int err;
+                const u64 *key = key_for(L.g_giant[g], &err);
+                if (!key) return err;
+                const int gal = galois_of_step(c, L.g_giant[g]);
+                memset(&a, 0, sizeof(a));
+                a.d = acc[g] + nlN;
+                a.d_item = cs;
+                a.galois = 1;
+                a.key = key;
+                a.key_digits_top = evk->digits;
+                a.ip_galois = gal;
+                a.ip_accumulate = first ? 0 : 1;
+                a.n_items = B;
+                a.level = lv;
+                FHE_TRY(keyswitch(a, KS_MODUP | KS_IP));
+                FHE_CU(launch_gather_acc(c->dc, acc[g], cs, c0acc, nlN, B, lv, gal, first ? 0 : 1, s));
+                first = false;
+            }
+            if (first) continue;   // no giant step for this output
+            u64 *op = out + o * cs;
+            a.add0 = c0acc;
+            a.add_item = nlN;
+            a.add_galois = 1;
+            a.base = op;
+            a.base_item = out_item;
+            a.out = op;
+            a.out_item = out_item;
+            FHE_TRY(keyswitch(a, KS_MODDOWN));
         }
+        tmp_free(c0acc);
         for (auto p : rb) tmp_free(p);
         for (auto p : acc) tmp_free(p);
         if (!pers) cudaFreeAsync(dw, s);

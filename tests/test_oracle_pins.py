@@ -375,3 +375,31 @@ def test_tower_reuse_count_matches_table1_last_column():
     for m in want:
         n, _ = planner.tower_reuse(planner.alternating_path(n_lin[m], n_act[m]), lam_q=2)
         assert n == want[m], m
+
+
+def test_hoisted_rotations_decrypt_to_rotated_slots(small):
+    """Rotations sharing one ModUp decrypt to the rotated slots (the
+    extended-basis automorphism of ModUp(c1) is a valid key-switch input)."""
+    prm, S, keys = small
+    rng = np.random.default_rng(11)
+    z = rng.uniform(-1, 1, prm.N // 2) + 1j * rng.uniform(-1, 1, prm.N // 2)
+    ct = S.encrypt(keys, S.encode(z, prm.scale, prm.L), 12)
+    rots = S.rotate_hoisted(ct, [1, 3, -1], keys)
+    for step, r in rots.items():
+        assert np.max(np.abs(S.decrypt_decode(keys, r) - np.roll(z, -step))) < 1e-6
+    # one step alone: same plaintext as the plain rotation, different noise
+    plain = S.rotate(ct, 3, keys)
+    d1 = S.decrypt_decode(keys, rots[3])
+    d2 = S.decrypt_decode(keys, plain)
+    assert np.max(np.abs(d1 - d2)) < 1e-6
+
+
+def test_lazy_rotation_sum_decrypts_to_the_sum(small):
+    """base + sum_g rot(ct_g, g) with a single ModDown decrypts to the sum."""
+    prm, S, keys = small
+    rng = np.random.default_rng(12)
+    zs = [rng.uniform(-1, 1, prm.N // 2) for _ in range(3)]
+    cts = [S.encrypt(keys, S.encode(z, prm.scale, prm.L), 20 + i) for i, z in enumerate(zs)]
+    out = S.rotate_sum_lazy([(cts[1], 1), (cts[2], 5)], keys, cts[0])
+    want = zs[0] + np.roll(zs[1], -1) + np.roll(zs[2], -5)
+    assert np.max(np.abs(S.decrypt_decode(keys, out).real - want)) < 1e-6
