@@ -109,6 +109,30 @@ def ks_weight(level, alpha):
     return nl + (nd * (nl + alpha) - nl) + 2 * alpha + 2 * nl
 
 
+# Integer roofline.  The key switch is bound by the 64-bit modular
+# arithmetic on the integer pipes, not by HBM.  Algorithmic work is counted in
+# modular multiplications (one per NTT butterfly, per basis-conversion term,
+# per key inner-product term, per output scaling).  Peak: 152 SMs x 64
+# 32-bit IMAD per clock per SM x 2.07 GHz, divided by the 10 IMADs of one
+# 64-bit Shoup multiplication (4 for the high product, 3 + 3 for the two low
+# products) = 2.01e12 modmul/s.
+ALU_PEAK_MODMUL = 152 * 64 * 2.07e9 / 10
+
+
+def ks_modmuls(level, alpha, logn):
+    """modular multiplications of one hybrid key switch at `level`"""
+    N = 1 << logn
+    bf = (N // 2) * logn
+    nl = level + 1
+    ext = nl + alpha
+    digits = [min(alpha, nl - j) for j in range(0, nl, alpha)]
+    nd = len(digits)
+    modup = nl * bf + sum((ext - d) * d * N + (ext - d) * bf for d in digits)
+    ip = 2 * nd * ext * N
+    moddown = 2 * alpha * bf + 2 * nl * alpha * N + 2 * nl * bf + 2 * nl * N
+    return modup + ip + moddown
+
+
 def program_ledger(prog, alpha):
     """key switches of one image and their weighted count (in top-level units)"""
     n_ks, w = 0, 0.0
@@ -295,6 +319,8 @@ def run_ours(args, rank, world):
     ks_total = sum(ks_ms) / 1e3
     peak, peak_kind = _peaks()
     achieved = ks_bytes / ks_total / 1e9
+    ks_mm = g * ks_modmuls(lv, alpha, pre["logn"])
+    alu_achieved = ks_mm / ks_total
     img_s_batch = aggregate_throughput(S * g, world, ms_batch)
     img_s_uniform = aggregate_throughput(B, world, ms_uniform)
     img_s_single = aggregate_throughput(1, world, ms_single)
@@ -336,10 +362,16 @@ def run_ours(args, rank, world):
         "e2e": {"value": round(aggregate_throughput(S * g, world, ms_e2e), 4), "unit": "img/s",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
-        "roofline": {"bound": "hbm", "kernel": "hybrid key switch (9 kernels), level %d, %d items (one group)" % (lv, g),
-                     "achieved": round(achieved, 1), "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "traffic": None,
-                     "algorithmic_bytes": int(ks_bytes),
+        "roofline": {"bound": "alu",
+                     "kernel": "hybrid key switch (9 kernels: ModUp, key inner product, ModDown), level %d, "
+                               "%d polynomials (one group of the pipeline)" % (lv, g),
+                     "achieved": round(alu_achieved / 1e9, 1), "peak": round(ALU_PEAK_MODMUL / 1e9, 1),
+                     "unit": "Gmodmul/s", "peak_kind": "derived (152 SMs x 64 IMAD/clk x 2.07 GHz / 10 IMAD "
+                                                       "per 64-bit modmul)",
+                     "frac": round(alu_achieved / ALU_PEAK_MODMUL, 4), "traffic": None,
+                     "algorithmic_modmuls": int(ks_mm),
+                     "hbm": {"achieved_gbs": round(achieved, 1), "peak_gbs": peak, "peak_kind": peak_kind,
+                             "frac": round(achieved / peak, 4), "algorithmic_bytes": int(ks_bytes)},
                      "kernel_ms": {k: round(v, 4) for k, v in zip(KS_KERNELS, ks_ms)}},
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

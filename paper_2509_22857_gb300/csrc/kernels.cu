@@ -26,13 +26,19 @@ void fhe_launch_counter_add(long long n) { g_launches.fetch_add((unsigned long l
 
 namespace {
 
+// Forward butterfly without Harvey's per-stage correction: t = w*Y mod q lies
+// in [0, 2q) for any 64-bit Y, so X + t and X - t + 2q grow by at most 2q per
+// stage.  Inputs below q stay below 17q after the 8 stages of one pass and
+// below 33q < 2^64 (q < 2^58) after both; the second pass reduces once.
 __device__ __forceinline__ void ct_bf(u64 &X, u64 &Y, ulonglong2 w, u64 q) {
-    const u64 two_q = 2 * q;
-    u64 x = X >= two_q ? X - two_q : X;
-    u64 t = mul_shoup_lazy(Y, w.x, w.y, q);
+    const u64 t = mul_shoup_lazy(Y, w.x, w.y, q);
+    const u64 x = X;
     X = x + t;
-    Y = x - t + two_q;
+    Y = x - t + 2 * q;
 }
+
+// full reduction of a lazy forward-NTT output (< 33q < 2^64)
+__device__ __forceinline__ u64 reduce_fwd(u64 x, const ModQ &m) { return barrett(U128{x, 0}, m); }
 
 __device__ __forceinline__ void gs_bf(u64 &X, u64 &Y, ulonglong2 w, u64 q) {
     const u64 two_q = 2 * q;
@@ -252,7 +258,7 @@ __global__ void __launch_bounds__(NT) k_ntt_fwd_row(DevCtx c, NttArgs a) {
     fwd_B<LOGR>(x, tau, row << LOGR, 1, c.logR1, TwGlobal{P.fwd, c.logN}, q);
     xchg_row_BA<LOGR>(x, sm, tau, rl);
 #pragma unroll
-    for (int k = 0; k < 16; k++) p[tau + Gm::S * k] = reduce_4q(x[k], q);
+    for (int k = 0; k < 16; k++) p[tau + Gm::S * k] = reduce_fwd(x[k], P.m);
 }
 
 // inverse pass 1 (rows)
@@ -454,7 +460,7 @@ __global__ void __launch_bounds__(NT) k_ks_modup_row(DevCtx c, LevelTab lt, KsAr
     fwd_B<LOGR>(x, tau, base, 1, c.logR1, TwGlobal{P.fwd, c.logN}, q);
     xchg_row_BA<LOGR>(x, sm, tau, rl);
 #pragma unroll
-    for (int k = 0; k < 16; k++) p[tau + Gm::S * k] = reduce_4q(x[k], q);
+    for (int k = 0; k < 16; k++) p[tau + Gm::S * k] = reduce_fwd(x[k], P.m);
 }
 
 // (4b) inner product with the key, acc_k[t] = sum_j ext_j[t] * key_j[k][t].
@@ -652,7 +658,7 @@ __global__ void __launch_bounds__(NT) k_ks_md_row_out(DevCtx c, LevelTab lt, KsA
 #pragma unroll
     for (int k = 0; k < 16; k++) {
         const int e = tau + Gm::S * k;
-        u64 v = sub_mod(ac[e], reduce_4q(x[k], q), q);
+        u64 v = sub_mod(ac[e], reduce_fwd(x[k], P.m), q);
         v = mul_shoup(v, pinv.x, pinv.y, q);
         if (addp) {
             const u64 *ap = addp + item * a.add_item + (long long)i * N;
@@ -773,7 +779,7 @@ __global__ void __launch_bounds__(NT) k_rs_row_out(DevCtx c, LevelTab lt, Rescal
 #pragma unroll
     for (int k = 0; k < 16; k++) {
         const int e = tau + Gm::S * k;
-        u64 v = sub_mod(src[e], reduce_4q(x[k], q), q);
+        u64 v = sub_mod(src[e], reduce_fwd(x[k], P.m), q);
         o[e] = mul_shoup(v, inv.x, inv.y, q);
     }
 }
