@@ -239,6 +239,11 @@ def run_ours(args, rank, world):
         barrier()
         return max_over_ranks(e0.elapsed_time(e1) / k, world)
 
+    # where the time goes: one uniform batch with events around every phase
+    outs, phase_ms = F.fhe_infer_profiled(ctx, model, evk, cts, B, n_out, stream)
+    for h in outs:
+        F.fhe_ct_free(h)
+
     # single-image baseline (one image per launch sequence)
     for _ in range(max(1, args.warmup)):
         infer(cts[:n_in], 1)
@@ -356,6 +361,7 @@ def run_ours(args, rank, world):
             "l2": "inputs larger than L2: every step streams %.1f GB of resident weight plaintexts "
                   "(L2 is 0.13 GB)" % (plaintext_bytes(prog, N) / 1e9),
             "setup_s": round(t_setup, 1),
+            "uniform_batch_phase_ms": {k: round(v, 1) for k, v in phase_ms.items()},
             "parallelism": "replicas" if world > 1 else "single",
         },
         "clocks": clocks,

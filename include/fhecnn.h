@@ -257,6 +257,16 @@ int fhe_infer(fhe_ctx *ctx, const fhe_model *model, const fhe_evk *evk, const fh
               size_t n_img, fhe_ct **out, void *stream);
 
 /*
+ * fhe_infer with a timing breakdown: CUDA events on `stream` around every
+ * phase; ms_by_kind[16] receives the summed milliseconds per phase kind:
+ * [FHE_STEP_RESCALE], [FHE_STEP_ACT], [FHE_STEP_ROTSUM], [FHE_STEP_CMUL],
+ * [FHE_STEP_DROP], [FHE_STEP_ADD], and for linear steps [10] baby-step
+ * rotations, [11] plaintext MAC, [12] giant-step rotations.
+ */
+int fhe_infer_profiled(fhe_ctx *ctx, const fhe_model *model, const fhe_evk *evk, const fhe_ct *const *in,
+                       size_t n_img, fhe_ct **out, void *stream, double *ms_by_kind);
+
+/*
  * Continuous batching with images at mixed levels.  The program is cut after
  * every activation (and its rescale) into S segments; a group of up to
  * `group` images enters per tick and leaves S-1 ticks later, so up to

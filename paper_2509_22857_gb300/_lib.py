@@ -95,6 +95,7 @@ def lib() -> ctypes.CDLL:
             "fhe_eval_quad_act": (c_int, [V, V, V, c_int, PP, c_size, V]),
             "fhe_eval_pool_dense": (c_int, [V, V, V, c_int, PP, c_size, PP, c_size, V]),
             "fhe_infer": (c_int, [V, V, V, PP, c_size, PP, V]),
+            "fhe_infer_profiled": (c_int, [V, V, V, PP, c_size, PP, V, P_DBL]),
             "fhe_pipeline_create": (c_int, [V, V, V, c_int, c_int, PP]),
             "fhe_pipeline_info": (c_int, [V, ctypes.POINTER(c_int), ctypes.POINTER(c_int), ctypes.POINTER(c_int),
                                           ctypes.POINTER(c_int)]),
@@ -334,6 +335,18 @@ def fhe_infer(ctx, model, evk, cts, n_img: int, n_out_per_img: int, stream=None)
     return [out[i] for i in range(n_img * n_out_per_img)]
 
 
+PHASES = {2: "rescale", 3: "activation", 4: "rotsum", 5: "cmul", 6: "drop", 7: "add",
+          10: "linear_baby_rotations", 11: "linear_mac", 12: "linear_giant_rotations"}
+
+
+def fhe_infer_profiled(ctx, model, evk, cts, n_img: int, n_out_per_img: int, stream=None):
+    """(output handles, {phase: ms})"""
+    out = (c_void * (n_img * n_out_per_img))()
+    ms = np.zeros(16, dtype=np.float64)
+    _check(lib().fhe_infer_profiled(ctx, model, evk, _handles(cts), n_img, out, _stream(stream), _ptr(ms, P_DBL)))
+    return [out[i] for i in range(n_img * n_out_per_img)], {PHASES[k]: float(ms[k]) for k in PHASES}
+
+
 def fhe_pipeline_create(ctx, model, evk, group: int, use_graphs: bool = True) -> int:
     h = c_void()
     _check(lib().fhe_pipeline_create(ctx, model, evk, group, int(use_graphs), ctypes.byref(h)))
@@ -428,6 +441,6 @@ EXPORTED = ["fhe_last_error", "fhe_kernel_launches", "fhe_ctx_create", "fhe_ctx_
             "fhe_rotate", "fhe_square", "fhe_rescale", "fhe_add", "fhe_mul_plain", "fhe_model_load",
             "fhe_model_free", "fhe_eval_conv", "fhe_eval_quad_act", "fhe_eval_pool_dense", "fhe_infer",
             "fhe_ntt_device", "fhe_evk_export", "fhe_sk_export", "fhe_encode_coeffs",
-            "fhe_profile_keyswitch", "fhe_rescale_noalloc", "fhe_pipeline_create", "fhe_pipeline_info",
+            "fhe_profile_keyswitch", "fhe_rescale_noalloc", "fhe_infer_profiled", "fhe_pipeline_create", "fhe_pipeline_info",
             "fhe_pipeline_tick", "fhe_pipeline_free", "fhe_server_create", "fhe_server_add_model",
             "fhe_server_submit", "fhe_server_poll", "fhe_server_stats", "fhe_server_destroy"]

@@ -247,6 +247,20 @@ struct Exec {
     std::vector<std::vector<char>> host_stage;
     Persist *pers = nullptr;              // non-null: pipeline mode
     int cur_step = -1;
+    // optional timing: events bracketing each phase, summed per phase kind
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> *prof = nullptr;
+    void mark(int kind, bool begin) {
+        if (!prof) return;
+        if (begin) {
+            cudaEvent_t a, b;
+            cudaEventCreate(&a);
+            cudaEventCreate(&b);
+            cudaEventRecord(a, s);
+            prof->push_back({kind, {a, b}});
+        } else {
+            cudaEventRecord(prof->back().second.second, s);
+        }
+    }
 
     long long ctst(int t) const { return 2ll * (m->tensors[t].level + 1) * m->ctx->N; }
     long long item(int t) const { return (long long)m->tensors[t].n_ct * ctst(t); }
@@ -358,6 +372,7 @@ struct Exec {
         std::vector<u64 *> rb(L.baby_ct.size(), nullptr);
         for (size_t k = 0; k < L.baby_ct.size(); k++) FHE_TRY(tmp(ti++, (size_t)B * cs * 8, &rb[k]));
         const long long nlN = (long long)(lv + 1) * c->N;
+        mark(10, true);
         for (size_t k = 0; k < L.baby_ct.size(); k++) {
             if (k > 0 && L.baby_ct[k] == L.baby_ct[k - 1]) continue;   // ModUp done for this input
             const u64 *x = in + L.baby_ct[k] * cs;
@@ -385,6 +400,7 @@ struct Exec {
                 FHE_TRY(keyswitch(a, KS_IP | KS_MODDOWN));
             }
         }
+        mark(10, false);
         // sources: the input ciphertexts, then the baby-step rotations
         const int n_in = m->tensors[st.src].n_ct;
         std::vector<MacSrc> hs;
@@ -440,7 +456,10 @@ struct Exec {
         ma.n_groups = ng;
         ma.n_items = B;
         ma.level = lv;
+        mark(11, true);
         FHE_CU(launch_mac(c->dc, ma, s));
+        mark(11, false);
+        mark(12, true);
         // giant steps: out_o += sum_g rot(acc_{o,g}, g) with one ModDown per
         // output: each term's ModUp and inner product accumulate in the
         // extended basis, the rotated c0 parts over Q
@@ -482,6 +501,7 @@ struct Exec {
             FHE_TRY(keyswitch(a, KS_MODDOWN));
         }
         tmp_free(c0acc);
+        mark(12, false);
         for (auto p : rb) tmp_free(p);
         for (auto p : acc) tmp_free(p);
         if (!pers) cudaFreeAsync(dw, s);
@@ -545,6 +565,7 @@ struct Exec {
         fhe_ctx *c = m->ctx;
         cur_step = i;
         FHE_TRY(alloc_t(st.dst));
+        if (st.kind != FHE_STEP_LINEAR) mark(st.kind, true);
         const MTensor &ti = m->tensors[st.src];
         const int n = B * ti.n_ct;
         switch (st.kind) {
@@ -574,6 +595,7 @@ struct Exec {
                               ctst(st.dst), n, 2, ti.level, 0, s));
             break;
         }
+        if (st.kind != FHE_STEP_LINEAR) mark(st.kind, false);
         if (m->last_use[st.src] == i) release(st.src);
         if (st.src2 >= 0 && m->last_use[st.src2] == i) release(st.src2);
         return FHE_OK;
@@ -587,8 +609,22 @@ int run_steps(Exec &e, int first, int last) {
 
 }  // namespace
 
+static int infer_impl(fhe_ctx *c, const fhe_model *mc, const fhe_evk *evk, const fhe_ct *const *in, size_t n_img,
+                      fhe_ct **out, void *stream, double *ms_by_kind);
+
 extern "C" int fhe_infer(fhe_ctx *c, const fhe_model *mc, const fhe_evk *evk, const fhe_ct *const *in, size_t n_img,
                          fhe_ct **out, void *stream) {
+    return infer_impl(c, mc, evk, in, n_img, out, stream, nullptr);
+}
+
+extern "C" int fhe_infer_profiled(fhe_ctx *c, const fhe_model *mc, const fhe_evk *evk, const fhe_ct *const *in,
+                                  size_t n_img, fhe_ct **out, void *stream, double *ms_by_kind) {
+    if (!ms_by_kind) return fhe_fail(FHE_E_INVAL, "null argument");
+    return infer_impl(c, mc, evk, in, n_img, out, stream, ms_by_kind);
+}
+
+static int infer_impl(fhe_ctx *c, const fhe_model *mc, const fhe_evk *evk, const fhe_ct *const *in, size_t n_img,
+                      fhe_ct **out, void *stream, double *ms_by_kind) {
     if (!c || !mc || !evk || !in || !out || n_img == 0) return fhe_fail(FHE_E_INVAL, "null argument");
     fhe_model *m = const_cast<fhe_model *>(mc);
     FHE_CU(cudaSetDevice(c->dev));
@@ -598,6 +634,8 @@ extern "C" int fhe_infer(fhe_ctx *c, const fhe_model *mc, const fhe_evk *evk, co
     e.B = (int)n_img;
     e.s = (cudaStream_t)stream;
     e.buf.assign(m->tensors.size(), nullptr);
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof;
+    if (ms_by_kind) e.prof = &prof;
     const MTensor &ti = m->tensors[m->input];
     for (size_t k = 0; k < n_img * ti.n_ct; k++) {
         if (!in[k] || in[k]->level != ti.level || in[k]->n_poly != 2)
@@ -633,6 +671,16 @@ extern "C" int fhe_infer(fhe_ctx *c, const fhe_model *mc, const fhe_evk *evk, co
     }
     cudaFreeAsync(e.buf[m->output], e.s);
     FHE_CU(cudaStreamSynchronize(e.s));
+    if (ms_by_kind) {
+        for (int k = 0; k < 16; k++) ms_by_kind[k] = 0;
+        for (auto &pr : prof) {
+            float ms = 0;
+            cudaEventElapsedTime(&ms, pr.second.first, pr.second.second);
+            if (pr.first >= 0 && pr.first < 16) ms_by_kind[pr.first] += ms;
+            cudaEventDestroy(pr.second.first);
+            cudaEventDestroy(pr.second.second);
+        }
+    }
     for (size_t k = 0; k < made.size(); k++) out[k] = made[k];
     return FHE_OK;
 }
