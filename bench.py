@@ -199,7 +199,7 @@ def run_ours(args, rank, world):
     net = synth.resnet20()
     raw = synth.params(net)
     prog = M.compile_network(net, raw, F.fhe_ctx_primes(ctx)[: pre["L"] + 1], pre["logn"], pre["log_scale"],
-                             "packed")
+                             "packed", pre["alpha"])
     sk, evk = F.fhe_keygen(ctx, synth.SEED_KEYS, sorted(prog.rotations))
     desc = M.ModelDesc(prog, N // 2)
     model = F.fhe_model_load(ctx, desc.desc)
@@ -424,9 +424,14 @@ def run_reference(args, rank, world):
     pre = synth.PRESETS[PRESET]
     prm = O.make_params(**dict(pre, logn=12))      # the plan depends on the primes' sizes only
     net = synth.resnet20()
-    comp = cnn.Compiler(prm, "packed")
+    raw = synth.params(net)
+    # the same baby-step / giant-step schedule as the GPU arm (host planning only)
+    from paper_2509_22857_gb300 import model as M
+    giants = M.giant_steps(M.compile_network(net, raw, prm.q, pre["logn"], pre["log_scale"], "packed",
+                                             pre["alpha"]))
+    comp = cnn.Compiler(prm, "packed", giants)
     comp.n = 1 << (pre["logn"] - 1)
-    prog = comp.compile(net, cnn.transform(net, synth.params(net)))
+    prog = comp.compile(net, cnn.transform(net, raw))
     unit = oracle_ledger(prog, pre["alpha"]) / ks_weight(pre["L"], pre["alpha"])
     _, S, keys, ct = oracle_rotation_seconds(pre, pre["L"])
     for _ in range(args.warmup):

@@ -311,12 +311,19 @@ class Compiler:
     """Builds the homomorphic program of a transformed network: layouts,
     diagonals, levels, scales and rescale points."""
 
-    def __init__(self, prm: C.Params, layout_kind: str):
+    def __init__(self, prm: C.Params, layout_kind: str, giants: Optional[List[int]] = None):
+        """giants: the giant-step size of each linear step in program order
+        (any split r = g + b with b = r mod G is a valid evaluation of the
+        same diagonals; the choice only moves work between baby and giant
+        rotations).  Default: one block for convolutions, 8 blocks for the
+        packed dense layer, the whole slot vector in the HW layout."""
         self.prm = prm
         self.n = prm.N // 2
         self.log_delta = math.log2(prm.scale)
         self.kind = layout_kind
         self.prog = Program()
+        self.giants = giants
+        self.n_linear = 0
 
     # -- tower reuse
     def _maybe_rescale(self, t: int) -> int:
@@ -331,6 +338,9 @@ class Compiler:
     def _linear(self, src: int, diags, G: int, Lout: Layout, w_scale: float,
                 bias_vecs: Optional[Dict[int, np.ndarray]], out_scale: Optional[float] = None) -> int:
         info = self.prog.tensors[src]
+        if self.giants is not None:
+            G = self.giants[self.n_linear]
+        self.n_linear += 1
         baby, groups = _bsgs(diags, G, self.n)
         prod_scale = info.scale * w_scale
         out = self.prog.new(TensorInfo(Lout, info.level, prod_scale if out_scale is None else out_scale))
@@ -340,7 +350,7 @@ class Compiler:
             for g in groups[o]:
                 if g:
                     self.prog.rot_steps.add(g)
-        self.prog.steps.append({"op": "linear", "src": src, "dst": out, "w_scale": w_scale,
+        self.prog.steps.append({"op": "linear", "src": src, "dst": out, "w_scale": w_scale, "giant": G,
                                 "bias_scale": prod_scale, "baby": baby, "groups": groups,
                                 "bias": bias_vecs or {}, "n_out": Lout.n_ct})
         return out
@@ -495,8 +505,9 @@ class Compiler:
         return self._maybe_rescale(out)
 
 
-def compile_he(net: List[Dict], t: Dict, prm: C.Params, layout_kind: str) -> Program:
-    return Compiler(prm, layout_kind).compile(net, t)
+def compile_he(net: List[Dict], t: Dict, prm: C.Params, layout_kind: str,
+               giants: Optional[List[int]] = None) -> Program:
+    return Compiler(prm, layout_kind, giants).compile(net, t)
 
 
 # =================================================================== running

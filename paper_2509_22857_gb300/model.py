@@ -12,7 +12,10 @@ Offline model preparation (run once per model, before inference):
   the gaps they leave (adaptive mapping);
 * every linear layer as diagonals in baby-step / giant-step form:
   out = sum_g rot_g( sum_(i,b) d'_(i,g,b) (.) rot_b(in_i) ), with
-  d'_(g,b) the diagonal of rotation g+b pre-rotated by -g;
+  d'_(g,b) the diagonal of rotation g+b pre-rotated by -g; the giant step
+  of a channel-packed convolution is k blocks of slots, k chosen per layer
+  by a key-switch cost model (``bsgs_cost``: baby steps share one ModUp per
+  input, giant steps share one ModDown per output);
 * levels, scales and rescale points by the tower-reuse rule of Sec. 4.3
   (rescale when round(log_Delta scale) exceeds round(log_Delta q_level)).
 
@@ -194,8 +197,40 @@ def _round_int(v: float) -> float:
     return math.copysign(math.floor(abs(v) + 0.5), v)
 
 
+def ks_cost(level: int, alpha: int) -> Tuple[float, float, float]:
+    """Cost, in length-N limb transforms, of the three parts of one hybrid key
+    switch at `level`: ModUp (inverse NTT of the level+1 limbs, then a forward
+    NTT of every digit on the limbs outside it), the key inner product (two
+    products per digit and extended limb, a quarter of a transform's
+    butterflies), ModDown (inverse NTT of 2 alpha special limbs, forward NTT
+    of 2 (level+1) limbs)."""
+    nl = level + 1
+    ext = nl + alpha
+    digits = [min(alpha, nl - j) for j in range(0, nl, alpha)]
+    modup = nl + sum(ext - d for d in digits)
+    ip = len(digits) * ext * 2 / 8
+    moddown = 2 * alpha + 2 * nl
+    return modup, ip, moddown
+
+
+def bsgs_cost(diag_keys, giant: int, level: int, alpha: int) -> float:
+    """Key-switch cost of a linear layer whose diagonals are diag_keys
+    {(out ct, in ct, r)} split as r = g + b, b = r mod giant: every input with
+    baby steps pays one ModUp, every baby step an inner product and a
+    ModDown; every giant step a ModUp and an inner product, every output with
+    giant steps one ModDown."""
+    mu, ip, md = ks_cost(level, alpha)
+    babies = {(i, r % giant) for (_, i, r) in diag_keys if r % giant}
+    giants = {(o, r - r % giant) for (o, _, r) in diag_keys if r - r % giant}
+    return (len({i for i, _ in babies}) * mu + len(babies) * (ip + md) + len(giants) * (mu + ip)
+            + len({o for o, _ in giants}) * md)
+
+
 class Planner:
-    def __init__(self, primes_q: Sequence[int], log_n: int, log_scale: float, layout: str):
+    def __init__(self, primes_q: Sequence[int], log_n: int, log_scale: float, layout: str, alpha: int = 3,
+                 max_giant_blocks: int = 8):
+        self.alpha = alpha
+        self.max_giant_blocks = max_giant_blocks
         self.q = list(primes_q)
         self.L = len(self.q) - 1
         self.n = 1 << (log_n - 1)
@@ -221,6 +256,18 @@ class Planner:
             return self._emit(kind=F.STEP_RESCALE, src=t, dst=self._t(info.layout, info.level - 1, info.scale / ql))
         return t
 
+    def _pick_giant(self, diag: Dict, block: int, level: int) -> int:
+        """giant step = k blocks, k in 1, 2, 4, .. max_giant_blocks: the
+        cheapest split by bsgs_cost (ties: the smaller k)"""
+        best = None
+        k = 1
+        while k <= self.max_giant_blocks and k * block <= self.n:
+            c = bsgs_cost(diag.keys(), k * block, level, self.alpha)
+            if best is None or c < best[0]:
+                best = (c, k * block)
+            k *= 2
+        return best[1]
+
     def _bsgs_step(self, src: int, diag: Dict, giant: int, dst_layout: SlotMap, w_scale: float,
                    bias: Optional[np.ndarray], bias_layout: SlotMap) -> int:
         info = self.p.tensors[src]
@@ -242,7 +289,7 @@ class Planner:
                 for ct, base in bias_layout.copies[ch]:
                     bias_vecs.setdefault(ct, np.zeros(self.n))[base + offs] = val
         return self._emit(kind=F.STEP_LINEAR, src=src, dst=dst, w_scale=w_scale, bias_scale=prod,
-                          groups=groups, bias=bias_vecs)
+                          groups=groups, bias=bias_vecs, giant=giant)
 
     def _shortcut_scale(self, info: TInfo, target: TInfo) -> float:
         ql = self.q[info.level]
@@ -274,8 +321,10 @@ class Planner:
             giant = self.n
         else:
             lout = map_packed(node["cout"], ho, wo, st, lin.row, lin.block, self.n)
-            giant = lin.block
+            giant = None
         diag = diagonals(prm["w"], node["stride"], node["pad"], lin, lout, self.n)
+        if giant is None:
+            giant = self._pick_giant(diag, lin.block, info.level)
         ws = self.delta if target is None else self._shortcut_scale(info, target)
         t = self._bsgs_step(src, diag, giant, lout, ws, prm["bias"], lout)
         t = self._rule(t)
@@ -369,8 +418,17 @@ class Planner:
         return self.p
 
 
-def compile_network(net, raw, primes_q, log_n, log_scale, layout) -> Program:
-    return Planner(primes_q, log_n, log_scale, layout).compile(net, prepare_params(net, raw))
+def compile_network(net, raw, primes_q, log_n, log_scale, layout, alpha: int = 3,
+                    max_giant_blocks: int = 8) -> Program:
+    """alpha: digit width of key switching (for the baby-step / giant-step
+    cost model); max_giant_blocks = 1 keeps the giant step at one block."""
+    return Planner(primes_q, log_n, log_scale, layout, alpha, max_giant_blocks).compile(net,
+                                                                                      prepare_params(net, raw))
+
+
+def giant_steps(prog: Program) -> List[int]:
+    """the giant-step size of every linear step, in program order"""
+    return [st["giant"] for st in prog.steps if st["kind"] == F.STEP_LINEAR]
 
 
 # =========================================================== to the C ABI

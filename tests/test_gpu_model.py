@@ -26,12 +26,14 @@ class Setup:
         self.pre = pre
         self.prm = O.make_params(**pre)
         self.S = O.CKKS(self.prm)
-        self.po = cnn.compile_he(self.net, cnn.transform(self.net, self.raw), self.prm, layout)
-        self.keys = self.S.keygen(synth.SEED_KEYS, sorted(self.po.rot_steps))
         self.ctx = F.fhe_ctx_create(pre["logn"], pre["L"], pre["q_bits"], pre["q0_bits"], pre["p_bits"],
                                     pre["alpha"], pre["log_scale"])
         self.pm = M.compile_network(self.net, self.raw, F.fhe_ctx_primes(self.ctx)[: pre["L"] + 1], pre["logn"],
-                                    pre["log_scale"], layout)
+                                    pre["log_scale"], layout, pre["alpha"])
+        # the oracle evaluates the same diagonals with the package's baby-step / giant-step split
+        self.po = cnn.compile_he(self.net, cnn.transform(self.net, self.raw), self.prm, layout,
+                                 M.giant_steps(self.pm))
+        self.keys = self.S.keygen(synth.SEED_KEYS, sorted(self.po.rot_steps))
         self.sk, self.evk = F.fhe_keygen(self.ctx, synth.SEED_KEYS, sorted(self.pm.rotations))
         self.desc = M.ModelDesc(self.pm, self.prm.N // 2)
         self.model = F.fhe_model_load(self.ctx, self.desc.desc)

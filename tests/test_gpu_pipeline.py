@@ -20,7 +20,8 @@ def mini():
                            pre["log_scale"])
     net = synth.resnet_mini()
     prog = M.compile_network(net, synth.params(net), F.fhe_ctx_primes(ctx)[: pre["L"] + 1], pre["logn"],
-                             pre["log_scale"], "packed")
+                             pre["log_scale"], "packed",
+                             pre["alpha"])
     sk, evk = F.fhe_keygen(ctx, synth.SEED_KEYS, sorted(prog.rotations))
     desc = M.ModelDesc(prog, N // 2)
     model = F.fhe_model_load(ctx, desc.desc)

@@ -23,7 +23,8 @@ def test_server_results_equal_alone():
     rots = set()
     for arch in ("resnet_mini", "vgg_mini"):
         net = synth.ARCHS[arch]()
-        prog = M.compile_network(net, synth.params(net), primes, pre["logn"], pre["log_scale"], "packed")
+        prog = M.compile_network(net, synth.params(net), primes, pre["logn"], pre["log_scale"], "packed",
+                                 pre["alpha"])
         progs.append(prog)
         rots |= prog.rotations
     sk, evk = F.fhe_keygen(ctx, synth.SEED_KEYS, sorted(rots))

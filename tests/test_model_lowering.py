@@ -17,10 +17,12 @@ def _both(arch, preset, layout):
     raw = synth.params(net)
     pre = synth.PRESETS[preset]
     prm = O.make_params(**dict(pre, logn=min(pre["logn"], 12)))   # primes' sizes fix the plan
-    c = cnn.Compiler(prm, layout)
+    pm = M.compile_network(net, raw, prm.q, pre["logn"], pre["log_scale"], layout, pre["alpha"])
+    # the baby-step / giant-step split is a schedule choice of the package's
+    # cost model; the oracle evaluates the same diagonals with the same split
+    c = cnn.Compiler(prm, layout, M.giant_steps(pm))
     c.n = 1 << (pre["logn"] - 1)
     po = c.compile(net, cnn.transform(net, raw))
-    pm = M.compile_network(net, raw, prm.q, pre["logn"], pre["log_scale"], layout)
     return po, pm
 
 
@@ -71,3 +73,18 @@ def test_input_slots_match_oracle():
     a = cnn.input_vectors(po, img, 2048)
     b = M.input_slots(pm, img, 2048)
     assert len(a) == len(b) and all(np.array_equal(x, y) for x, y in zip(a, b))
+
+
+def test_cost_model_prefers_wider_baby_steps_for_wide_layers():
+    """A 16-channel packed convolution: giant steps of one block need 15 giant
+    rotations per output; the cost model moves part of them to hoisted baby
+    steps, and never picks a split that costs more than one block."""
+    po, pm = _both("resnet_mini", "resnet_mini", "packed")
+    lin = [s for s in pm.steps if s["kind"] == 1]
+    blk = pm.tensors[pm.input].layout.block
+    assert any(s["giant"] > blk for s in lin)
+    for s in lin:
+        keys = {(o, i, (g + b)) for (o, g), terms in s["groups"].items() for (i, b, _) in terms}
+        lv = pm.tensors[s["src"]].level
+        assert M.bsgs_cost(keys, s["giant"], lv, 3) <= M.bsgs_cost(keys, blk, lv, 3)
+

@@ -121,3 +121,42 @@ def test_resnet20_program_levels_follow_tower_reuse():
     assert prog.tensors[prog.output_tensor].level == 0
     assert n_rescale >= 20
     assert prm.L == 20
+
+
+@pytest.mark.slow
+def test_giant_step_choice_keeps_the_layer_function():
+    """The first convolution of the mini ResNet under CKKS with giant steps of
+    one block and of four blocks (more baby steps, fewer giant steps): both
+    decrypt to the float64 convolution (the split is a schedule choice)."""
+    net = synth.resnet_mini()
+    raw = synth.params(net)
+    t = cnn.transform(net, raw)
+    pre = synth.PRESETS["resnet_mini"]
+    prm = C.make_params(**pre)
+    S = C.CKKS(prm)
+    img = synth.image(0, 3, 8, 8)
+    ref = cnn.conv2d(img, t[1]["w"], 1, 1) + t[1]["bias"][:, None, None]
+    n_lin = sum(1 for s in cnn.compile_he(net, t, prm, "packed").steps if s["op"] == "linear")
+    got = []
+    for k in (1, 4):
+        prog = cnn.compile_he(net, t, prm, "packed", [64 * k] * n_lin)
+        st = prog.steps[0]
+        assert st["op"] == "linear" and st["giant"] == 64 * k
+        keys = S.keygen(synth.SEED_KEYS, sorted(prog.rot_steps))
+        cts = cnn.encrypt_input(S, keys, prog, img, 0, synth.enc_seed)
+        vals = cnn.run_he(S, keys, prog, cts, stop_after=0)
+        out = vals[st["dst"]]
+        L = prog.tensors[st["dst"]].layout
+        z = [S.decrypt_decode(keys, ct).real for ct in out]
+        got.append(np.array([[[z[L.rep[c][0][0]][L.slot(L.rep[c][0][1], h, w)] for w in range(8)]
+                              for h in range(8)] for c in range(len(L.rep))]))
+        # fewer giant rotations with the wider baby steps
+        n_giant = sum(1 for gs in st["groups"].values() for g in gs if g)
+        n_baby = len(st["baby"])
+        if k == 1:
+            g1, b1 = n_giant, n_baby
+        else:
+            assert n_giant < g1 and n_baby > b1
+    # key-switching noise at Delta = 2^25, N = 2^12 is about 1e-4 on these values
+    for y in got:
+        assert np.max(np.abs(y - ref)) < 2e-3
