@@ -346,8 +346,9 @@ def run_ours(args, rank, world):
         "data": "synthetic",
         "config": {
             "workload": "ResNet-20 (16/32/64, 3x3 blocks, 1x1 stride-2 shortcuts), 32x32x3 seeded uniform "
-                        "images, 10 classes; CKKS N=2^16, Delta=2^25, q0 40-bit + 20 x 50-bit, 3 x 58-bit "
-                        "special primes, digit width 3; channel-packed layout",
+                        "images, 10 classes; CKKS N=2^16, Delta=2^25, q0 40-bit + 20 x 50-bit, %d x 58-bit "
+                        "special primes, digit width %d (dnum %d); channel-packed layout"
+                        % (pre["alpha"], pre["alpha"], -(-(pre["L"] + 1) // pre["alpha"])),
             "batch": S * g,
             "mixed_levels": True,
             "pipeline": "%d segments (cut after each activation), a group of %d images enters per tick; "
@@ -410,10 +411,10 @@ def cpu_baseline(prog, weighted_ks, pre):
     secs = oracle_rotation_seconds(pre, pre["L"])[0]
     per_img = secs * weighted_ks / ks_weight(pre["L"], pre["alpha"])
     return {"value": round(1.0 / per_img, 8), "unit": "img/s", "cores": 1, "kind": "oracle",
-            "sample": "one hybrid-key-switch rotation at the top level (N=2^16, 21+3 primes) timed on the CPU "
+            "sample": "one hybrid-key-switch rotation at the top level (N=2^16, 21 + %d primes) timed on the CPU "
                       "oracle (%.1f s), scaled by the image's key switches weighted by limb transforms "
                       "(%.0f top-level equivalents); plaintext products and additions not counted" %
-                      (secs, weighted_ks / ks_weight(pre["L"], pre["alpha"]))}
+                      (pre["alpha"], secs, weighted_ks / ks_weight(pre["L"], pre["alpha"]))}
 
 
 def run_reference(args, rank, world):
@@ -458,13 +459,16 @@ def run_ks_only(args):
     detailed profiles of the key-switching kernels."""
     import torch
     from paper_2509_22857_gb300 import _lib as F
-    pre = synth.PRESETS[PRESET]
+    pre = dict(synth.PRESETS[PRESET])
+    if args.alpha is not None:
+        pre["alpha"] = args.alpha
     ctx = F.fhe_ctx_create(pre["logn"], pre["L"], pre["q_bits"], pre["q0_bits"], pre["p_bits"], pre["alpha"],
                            pre["log_scale"], 0)
     sk, evk = F.fhe_keygen(ctx, synth.SEED_KEYS, [])
     level = pre["L"] if args.ks_level is None else args.ks_level
     ms = F.fhe_profile_keyswitch(ctx, evk, level, args.batch, max(1, args.steps), torch.cuda.current_stream())
-    print(json.dumps({"level": level, "items": args.batch, "kernel_ms": dict(zip(KS_KERNELS, ms)),
+    print(json.dumps({"level": level, "alpha": pre["alpha"], "items": args.batch,
+                      "kernel_ms": dict(zip(KS_KERNELS, ms)),
                       "total_ms": sum(ms), "us_per_item": sum(ms) / args.batch * 1e3}))
     F.fhe_evk_free(evk)
     F.fhe_sk_free(sk)
@@ -481,6 +485,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ks-only", action="store_true", help="time only the top-level key switch")
     ap.add_argument("--ks-level", type=int, default=None)
+    ap.add_argument("--alpha", type=int, default=None, help="--ks-only: digit width (special primes)")
     args = ap.parse_args()
     if args.ks_only:
         run_ks_only(args)

@@ -85,63 +85,72 @@ struct TwShared {
 
 // ---- stages.  jb + e*js is the global index of local element e.  In every
 // stage the butterflies of a group of 2*half consecutive registers share one
-// twiddle, which is loaded once per group.
+// twiddle, which is loaded once per group.  Each stage is its own template
+// instance so that every register index is a compile-time constant (the
+// 16-element tile then stays in registers instead of local memory).
+// Layout A: stages s = 0..3 on elements strided by S; layout B: stages
+// s = 4..LOGR-1 on 16 contiguous elements.
+template <int LOGR, int s>
+struct StageGeo {
+    static constexpr int half = s < 4 ? (8 >> s) : ((1 << LOGR) >> (s + 1));
+    // local index of the first element of the group that starts at register k0
+    __device__ static __forceinline__ int elem(int tau, int k0) {
+        return s < 4 ? tau + Geo<LOGR>::S * k0 : 16 * tau + k0;
+    }
+};
+
+template <int LOGR, int s, class TW>
+__device__ __forceinline__ void fwd_stage(u64 (&x)[16], int tau, int jb, int js, int sg0, TW tw, u64 q) {
+    using G = StageGeo<LOGR, s>;
+#pragma unroll
+    for (int k0 = 0; k0 < 16; k0 += 2 * G::half) {
+        const ulonglong2 w = tw(sg0 + s, jb + G::elem(tau, k0) * js);
+#pragma unroll
+        for (int u = 0; u < G::half; u++) ct_bf(x[k0 + u], x[k0 + u + G::half], w, q);
+    }
+}
+
+template <int LOGR, int s, class TW>
+__device__ __forceinline__ void inv_stage(u64 (&x)[16], int tau, int jb, int js, int sg0, TW tw, u64 q) {
+    using G = StageGeo<LOGR, s>;
+#pragma unroll
+    for (int k0 = 0; k0 < 16; k0 += 2 * G::half) {
+        const ulonglong2 w = tw(sg0 + s, jb + G::elem(tau, k0) * js);
+#pragma unroll
+        for (int u = 0; u < G::half; u++) gs_bf(x[k0 + u], x[k0 + u + G::half], w, q);
+    }
+}
+
 template <int LOGR, class TW>
 __device__ __forceinline__ void fwd_A(u64 (&x)[16], int tau, int jb, int js, int sg0, TW tw, u64 q) {
-    constexpr int S = Geo<LOGR>::S;
-#pragma unroll
-    for (int s = 0; s < 4; s++) {
-        const int half = 8 >> s;
-#pragma unroll
-        for (int k0 = 0; k0 < 16; k0 += 2 * half) {
-            const ulonglong2 w = tw(sg0 + s, jb + (tau + S * k0) * js);
-#pragma unroll
-            for (int u = 0; u < half; u++) ct_bf(x[k0 + u], x[k0 + u + half], w, q);
-        }
-    }
+    fwd_stage<LOGR, 0>(x, tau, jb, js, sg0, tw, q);
+    fwd_stage<LOGR, 1>(x, tau, jb, js, sg0, tw, q);
+    fwd_stage<LOGR, 2>(x, tau, jb, js, sg0, tw, q);
+    fwd_stage<LOGR, 3>(x, tau, jb, js, sg0, tw, q);
 }
 
 template <int LOGR, class TW>
 __device__ __forceinline__ void fwd_B(u64 (&x)[16], int tau, int jb, int js, int sg0, TW tw, u64 q) {
-#pragma unroll
-    for (int s = 4; s < LOGR; s++) {
-        const int half = (1 << LOGR) >> (s + 1);
-#pragma unroll
-        for (int k0 = 0; k0 < 16; k0 += 2 * half) {
-            const ulonglong2 w = tw(sg0 + s, jb + (16 * tau + k0) * js);
-#pragma unroll
-            for (int u = 0; u < half; u++) ct_bf(x[k0 + u], x[k0 + u + half], w, q);
-        }
-    }
+    if constexpr (LOGR > 4) fwd_stage<LOGR, 4>(x, tau, jb, js, sg0, tw, q);
+    if constexpr (LOGR > 5) fwd_stage<LOGR, 5>(x, tau, jb, js, sg0, tw, q);
+    if constexpr (LOGR > 6) fwd_stage<LOGR, 6>(x, tau, jb, js, sg0, tw, q);
+    if constexpr (LOGR > 7) fwd_stage<LOGR, 7>(x, tau, jb, js, sg0, tw, q);
 }
 
 template <int LOGR, class TW>
 __device__ __forceinline__ void inv_B(u64 (&x)[16], int tau, int jb, int js, int sg0, TW tw, u64 q) {
-#pragma unroll
-    for (int s = LOGR - 1; s >= 4; s--) {
-        const int half = (1 << LOGR) >> (s + 1);
-#pragma unroll
-        for (int k0 = 0; k0 < 16; k0 += 2 * half) {
-            const ulonglong2 w = tw(sg0 + s, jb + (16 * tau + k0) * js);
-#pragma unroll
-            for (int u = 0; u < half; u++) gs_bf(x[k0 + u], x[k0 + u + half], w, q);
-        }
-    }
+    if constexpr (LOGR > 7) inv_stage<LOGR, 7>(x, tau, jb, js, sg0, tw, q);
+    if constexpr (LOGR > 6) inv_stage<LOGR, 6>(x, tau, jb, js, sg0, tw, q);
+    if constexpr (LOGR > 5) inv_stage<LOGR, 5>(x, tau, jb, js, sg0, tw, q);
+    if constexpr (LOGR > 4) inv_stage<LOGR, 4>(x, tau, jb, js, sg0, tw, q);
 }
 
 template <int LOGR, class TW>
 __device__ __forceinline__ void inv_A(u64 (&x)[16], int tau, int jb, int js, int sg0, TW tw, u64 q) {
-    constexpr int S = Geo<LOGR>::S;
-#pragma unroll
-    for (int s = 3; s >= 0; s--) {
-        const int half = 8 >> s;
-#pragma unroll
-        for (int k0 = 0; k0 < 16; k0 += 2 * half) {
-            const ulonglong2 w = tw(sg0 + s, jb + (tau + S * k0) * js);
-#pragma unroll
-            for (int u = 0; u < half; u++) gs_bf(x[k0 + u], x[k0 + u + half], w, q);
-        }
-    }
+    inv_stage<LOGR, 3>(x, tau, jb, js, sg0, tw, q);
+    inv_stage<LOGR, 2>(x, tau, jb, js, sg0, tw, q);
+    inv_stage<LOGR, 1>(x, tau, jb, js, sg0, tw, q);
+    inv_stage<LOGR, 0>(x, tau, jb, js, sg0, tw, q);
 }
 
 // stage the first 2^LOGR twiddles (all a column pass uses) in shared memory
@@ -211,6 +220,10 @@ __device__ __forceinline__ void xchg_row_BA(u64 (&x)[16], u64 *sm, int tau, int 
 }
 
 constexpr int SMEM_WORDS = 4096 + 256;
+// elements per thread whose basis-conversion sums are accumulated together
+#ifndef CONV_CHUNK
+#define CONV_CHUNK 4
+#endif
 
 // ================================================================ plain NTT
 
@@ -411,21 +424,21 @@ __global__ void __launch_bounds__(NT, 3) k_ks_modup_col(DevCtx c, LevelTab lt, K
     const long long sc = (long long)Gm::S << logC;
     u64 x[16];
 #pragma unroll
-    for (int h8 = 0; h8 < 16; h8 += 8) {
-        U128 acc[8];
+    for (int h8 = 0; h8 < 16; h8 += CONV_CHUNK) {
+        U128 acc[CONV_CHUNK];
 #pragma unroll
-        for (int k = 0; k < 8; k++) acc[k] = U128{0, 0};
+        for (int k = 0; k < CONV_CHUNK; k++) acc[k] = U128{0, 0};
         for (int u = 0; u < nu; u++) {
             const u64 h = hat[u * ext + t];
             const u64 *yp = y + ((long long)(d_lo + u) << c.logN) + col + ((long long)tau << logC) + h8 * sc;
-            u64 v[8];
+            u64 v[CONV_CHUNK];
 #pragma unroll
-            for (int k = 0; k < 8; k++) v[k] = yp[k * sc];
+            for (int k = 0; k < CONV_CHUNK; k++) v[k] = yp[k * sc];
 #pragma unroll
-            for (int k = 0; k < 8; k++) mac(acc[k], v[k], h);
+            for (int k = 0; k < CONV_CHUNK; k++) mac(acc[k], v[k], h);
         }
 #pragma unroll
-        for (int k = 0; k < 8; k++) x[h8 + k] = barrett(acc[k], P.m);
+        for (int k = 0; k < CONV_CHUNK; k++) x[h8 + k] = barrett(acc[k], P.m);
     }
     fwd_A<LOGR>(x, tau, col, 1 << logC, 0, tws, q);
     xchg_col_AB<LOGR>(x, sm, tau, cl);
@@ -436,7 +449,7 @@ __global__ void __launch_bounds__(NT, 3) k_ks_modup_col(DevCtx c, LevelTab lt, K
 
 // (4) ModUp: NTT rows of every converted limb, in place
 template <int LOGR>
-__global__ void __launch_bounds__(NT) k_ks_modup_row(DevCtx c, LevelTab lt, KsArgs a, KsLayout ly) {
+__global__ void __launch_bounds__(NT, 3) k_ks_modup_row(DevCtx c, LevelTab lt, KsArgs a, KsLayout ly) {
     using Gm = Geo<LOGR>;
     __shared__ u64 sm[SMEM_WORDS];
     const int ext = lt.ext, nd = lt.n_digits;
@@ -607,21 +620,21 @@ __global__ void __launch_bounds__(NT, 3) k_ks_md_conv_col(DevCtx c, LevelTab lt,
     const long long sc = (long long)Gm::S << logC;
     u64 x[16];
 #pragma unroll
-    for (int h8 = 0; h8 < 16; h8 += 8) {
-        U128 acc[8];
+    for (int h8 = 0; h8 < 16; h8 += CONV_CHUNK) {
+        U128 acc[CONV_CHUNK];
 #pragma unroll
-        for (int k = 0; k < 8; k++) acc[k] = U128{0, 0};
+        for (int k = 0; k < CONV_CHUNK; k++) acc[k] = U128{0, 0};
         for (int u = 0; u < al; u++) {
             const u64 h = c.md_phat[u * (c.L + 1) + i];
             const u64 *zp = z + (long long)u * N + col + ((long long)tau << logC) + h8 * sc;
-            u64 v[8];
+            u64 v[CONV_CHUNK];
 #pragma unroll
-            for (int k = 0; k < 8; k++) v[k] = zp[k * sc];
+            for (int k = 0; k < CONV_CHUNK; k++) v[k] = zp[k * sc];
 #pragma unroll
-            for (int k = 0; k < 8; k++) mac(acc[k], v[k], h);
+            for (int k = 0; k < CONV_CHUNK; k++) mac(acc[k], v[k], h);
         }
 #pragma unroll
-        for (int k = 0; k < 8; k++) x[h8 + k] = sub_mod(barrett(acc[k], P.m), halfp, q);
+        for (int k = 0; k < CONV_CHUNK; k++) x[h8 + k] = sub_mod(barrett(acc[k], P.m), halfp, q);
     }
     fwd_A<LOGR>(x, tau, col, 1 << logC, 0, tws, q);
     xchg_col_AB<LOGR>(x, sm, tau, cl);
@@ -632,7 +645,7 @@ __global__ void __launch_bounds__(NT, 3) k_ks_md_conv_col(DevCtx c, LevelTab lt,
 
 // (8) ModDown: NTT rows, out_k = (acc_k - conv) * P^-1 (+ addend) (+= out)
 template <int LOGR>
-__global__ void __launch_bounds__(NT) k_ks_md_row_out(DevCtx c, LevelTab lt, KsArgs a, KsLayout ly) {
+__global__ void __launch_bounds__(NT, 3) k_ks_md_row_out(DevCtx c, LevelTab lt, KsArgs a, KsLayout ly) {
     using Gm = Geo<LOGR>;
     __shared__ u64 sm[SMEM_WORDS];
     const int nl = a.level + 1;
@@ -755,7 +768,7 @@ __global__ void __launch_bounds__(NT) k_rs_conv_col(DevCtx c, LevelTab lt, Resca
 }
 
 template <int LOGR>
-__global__ void __launch_bounds__(NT) k_rs_row_out(DevCtx c, LevelTab lt, RescaleArgs a) {
+__global__ void __launch_bounds__(NT, 3) k_rs_row_out(DevCtx c, LevelTab lt, RescaleArgs a) {
     using Gm = Geo<LOGR>;
     __shared__ u64 sm[SMEM_WORDS];
     const int lv = a.level;
@@ -878,7 +891,10 @@ __global__ void k_decrypt(DevCtx c, const u64 *ct, const u64 *s, u64 *m, int lev
 // images (thread = coefficient x image) and computes every output group of
 // the step: the rotated inputs it reads stay in L1 across groups, and the
 // CTAs of the image tiles of one coefficient tile run back to back so each
-// plaintext tile is fetched from HBM once per batch.
+// plaintext tile is fetched from HBM once per batch.  Products are summed in
+// 128 bits and reduced only when the sum could leave Barrett's range: with
+// b = bitlen(q), K products of residues stay below K q^2 < 2^(b+62) for
+// K <= 2^(62-b) (4096 terms for 50-bit primes).
 #define MAC_TC 32
 #define MAC_IB 8
 __global__ void __launch_bounds__(256) k_mac(DevCtx c, MacArgs a) {
@@ -890,18 +906,45 @@ __global__ void __launch_bounds__(256) k_mac(DevCtx c, MacArgs a) {
     if (img >= a.n_items) return;
     const long long off = (long long)limb * N + blockIdx.y * MAC_TC + cl;
     const long long P = (long long)(a.level + 1) * N;
+    // products summed before a reduction (one slot kept for the carried residue)
+    const int kmax = (m.b >= 61 ? 2 : (1 << min(62 - m.b, 20))) - 1;
     for (int g = 0; g < a.n_groups; g++) {
         const MacGroup G = a.groups[g];
         U128 acc0 = {0, 0}, acc1 = {0, 0};
         int cnt = 0;
-        for (int t = G.term_begin; t < G.term_end; t++) {
+        int t = G.term_begin;
+        // four terms per iteration: their loads are in flight together
+        for (; t + 4 <= G.term_end; t += 4) {
+            u64 p[4], x0[4], x1[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const MacTerm T = a.terms[t + k];
+                const MacSrc S = a.srcs[T.src];
+                const u64 *sp = S.base + (long long)img * S.item + off;
+                p[k] = __ldg(&T.pt[off]);
+                x0[k] = sp[0];
+                x1[k] = sp[P];
+            }
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                mac(acc0, p[k], x0[k]);
+                mac(acc1, p[k], x1[k]);
+            }
+            cnt += 4;
+            if (cnt + 4 > kmax) {
+                acc0 = U128{barrett(acc0, m), 0};
+                acc1 = U128{barrett(acc1, m), 0};
+                cnt = 0;
+            }
+        }
+        for (; t < G.term_end; t++) {
             const MacTerm T = a.terms[t];
             const MacSrc S = a.srcs[T.src];
             const u64 p = __ldg(&T.pt[off]);
             const u64 *sp = S.base + (long long)img * S.item + off;
             mac(acc0, p, sp[0]);
             mac(acc1, p, sp[P]);
-            if (++cnt == 7) {
+            if (++cnt == kmax) {
                 acc0 = U128{barrett(acc0, m), 0};
                 acc1 = U128{barrett(acc1, m), 0};
                 cnt = 0;

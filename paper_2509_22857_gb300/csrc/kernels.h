@@ -171,6 +171,7 @@ struct MacArgs {
     int n_groups;
     int n_items;
     int level;
+    int n_srcs;               // entries of srcs
 };
 cudaError_t launch_mac(const DevCtx &c, const MacArgs &a, cudaStream_t s);
 

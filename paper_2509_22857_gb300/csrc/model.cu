@@ -454,6 +454,7 @@ struct Exec {
         ma.terms = (const MacTerm *)(dw + gb);
         ma.srcs = (const MacSrc *)(dw + gb + tb);
         ma.n_groups = ng;
+        ma.n_srcs = (int)hs.size();
         ma.n_items = B;
         ma.level = lv;
         mark(11, true);

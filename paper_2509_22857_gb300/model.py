@@ -198,18 +198,20 @@ def _round_int(v: float) -> float:
 
 
 def ks_cost(level: int, alpha: int) -> Tuple[float, float, float]:
-    """Cost, in length-N limb transforms, of the three parts of one hybrid key
-    switch at `level`: ModUp (inverse NTT of the level+1 limbs, then a forward
-    NTT of every digit on the limbs outside it), the key inner product (two
-    products per digit and extended limb, a quarter of a transform's
-    butterflies), ModDown (inverse NTT of 2 alpha special limbs, forward NTT
+    """Cost, in length-N limb transforms (8 modular products per coefficient),
+    of the three parts of one hybrid key switch at `level`: ModUp (inverse NTT
+    of the level+1 limbs; per digit a basis conversion of its d primes to the
+    ext - d others, d products per output coefficient, and their forward
+    NTT), the key inner product (two products per digit and extended limb),
+    ModDown (inverse NTT of 2 alpha special limbs, conversion of both
+    polynomials to the level+1 primes with alpha products each, forward NTT
     of 2 (level+1) limbs)."""
     nl = level + 1
     ext = nl + alpha
     digits = [min(alpha, nl - j) for j in range(0, nl, alpha)]
-    modup = nl + sum(ext - d for d in digits)
+    modup = nl + sum((ext - d) * (1 + d / 8) for d in digits)
     ip = len(digits) * ext * 2 / 8
-    moddown = 2 * alpha + 2 * nl
+    moddown = 2 * alpha + 2 * nl * (1 + alpha / 8)
     return modup, ip, moddown
 
 

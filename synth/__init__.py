@@ -14,6 +14,12 @@ workloads; no dataset items are reproduced):
   dense bias              N(0, 0.01), seed 2 (after the batch-norm draws)
   activation coefficients a ~ N(0.1,0.02), b ~ N(0.5,0.05), c ~ N(0,0.01),
                           one triple per activation layer, seed 3
+  ensemble member m       weights and batch norm from seeds 1 + 100 m and
+                          2 + 100 m; the activation polynomial of a layer
+                          (seed 3) is shared by the members
+  clustered weights       per layer, joint k-means in R^M over the members'
+                          weight draws (k centroids, ``cluster_joint``);
+                          every weight is replaced by its centroid's entry
 """
 from __future__ import annotations
 
@@ -35,9 +41,9 @@ def image(i: int, c: int, h: int, w: int) -> np.ndarray:
 
 # ----------------------------------------------------------------- shapes
 
-def _conv(src, cin, cout, k, stride, pad, name):
+def _conv(src, cin, cout, k, stride, pad, name, bn=True):
     return {"op": "conv", "src": src, "cin": cin, "cout": cout, "k": k,
-            "stride": stride, "pad": pad, "bn": True, "name": name}
+            "stride": stride, "pad": pad, "bn": bn, "name": name}
 
 
 def tiny() -> List[Dict]:
@@ -51,7 +57,7 @@ def tiny() -> List[Dict]:
     return net
 
 
-def resnet(widths=(16, 32, 64), blocks=3, in_hw=32, num_classes=10) -> List[Dict]:
+def resnet(widths=(16, 32, 64), blocks=3, in_hw=32, num_classes=10, bn=True) -> List[Dict]:
     """CIFAR-style ResNet: conv 3->widths[0], len(widths) stages of `blocks`
     basic blocks (the first block of every later stage has stride 2 and a
     1x1 stride-2 convolution on the shortcut, the others identity
@@ -64,7 +70,7 @@ def resnet(widths=(16, 32, 64), blocks=3, in_hw=32, num_classes=10) -> List[Dict
         net.append(node)
         return len(net) - 1
 
-    x = add(_conv(0, 3, widths[0], 3, 1, 1, "conv1"))
+    x = add(_conv(0, 3, widths[0], 3, 1, 1, "conv1", bn))
     x = add({"op": "act", "src": x})
     cin = widths[0]
     hw = in_hw
@@ -72,11 +78,11 @@ def resnet(widths=(16, 32, 64), blocks=3, in_hw=32, num_classes=10) -> List[Dict
         for b in range(blocks):
             stride = 2 if (s > 0 and b == 0) else 1
             hw //= stride
-            a = add(_conv(x, cin, cout, 3, stride, 1, "s%db%da" % (s + 1, b + 1)))
+            a = add(_conv(x, cin, cout, 3, stride, 1, "s%db%da" % (s + 1, b + 1), bn))
             a = add({"op": "act", "src": a})
-            m = add(_conv(a, cout, cout, 3, 1, 1, "s%db%db" % (s + 1, b + 1)))
+            m = add(_conv(a, cout, cout, 3, 1, 1, "s%db%db" % (s + 1, b + 1), bn))
             if stride != 1 or cin != cout:
-                sc = add(_conv(x, cin, cout, 1, stride, 0, "s%db%dsc" % (s + 1, b + 1)))
+                sc = add(_conv(x, cin, cout, 1, stride, 0, "s%db%dsc" % (s + 1, b + 1), bn))
             else:
                 sc = x
             y = add({"op": "add", "src": [m, sc]})
@@ -97,6 +103,22 @@ def resnet_mini() -> List[Dict]:
     """A ResNet with the same structure at a small size (8x8x3 input,
     4/8/16 channels, one block per stage) for full-network parity tests."""
     return resnet((4, 8, 16), 1, 8, 10)
+
+
+def resnet18(num_classes: int = 200) -> List[Dict]:
+    """ResNet-18 for 64x64x3 (Tiny-ImageNet shape): 3x3 stem, four stages of
+    two basic blocks with 64/128/256/512 channels (stride 2 and a 1x1
+    shortcut convolution at each later stage), global 8x8 average pool,
+    dense 512->num_classes.  No batch norm: the weights are clustered after
+    folding, so the synthetic model is drawn already folded (see
+    ``cluster_joint``)."""
+    return resnet((64, 128, 256, 512), 2, 64, num_classes, bn=False)
+
+
+def resnet18_mini() -> List[Dict]:
+    """ResNet-18's structure (four stages of two basic blocks, 18 levels) at
+    a small size: 16x16x3, 2/2/4/4 channels, global 2x2 pool, 10 classes."""
+    return resnet((2, 2, 4, 4), 2, 16, 10, bn=False)
 
 
 def vgg(cfg=(64, "M", 128, "M", 256, 256, "M", 512, 512, "M", 512, 512, "M"), in_hw=32,
@@ -139,15 +161,19 @@ def vgg_mini() -> List[Dict]:
     return vgg(cfg=(4, "M", 8, "M", "M"), in_hw=8, fc=(8,), num_classes=10)
 
 
-ARCHS = {"tiny": tiny, "resnet20": resnet20, "resnet_mini": resnet_mini, "vgg11": vgg11, "vgg_mini": vgg_mini}
+ARCHS = {"tiny": tiny, "resnet20": resnet20, "resnet_mini": resnet_mini, "vgg11": vgg11, "vgg_mini": vgg_mini,
+         "resnet18": resnet18, "resnet18_mini": resnet18_mini}
 
 
 # ------------------------------------------------------------- parameters
 
-def params(net: List[Dict]) -> Dict[int, Dict[str, np.ndarray]]:
-    """Raw (unfolded) parameters keyed by node index, drawn in node order."""
-    rw = np.random.default_rng(SEED_WEIGHTS)
-    rb = np.random.default_rng(SEED_BN)
+def params(net: List[Dict], model: int = 0) -> Dict[int, Dict[str, np.ndarray]]:
+    """Raw (unfolded) parameters keyed by node index, drawn in node order;
+    `model` selects an ensemble member (its own weight and batch-norm draws,
+    the shared activation polynomials).  A convolution without batch norm
+    gets the identity (gamma 1, beta 0, mu 0, sigma 1)."""
+    rw = np.random.default_rng(SEED_WEIGHTS + 100 * model)
+    rb = np.random.default_rng(SEED_BN + 100 * model)
     ra = np.random.default_rng(SEED_ACT)
     out: Dict[int, Dict[str, np.ndarray]] = {}
     for i, nd in enumerate(net):
@@ -155,20 +181,64 @@ def params(net: List[Dict]) -> Dict[int, Dict[str, np.ndarray]]:
             fan_in = nd["cin"] * nd["k"] * nd["k"]
             w = rw.normal(0.0, fan_in ** -0.5, size=(nd["cout"], nd["cin"], nd["k"], nd["k"]))
             c = nd["cout"]
-            out[i] = {
-                "w": w,
-                "bias": np.zeros(c),
-                "gamma": rb.uniform(0.5, 1.5, c),
-                "beta": rb.normal(0.0, 0.1, c),
-                "mu": rb.normal(0.0, 0.1, c),
-                "sigma": rb.uniform(0.5, 1.5, c),
-            }
+            if nd.get("bn", True):
+                bn = {"gamma": rb.uniform(0.5, 1.5, c), "beta": rb.normal(0.0, 0.1, c),
+                      "mu": rb.normal(0.0, 0.1, c), "sigma": rb.uniform(0.5, 1.5, c)}
+            else:
+                bn = {"gamma": np.ones(c), "beta": np.zeros(c), "mu": np.zeros(c), "sigma": np.ones(c)}
+            out[i] = dict(w=w, bias=np.zeros(c), **bn)
         elif nd["op"] == "dense":
             w = rw.normal(0.0, nd["cin"] ** -0.5, size=(nd["cout"], nd["cin"]))
             out[i] = {"w": w, "bias": rb.normal(0.0, 0.01, nd["cout"])}
         elif nd["op"] == "act":
             out[i] = {"a": ra.normal(0.1, 0.02), "b": ra.normal(0.5, 0.05),
                       "c": ra.normal(0.0, 0.01)}
+    return out
+
+
+def kmeans(points: np.ndarray, k: int, iters: int = 100):
+    """Lloyd's k-means on points [n, d] (float64), deterministic: the initial
+    centroids are the points at ranks floor((j + 1/2) n / k) of the order by
+    (first coordinate, index); an assignment goes to the nearest centroid
+    (squared Euclidean distance as |c|^2 - 2 p.c, ties to the lower index);
+    a centroid is the mean of its points (an empty cluster keeps its
+    centroid); stops when no
+    assignment changes or after `iters` rounds.  Returns (centroids [k, d],
+    assignment [n])."""
+    n = len(points)
+    order = np.lexsort((np.arange(n), points[:, 0]))
+    k = min(k, n)
+    cent = points[order[((np.arange(k) + 0.5) * n / k).astype(np.int64)]].copy()
+    assign = None
+    for _ in range(iters):
+        # |p - c|^2 = |c|^2 - 2 p.c + |p|^2; |p|^2 is the same for every c
+        d2 = (cent * cent).sum(axis=1)[None, :] - 2.0 * (points @ cent.T)
+        new = np.argmin(d2, axis=1)
+        if assign is not None and np.array_equal(new, assign):
+            break
+        assign = new
+        cnt = np.bincount(assign, minlength=k)
+        for dim in range(points.shape[1]):
+            tot = np.bincount(assign, weights=points[:, dim], minlength=k)
+            cent[cnt > 0, dim] = tot[cnt > 0] / cnt[cnt > 0]
+    return cent, assign
+
+
+def cluster_joint(raws: List[Dict[int, Dict[str, np.ndarray]]], net: List[Dict], k: int = 16):
+    """Joint weight clustering of an ensemble: for every convolution and
+    dense layer, the M members' weights at one position form a point of R^M;
+    k-means (``kmeans``) over all positions of the layer gives k centroid
+    vectors, and member m's weight becomes entry m of its position's
+    centroid.  Returns new parameter dicts (other entries shared)."""
+    out = [{i: dict(p) for i, p in r.items()} for r in raws]
+    for i, nd in enumerate(net):
+        if nd["op"] not in ("conv", "dense"):
+            continue
+        shape = raws[0][i]["w"].shape
+        pts = np.stack([r[i]["w"].reshape(-1) for r in raws], axis=1)
+        cent, assign = kmeans(pts, k)
+        for m in range(len(raws)):
+            out[m][i]["w"] = cent[assign, m].reshape(shape)
     return out
 
 
@@ -179,10 +249,14 @@ def enc_seed(image_index: int, ct_index: int) -> int:
 
 # CKKS parameter presets: ring degree 2^logn; q_1..q_L of q_bits, q_0 of
 # q0_bits, alpha special primes of p_bits (alpha is also the digit width of
-# hybrid key switching); default scale Delta = 2^log_scale.
+# hybrid key switching); default scale Delta = 2^log_scale.  The N = 2^16
+# networks use dnum = 3 digits at the top level: alpha = 7 special primes of
+# 58 bits (406 bits) cover a digit of seven 50-bit primes.
 PRESETS = {
     "tiny": dict(logn=13, L=4, q_bits=40, q0_bits=40, p_bits=40, alpha=1, log_scale=40),
     "resnet_mini": dict(logn=12, L=8, q_bits=50, q0_bits=40, p_bits=58, alpha=3, log_scale=25),
-    "vgg11": dict(logn=16, L=11, q_bits=50, q0_bits=40, p_bits=58, alpha=3, log_scale=25),
-    "resnet20": dict(logn=16, L=20, q_bits=50, q0_bits=40, p_bits=58, alpha=3, log_scale=25),
+    "vgg11": dict(logn=16, L=11, q_bits=50, q0_bits=40, p_bits=58, alpha=7, log_scale=25),
+    "resnet20": dict(logn=16, L=20, q_bits=50, q0_bits=40, p_bits=58, alpha=7, log_scale=25),
+    "resnet18": dict(logn=16, L=18, q_bits=50, q0_bits=40, p_bits=58, alpha=7, log_scale=25),
+    "resnet18_mini": dict(logn=12, L=18, q_bits=50, q0_bits=40, p_bits=58, alpha=7, log_scale=25),
 }

@@ -15,7 +15,10 @@ TINY = dict(logn=13, L=4, q_bits=40, q0_bits=40, p_bits=40, alpha=1, log_scale=4
 # prime widths of the ResNet-20 chain (40-bit q0, 50-bit q_i, 58-bit p_j):
 # basis conversions between primes of different widths
 WIDE = dict(logn=12, L=6, q_bits=50, q0_bits=40, p_bits=58, alpha=3, log_scale=25)
-CFGS = {"small": SMALL, "tiny": TINY, "wide": WIDE}
+# the ResNet-20 chain and digits (21 Q primes, dnum = 3 digits of 7 primes,
+# 7 special primes) on a small ring; lower levels have a ragged last digit
+DNUM3 = dict(logn=12, L=20, q_bits=50, q0_bits=40, p_bits=58, alpha=7, log_scale=25)
+CFGS = {"small": SMALL, "tiny": TINY, "wide": WIDE, "dnum3": DNUM3}
 
 
 @pytest.fixture(scope="module", params=list(CFGS))
