@@ -140,8 +140,8 @@ def program_ledger(prog, alpha):
         t_in = prog.tensors[st["src"]]
         lv = t_in.level
         if st["kind"] == 1:
-            babies = {(i, b) for terms in st["groups"].values() for (i, b, _) in terms if b}
-            giants = [k for k in st["groups"] if k[1]]
+            babies = {(i, b) for i, b in zip(st["t_ct"], st["t_baby"]) if b}
+            giants = {(o, g) for o, g in zip(st["t_out"], st["t_giant"]) if g}
             k = len(babies) + len(giants)
         elif st["kind"] == 3:
             k = t_in.layout.n_ct
@@ -158,7 +158,7 @@ def plaintext_bytes(prog, N):
     total = 0
     for st in prog.steps:
         if st["kind"] == 1:
-            n_pt = sum(len(t) for t in st["groups"].values()) + len(st["bias"])
+            n_pt = len(st["vecs"]) + len(st["bias"])
             total += n_pt * (prog.tensors[st["src"]].level + 1) * N * 8
     return total
 

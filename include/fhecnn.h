@@ -185,8 +185,10 @@ int fhe_mul_plain(fhe_ctx *ctx, const fhe_ct *a, const fhe_pt *pt, fhe_ct **out,
  *   automorphism is applied to the extended limbs), and the giant-step
  *   rotations of one output share one ModDown (their inner products are summed
  *   in the extended basis Q_l u P first).
- *   where term vectors (n_slots doubles each) are encoded at w_scale and the
- *   bias vectors at bias_scale, both at the input's level.
+ *   where the term vectors (rows of vecs, n_slots doubles each; terms that
+ *   share a row share one plaintext in HBM, as clustered weights do,
+ *   Sec. 5.2) are encoded at w_scale and the bias vectors at bias_scale,
+ *   both at the input's level.
  * ACT: c1 and c0 are integers (given as integral doubles of any size) that
  *   are already scaled: out = x^2 + c1*x + c0 (c0 added to poly 0).
  * CMUL: out = value * x (value an integral double).
@@ -205,7 +207,9 @@ typedef struct {
     const int32_t *group_term_begin; /* [n_groups + 1] */
     const int32_t *term_ct;          /* [n_terms] input ciphertext index */
     const int32_t *term_baby;        /* [n_terms] baby rotation step b */
-    const double *term_vec;          /* [n_terms][n_slots] */
+    const int32_t *term_vec_id;      /* [n_terms] row of vecs */
+    int n_vecs;                      /* distinct term vectors (one plaintext each) */
+    const double *vecs;              /* [n_vecs][n_slots] */
     int n_bias;
     const int32_t *bias_out;         /* [n_bias] output ciphertext index */
     const double *bias_vec;          /* [n_bias][n_slots] */

@@ -75,6 +75,7 @@ def lib():
             "orc_vec_add_scalar": (None, [U64P, u64, U64P, sz, u64]),
             "orc_vec_from_signed": (None, [I64P, U64P, sz, u64]),
             "orc_basis_convert": (None, [U64P, U64P, i32, u64, U64P, sz]),
+            "orc_conv_overflow": (None, [U64P, U64P, i32, U64P, sz]),
             "orc_chacha20_block": (None, [U32P, u32, U32P, U32P]),
             "orc_stream_words": (None, [u64, u32, u32, u32, U32P, sz]),
             "orc_sample_uniform": (None, [u64, u32, u32, u32, u64, U64P, sz]),
@@ -203,6 +204,17 @@ def basis_convert(x: np.ndarray, q_in: Sequence[int], t: int) -> np.ndarray:
     n = x.shape[-1]
     out = np.empty(n, dtype=np.uint64)
     lib().orc_basis_convert(_p(x, U64P), _p(qi, U64P), len(q_in), t, _p(out, U64P), n)
+    return out
+
+
+def conv_overflow(x: np.ndarray, q_in: Sequence[int]) -> np.ndarray:
+    """u with basis_convert(x, q_in, t) = x + u*Qin (mod t): the number of
+    times the fast conversion overshoots, found exactly (0 <= u < len(q_in))."""
+    x = np.ascontiguousarray(x, dtype=np.uint64)
+    qi = np.array(q_in, dtype=np.uint64)
+    n = x.shape[-1]
+    out = np.empty(n, dtype=np.uint64)
+    lib().orc_conv_overflow(_p(x, U64P), _p(qi, U64P), len(q_in), _p(out, U64P), n)
     return out
 
 
@@ -626,7 +638,11 @@ class CKKS:
         return acc
 
     def moddown(self, acc: np.ndarray, level: int) -> np.ndarray:
-        """(acc - [acc]_P centred) * P^-1 over Q_level: [2][level+1][N]"""
+        """(acc - [acc]_P centred) * P^-1 over Q_level: [2][level+1][N], i.e.
+        acc / P rounded to the nearest integer.  [acc]_P + floor(P/2) is
+        brought from the special primes to each q_i exactly: the fast
+        conversion's overshoot u*P is removed (conv_overflow), then floor(P/2)
+        is subtracted, which centres the representative."""
         prm = self.prm
         Qidx = list(range(level + 1))
         Pidx = list(range(prm.L + 1, prm.L + 1 + prm.alpha))
@@ -636,9 +652,11 @@ class CKKS:
         for r in range(2):
             p_part = self.from_ntt(acc[r, len(Qidx):], Pidx)
             p_part = np.stack([vadd_scalar(p_part[m], half_p % pq[m], pq[m]) for m in range(len(pq))])
+            u = conv_overflow(p_part, pq)
             for i in Qidx:
                 qi = prm.primes[i]
                 conv = basis_convert(p_part, pq, qi)
+                conv = vsub(conv, vmul_scalar(u, prm.P % qi, qi), qi)
                 conv = vsub(conv, np.full(prm.N, half_p % qi, dtype=np.uint64), qi)
                 conv = ntt(conv, qi, prm.psi[i])
                 out[r, i] = vmul_scalar(vsub(acc[r, i], conv, qi), invmod(prm.P % qi, qi), qi)

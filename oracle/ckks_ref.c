@@ -275,6 +275,91 @@ void orc_basis_convert(const uint64_t *in, const uint64_t *q_in, int n_in,
     free(hat_t);
 }
 
+/*
+ * Overflow of the fast conversion above: with y_i = [x_i (Qin/q_i)^-1]_{q_i}
+ * the sum  sum_i y_i (Qin/q_i)  equals x + u Qin for the x in [0, Qin) whose
+ * residues are x_i, and u = floor(sum_i y_i / q_i) < n_in.  u is found here
+ * exactly: the sum is formed as a multi-word integer and Qin is subtracted
+ * while it is not below Qin.  (Words are little-endian 64-bit.)
+ */
+static void mp_mul_word(const uint64_t *a, int w, uint64_t b, uint64_t *out) {
+    u128 carry = 0;
+    for (int k = 0; k < w; k++) {
+        u128 t = (u128)a[k] * b + carry;
+        out[k] = (uint64_t)t;
+        carry = t >> 64;
+    }
+}
+
+static void mp_add(uint64_t *a, const uint64_t *b, int w) {
+    u128 carry = 0;
+    for (int k = 0; k < w; k++) {
+        u128 t = (u128)a[k] + b[k] + carry;
+        a[k] = (uint64_t)t;
+        carry = t >> 64;
+    }
+}
+
+static int mp_cmp(const uint64_t *a, const uint64_t *b, int w) {
+    for (int k = w - 1; k >= 0; k--) {
+        if (a[k] != b[k]) return a[k] > b[k] ? 1 : -1;
+    }
+    return 0;
+}
+
+static void mp_sub(uint64_t *a, const uint64_t *b, int w) {
+    uint64_t borrow = 0;
+    for (int k = 0; k < w; k++) {
+        uint64_t bk = b[k] + borrow;
+        uint64_t nb = (bk < borrow) || (a[k] < bk);
+        a[k] -= bk;
+        borrow = nb;
+    }
+}
+
+void orc_conv_overflow(const uint64_t *in, const uint64_t *q_in, int n_in, uint64_t *u_out, size_t n) {
+    const int w = n_in + 1;
+    uint64_t *qhat = (uint64_t *)calloc((size_t)n_in * w, sizeof(uint64_t));
+    uint64_t *qall = (uint64_t *)calloc(w, sizeof(uint64_t));
+    uint64_t *tmp = (uint64_t *)calloc(w, sizeof(uint64_t));
+    uint64_t *acc = (uint64_t *)calloc(w, sizeof(uint64_t));
+    uint64_t *hat_inv = (uint64_t *)malloc(n_in * sizeof(uint64_t));
+    qall[0] = 1;
+    for (int i = 0; i < n_in; i++) {
+        mp_mul_word(qall, w, q_in[i], tmp);
+        memcpy(qall, tmp, w * sizeof(uint64_t));
+        uint64_t *h = qhat + (size_t)i * w;
+        h[0] = 1;
+        uint64_t hm = 1;
+        for (int k = 0; k < n_in; k++) {
+            if (k == i) continue;
+            mp_mul_word(h, w, q_in[k], tmp);
+            memcpy(h, tmp, w * sizeof(uint64_t));
+            hm = orc_mulmod(hm, q_in[k] % q_in[i], q_in[i]);
+        }
+        hat_inv[i] = orc_invmod(hm, q_in[i]);
+    }
+    for (size_t k = 0; k < n; k++) {
+        memset(acc, 0, w * sizeof(uint64_t));
+        for (int i = 0; i < n_in; i++) {
+            uint64_t y = orc_mulmod(in[(size_t)i * n + k], hat_inv[i], q_in[i]);
+            mp_mul_word(qhat + (size_t)i * w, w, y, tmp);
+            mp_add(acc, tmp, w);
+        }
+        uint64_t u = 0;
+        while (mp_cmp(acc, qall, w) >= 0) {
+            mp_sub(acc, qall, w);
+            u++;
+        }
+        u_out[k] = u;
+    }
+    free(qhat);
+    free(qall);
+    free(tmp);
+    free(acc);
+    free(hat_inv);
+}
+
 /* --------------------------------------------------------------- ChaCha20 */
 
 static uint32_t rotl32(uint32_t x, int r) { return (x << r) | (x >> (32 - r)); }

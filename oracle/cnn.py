@@ -198,6 +198,20 @@ def packed_layout(c: int, H: int, W: int, st: int, Wp: int, B: int, n_slots: int
     return Layout(c // nb, rep, H, W, st, Wp, B)
 
 
+def hw_ensemble_layout(c: int, H: int, W: int, n_slots: int, members: int) -> Layout:
+    """HW layout shared by an ensemble of `members` networks (Sec. 5.3):
+    channel c alone in ciphertext c, member m's copy in block m; the other
+    blocks stay zero."""
+    B = H * W
+    assert members * B <= n_slots
+    return Layout(c, [[(ch, m * B) for m in range(members)] for ch in range(c)], H, W, 1, W, B)
+
+
+def forward_ensemble(net: List[Dict], raws: List[Dict], img: np.ndarray) -> np.ndarray:
+    """Averaged logits of the ensemble members (float64)."""
+    return sum(forward_plain(net, r, img) for r in raws) / float(len(raws))
+
+
 def single_layout(c: int, B: int, n_slots: int) -> Layout:
     """One value per channel, channel k at block k (no replicas)."""
     nb = n_slots // B
@@ -243,18 +257,23 @@ class Program:
         return k
 
 
-def _lower_conv(w: np.ndarray, stride: int, pad: int, Lin: Layout, Lout: Layout,
+def _lower_conv(w, stride: int, pad: int, Lin: Layout, Lout: Layout,
                 n_slots: int) -> Dict[Tuple[int, int, int], np.ndarray]:
     """Diagonals {(out ct, in ct, r): vector} of a convolution between
     layouts: out slot so reads in slot si = so + r (mod n).  For each output
     replica, each input channel is read from its replica whose base is the
-    smallest distance (base_in - base_out) mod n after it (ties: lower ct)."""
-    cout, cin, k, _ = w.shape
+    smallest distance (base_in - base_out) mod n after it (ties: lower ct).
+    w is one weight tensor, or a list: replica k of every output channel
+    uses w[k] (an ensemble member per block)."""
+    wl = w if isinstance(w, list) else None
+    w0 = wl[0] if wl is not None else w
+    cout, cin, k, _ = w0.shape
     diags: Dict[Tuple[int, int, int], np.ndarray] = {}
     hs = np.arange(Lout.H)
     ws = np.arange(Lout.W)
     for o in range(cout):
-        for (oct_, obase) in Lout.rep[o]:
+        for rk, (oct_, obase) in enumerate(Lout.rep[o]):
+            w = wl[rk] if wl is not None else w0
             so = obase + (hs[:, None] * Lout.st) * Lout.Wp + ws[None, :] * Lout.st
             for i in range(cin):
                 ict, ibase = min(Lin.rep[i], key=lambda cb: ((cb[1] - obase) % n_slots, cb[0]))
@@ -296,14 +315,17 @@ def _bsgs(diags, G: int, n_slots: int):
     return sorted(baby), groups
 
 
-def _bias_vector(bias: np.ndarray, Lout: Layout, n_slots: int) -> Dict[int, np.ndarray]:
+def _bias_vector(bias, Lout: Layout, n_slots: int) -> Dict[int, np.ndarray]:
+    """bias: one vector over channels, or a list (replica k uses bias[k])"""
+    bl = bias if isinstance(bias, list) else None
     vecs: Dict[int, np.ndarray] = {}
-    for o in range(len(bias)):
-        for (ct, base) in Lout.rep[o]:
+    for o in range(len(bl[0] if bl is not None else bias)):
+        for rk, (ct, base) in enumerate(Lout.rep[o]):
+            b = bl[rk] if bl is not None else bias
             v = vecs.setdefault(ct, np.zeros(n_slots))
             for h in range(Lout.H):
                 for w in range(Lout.W):
-                    v[Lout.slot(base, h, w)] = bias[o]
+                    v[Lout.slot(base, h, w)] = b[o]
     return vecs
 
 
@@ -311,7 +333,7 @@ class Compiler:
     """Builds the homomorphic program of a transformed network: layouts,
     diagonals, levels, scales and rescale points."""
 
-    def __init__(self, prm: C.Params, layout_kind: str, giants: Optional[List[int]] = None):
+    def __init__(self, prm: C.Params, layout_kind: str, giants: Optional[List[int]] = None, members: int = 1):
         """giants: the giant-step size of each linear step in program order
         (any split r = g + b with b = r mod G is a valid evaluation of the
         same diagonals; the choice only moves work between baby and giant
@@ -324,6 +346,7 @@ class Compiler:
         self.prog = Program()
         self.giants = giants
         self.n_linear = 0
+        self.members = members
 
     # -- tower reuse
     def _maybe_rescale(self, t: int) -> int:
@@ -355,7 +378,15 @@ class Compiler:
                                 "bias": bias_vecs or {}, "n_out": Lout.n_ct})
         return out
 
-    def compile(self, net: List[Dict], t: Dict) -> Program:
+    def compile(self, net: List[Dict], t) -> Program:
+        """t: one model's transformed parameters, or a list of them (an
+        ensemble in the hw_ens layout; the members share activation
+        polynomials and shortcut multipliers)."""
+        ts = t if isinstance(t, list) else [t]
+        t = ts[0]
+        for i, nd in enumerate(net):
+            if nd["op"] in ("act", "add"):
+                assert all(x[i] == t[i] for x in ts), "members must share activations and shortcuts"
         prm, n = self.prm, self.n
         node_t: Dict[int, int] = {}
         shortcut_convs = {nd["src"][1] for nd in net if nd["op"] == "add"
@@ -365,6 +396,8 @@ class Compiler:
             if op == "input":
                 if self.kind == "hw":
                     L0 = hw_layout(nd["c"], nd["h"], nd["w"], n)
+                elif self.kind == "hw_ens":
+                    L0 = hw_ensemble_layout(nd["c"], nd["h"], nd["w"], n, self.members)
                 else:
                     L0 = packed_layout(nd["c"], nd["h"], nd["w"], 1, nd["w"], nd["h"] * nd["w"], n)
                 node_t[i] = self.prog.new(TensorInfo(L0, prm.L, prm.scale))
@@ -372,7 +405,7 @@ class Compiler:
             elif op == "conv":
                 if i in shortcut_convs:
                     continue
-                node_t[i] = self._conv(node_t[nd["src"]], nd, t[i], None)
+                node_t[i] = self._conv(node_t[nd["src"]], nd, [x[i] for x in ts], None)
             elif op == "act":
                 src = node_t[nd["src"]]
                 info = self.prog.tensors[src]
@@ -401,14 +434,14 @@ class Compiler:
                 ta = node_t[a]
                 ia = self.prog.tensors[ta]
                 if net[b]["op"] == "conv":
-                    tb = self._conv(node_t[net[b]["src"]], net[b], t[b], ia)
+                    tb = self._conv(node_t[net[b]["src"]], net[b], [x[b] for x in ts], ia)
                 else:
                     tb = self._shortcut_const(node_t[b], t[i]["shortcut_const"], ia)
                 out = self.prog.new(TensorInfo(ia.layout, ia.level, ia.scale))
                 self.prog.steps.append({"op": "add", "src": [ta, tb], "dst": out})
                 node_t[i] = out
             elif op == "dense":
-                node_t[i] = self._dense(node_t[nd["src"]], nd, t[i])
+                node_t[i] = self._dense(node_t[nd["src"]], nd, [x[i] for x in ts])
         self.prog.output_tensor = node_t[len(net) - 1]
         return self.prog
 
@@ -442,33 +475,42 @@ class Compiler:
         info.scale = target.scale
         return t
 
-    def _conv(self, src: int, nd: Dict, tp: Dict, target: Optional[TensorInfo]) -> int:
+    def _conv(self, src: int, nd: Dict, tps: List[Dict], target: Optional[TensorInfo]) -> int:
+        """tps: the layer's parameters of every member (one entry unless the
+        layout is hw_ens, where output replica k uses member k)"""
         info = self.prog.tensors[src]
         Lin = info.layout
         Ho = (Lin.H + 2 * nd["pad"] - nd["k"]) // nd["stride"] + 1
         Wo = (Lin.W + 2 * nd["pad"] - nd["k"]) // nd["stride"] + 1
         st = Lin.st * nd["stride"]
-        if self.kind == "hw":
+        if self.kind in ("hw", "hw_ens"):
             Lout = Layout(nd["cout"], [[(o, base) for (_, base) in Lin.rep[0]] for o in range(nd["cout"])],
                           Ho, Wo, st, Lin.Wp, Lin.B)
             G = self.n
         else:
             Lout = packed_layout(nd["cout"], Ho, Wo, st, Lin.Wp, Lin.B, self.n)
             G = Lin.B
-        diags = _lower_conv(tp["w"], nd["stride"], nd["pad"], Lin, Lout, self.n)
+        if self.kind == "hw_ens":
+            w_in, b_in = [tp["w"] for tp in tps], [tp["bias"] for tp in tps]
+        else:
+            w_in, b_in = tps[0]["w"], tps[0]["bias"]
+        diags = _lower_conv(w_in, nd["stride"], nd["pad"], Lin, Lout, self.n)
         w_scale = self.prm.scale if target is None else self._target_scale(info, target)[0]
-        bias = _bias_vector(tp["bias"], Lout, self.n)
+        bias = _bias_vector(b_in, Lout, self.n)
         out = self._linear(src, diags, G, Lout, w_scale, bias)
         out = self._maybe_rescale(out)
         if target is not None:
             out = self._align(out, target)
         return out
 
-    def _dense(self, src: int, nd: Dict, tp: Dict) -> int:
+    def _dense(self, src: int, nd: Dict, tps: List[Dict]) -> int:
         info = self.prog.tensors[src]
         Lin = info.layout
         cout = nd["cout"]
+        tp = tps[0]
         w = tp["w"]
+        if self.kind == "hw_ens":
+            return self._dense_ensemble(src, nd, tps)
         if self.kind == "hw":
             # per-output partial products in block k, then a sum over the block
             cin = len(Lin.rep)
@@ -505,9 +547,49 @@ class Compiler:
         return self._maybe_rescale(out)
 
 
-def compile_he(net: List[Dict], t: Dict, prm: C.Params, layout_kind: str,
-               giants: Optional[List[int]] = None) -> Program:
-    return Compiler(prm, layout_kind, giants).compile(net, t)
+    def _dense_ensemble(self, src: int, nd: Dict, tps: List[Dict]) -> int:
+        """Ensemble dense layer and average (Sec. 5.3) in the HW layout: the
+        pooled feature of channel c, member m, sits in ciphertext c at slot
+        m*B; logit k of member m is accumulated at slot m*B + k from the
+        diagonal r = -k with weight w_m[k, c] / M (the 1/M of the average
+        folded into the weights and bias); every diagonal is a giant step
+        (G = 1).  Then the blocks are summed with rotations by B, 2B, ..,
+        so the average of logit k lands in slot k."""
+        info = self.prog.tensors[src]
+        Lin = info.layout
+        cout, M, B = nd["cout"], self.members, Lin.B
+        assert Lin.H == 1 and Lin.W == 1 and cout <= B
+        diags: Dict[Tuple[int, int, int], np.ndarray] = {}
+        for c in range(len(Lin.rep)):
+            ict = Lin.rep[c][0][0]
+            for k in range(cout):
+                v = diags.setdefault((0, ict, (-k) % self.n), np.zeros(self.n))
+                for m in range(M):
+                    assert Lin.rep[c][m][1] == m * B
+                    v[m * B + k] = tps[m]["w"][k, c] / float(M)
+        Lpart = Layout(1, [[(0, m * B + k) for m in range(M)] for k in range(cout)], 1, 1, 1, 1, B)
+        bias = np.zeros(self.n)
+        for k in range(cout):
+            for m in range(M):
+                bias[m * B + k] = tps[m]["bias"][k] / float(M)
+        out = self._linear(src, diags, 1, Lpart, self.prm.scale, {0: bias})
+        out = self._maybe_rescale(out)
+        oi = self.prog.tensors[out]
+        steps = []
+        span = 1
+        while span < M:
+            steps.append(span * B)
+            span *= 2
+        res = self.prog.new(TensorInfo(Layout(1, [[(0, k)] for k in range(cout)], 1, 1, 1, 1, B), oi.level,
+                                       oi.scale))
+        self.prog.steps.append({"op": "rotsum", "src": out, "dst": res, "steps": steps})
+        self.prog.rot_steps.update(steps)
+        return res
+
+
+def compile_he(net: List[Dict], t, prm: C.Params, layout_kind: str,
+               giants: Optional[List[int]] = None, members: int = 1) -> Program:
+    return Compiler(prm, layout_kind, giants, members).compile(net, t)
 
 
 # =================================================================== running

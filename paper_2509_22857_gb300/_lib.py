@@ -34,7 +34,8 @@ class FheStepDesc(ctypes.Structure):
                 ("w_scale", c_double), ("bias_scale", c_double),
                 ("n_groups", c_int), ("group_out", P_I32), ("group_giant", P_I32),
                 ("group_term_begin", P_I32), ("term_ct", P_I32), ("term_baby", P_I32),
-                ("term_vec", P_DBL), ("n_bias", c_int), ("bias_out", P_I32), ("bias_vec", P_DBL),
+                ("term_vec_id", P_I32), ("n_vecs", c_int), ("vecs", P_DBL),
+                ("n_bias", c_int), ("bias_out", P_I32), ("bias_vec", P_DBL),
                 ("c1", c_double), ("c0", c_double), ("value", c_double),
                 ("n_steps", c_int), ("steps", P_I32), ("level", c_int)]
 

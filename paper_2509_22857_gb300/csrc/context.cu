@@ -343,6 +343,23 @@ static int build_tables(fhe_ctx *c) {
     c->dc.md_halfp = (const u64 *)d;
     FHE_TRY(upload(c, pinv.data(), pinv.size() * sizeof(ulonglong2), &d));
     c->dc.md_pinv = (const ulonglong2 *)d;
+    // exact ModDown: fixed-point weights 2^E / p_m and P mod q_i
+    int min_bits = 64;
+    for (int m = 0; m < al; m++) min_bits = std::min(min_bits, 64 - __builtin_clzll(c->primes[L + 1 + m]));
+    const int E = 63 + min_bits;
+    std::vector<u64> mw(al), pmod(L + 1);
+    for (int m = 0; m < al; m++) mw[m] = (u64)(((unsigned __int128)1 << E) / c->primes[L + 1 + m]);
+    for (int i = 0; i <= L; i++) {
+        const u64 q = c->primes[i];
+        u64 pm = 1;
+        for (int u = 0; u < al; u++) pm = h_mulmod(pm, c->primes[L + 1 + u] % q, q);
+        pmod[i] = pm;
+    }
+    c->dc.md_E = E;
+    FHE_TRY(upload(c, mw.data(), al * 8, &d));
+    c->dc.md_w = (const u64 *)d;
+    FHE_TRY(upload(c, pmod.data(), pmod.size() * 8, &d));
+    c->dc.md_pmod = (const u64 *)d;
 
     // per-level tables
     c->lt.resize(L + 1);

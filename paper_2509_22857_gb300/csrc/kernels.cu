@@ -327,7 +327,7 @@ __global__ void __launch_bounds__(NT) k_ntt_inv_col(DevCtx c, NttArgs a) {
 // ================================================================ key switching
 
 struct KsLayout {
-    long long y, mu, acc, z, md;   // word offsets inside one item's workspace
+    long long y, mu, acc, z, md, u;   // word offsets inside one item's workspace
 };
 
 __host__ __device__ inline KsLayout ks_layout(int level, int n_digits, int alpha, int logN) {
@@ -339,6 +339,7 @@ __host__ __device__ inline KsLayout ks_layout(int level, int n_digits, int alpha
     L.acc = L.mu + (long long)n_digits * ext * N;
     L.z = L.acc + 2ll * ext * N;
     L.md = L.z + 2ll * alpha * N;
+    L.u = L.md + 2ll * (level + 1) * N;
     return L;
 }
 
@@ -598,6 +599,26 @@ __global__ void __launch_bounds__(NT) k_ks_md_intt_col(DevCtx c, LevelTab lt, Ks
     }
 }
 
+// (6b) ModDown: overshoot of the fast conversion from P, per coefficient:
+// z_m = [x (P/p_m)^-1]_{p_m} for x = [acc]_P + floor(P/2) in [0, P), and
+// sum_m z_m (P/p_m) = x + u P with u = floor(sum_m z_m / p_m).  The sum is
+// taken in fixed point, sum_m z_m floor(2^E / p_m) < 2^(E+3) in 128 bits;
+// it falls short of 2^E sum_m z_m / p_m by less than alpha 2^58, so its
+// integer part is u unless x / P lies within 2^-60 of 1.
+__global__ void k_ks_md_overflow(DevCtx c, KsArgs a, KsLayout ly) {
+    const long long N = 1ll << c.logN;
+    const int job = blockIdx.y, item = job / 2, kk = job % 2;
+    const int al = c.alpha;
+    const u64 *z = a.ws + item * a.ws_item + ly.z + (long long)kk * al * N;
+    u64 *u = a.ws + item * a.ws_item + ly.u + (long long)kk * N;
+    const int sh = c.md_E - 64;
+    for (long long j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += (long long)gridDim.x * blockDim.x) {
+        U128 s = {0, 0};
+        for (int m = 0; m < al; m++) mac(s, z[(long long)m * N + j], __ldg(&c.md_w[m]));
+        u[j] = s.hi >> sh;
+    }
+}
+
 // (7) ModDown: basis conversion P -> q_i (minus floor(P/2)) fused with NTT columns
 template <int LOGR>
 __global__ void __launch_bounds__(NT, 3) k_ks_md_conv_col(DevCtx c, LevelTab lt, KsArgs a, KsLayout ly) {
@@ -617,6 +638,8 @@ __global__ void __launch_bounds__(NT, 3) k_ks_md_conv_col(DevCtx c, LevelTab lt,
     const u64 *z = a.ws + item * a.ws_item + ly.z + (long long)kk * al * N;
     u64 *dst = a.ws + item * a.ws_item + ly.md + ((long long)(kk * nl + i) << c.logN);
     const u64 halfp = c.md_halfp[i];
+    const u64 pmod = c.md_pmod[i];
+    const u64 *uo = a.ws + item * a.ws_item + ly.u + (long long)kk * N;
     const long long sc = (long long)Gm::S << logC;
     u64 x[16];
 #pragma unroll
@@ -634,7 +657,11 @@ __global__ void __launch_bounds__(NT, 3) k_ks_md_conv_col(DevCtx c, LevelTab lt,
             for (int k = 0; k < CONV_CHUNK; k++) mac(acc[k], v[k], h);
         }
 #pragma unroll
-        for (int k = 0; k < CONV_CHUNK; k++) x[h8 + k] = sub_mod(barrett(acc[k], P.m), halfp, q);
+        for (int k = 0; k < CONV_CHUNK; k++) {
+            // exact conversion: remove u P (u < alpha, so u * (P mod q) < 2^64)
+            const u64 uP = barrett(U128{uo[col + ((long long)tau << logC) + (h8 + k) * sc] * pmod, 0}, P.m);
+            x[h8 + k] = sub_mod(sub_mod(barrett(acc[k], P.m), halfp, q), uP, q);
+        }
     }
     fwd_A<LOGR>(x, tau, col, 1 << logC, 0, tws, q);
     xchg_col_AB<LOGR>(x, sm, tau, cl);
@@ -1129,7 +1156,7 @@ static inline int tiles_col(const DevCtx &c) { return 1 << (c.logN - 12); }  // 
 size_t ks_workspace_words(const DevCtx &c, int level) {
     const int nd = (level + c.alpha) / c.alpha;
     KsLayout L = ks_layout(level, nd, c.alpha, c.logN);
-    return (size_t)(L.md + 2ll * (level + 1) * (1ll << c.logN));
+    return (size_t)(L.u + 2ll * (1ll << c.logN));
 }
 
 cudaError_t launch_ntt(const DevCtx &c, const NttArgs &a, bool inverse, cudaStream_t s) {
@@ -1171,6 +1198,10 @@ cudaError_t launch_keyswitch(const DevCtx &c, const LevelTab &lt, const KsArgs &
     if (phases & KS_MODDOWN) DISPATCH_LOGR(c.logR2, k_ks_md_intt_row, dim3(tc, B * 2 * c.alpha), c, lt, a, ly);
     KS_EV(5);
     if (phases & KS_MODDOWN) DISPATCH_LOGR(c.logR1, k_ks_md_intt_col, dim3(tc, B * 2 * c.alpha), c, lt, a, ly);
+    if (phases & KS_MODDOWN) {
+        COUNT_LAUNCH();
+        k_ks_md_overflow<<<dim3((unsigned)((1ll << c.logN) / 256), B * 2), 256, 0, s>>>(c, a, ly);
+    }
     KS_EV(6);
     if (phases & KS_MODDOWN) DISPATCH_LOGR(c.logR1, k_ks_md_conv_col, dim3(tc, B * 2 * nl), c, lt, a, ly);
     KS_EV(7);

@@ -45,6 +45,11 @@ struct DevCtx {
     const u64 *md_phat;             // [alpha][L+1] Phat_m mod q_i
     const u64 *md_halfp;            // [L+1] floor(P/2) mod q_i
     const ulonglong2 *md_pinv;      // [L+1] P^-1 mod q_i (Shoup)
+    // exact conversion from P: u = floor(sum_m z_m w_m / 2^md_E) counts the
+    // multiples of P the fast conversion adds; w_m = floor(2^md_E / p_m)
+    const u64 *md_w;                // [alpha]
+    const u64 *md_pmod;             // [L+1] P mod q_i
+    int md_E;                       // 63 + smallest bit length of the p_m
 };
 
 __host__ __device__ inline int ext_prime(int l, int level, int L) {
@@ -80,7 +85,7 @@ struct KsArgs {
     int n_items;
     int level;
     // workspace (item-major): y [level+1], mu [digits][ext], acc [2][ext],
-    // z [2][alpha], md [2][level+1] limbs; sized by the caller
+    // z [2][alpha], md [2][level+1], u [2] limbs; sized by the caller
     u64 *ws;
     long long ws_item;      // words per item
 };

@@ -82,8 +82,10 @@ static int load_linear(fhe_model *m, const fhe_step_desc &sd, MStep &st) {
     if (sd.n_groups < 0 || (sd.n_groups > 0 && (!sd.group_out || !sd.group_giant || !sd.group_term_begin)))
         return fhe_fail(FHE_E_INVAL, "linear step: missing group arrays");
     const int n_terms = sd.n_groups > 0 ? sd.group_term_begin[sd.n_groups] : 0;
-    if (n_terms > 0 && (!sd.term_ct || !sd.term_baby || !sd.term_vec))
+    if (n_terms > 0 && (!sd.term_ct || !sd.term_baby || !sd.term_vec_id || !sd.vecs || sd.n_vecs < 1))
         return fhe_fail(FHE_E_INVAL, "linear step: missing term arrays");
+    // every distinct vector is encoded once; its terms share the plaintext
+    std::vector<u64 *> vec_pt(n_terms > 0 ? sd.n_vecs : 0, nullptr);
     std::set<std::pair<int, int>> baby;
     std::vector<int> has_zero(tout.n_ct, 0);
     for (int g = 0; g < sd.n_groups; g++) {
@@ -109,9 +111,10 @@ static int load_linear(fhe_model *m, const fhe_step_desc &sd, MStep &st) {
         L.t_ct.push_back(ct);
         L.t_baby.push_back(b);
         if (galois_of_step(c, b) != 1) baby.insert({ct, b});
-        u64 *pt;
-        FHE_TRY(encode_vec(m, sd.term_vec + (size_t)t * ns, sd.w_scale, L.level, &pt));
-        L.t_pt.push_back(pt);
+        const int v = sd.term_vec_id[t];
+        if (v < 0 || v >= sd.n_vecs) return fhe_fail(FHE_E_INVAL, "linear step: vector index");
+        if (!vec_pt[v]) FHE_TRY(encode_vec(m, sd.vecs + (size_t)v * ns, sd.w_scale, L.level, &vec_pt[v]));
+        L.t_pt.push_back(vec_pt[v]);
     }
     for (auto &p : baby) {
         L.baby_ct.push_back(p.first);

@@ -99,6 +99,15 @@ def map_hw(c, H, W, n_slots) -> SlotMap:
     return SlotMap(c, [[(ch, base) for base in bases] for ch in range(c)], H, W, 1, W, blk)
 
 
+def map_hw_ensemble(c, H, W, n_slots, members: int) -> SlotMap:
+    """HW layout of an ensemble (Sec. 5.3): channel c in ciphertext c, member
+    m's values in block m (blocks >= members stay empty)."""
+    blk = H * W
+    if members * blk > n_slots:
+        raise ValueError("the ensemble does not fit in the free blocks")
+    return SlotMap(c, [[(ch, m * blk) for m in range(members)] for ch in range(c)], H, W, 1, W, blk)
+
+
 def map_packed(c, H, W, st, row, blk, n_slots) -> SlotMap:
     nb = n_slots // blk
     if c <= nb:
@@ -171,6 +180,65 @@ def diagonals(w: np.ndarray, stride: int, pad: int, src: SlotMap, dst: SlotMap, 
 # =========================================================== program
 
 @dataclass
+class Terms:
+    """The diagonals of a linear layer as arrays: term t adds vecs[vid[t]]
+    (.) rot(in[ct[t]], r[t]) into output ciphertext out[t].  Equal vectors
+    share one table entry (one encoded plaintext)."""
+    out: np.ndarray
+    ct: np.ndarray
+    r: np.ndarray
+    vid: np.ndarray
+    vecs: List[np.ndarray]
+
+
+def terms_of(diag: Dict) -> Terms:
+    keys = sorted(diag)
+    a = np.array(keys, dtype=np.int64).reshape(-1, 3)
+    return Terms(a[:, 0], a[:, 1], a[:, 2], np.arange(len(keys)), [diag[k] for k in keys])
+
+
+def diagonals_hw(ws: Sequence[np.ndarray], stride: int, pad: int, src: SlotMap, dst: SlotMap,
+                 n_slots: int) -> Terms:
+    """Convolution between HW layouts (channel c in ciphertext c): output
+    replica k reads input replica k (same block), with weights ws[k]
+    [cout, cin, k, k] (the replica's ensemble member).  For a kernel offset
+    (dh, dw) every term reads rotation r = ((dh-pad) row + (dw-pad)) st_in,
+    and its vector holds weight ws[k][o, i, dh, dw] on the valid output
+    positions of replica k."""
+    cout, cin, kh, kw = ws[0].shape
+    oh = np.repeat(np.arange(dst.H), dst.W)
+    ow = np.tile(np.arange(dst.W), dst.H)
+    bases = [b for _, b in dst.copies[0]]
+    if [b for _, b in src.copies[0]] != bases or len(ws) != len(bases):
+        raise ValueError("HW convolution: replicas of input and output differ")
+    o_idx, i_idx = np.meshgrid(np.arange(cout), np.arange(cin), indexing="ij")
+    o_idx, i_idx = o_idx.reshape(-1), i_idx.reshape(-1)
+    outs, cts, rs, vids, vecs = [], [], [], [], []
+    for dh in range(kh):
+        ih = oh * stride + dh - pad
+        for dw in range(kw):
+            iw = ow * stride + dw - pad
+            ok = (ih >= 0) & (ih < src.H) & (iw >= 0) & (iw < src.W)
+            if not ok.any():
+                continue
+            r = (((dh - pad) * src.st) * src.row + (dw - pad) * src.st) % n_slots
+            so = oh[ok] * dst.st * dst.row + ow[ok] * dst.st
+            tup = np.stack([w[:, :, dh, dw].reshape(-1) for w in ws], axis=1)
+            uniq, inv = np.unique(tup, axis=0, return_inverse=True)
+            base_vid = len(vecs)
+            for u in uniq:
+                v = np.zeros(n_slots)
+                for k, b in enumerate(bases):
+                    v[b + so] = u[k]
+                vecs.append(v)
+            outs.append(o_idx)
+            cts.append(i_idx)
+            rs.append(np.full(len(o_idx), r, dtype=np.int64))
+            vids.append(base_vid + inv.reshape(-1))
+    return Terms(np.concatenate(outs), np.concatenate(cts), np.concatenate(rs), np.concatenate(vids), vecs)
+
+
+@dataclass
 class TInfo:
     layout: SlotMap
     level: int
@@ -215,22 +283,32 @@ def ks_cost(level: int, alpha: int) -> Tuple[float, float, float]:
     return modup, ip, moddown
 
 
-def bsgs_cost(diag_keys, giant: int, level: int, alpha: int) -> float:
-    """Key-switch cost of a linear layer whose diagonals are diag_keys
-    {(out ct, in ct, r)} split as r = g + b, b = r mod giant: every input with
-    baby steps pays one ModUp, every baby step an inner product and a
-    ModDown; every giant step a ModUp and an inner product, every output with
-    giant steps one ModDown."""
+def bsgs_cost(terms: Terms, giant: int, level: int, alpha: int) -> float:
+    """Key-switch cost of a linear layer whose diagonals are `terms`, split as
+    r = g + b, b = r mod giant: every input with baby steps pays one ModUp,
+    every baby step an inner product and a ModDown; every giant step a ModUp
+    and an inner product, every output with giant steps one ModDown."""
     mu, ip, md = ks_cost(level, alpha)
-    babies = {(i, r % giant) for (_, i, r) in diag_keys if r % giant}
-    giants = {(o, r - r % giant) for (o, _, r) in diag_keys if r - r % giant}
-    return (len({i for i, _ in babies}) * mu + len(babies) * (ip + md) + len(giants) * (mu + ip)
-            + len({o for o, _ in giants}) * md)
+    b = terms.r % giant
+    g = terms.r - b
+    babies = np.unique(np.stack([terms.ct[b != 0], b[b != 0]], axis=1), axis=0)
+    giants = np.unique(np.stack([terms.out[g != 0], g[g != 0]], axis=1), axis=0)
+    return (len(np.unique(babies[:, 0])) * mu + len(babies) * (ip + md) + len(giants) * (mu + ip)
+            + len(np.unique(giants[:, 0])) * md)
+
+
+def groups_of(st: Dict) -> Dict[Tuple[int, int], List]:
+    """{(out ct, giant step): [(in ct, baby step, vector)]} of a linear step"""
+    groups: Dict[Tuple[int, int], List] = {}
+    for o, g, i, b, v in zip(st["t_out"], st["t_giant"], st["t_ct"], st["t_baby"], st["t_vid"]):
+        groups.setdefault((int(o), int(g)), []).append((int(i), int(b), st["vecs"][v]))
+    return groups
 
 
 class Planner:
     def __init__(self, primes_q: Sequence[int], log_n: int, log_scale: float, layout: str, alpha: int = 3,
-                 max_giant_blocks: int = 8):
+                 max_giant_blocks: int = 8, members: int = 1):
+        self.members = members
         self.alpha = alpha
         self.max_giant_blocks = max_giant_blocks
         self.q = list(primes_q)
@@ -258,40 +336,54 @@ class Planner:
             return self._emit(kind=F.STEP_RESCALE, src=t, dst=self._t(info.layout, info.level - 1, info.scale / ql))
         return t
 
-    def _pick_giant(self, diag: Dict, block: int, level: int) -> int:
+    def _pick_giant(self, terms: Terms, block: int, level: int) -> int:
         """giant step = k blocks, k in 1, 2, 4, .. max_giant_blocks: the
         cheapest split by bsgs_cost (ties: the smaller k)"""
         best = None
         k = 1
         while k <= self.max_giant_blocks and k * block <= self.n:
-            c = bsgs_cost(diag.keys(), k * block, level, self.alpha)
+            c = bsgs_cost(terms, k * block, level, self.alpha)
             if best is None or c < best[0]:
                 best = (c, k * block)
             k *= 2
         return best[1]
 
-    def _bsgs_step(self, src: int, diag: Dict, giant: int, dst_layout: SlotMap, w_scale: float,
-                   bias: Optional[np.ndarray], bias_layout: SlotMap) -> int:
+    def _bias_vecs(self, biases: Sequence[np.ndarray], layout: SlotMap) -> Dict[int, np.ndarray]:
+        """bias of channel ch, replica k (the member biases[k]), on the
+        channel's positions"""
+        out: Dict[int, np.ndarray] = {}
+        offs = layout.offsets()
+        for ch in range(len(layout.copies)):
+            for k, (ct, base) in enumerate(layout.copies[ch]):
+                out.setdefault(ct, np.zeros(self.n))[base + offs] = biases[min(k, len(biases) - 1)][ch]
+        return out
+
+    def _bsgs_step(self, src: int, terms: Terms, giant: int, dst_layout: SlotMap, w_scale: float,
+                   bias_vecs: Dict[int, np.ndarray]) -> int:
         info = self.p.tensors[src]
         prod = info.scale * w_scale
         dst = self._t(dst_layout, info.level, prod)
-        groups: Dict[Tuple[int, int], List] = {}
-        for (o, i, r), vec in diag.items():
-            b = r % giant
-            g = r - b
-            groups.setdefault((o, g), []).append((i, b, np.roll(vec, g)))
-            if b:
-                self.p.rotations.add(b)
-            if g:
-                self.p.rotations.add(g)
-        bias_vecs = {}
-        if bias is not None:
-            offs = bias_layout.offsets()
-            for ch, val in enumerate(bias):
-                for ct, base in bias_layout.copies[ch]:
-                    bias_vecs.setdefault(ct, np.zeros(self.n))[base + offs] = val
+        b = terms.r % giant
+        g = terms.r - b
+        # each term's vector is pre-rotated by -g; equal results share an entry
+        pairs, inv = np.unique(np.stack([terms.vid, g], axis=1), axis=0, return_inverse=True)
+        table: Dict[bytes, int] = {}
+        vecs: List[np.ndarray] = []
+        remap = np.empty(len(pairs), dtype=np.int64)
+        for j, (v, gg) in enumerate(pairs):
+            rolled = np.roll(terms.vecs[v], gg) if gg else terms.vecs[v]
+            key = rolled.tobytes()
+            if key not in table:
+                table[key] = len(vecs)
+                vecs.append(rolled)
+            remap[j] = table[key]
+        vid = remap[inv.reshape(-1)]
+        order = np.lexsort((b, terms.ct, g, terms.out))
+        self.p.rotations.update(int(x) for x in np.unique(b) if x)
+        self.p.rotations.update(int(x) for x in np.unique(g) if x)
         return self._emit(kind=F.STEP_LINEAR, src=src, dst=dst, w_scale=w_scale, bias_scale=prod,
-                          groups=groups, bias=bias_vecs, giant=giant)
+                          t_out=terms.out[order], t_giant=g[order], t_ct=terms.ct[order], t_baby=b[order],
+                          t_vid=vid[order], vecs=vecs, bias=bias_vecs, giant=giant)
 
     def _shortcut_scale(self, info: TInfo, target: TInfo) -> float:
         ql = self.q[info.level]
@@ -310,29 +402,35 @@ class Planner:
         info.scale = target.scale
         return t
 
-    # ---- layers
-    def conv(self, src: int, node: Dict, prm: Dict, target: Optional[TInfo] = None) -> int:
+    # ---- layers (ps: the layer's parameters of every ensemble member)
+    def conv(self, src: int, node: Dict, ps: List[Dict], target: Optional[TInfo] = None) -> int:
         info = self.p.tensors[src]
         lin = info.layout
         ho = (lin.H + 2 * node["pad"] - node["k"]) // node["stride"] + 1
         wo = (lin.W + 2 * node["pad"] - node["k"]) // node["stride"] + 1
         st = lin.st * node["stride"]
-        if self.layout == "hw":
+        if self.layout in ("hw", "hw_ens"):
             lout = SlotMap(node["cout"], [[(o, base) for (_, base) in lin.copies[0]] for o in range(node["cout"])],
                            ho, wo, st, lin.row, lin.block)
+            reps = len(lin.copies[0])
+            ws = [ps[k if self.layout == "hw_ens" else 0]["w"] for k in range(reps)]
+            terms = diagonals_hw(ws, node["stride"], node["pad"], lin, lout, self.n)
             giant = self.n
+            bias = self._bias_vecs([ps[k if self.layout == "hw_ens" else 0]["bias"] for k in range(reps)], lout)
         else:
             lout = map_packed(node["cout"], ho, wo, st, lin.row, lin.block, self.n)
-            giant = None
-        diag = diagonals(prm["w"], node["stride"], node["pad"], lin, lout, self.n)
-        if giant is None:
-            giant = self._pick_giant(diag, lin.block, info.level)
-        ws = self.delta if target is None else self._shortcut_scale(info, target)
-        t = self._bsgs_step(src, diag, giant, lout, ws, prm["bias"], lout)
+            terms = terms_of(diagonals(ps[0]["w"], node["stride"], node["pad"], lin, lout, self.n))
+            giant = self._pick_giant(terms, lin.block, info.level)
+            bias = self._bias_vecs([ps[0]["bias"]], lout)
+        ws_scale = self.delta if target is None else self._shortcut_scale(info, target)
+        t = self._bsgs_step(src, terms, giant, lout, ws_scale, bias)
         t = self._rule(t)
         return t if target is None else self._land_on(t, target)
 
-    def act(self, src: int, prm: Dict) -> int:
+    def act(self, src: int, ps: List[Dict]) -> int:
+        prm = ps[0]
+        if any(p["c1"] != prm["c1"] or p["c0"] != prm["c0"] for p in ps):
+            raise ValueError("ensemble members must share the activation polynomial")
         info = self.p.tensors[src]
         s = info.scale
         s2 = s * s
@@ -349,7 +447,10 @@ class Planner:
         self.p.rotations.update(steps)
         return self._emit(kind=F.STEP_ROTSUM, src=src, dst=self._t(lp, info.level, info.scale), steps=steps)
 
-    def shortcut_identity(self, src: int, value: float, target: TInfo) -> int:
+    def shortcut_identity(self, src: int, ps: List[Dict], target: TInfo) -> int:
+        value = ps[0]["shortcut"]
+        if any(p["shortcut"] != value for p in ps):
+            raise ValueError("ensemble members must share the shortcut multiplier")
         info = self.p.tensors[src]
         ws = self._shortcut_scale(info, target)
         dst = self._t(info.layout, info.level, info.scale * ws)
@@ -360,13 +461,13 @@ class Planner:
         ia = self.p.tensors[a]
         return self._emit(kind=F.STEP_ADD, src=a, src2=b, dst=self._t(ia.layout, ia.level, ia.scale))
 
-    def dense(self, src: int, node: Dict, prm: Dict) -> int:
+    def dense(self, src: int, node: Dict, ps: List[Dict]) -> int:
         info = self.p.tensors[src]
         lin = info.layout
-        w = prm["w"]
         cout = node["cout"]
         if self.layout == "hw":
             # products in block k of ciphertext 0, then a sum over the block
+            w = ps[0]["w"]
             offs = lin.offsets()
             diag = {}
             for c in range(len(lin.copies)):
@@ -375,7 +476,7 @@ class Planner:
                     ct, base = _pick_copy(lin.copies[c], k * lin.block, self.n)
                     vec[base + offs] = w[k, c * len(offs):(c + 1) * len(offs)]
             part = SlotMap(1, [[(0, k * lin.block)] for k in range(cout)], 1, 1, 1, 1, lin.block)
-            t = self._bsgs_step(src, diag, self.n, part, self.delta, prm["bias"], part)
+            t = self._bsgs_step(src, terms_of(diag), self.n, part, self.delta, self._bias_vecs([ps[0]["bias"]], part))
             t = self._rule(t)
             ti = self.p.tensors[t]
             steps = [lin.st << m for m in range(int(math.log2(lin.W)))] + \
@@ -383,49 +484,100 @@ class Planner:
             self.p.rotations.update(steps)
             return self._emit(kind=F.STEP_ROTSUM, src=t, steps=steps,
                               dst=self._t(map_single(cout, lin.block, self.n), ti.level, ti.scale))
+        if self.layout == "hw_ens":
+            return self._dense_ensemble(src, node, ps)
         lout = map_single(cout, lin.block, self.n)
-        diag = diagonals(w.reshape(cout, -1, 1, 1), 1, 0, lin, lout, self.n)
-        t = self._bsgs_step(src, diag, 8 * lin.block, lout, self.delta, prm["bias"], lout)
+        terms = terms_of(diagonals(ps[0]["w"].reshape(cout, -1, 1, 1), 1, 0, lin, lout, self.n))
+        t = self._bsgs_step(src, terms, 8 * lin.block, lout, self.delta, self._bias_vecs([ps[0]["bias"]], lout))
         return self._rule(t)
 
-    def compile(self, net: List[Dict], prm: Dict) -> Program:
+    def _dense_ensemble(self, src: int, node: Dict, ps: List[Dict]) -> int:
+        """Dense layer of an ensemble in the HW layout, then the ensemble
+        average (Sec. 5.3).  Input channel c (ciphertext c) holds member m's
+        pooled feature at slot m*B; output k of member m goes to slot
+        m*B + k, read at rotation r = -k, with weight w_m[k, c] / M; giant
+        steps only (each partial sum sum_c d_(c,g) (.) in_c is rotated once).
+        Then the M blocks are summed by rotations of B, 2B, 4B, ..: the
+        averaged logit k ends in slot k of block 0."""
+        info = self.p.tensors[src]
+        lin = info.layout
+        cout, M, B = node["cout"], self.members, lin.block
+        if lin.H != 1 or lin.W != 1 or cout > B:
+            raise ValueError("ensemble dense layer: expects one pooled feature per channel and cout <= block")
+        cin = len(lin.copies)
+        ws = [p["w"] / float(M) for p in ps]
+        o_idx = np.zeros(cout * cin, dtype=np.int64)
+        k_idx, c_idx = np.meshgrid(np.arange(cout), np.arange(cin), indexing="ij")
+        k_idx, c_idx = k_idx.reshape(-1), c_idx.reshape(-1)
+        tup = np.stack([w.reshape(cout, cin).reshape(-1) for w in ws], axis=1)
+        # one vector per (member weights, k): values at slots m*B + k
+        key = np.concatenate([tup, k_idx[:, None].astype(np.float64)], axis=1)
+        uniq, inv = np.unique(key, axis=0, return_inverse=True)
+        vecs = []
+        for u in uniq:
+            v = np.zeros(self.n)
+            kk = int(u[-1])
+            for m in range(M):
+                v[m * B + kk] = u[m]
+            vecs.append(v)
+        terms = Terms(o_idx, c_idx, (-k_idx) % self.n, inv.reshape(-1), vecs)
+        part = SlotMap(1, [[(0, m * B + k) for m in range(M)] for k in range(cout)], 1, 1, 1, 1, B)
+        bias = self._bias_vecs([p["bias"] / float(M) for p in ps], part)
+        t = self._bsgs_step(src, terms, 1, part, self.delta, bias)
+        t = self._rule(t)
+        ti = self.p.tensors[t]
+        steps = [B << j for j in range(max(0, (M - 1).bit_length()))]
+        self.p.rotations.update(steps)
+        return self._emit(kind=F.STEP_ROTSUM, src=t, steps=steps,
+                          dst=self._t(SlotMap(1, [[(0, k)] for k in range(cout)], 1, 1, 1, 1, B), ti.level,
+                                      ti.scale))
+
+    def compile(self, net: List[Dict], prms: List[Dict]) -> Program:
         node_t: Dict[int, int] = {}
         later = {n["src"][1] for n in net if n["op"] == "add" and net[n["src"][1]]["op"] == "conv"}
         for idx, node in enumerate(net):
             kind = node["op"]
+            ps = [p.get(idx) for p in prms]
             if kind == "input":
                 if self.layout == "hw":
                     lay = map_hw(node["c"], node["h"], node["w"], self.n)
+                elif self.layout == "hw_ens":
+                    lay = map_hw_ensemble(node["c"], node["h"], node["w"], self.n, self.members)
                 else:
                     lay = map_packed(node["c"], node["h"], node["w"], 1, node["w"], node["h"] * node["w"], self.n)
                 node_t[idx] = self.p.input = self._t(lay, self.L, self.delta)
             elif kind == "conv":
                 if idx not in later:
-                    node_t[idx] = self.conv(node_t[node["src"]], node, prm[idx])
+                    node_t[idx] = self.conv(node_t[node["src"]], node, ps)
             elif kind == "act":
-                node_t[idx] = self.act(node_t[node["src"]], prm[idx])
+                node_t[idx] = self.act(node_t[node["src"]], ps)
             elif kind == "pool":
                 node_t[idx] = self.pool(node_t[node["src"]], node["k"])
             elif kind == "add":
                 a, b = node["src"]
                 main = self.p.tensors[node_t[a]]
                 if net[b]["op"] == "conv":
-                    sc = self.conv(node_t[net[b]["src"]], net[b], prm[b], target=main)
+                    sc = self.conv(node_t[net[b]["src"]], net[b], [p[b] for p in prms], target=main)
                 else:
-                    sc = self.shortcut_identity(node_t[b], prm[idx]["shortcut"], main)
+                    sc = self.shortcut_identity(node_t[b], ps, main)
                 node_t[idx] = self.add(node_t[a], sc)
             elif kind == "dense":
-                node_t[idx] = self.dense(node_t[node["src"]], node, prm[idx])
+                node_t[idx] = self.dense(node_t[node["src"]], node, ps)
         self.p.output = node_t[len(net) - 1]
         return self.p
 
 
 def compile_network(net, raw, primes_q, log_n, log_scale, layout, alpha: int = 3,
                     max_giant_blocks: int = 8) -> Program:
-    """alpha: digit width of key switching (for the baby-step / giant-step
+    """raw: one model's raw parameters, or a list of them (an ensemble, laid
+    out with layout "hw_ens": member m in block m of every ciphertext).
+    alpha: digit width of key switching (for the baby-step / giant-step
     cost model); max_giant_blocks = 1 keeps the giant step at one block."""
-    return Planner(primes_q, log_n, log_scale, layout, alpha, max_giant_blocks).compile(net,
-                                                                                      prepare_params(net, raw))
+    raws = raw if isinstance(raw, (list, tuple)) else [raw]
+    if len(raws) > 1 and layout != "hw_ens":
+        raise ValueError("an ensemble needs the hw_ens layout")
+    prms = [prepare_params(net, r) for r in raws]
+    return Planner(primes_q, log_n, log_scale, layout, alpha, max_giant_blocks, len(raws)).compile(net, prms)
 
 
 def giant_steps(prog: Program) -> List[int]:
@@ -464,24 +616,24 @@ class ModelDesc:
             d.src2 = st.get("src2", -1)
             d.dst = st["dst"]
             if st["kind"] == F.STEP_LINEAR:
-                g_out, g_g, g_tb, t_ct, t_b, vecs = [], [], [0], [], [], []
-                for (o, g), terms in sorted(st["groups"].items()):
-                    g_out.append(o)
-                    g_g.append(g)
-                    for (ct, b, v) in terms:
-                        t_ct.append(ct)
-                        t_b.append(b)
-                        vecs.append(v)
-                    g_tb.append(len(t_ct))
+                t_out, t_g = st["t_out"], st["t_giant"]
+                n_t = len(t_out)
+                if n_t:
+                    cut = np.flatnonzero((t_out[1:] != t_out[:-1]) | (t_g[1:] != t_g[:-1])) + 1
+                    starts = np.concatenate([[0], cut])
+                else:
+                    starts = np.zeros(0, dtype=np.int64)
                 d.w_scale = st["w_scale"]
                 d.bias_scale = st["bias_scale"]
-                d.n_groups = len(g_out)
-                d.group_out = p32(arr(g_out, np.int32))
-                d.group_giant = p32(arr(g_g, np.int32))
-                d.group_term_begin = p32(arr(g_tb, np.int32))
-                d.term_ct = p32(arr(t_ct or [0], np.int32))
-                d.term_baby = p32(arr(t_b or [0], np.int32))
-                d.term_vec = pd(arr(np.stack(vecs) if vecs else np.zeros((1, n_slots)), np.float64))
+                d.n_groups = len(starts)
+                d.group_out = p32(arr(t_out[starts] if n_t else [0], np.int32))
+                d.group_giant = p32(arr(t_g[starts] if n_t else [0], np.int32))
+                d.group_term_begin = p32(arr(np.concatenate([starts, [n_t]]), np.int32))
+                d.term_ct = p32(arr(st["t_ct"] if n_t else [0], np.int32))
+                d.term_baby = p32(arr(st["t_baby"] if n_t else [0], np.int32))
+                d.term_vec_id = p32(arr(st["t_vid"] if n_t else [0], np.int32))
+                d.n_vecs = len(st["vecs"])
+                d.vecs = pd(arr(np.stack(st["vecs"]) if st["vecs"] else np.zeros((1, n_slots)), np.float64))
                 bo = sorted(st["bias"])
                 d.n_bias = len(bo)
                 d.bias_out = p32(arr(bo or [0], np.int32))

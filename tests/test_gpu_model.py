@@ -11,7 +11,11 @@ from oracle import cnn
 pytestmark = pytest.mark.gpu
 
 CASES = {"tiny": ("tiny", "tiny", "hw"), "mini": ("resnet_mini", "resnet_mini", "packed"),
-         "vgg_mini": ("vgg_mini", "resnet_mini", "packed")}
+         "vgg_mini": ("vgg_mini", "resnet_mini", "packed"),
+         # ResNet-18's structure, an ensemble of 3 in the HW layout, weights
+         # clustered jointly to 4 values per layer
+         "ens": ("resnet18_mini", "resnet18_mini", "hw_ens")}
+ENSEMBLE = 3
 
 
 class Setup:
@@ -21,7 +25,14 @@ class Setup:
         arch, preset, layout = CASES[case]
         self.F, self.M = F, M
         self.net = synth.ARCHS[arch]()
-        self.raw = synth.params(self.net)
+        if layout == "hw_ens":
+            self.raws = synth.cluster_joint([synth.params(self.net, m) for m in range(ENSEMBLE)], self.net, 4)
+            self.raw = self.raws
+            t = [cnn.transform(self.net, r) for r in self.raws]
+        else:
+            self.raws = None
+            self.raw = synth.params(self.net)
+            t = cnn.transform(self.net, self.raw)
         pre = synth.PRESETS[preset]
         self.pre = pre
         self.prm = O.make_params(**pre)
@@ -31,8 +42,9 @@ class Setup:
         self.pm = M.compile_network(self.net, self.raw, F.fhe_ctx_primes(self.ctx)[: pre["L"] + 1], pre["logn"],
                                     pre["log_scale"], layout, pre["alpha"])
         # the oracle evaluates the same diagonals with the package's baby-step / giant-step split
-        self.po = cnn.compile_he(self.net, cnn.transform(self.net, self.raw), self.prm, layout,
-                                 M.giant_steps(self.pm))
+        self.po = cnn.compile_he(self.net, t, self.prm, layout, M.giant_steps(self.pm),
+                                 ENSEMBLE if layout == "hw_ens" else 1)
+        self._oracle_cache = {}
         self.keys = self.S.keygen(synth.SEED_KEYS, sorted(self.po.rot_steps))
         self.sk, self.evk = F.fhe_keygen(self.ctx, synth.SEED_KEYS, sorted(self.pm.rotations))
         self.desc = M.ModelDesc(self.pm, self.prm.N // 2)
@@ -50,9 +62,16 @@ class Setup:
         return img, out
 
     def oracle_outputs(self, i):
-        img = synth.image(i, self.inp["c"], self.inp["h"], self.inp["w"])
-        cts = cnn.encrypt_input(self.S, self.keys, self.po, img, i, synth.enc_seed)
-        return cnn.run_he(self.S, self.keys, self.po, cts)
+        if i not in self._oracle_cache:
+            img = synth.image(i, self.inp["c"], self.inp["h"], self.inp["w"])
+            cts = cnn.encrypt_input(self.S, self.keys, self.po, img, i, synth.enc_seed)
+            self._oracle_cache[i] = cnn.run_he(self.S, self.keys, self.po, cts)
+        return self._oracle_cache[i]
+
+    def reference_logits(self, img):
+        if self.raws is not None:
+            return cnn.forward_ensemble(self.net, self.raws, img)
+        return cnn.forward_plain(self.net, self.raw, img)
 
     def coef(self, ct):
         prm = self.prm
@@ -96,7 +115,7 @@ def test_network_bit_exact_and_logits(setup):
         assert lv == r.level and sc == r.scale
         assert np.array_equal(buf, s.coef(r))
     y = s.logits(outs)
-    want = cnn.forward_plain(s.net, s.raw, img)
+    want = s.reference_logits(img)
     assert np.max(np.abs(y - want)) < 1e-3
     assert np.argmax(y) == np.argmax(want)
     for h in outs + cts:
@@ -124,7 +143,7 @@ def test_per_layer_entry_points(setup):
     reproduce the oracle's tensors of those steps."""
     s = setup
     F = s.F
-    ref = s.oracle_outputs(1)
+    ref = s.oracle_outputs(0)
     kinds = [st["kind"] for st in s.pm.steps]
     # first linear step (a convolution), the first activation, the first rotsum
     for kind, call in ((1, "conv"), (3, "act"), (4, "pool")):

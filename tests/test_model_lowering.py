@@ -36,7 +36,7 @@ def _check(po, pm):
     for a, b in zip(lo, lm):
         ga = {(o, g): sorted((i, bb, v.tobytes()) for (i, bb, v) in terms)
               for o, gs in a["groups"].items() for g, terms in gs.items()}
-        gb = {k: sorted((i, bb, v.tobytes()) for (i, bb, v) in terms) for k, terms in b["groups"].items()}
+        gb = {k: sorted((i, bb, v.tobytes()) for (i, bb, v) in terms) for k, terms in M.groups_of(b).items()}
         assert ga == gb
         assert a["w_scale"] == b["w_scale"] and a["bias_scale"] == b["bias_scale"]
         assert {k: v.tobytes() for k, v in a["bias"].items()} == {k: v.tobytes() for k, v in b["bias"].items()}
@@ -84,7 +84,31 @@ def test_cost_model_prefers_wider_baby_steps_for_wide_layers():
     blk = pm.tensors[pm.input].layout.block
     assert any(s["giant"] > blk for s in lin)
     for s in lin:
-        keys = {(o, i, (g + b)) for (o, g), terms in s["groups"].items() for (i, b, _) in terms}
+        terms = M.Terms(s["t_out"], s["t_ct"], s["t_giant"] + s["t_baby"], s["t_vid"], s["vecs"])
         lv = pm.tensors[s["src"]].level
-        assert M.bsgs_cost(keys, s["giant"], lv, 3) <= M.bsgs_cost(keys, blk, lv, 3)
+        assert M.bsgs_cost(terms, s["giant"], lv, 3) <= M.bsgs_cost(terms, blk, lv, 3)
 
+
+
+def _ensemble_both(k=4, members=3):
+    net = synth.resnet18_mini()
+    raws = synth.cluster_joint([synth.params(net, m) for m in range(members)], net, k)
+    pre = synth.PRESETS["resnet18_mini"]
+    prm = O.make_params(**pre)
+    pm = M.compile_network(net, raws, prm.q, pre["logn"], pre["log_scale"], "hw_ens", pre["alpha"])
+    po = cnn.compile_he(net, [cnn.transform(net, r) for r in raws], prm, "hw_ens", M.giant_steps(pm), members)
+    return po, pm
+
+
+def test_clustered_ensemble_program_matches_oracle():
+    """ResNet-18's structure, three members in blocks 0..2 of the HW layout,
+    weights clustered jointly (4 centroids per layer): same program as the
+    oracle's, and every convolution needs at most 4 x 9 distinct plaintexts."""
+    po, pm = _ensemble_both()
+    _check(po, pm)
+    for st in pm.steps:
+        if st["kind"] == 1 and len(pm.tensors[st["src"]].layout.copies[0]) == 3 \
+                and pm.tensors[st["src"]].layout.H > 1:
+            assert len(st["vecs"]) <= 4 * 9
+    # 18 levels along the network (Table 1, ResNet-18 P2FRT = 18): output on q_0
+    assert pm.tensors[pm.output].level == 0

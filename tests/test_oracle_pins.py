@@ -345,6 +345,72 @@ def test_rescale_is_rounded_division(small):
     assert out.level == lv - 1 and out.scale == 2.0 ** 60 / ql
 
 
+def test_moddown_is_rounded_division_by_p():
+    """ModDown(acc) equals round(acc / P) for every coefficient, with acc taken
+    as its centred integer in (-PQ/2, PQ/2] (big integers; three special primes
+    so that the fast conversion from P overshoots by up to 2P)."""
+    prm = C.make_params(logn=5, L=2, q_bits=40, q0_bits=45, p_bits=50, alpha=3, log_scale=30)
+    S = C.CKKS(prm)
+    lv = prm.L
+    ext = S.ext_primes(lv)
+    rng = np.random.default_rng(9)
+    acc_coef = np.stack([np.stack([rng.integers(0, prm.primes[t], prm.N, dtype=np.uint64) for t in ext])
+                         for _ in range(2)])
+    acc = np.stack([np.stack([C.ntt(acc_coef[r, k], prm.primes[t], prm.psi[t]) for k, t in enumerate(ext)])
+                    for r in range(2)])
+    out = S.moddown(acc, lv)
+    PQ = prm.P
+    Q = 1
+    for q in prm.q[:lv + 1]:
+        Q *= q
+        PQ *= q
+    terms = []
+    for k, t in enumerate(ext):
+        pt = prm.primes[t]
+        Mk = PQ // pt
+        terms.append((Mk * pow(Mk % pt, -1, pt)) % PQ)
+    for r in range(2):
+        got = S.crt(np.stack([C.intt(out[r, t], prm.q[t], prm.psi[t]) for t in range(lv + 1)]))
+        for c in range(prm.N):
+            x = sum(int(acc_coef[r, k, c]) * terms[k] for k in range(len(ext))) % PQ
+            if x > PQ // 2:
+                x -= PQ
+            rounded = (2 * x + prm.P) // (2 * prm.P)        # floor(x/P + 1/2)
+            assert (got[c] - rounded) % Q == 0
+
+
+def test_conv_overflow_counts_the_overshoot():
+    """basis_convert(x) - conv_overflow(x)*Qin reproduces x exactly (CRT)."""
+    qs = C.gen_primes(50, 4, 1 << 13)
+    rng = np.random.default_rng(10)
+    Qin = 1
+    for q in qs:
+        Qin *= q
+    xs = [int(a) * int(b) % Qin for a, b in zip(rng.integers(1, 2 ** 62, 64, dtype=np.int64),
+                                                 rng.integers(1, 2 ** 62, 64, dtype=np.int64))]
+    res = np.array([[x % q for x in xs] for q in qs], dtype=np.uint64)
+    u = C.conv_overflow(res, qs)
+    assert u.max() < len(qs)
+    t = C.gen_primes(58, 1, 1 << 13)[0]
+    conv = C.basis_convert(res, qs, t)
+    for k, x in enumerate(xs):
+        assert (int(conv[k]) - int(u[k]) * Qin) % t == x % t
+
+
+def test_rotation_error_not_concentrated_in_one_slot():
+    """After an exact ModDown the key-switching error has no constant bias:
+    the decoded error of a rotation at slot 0 (where a per-coefficient bias
+    times s would concentrate) is of the size of the other slots'."""
+    prm = C.make_params(logn=12, L=3, q_bits=50, q0_bits=40, p_bits=58, alpha=3, log_scale=25)
+    S = C.CKKS(prm)
+    keys = S.keygen(11, [1])
+    z = np.random.default_rng(0).uniform(-0.01, 0.01, prm.N // 2)
+    ct = S.encrypt(keys, S.encode(z, 2.0 ** 25, prm.L), 5)
+    e = S.decrypt_decode(keys, S.rotate(ct, 1, keys)).real - np.roll(z, -1)
+    assert abs(e[0]) < 2 * np.abs(e[1:]).max()
+    assert np.abs(e).max() < 1e-3
+
+
 # ------------------------------------------------------------------ planner
 
 def test_table1_levels():
