@@ -199,7 +199,7 @@ def run_ours(args, rank, world):
     net = synth.resnet20()
     raw = synth.params(net)
     prog = M.compile_network(net, raw, F.fhe_ctx_primes(ctx)[: pre["L"] + 1], pre["logn"], pre["log_scale"],
-                             "packed", pre["alpha"])
+                             "packed", pre["alpha"], input_lambda=synth.INPUT_LAMBDA[PRESET])
     sk, evk = F.fhe_keygen(ctx, synth.SEED_KEYS, sorted(prog.rotations))
     desc = M.ModelDesc(prog, N // 2)
     model = F.fhe_model_load(ctx, desc.desc)
@@ -213,7 +213,7 @@ def run_ours(args, rank, world):
     for i in range(B):
         img = synth.image(rank * B + i, 3, 32, 32)
         for k, v in enumerate(M.input_slots(prog, img, N // 2)):
-            pt = F.fhe_encode(ctx, v, 2.0 ** pre["log_scale"], pre["L"])
+            pt = F.fhe_encode(ctx, v, M.input_scale(prog), pre["L"])
             cts.append(F.fhe_encrypt(ctx, sk, pt, synth.enc_seed(rank * B + i, k)))
             F.fhe_pt_free(pt)
 
@@ -291,7 +291,7 @@ def run_ours(args, rank, world):
     # its group (H2D + NTT), runs, and exports the finished group (inverse
     # NTT + D2H)
     host_in = [F.fhe_ct_export(h, N)[0] for h in cts]
-    lvl_in, sc_in = pre["L"], 2.0 ** pre["log_scale"]
+    lvl_in, sc_in = pre["L"], M.input_scale(prog)
 
     def e2e_step():
         for _ in range(S):
@@ -346,9 +346,10 @@ def run_ours(args, rank, world):
         "data": "synthetic",
         "config": {
             "workload": "ResNet-20 (16/32/64, 3x3 blocks, 1x1 stride-2 shortcuts), 32x32x3 seeded uniform "
-                        "images, 10 classes; CKKS N=2^16, Delta=2^25, q0 40-bit + 20 x 50-bit, %d x 58-bit "
+                        "images, 10 classes; CKKS N=2^16, Delta=2^%d, q0 %d-bit + %d x %d-bit, %d x %d-bit "
                         "special primes, digit width %d (dnum %d); channel-packed layout"
-                        % (pre["alpha"], pre["alpha"], -(-(pre["L"] + 1) // pre["alpha"])),
+                        % (pre["log_scale"], pre["q0_bits"], pre["L"], pre["q_bits"], pre["alpha"], pre["p_bits"],
+                           pre["alpha"], -(-(pre["L"] + 1) // pre["alpha"])),
             "batch": S * g,
             "mixed_levels": True,
             "pipeline": "%d segments (cut after each activation), a group of %d images enters per tick; "
@@ -428,9 +429,10 @@ def run_reference(args, rank, world):
     raw = synth.params(net)
     # the same baby-step / giant-step schedule as the GPU arm (host planning only)
     from paper_2509_22857_gb300 import model as M
+    lam = synth.INPUT_LAMBDA[PRESET]
     giants = M.giant_steps(M.compile_network(net, raw, prm.q, pre["logn"], pre["log_scale"], "packed",
-                                             pre["alpha"]))
-    comp = cnn.Compiler(prm, "packed", giants)
+                                             pre["alpha"], input_lambda=lam))
+    comp = cnn.Compiler(prm, "packed", giants, 1, lam)
     comp.n = 1 << (pre["logn"] - 1)
     prog = comp.compile(net, cnn.transform(net, raw))
     unit = oracle_ledger(prog, pre["alpha"]) / ks_weight(pre["L"], pre["alpha"])
@@ -451,6 +453,143 @@ def run_reference(args, rank, world):
             "cpu_baseline": {"value": round(v, 8), "unit": "img/s", "cores": 1, "kind": "oracle",
                              "sample": "one top-level rotation per step"},
             "e2e": {"value": round(v, 8), "unit": "img/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def run_resnet18(args):
+    """ResNet-18 for 64x64x3 / 200 classes, an ensemble of 3 members in the
+    HW layout (member m in block m), weights clustered jointly to 16 values
+    per layer: one uniform batch of `batch` images through the whole network
+    (fhe_infer); its logits are checked against the float64 ensemble in
+    tests/test_gpu_fullsize.py."""
+    import torch
+    from paper_2509_22857_gb300 import _lib as F
+    from paper_2509_22857_gb300 import model as M
+    pre = synth.PRESETS["resnet18"]
+    N = 1 << pre["logn"]
+    B = args.batch
+    t0 = time.time()
+    ctx = F.fhe_ctx_create(pre["logn"], pre["L"], pre["q_bits"], pre["q0_bits"], pre["p_bits"], pre["alpha"],
+                           pre["log_scale"], 0)
+    net = synth.resnet18()
+    raws = synth.cluster_joint([synth.params(net, m) for m in range(3)], net, 16)
+    prog = M.compile_network(net, raws, F.fhe_ctx_primes(ctx)[: pre["L"] + 1], pre["logn"], pre["log_scale"],
+                             "hw_ens", pre["alpha"], input_lambda=synth.INPUT_LAMBDA["resnet18"])
+    sk, evk = F.fhe_keygen(ctx, synth.SEED_KEYS, sorted(prog.rotations))
+    desc = M.ModelDesc(prog, N // 2)
+    model = F.fhe_model_load(ctx, desc.desc)
+    t_setup = time.time() - t0
+    n_out = prog.tensors[prog.output].layout.n_ct
+    cts = []
+    for i in range(B):
+        img = synth.image(i, 3, 64, 64)
+        for k, v in enumerate(M.input_slots(prog, img, N // 2)):
+            pt = F.fhe_encode(ctx, v, M.input_scale(prog), pre["L"])
+            cts.append(F.fhe_encrypt(ctx, sk, pt, synth.enc_seed(i, k)))
+            F.fhe_pt_free(pt)
+    stream = torch.cuda.current_stream()
+    outs, phase_ms = F.fhe_infer_profiled(ctx, model, evk, cts, B, n_out, stream)
+    torch.cuda.synchronize()
+    for h in outs:
+        F.fhe_ct_free(h)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    outs = F.fhe_infer(ctx, model, evk, cts, B, n_out, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    n_ks, _ = program_ledger(prog, pre["alpha"])
+    res = {"workload": "ResNet-18 ensemble of 3 (64x64x3, 200 classes), HW layout, 16 joint clusters per layer; "
+                       "CKKS N=2^16, 19 + %d primes" % pre["alpha"],
+           "batch": B, "img_s": round(B / (ms / 1e3), 4), "ms_per_batch": round(ms, 1),
+           "phase_ms": {k: round(v, 1) for k, v in phase_ms.items()}, "setup_s": round(t_setup, 1),
+           "keyswitches_per_img": n_ks, "distinct_plaintexts": sum(len(st["vecs"]) for st in prog.steps
+                                                                  if st["kind"] == 1)}
+    print(json.dumps(res), flush=True)
+    for h in outs + cts:
+        F.fhe_ct_free(h)
+    F.fhe_model_free(model)
+    F.fhe_evk_free(evk)
+    F.fhe_sk_free(sk)
+    F.fhe_ctx_destroy(ctx)
+
+
+def run_serving(args):
+    """Serving stream: Poisson arrivals (rate args.rate) of single-image
+    requests drawn 50/30/20 from VGG-, ResNet-20- and ResNet-18-ensemble-
+    shaped models (their small forms, one ring N = 2^12 and one key set),
+    submitted to the continuous-batching server at their arrival times;
+    reports p50 / p99 latency and the images per second completed."""
+    from paper_2509_22857_gb300 import _lib as F
+    from paper_2509_22857_gb300 import model as M
+    pre = synth.PRESETS["resnet18_mini"]
+    N = 1 << pre["logn"]
+    ctx = F.fhe_ctx_create(pre["logn"], pre["L"], pre["q_bits"], pre["q0_bits"], pre["p_bits"], pre["alpha"],
+                           pre["log_scale"], 0)
+    primes = F.fhe_ctx_primes(ctx)[: pre["L"] + 1]
+    specs = [("vgg_mini", "packed", None), ("resnet_mini", "packed", None), ("resnet18_mini", "hw_ens", 3)]
+    progs, rots = [], set()
+    for arch, layout, members in specs:
+        net = synth.ARCHS[arch]()
+        raw = synth.cluster_joint([synth.params(net, m) for m in range(members)], net, 4) if members else \
+            synth.params(net)
+        progs.append((net, M.compile_network(net, raw, primes, pre["logn"], pre["log_scale"], layout,
+                                             pre["alpha"])))
+        rots |= progs[-1][1].rotations
+    sk, evk = F.fhe_keygen(ctx, synth.SEED_KEYS, sorted(rots))
+    descs = [M.ModelDesc(p, N // 2) for _, p in progs]
+    models = [F.fhe_model_load(ctx, d.desc) for d in descs]
+    server = F.fhe_server_create(ctx, evk)
+    mids = [F.fhe_server_add_model(server, m, 4) for m in models]
+    rng = np.random.default_rng(5)
+    n_req = args.requests
+    which = rng.choice(3, size=n_req, p=[0.5, 0.3, 0.2])
+    gaps = rng.exponential(1.0 / args.rate, size=n_req)
+    # client side: every request's image encrypted before the stream starts
+    reqs = []
+    for r in range(n_req):
+        net, prog = progs[which[r]]
+        inp = net[0]
+        img = synth.image(r, inp["c"], inp["h"], inp["w"])
+        cts = []
+        for k, v in enumerate(M.input_slots(prog, img, N // 2)):
+            pt = F.fhe_encode(ctx, v, M.input_scale(prog), pre["L"])
+            cts.append(F.fhe_encrypt(ctx, sk, pt, synth.enc_seed(r, k)))
+            F.fhe_pt_free(pt)
+        reqs.append(cts)
+    t0 = time.perf_counter()
+    t_next = t0
+    tickets = []
+    for r in range(n_req):
+        t_next += gaps[r]
+        d = t_next - time.perf_counter()
+        if d > 0:
+            time.sleep(d)
+        tickets.append(F.fhe_server_submit(server, mids[which[r]], reqs[r]))
+    lat = []
+    for r, t in enumerate(tickets):
+        n_out = progs[which[r]][1].tensors[progs[which[r]][1].output].layout.n_ct
+        outs, ms = F.fhe_server_poll(server, t, True, n_out)
+        lat.append(ms)
+        for h in outs:
+            F.fhe_ct_free(h)
+    t_end = time.perf_counter()
+    done, p50, p99 = F.fhe_server_stats(server)
+    per_model = {specs[k][0]: {"requests": int((which == k).sum()),
+                               "p50_ms": round(float(np.percentile([l for l, w in zip(lat, which) if w == k], 50)), 2),
+                               "p99_ms": round(float(np.percentile([l for l, w in zip(lat, which) if w == k], 99)), 2)}
+                 for k in range(3)}
+    print(json.dumps({"workload": "serving: Poisson %.1f req/s, %d single-image requests, 50/30/20 VGG / ResNet-20 / "
+                                  "ResNet-18-ensemble shapes (small forms, N=2^12, %d primes)"
+                                  % (args.rate, n_req, pre["L"] + 1 + pre["alpha"]),
+                      "completed": done, "p50_ms": round(p50, 2), "p99_ms": round(p99, 2),
+                      "img_s": round(done / (t_end - t0), 3), "per_model": per_model}), flush=True)
+    F.fhe_server_destroy(server)
+    for m in models:
+        F.fhe_model_free(m)
+    F.fhe_evk_free(evk)
+    F.fhe_sk_free(sk)
+    F.fhe_ctx_destroy(ctx)
 
 
 def run_ks_only(args):
@@ -486,9 +625,20 @@ def main():
     ap.add_argument("--ks-only", action="store_true", help="time only the top-level key switch")
     ap.add_argument("--ks-level", type=int, default=None)
     ap.add_argument("--alpha", type=int, default=None, help="--ks-only: digit width (special primes)")
+    ap.add_argument("--workload", default="resnet20", choices=["resnet20", "resnet18_ensemble", "serving"],
+                    help="resnet18_ensemble: one batch of the clustered ResNet-18 ensemble; serving: a Poisson "
+                         "request stream through the server (neither is the bench line)")
+    ap.add_argument("--requests", type=int, default=1000, help="serving: number of requests")
+    ap.add_argument("--rate", type=float, default=20.0, help="serving: mean arrivals per second")
     args = ap.parse_args()
     if args.ks_only:
         run_ks_only(args)
+        return
+    if args.workload == "resnet18_ensemble":
+        run_resnet18(args)
+        return
+    if args.workload == "serving":
+        run_serving(args)
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

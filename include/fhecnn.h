@@ -93,6 +93,13 @@ int fhe_ctx_create(const fhe_params *params, fhe_ctx **out);
 int fhe_ctx_destroy(fhe_ctx *ctx);
 /* q_0..q_L then p_0..p_{alpha-1} into out[cap]; *n = count (test hook). */
 int fhe_ctx_primes(const fhe_ctx *ctx, uint64_t *out, size_t cap, size_t *n);
+/* Execution tuning of a context (no effect on results; the paper has no
+ * counterpart): a linear step processes its input ciphertexts in chunks of
+ * at most lin_chunk_srcs MAC sources (inputs plus their baby-step
+ * rotations; >= 2, default 160), so that the rotated copies of a wide
+ * HW-layout layer are made and consumed a chunk at a time.  Returns
+ * FHE_E_INVAL for a value below 2. */
+int fhe_ctx_set_linear_chunk(fhe_ctx *ctx, int lin_chunk_srcs);
 
 /* ---------------------------------------------------------------- client */
 

@@ -329,11 +329,19 @@ def _bias_vector(bias, Lout: Layout, n_slots: int) -> Dict[int, np.ndarray]:
     return vecs
 
 
+# Scale of the classifier's plaintexts: Delta * 2^6.  Its folded weights
+# (pool divisor and activation coefficient included) are ~1e-5 on a few
+# slots, and a plaintext's coefficients are of order Delta |w|
+# sqrt(nonzero slots) / N; at Delta they would mostly round to zero.
+CLASSIFIER_SCALE_BITS = 6
+
+
 class Compiler:
     """Builds the homomorphic program of a transformed network: layouts,
     diagonals, levels, scales and rescale points."""
 
-    def __init__(self, prm: C.Params, layout_kind: str, giants: Optional[List[int]] = None, members: int = 1):
+    def __init__(self, prm: C.Params, layout_kind: str, giants: Optional[List[int]] = None, members: int = 1,
+                 input_lambda: int = 1):
         """giants: the giant-step size of each linear step in program order
         (any split r = g + b with b = r mod G is a valid evaluation of the
         same diagonals; the choice only moves work between baby and giant
@@ -347,6 +355,8 @@ class Compiler:
         self.giants = giants
         self.n_linear = 0
         self.members = members
+        # the client encrypts the image at scale Delta^input_lambda
+        self.input_lambda = input_lambda
 
     # -- tower reuse
     def _maybe_rescale(self, t: int) -> int:
@@ -400,7 +410,7 @@ class Compiler:
                     L0 = hw_ensemble_layout(nd["c"], nd["h"], nd["w"], n, self.members)
                 else:
                     L0 = packed_layout(nd["c"], nd["h"], nd["w"], 1, nd["w"], nd["h"] * nd["w"], n)
-                node_t[i] = self.prog.new(TensorInfo(L0, prm.L, prm.scale))
+                node_t[i] = self.prog.new(TensorInfo(L0, prm.L, prm.scale ** self.input_lambda))
                 self.prog.input_tensor = node_t[i]
             elif op == "conv":
                 if i in shortcut_convs:
@@ -441,7 +451,7 @@ class Compiler:
                 self.prog.steps.append({"op": "add", "src": [ta, tb], "dst": out})
                 node_t[i] = out
             elif op == "dense":
-                node_t[i] = self._dense(node_t[nd["src"]], nd, [x[i] for x in ts])
+                node_t[i] = self._dense(node_t[nd["src"]], nd, [x[i] for x in ts], i == len(net) - 1)
         self.prog.output_tensor = node_t[len(net) - 1]
         return self.prog
 
@@ -503,14 +513,15 @@ class Compiler:
             out = self._align(out, target)
         return out
 
-    def _dense(self, src: int, nd: Dict, tps: List[Dict]) -> int:
+    def _dense(self, src: int, nd: Dict, tps: List[Dict], classifier: bool = False) -> int:
         info = self.prog.tensors[src]
         Lin = info.layout
         cout = nd["cout"]
         tp = tps[0]
         w = tp["w"]
+        w_scale = self.prm.scale * (2.0 ** CLASSIFIER_SCALE_BITS if classifier else 1.0)
         if self.kind == "hw_ens":
-            return self._dense_ensemble(src, nd, tps)
+            return self._dense_ensemble(src, nd, tps, w_scale)
         if self.kind == "hw":
             # per-output partial products in block k, then a sum over the block
             cin = len(Lin.rep)
@@ -527,7 +538,7 @@ class Compiler:
             bias = np.zeros(self.n)
             for k in range(cout):
                 bias[k * Lin.B] = tp["bias"][k]
-            out = self._linear(src, diags, self.n, Lpart, self.prm.scale, {0: bias})
+            out = self._linear(src, diags, self.n, Lpart, w_scale, {0: bias})
             out = self._maybe_rescale(out)
             oi = self.prog.tensors[out]
             steps = [Lin.st * (1 << m) for m in range(int(math.log2(Lin.W)))] + \
@@ -543,18 +554,19 @@ class Compiler:
         Lo = single_layout(cout, Lin.B, self.n)
         diags = _lower_conv(w[:, :, None, None], 1, 0, Lin, Lo, self.n)
         bias = _bias_vector(tp["bias"], Lo, self.n)
-        out = self._linear(src, diags, 8 * Lin.B, Lo, self.prm.scale, bias)
+        out = self._linear(src, diags, 8 * Lin.B, Lo, w_scale, bias)
         return self._maybe_rescale(out)
 
 
-    def _dense_ensemble(self, src: int, nd: Dict, tps: List[Dict]) -> int:
+    def _dense_ensemble(self, src: int, nd: Dict, tps: List[Dict], w_scale: float) -> int:
         """Ensemble dense layer and average (Sec. 5.3) in the HW layout: the
         pooled feature of channel c, member m, sits in ciphertext c at slot
         m*B; logit k of member m is accumulated at slot m*B + k from the
         diagonal r = -k with weight w_m[k, c] / M (the 1/M of the average
         folded into the weights and bias); every diagonal is a giant step
-        (G = 1).  Then the blocks are summed with rotations by B, 2B, ..,
-        so the average of logit k lands in slot k."""
+        (G = 1).  Then, before the rescale (at the product's larger scale,
+        where rotation noise is negligible), the blocks are summed with
+        rotations by B, 2B, .., so the average of logit k lands in slot k."""
         info = self.prog.tensors[src]
         Lin = info.layout
         cout, M, B = nd["cout"], self.members, Lin.B
@@ -572,8 +584,7 @@ class Compiler:
         for k in range(cout):
             for m in range(M):
                 bias[m * B + k] = tps[m]["bias"][k] / float(M)
-        out = self._linear(src, diags, 1, Lpart, self.prm.scale, {0: bias})
-        out = self._maybe_rescale(out)
+        out = self._linear(src, diags, 1, Lpart, w_scale, {0: bias})
         oi = self.prog.tensors[out]
         steps = []
         span = 1
@@ -584,12 +595,12 @@ class Compiler:
                                        oi.scale))
         self.prog.steps.append({"op": "rotsum", "src": out, "dst": res, "steps": steps})
         self.prog.rot_steps.update(steps)
-        return res
+        return self._maybe_rescale(res)
 
 
 def compile_he(net: List[Dict], t, prm: C.Params, layout_kind: str,
-               giants: Optional[List[int]] = None, members: int = 1) -> Program:
-    return Compiler(prm, layout_kind, giants, members).compile(net, t)
+               giants: Optional[List[int]] = None, members: int = 1, input_lambda: int = 1) -> Program:
+    return Compiler(prm, layout_kind, giants, members, input_lambda).compile(net, t)
 
 
 # =================================================================== running
@@ -609,8 +620,9 @@ def encrypt_input(S: C.CKKS, keys: C.Keys, prog: Program, img: np.ndarray, image
                   enc_seed) -> List[C.Ciphertext]:
     prm = S.prm
     out = []
+    scale = prog.tensors[prog.input_tensor].scale
     for k, v in enumerate(input_vectors(prog, img, prm.N // 2)):
-        pt = S.encode(v, prm.scale, prm.L)
+        pt = S.encode(v, scale, prm.L)
         out.append(S.encrypt(keys, pt, enc_seed(image_index, k)))
     return out
 

@@ -70,6 +70,7 @@ def lib() -> ctypes.CDLL:
             "fhe_kernel_launches": (ctypes.c_uint64, []),
             "fhe_ctx_create": (c_int, [ctypes.POINTER(FheParams), PP]),
             "fhe_ctx_destroy": (c_int, [V]),
+            "fhe_ctx_set_linear_chunk": (c_int, [V, c_int]),
             "fhe_ctx_primes": (c_int, [V, P_U64, c_size, ctypes.POINTER(c_size)]),
             "fhe_keygen": (c_int, [V, c_u64, P_I32, c_size, PP, PP]),
             "fhe_sk_free": (c_int, [V]),
@@ -156,6 +157,10 @@ def fhe_ctx_create(log_n, L, q_bits, q0_bits, p_bits, alpha, log_scale, device=0
 
 def fhe_ctx_destroy(ctx):
     _check(lib().fhe_ctx_destroy(ctx))
+
+
+def fhe_ctx_set_linear_chunk(ctx, lin_chunk_srcs: int):
+    _check(lib().fhe_ctx_set_linear_chunk(ctx, int(lin_chunk_srcs)))
 
 
 def fhe_ctx_primes(ctx) -> List[int]:
@@ -436,7 +441,8 @@ def fhe_sk_export(sk, n_words: int) -> np.ndarray:
     return out
 
 
-EXPORTED = ["fhe_last_error", "fhe_kernel_launches", "fhe_ctx_create", "fhe_ctx_destroy", "fhe_ctx_primes", "fhe_keygen",
+EXPORTED = ["fhe_last_error", "fhe_kernel_launches", "fhe_ctx_create", "fhe_ctx_destroy", "fhe_ctx_primes",
+            "fhe_ctx_set_linear_chunk", "fhe_keygen",
             "fhe_sk_free", "fhe_evk_free", "fhe_evk_galois", "fhe_encode", "fhe_pt_free", "fhe_encrypt",
             "fhe_decrypt", "fhe_decode", "fhe_ct_free", "fhe_ct_info", "fhe_ct_export", "fhe_ct_import",
             "fhe_rotate", "fhe_square", "fhe_rescale", "fhe_add", "fhe_mul_plain", "fhe_model_load",

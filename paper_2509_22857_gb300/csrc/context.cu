@@ -466,6 +466,12 @@ extern "C" int fhe_ctx_destroy(fhe_ctx *ctx) {
     return FHE_OK;
 }
 
+extern "C" int fhe_ctx_set_linear_chunk(fhe_ctx *ctx, int lin_chunk_srcs) {
+    if (!ctx || lin_chunk_srcs < 2) return fhe_fail(FHE_E_INVAL, "linear chunk must be at least 2 sources");
+    ctx->lin_chunk_srcs = lin_chunk_srcs;
+    return FHE_OK;
+}
+
 extern "C" int fhe_ctx_primes(const fhe_ctx *ctx, uint64_t *out, size_t cap, size_t *n) {
     if (!ctx || !n) return fhe_fail(FHE_E_INVAL, "null argument");
     *n = ctx->primes.size();

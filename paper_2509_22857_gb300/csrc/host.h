@@ -70,6 +70,7 @@ struct fhe_ctx {
     u64 *rs_ws = nullptr;
     size_t rs_ws_words = 0;
     int dev = 0;
+    int lin_chunk_srcs = 160;         // MAC sources per chunk of a linear step
 };
 
 struct fhe_ct {

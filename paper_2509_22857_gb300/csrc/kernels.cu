@@ -914,24 +914,23 @@ __global__ void k_decrypt(DevCtx c, const u64 *ct, const u64 *s, u64 *m, int lev
     }
 }
 
-// ---- pt-MAC.  A CTA owns 32 consecutive coefficients of one limb for 8
-// images (thread = coefficient x image) and computes every output group of
-// the step: the rotated inputs it reads stay in L1 across groups, and the
-// CTAs of the image tiles of one coefficient tile run back to back so each
-// plaintext tile is fetched from HBM once per batch.  Products are summed in
+// ---- pt-MAC.  A CTA owns `tc` consecutive coefficients of one limb for
+// 256/tc images (thread = coefficient x image; tc = 32 for 8 or more images,
+// up to 256 for one image, so no thread idles on small batches) and computes
+// every output group of the step: the rotated inputs it reads stay in L1
+// across groups, and the CTAs of the image tiles of one coefficient tile run
+// back to back so each plaintext tile is fetched from HBM once per batch.  Products are summed in
 // 128 bits and reduced only when the sum could leave Barrett's range: with
 // b = bitlen(q), K products of residues stay below K q^2 < 2^(b+62) for
 // K <= 2^(62-b) (4096 terms for 50-bit primes).
-#define MAC_TC 32
-#define MAC_IB 8
-__global__ void __launch_bounds__(256) k_mac(DevCtx c, MacArgs a) {
+__global__ void __launch_bounds__(256) k_mac(DevCtx c, MacArgs a, int tc) {
     const int limb = blockIdx.z;
     const ModQ m = c.primes[limb].m;
     const long long N = 1ll << c.logN;
-    const int cl = threadIdx.x % MAC_TC, il = threadIdx.x / MAC_TC;
-    const int img = blockIdx.x * MAC_IB + il;
+    const int cl = threadIdx.x % tc, il = threadIdx.x / tc;
+    const int img = blockIdx.x * (256 / tc) + il;
     if (img >= a.n_items) return;
-    const long long off = (long long)limb * N + blockIdx.y * MAC_TC + cl;
+    const long long off = (long long)limb * N + (long long)blockIdx.y * tc + cl;
     const long long P = (long long)(a.level + 1) * N;
     // products summed before a reduction (one slot kept for the carried residue)
     const int kmax = (m.b >= 61 ? 2 : (1 << min(62 - m.b, 20))) - 1;
@@ -979,8 +978,13 @@ __global__ void __launch_bounds__(256) k_mac(DevCtx c, MacArgs a) {
         }
         u64 *o = G.out + (long long)img * G.out_item + off;
         const u64 b = G.bias ? __ldg(&G.bias[off]) : 0;
-        o[0] = add_mod(barrett(acc0, m), b, m.q);
-        o[P] = barrett(acc1, m);
+        u64 r0 = add_mod(barrett(acc0, m), b, m.q), r1 = barrett(acc1, m);
+        if (G.accumulate) {
+            r0 = add_mod(r0, o[0], m.q);
+            r1 = add_mod(r1, o[P], m.q);
+        }
+        o[0] = r0;
+        o[P] = r1;
     }
 }
 
@@ -1280,9 +1284,14 @@ cudaError_t launch_decrypt(const DevCtx &c, const u64 *ct, const u64 *s_ntt, u64
 
 cudaError_t launch_mac(const DevCtx &c, const MacArgs &a, cudaStream_t s) {
     if (a.n_groups == 0) return cudaSuccess;
-    dim3 g((a.n_items + MAC_IB - 1) / MAC_IB, (unsigned)((1ll << c.logN) / MAC_TC), a.level + 1);
+    // images per CTA: the batch rounded up to a power of two, at most 8
+    int ib = 1;
+    while (ib < 8 && ib < a.n_items) ib *= 2;
+    const int tc = 256 / ib;
+    if ((1ll << c.logN) % tc) return cudaErrorInvalidValue;
+    dim3 g((a.n_items + ib - 1) / ib, (unsigned)((1ll << c.logN) / tc), a.level + 1);
     COUNT_LAUNCH();
-    k_mac<<<g, 256, 0, s>>>(c, a);
+    k_mac<<<g, 256, 0, s>>>(c, a, tc);
     return cudaGetLastError();
 }
 

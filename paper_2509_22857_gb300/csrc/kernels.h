@@ -168,6 +168,7 @@ struct MacGroup {
     long long out_item;   // per-image stride of out
     const u64 *bias;      // plaintext added to poly 0 (nullable)
     int term_begin, term_end;
+    int accumulate;       // add to the output's current value instead of overwriting it
 };
 struct MacArgs {
     const MacGroup *groups;   // device arrays

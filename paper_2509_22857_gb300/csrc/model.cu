@@ -250,6 +250,7 @@ struct Exec {
     std::vector<std::vector<char>> host_stage;
     Persist *pers = nullptr;              // non-null: pipeline mode
     int cur_step = -1;
+    int list_sub = 0;                     // which work list of the current step
     // optional timing: events bracketing each phase, summed per phase kind
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> *prof = nullptr;
     void mark(int kind, bool begin) {
@@ -310,7 +311,7 @@ struct Exec {
             FHE_CU(cudaMemcpyAsync(*out, host_stage.back().data(), bytes, cudaMemcpyHostToDevice, s));
             return FHE_OK;
         }
-        auto key = std::make_pair(pers->variant, cur_step);
+        auto key = std::make_pair(pers->variant, cur_step * 65536 + list_sub);
         auto it = pers->lists.find(key);
         if (it == pers->lists.end()) {
             void *p;
@@ -361,6 +362,13 @@ struct Exec {
         return keyswitch(a);
     }
 
+    // Input chunks of a linear step: consecutive input ciphertexts whose
+    // baby-step rotations (B images each) fit LIN_CHUNK_BYTES and whose
+    // sources number at most the context's lin_chunk_srcs, so that the
+    // source tiles a MAC CTA reads stay in L1 across the output groups.  A
+    // step whose inputs all fit is one chunk; chunking changes no result.
+    static constexpr size_t LIN_CHUNK_BYTES = 32ull << 30;
+
     int linear(const MStep &st) {
         const MLinear &L = st.lin;
         fhe_ctx *c = m->ctx;
@@ -369,100 +377,142 @@ struct Exec {
         const u64 *in = buf[st.src];
         u64 *out = buf[st.dst];
         const long long in_item = item(st.src), out_item = item(st.dst);
-        int ti = 0;
-        // baby-step rotations of the inputs: the rotations of one input share
-        // its ModUp (hoisting); each then needs an inner product and a ModDown
-        std::vector<u64 *> rb(L.baby_ct.size(), nullptr);
-        for (size_t k = 0; k < L.baby_ct.size(); k++) FHE_TRY(tmp(ti++, (size_t)B * cs * 8, &rb[k]));
-        const long long nlN = (long long)(lv + 1) * c->N;
-        mark(10, true);
-        for (size_t k = 0; k < L.baby_ct.size(); k++) {
-            if (k > 0 && L.baby_ct[k] == L.baby_ct[k - 1]) continue;   // ModUp done for this input
-            const u64 *x = in + L.baby_ct[k] * cs;
-            KsArgs a;
-            memset(&a, 0, sizeof(a));
-            a.d = x + nlN;
-            a.d_item = in_item;
-            a.galois = 1;
-            a.n_items = B;
-            a.level = lv;
-            FHE_TRY(keyswitch(a, KS_MODUP));
-            for (size_t kk = k; kk < L.baby_ct.size() && L.baby_ct[kk] == L.baby_ct[k]; kk++) {
-                int err;
-                const u64 *key = key_for(L.baby_step[kk], &err);
-                if (!key) return err;
-                const int gal = galois_of_step(c, L.baby_step[kk]);
-                a.key = key;
-                a.key_digits_top = evk->digits;
-                a.ip_galois = gal;
-                a.add0 = x;
-                a.add_item = in_item;
-                a.add_galois = gal;
-                a.out = rb[kk];
-                a.out_item = cs;
-                FHE_TRY(keyswitch(a, KS_IP | KS_MODDOWN));
-            }
-        }
-        mark(10, false);
-        // sources: the input ciphertexts, then the baby-step rotations
         const int n_in = m->tensors[st.src].n_ct;
-        std::vector<MacSrc> hs;
-        for (int ct = 0; ct < n_in; ct++) hs.push_back(MacSrc{in + ct * cs, in_item});
-        for (size_t k = 0; k < rb.size(); k++) hs.push_back(MacSrc{rb[k], cs});
-        auto src_of = [&](int ct, int b) -> int {
-            if (galois_of_step(c, b) == 1) return ct;
-            for (size_t k = 0; k < L.baby_ct.size(); k++)
-                if (L.baby_ct[k] == ct && L.baby_step[k] == b) return n_in + (int)k;
-            return -1;
-        };
+        const long long nlN = (long long)(lv + 1) * c->N;
+        // babies of each input, then the chunks
+        std::vector<int> nb(n_in, 0), first_baby(n_in + 1, 0);
+        for (size_t k = 0; k < L.baby_ct.size(); k++) nb[L.baby_ct[k]]++;
+        for (int ct = 0; ct < n_in; ct++) first_baby[ct + 1] = first_baby[ct] + nb[ct];
+        const size_t baby_bytes = (size_t)B * cs * 8;
+        std::vector<int> cut{0};
+        int max_babies = 0;
+        {
+            int b = 0, srcs = 0;
+            for (int ct = 0; ct < n_in; ct++) {
+                const bool full = ct > cut.back() &&
+                                  ((size_t)(b + nb[ct]) * baby_bytes > LIN_CHUNK_BYTES ||
+                                   srcs + nb[ct] + 1 > m->ctx->lin_chunk_srcs);
+                if (full) {
+                    max_babies = std::max(max_babies, b);
+                    cut.push_back(ct);
+                    b = 0;
+                    srcs = 0;
+                }
+                b += nb[ct];
+                srcs += nb[ct] + 1;
+            }
+            max_babies = std::max(max_babies, b);
+            cut.push_back(n_in);
+        }
+        int ti = 0;
+        std::vector<u64 *> rb(max_babies, nullptr);
+        for (int k = 0; k < max_babies; k++) FHE_TRY(tmp(ti++, baby_bytes, &rb[k]));
         // accumulators of the giant steps (g != 0); g == 0 goes straight to out
         const int ng = (int)L.g_out.size();
         std::vector<u64 *> acc(ng, nullptr);
-        std::vector<MacGroup> hg(ng);
-        std::vector<MacTerm> ht;
-        for (int g = 0; g < ng; g++) {
-            const int o = L.g_out[g];
-            MacGroup &G = hg[g];
-            if (galois_of_step(c, L.g_giant[g]) == 1) {
-                G.out = out + o * cs;
-                G.out_item = out_item;
-                G.bias = L.bias_pt[o];
-            } else {
-                FHE_TRY(tmp(ti++, (size_t)B * cs * 8, &acc[g]));
-                G.out = acc[g];
-                G.out_item = cs;
-                G.bias = nullptr;
+        for (int g = 0; g < ng; g++)
+            if (galois_of_step(c, L.g_giant[g]) != 1) FHE_TRY(tmp(ti++, (size_t)B * cs * 8, &acc[g]));
+        for (size_t ch = 0; ch + 1 < cut.size(); ch++) {
+            const int lo = cut[ch], hi = cut[ch + 1];
+            // baby-step rotations of this chunk's inputs: the rotations of one
+            // input share its ModUp (hoisting); each then needs an inner
+            // product and a ModDown
+            mark(10, true);
+            for (int ct = lo; ct < hi; ct++) {
+                if (!nb[ct]) continue;
+                const u64 *x = in + ct * cs;
+                KsArgs a;
+                memset(&a, 0, sizeof(a));
+                a.d = x + nlN;
+                a.d_item = in_item;
+                a.galois = 1;
+                a.n_items = B;
+                a.level = lv;
+                FHE_TRY(keyswitch(a, KS_MODUP));
+                for (int kk = first_baby[ct]; kk < first_baby[ct + 1]; kk++) {
+                    int err;
+                    const u64 *key = key_for(L.baby_step[kk], &err);
+                    if (!key) return err;
+                    const int gal = galois_of_step(c, L.baby_step[kk]);
+                    a.key = key;
+                    a.key_digits_top = evk->digits;
+                    a.ip_galois = gal;
+                    a.add0 = x;
+                    a.add_item = in_item;
+                    a.add_galois = gal;
+                    a.out = rb[kk - first_baby[lo]];
+                    a.out_item = cs;
+                    FHE_TRY(keyswitch(a, KS_IP | KS_MODDOWN));
+                }
             }
-            G.term_begin = (int)ht.size();
-            for (int t = L.g_tb[g]; t < L.g_te[g]; t++) {
-                MacTerm T;
-                T.src = src_of(L.t_ct[t], L.t_baby[t]);
-                T.pad_ = 0;
-                if (T.src < 0) return fhe_fail(FHE_E_INVAL, "internal: missing baby rotation");
-                T.pt = L.t_pt[t];
-                ht.push_back(T);
+            mark(10, false);
+            // sources: the input ciphertexts, then this chunk's baby-step rotations
+            std::vector<MacSrc> hs;
+            for (int ct = 0; ct < n_in; ct++) hs.push_back(MacSrc{in + ct * cs, in_item});
+            for (int kk = first_baby[lo]; kk < first_baby[hi]; kk++) hs.push_back(MacSrc{rb[kk - first_baby[lo]], cs});
+            auto src_of = [&](int ct, int b) -> int {
+                if (galois_of_step(c, b) == 1) return ct;
+                for (int kk = first_baby[ct]; kk < first_baby[ct + 1]; kk++)
+                    if (L.baby_step[kk] == b) return n_in + (kk - first_baby[lo]);
+                return -1;
+            };
+            std::vector<MacGroup> hg;
+            std::vector<MacTerm> ht;
+            for (int g = 0; g < ng; g++) {
+                // the group's terms of this chunk (terms are ordered by input ct)
+                int tb = L.g_tb[g], te = L.g_te[g];
+                while (tb < te && L.t_ct[tb] < lo) tb++;
+                int tc = tb;
+                while (tc < te && L.t_ct[tc] < hi) tc++;
+                if (ch > 0 && tc == tb) continue;
+                const int o = L.g_out[g];
+                MacGroup G;
+                if (!acc[g]) {
+                    G.out = out + o * cs;
+                    G.out_item = out_item;
+                    G.bias = ch == 0 ? L.bias_pt[o] : nullptr;
+                } else {
+                    G.out = acc[g];
+                    G.out_item = cs;
+                    G.bias = nullptr;
+                }
+                G.accumulate = ch > 0 ? 1 : 0;
+                G.term_begin = (int)ht.size();
+                for (int t = tb; t < tc; t++) {
+                    MacTerm T;
+                    T.src = src_of(L.t_ct[t], L.t_baby[t]);
+                    T.pad_ = 0;
+                    if (T.src < 0) return fhe_fail(FHE_E_INVAL, "internal: missing baby rotation");
+                    T.pt = L.t_pt[t];
+                    ht.push_back(T);
+                }
+                G.term_end = (int)ht.size();
+                hg.push_back(G);
             }
-            G.term_end = (int)ht.size();
+            if (hg.empty()) continue;
+            const size_t gb = hg.size() * sizeof(MacGroup), tb_ = ht.size() * sizeof(MacTerm),
+                         sb = hs.size() * sizeof(MacSrc);
+            std::vector<char> lst(gb + tb_ + sb);
+            memcpy(lst.data(), hg.data(), gb);
+            if (tb_) memcpy(lst.data() + gb, ht.data(), tb_);
+            memcpy(lst.data() + gb + tb_, hs.data(), sb);
+            char *dw;
+            list_sub = (int)ch;
+            FHE_TRY(work_list(lst.data(), lst.size(), &dw));
+            list_sub = 0;
+            MacArgs ma;
+            ma.groups = (const MacGroup *)dw;
+            ma.terms = (const MacTerm *)(dw + gb);
+            ma.srcs = (const MacSrc *)(dw + gb + tb_);
+            ma.n_groups = (int)hg.size();
+            ma.n_srcs = (int)hs.size();
+            ma.n_items = B;
+            ma.level = lv;
+            mark(11, true);
+            FHE_CU(launch_mac(c->dc, ma, s));
+            mark(11, false);
+            if (!pers) cudaFreeAsync(dw, s);
         }
-        const size_t gb = hg.size() * sizeof(MacGroup), tb = ht.size() * sizeof(MacTerm),
-                     sb = hs.size() * sizeof(MacSrc);
-        std::vector<char> lst(gb + tb + sb);
-        memcpy(lst.data(), hg.data(), gb);
-        if (tb) memcpy(lst.data() + gb, ht.data(), tb);
-        memcpy(lst.data() + gb + tb, hs.data(), sb);
-        char *dw;
-        FHE_TRY(work_list(lst.data(), lst.size(), &dw));
-        MacArgs ma;
-        ma.groups = (const MacGroup *)dw;
-        ma.terms = (const MacTerm *)(dw + gb);
-        ma.srcs = (const MacSrc *)(dw + gb + tb);
-        ma.n_groups = ng;
-        ma.n_srcs = (int)hs.size();
-        ma.n_items = B;
-        ma.level = lv;
-        mark(11, true);
-        FHE_CU(launch_mac(c->dc, ma, s));
-        mark(11, false);
         mark(12, true);
         // giant steps: out_o += sum_g rot(acc_{o,g}, g) with one ModDown per
         // output: each term's ModUp and inner product accumulate in the
@@ -508,7 +558,6 @@ struct Exec {
         mark(12, false);
         for (auto p : rb) tmp_free(p);
         for (auto p : acc) tmp_free(p);
-        if (!pers) cudaFreeAsync(dw, s);
         return FHE_OK;
     }
 

@@ -305,10 +305,21 @@ def groups_of(st: Dict) -> Dict[Tuple[int, int], List]:
     return groups
 
 
+# The classifier (the network's last dense layer) has tiny, sparse weights
+# once the pool divisor and the activation's leading coefficient are folded
+# into it (about 1e-5 on a few slots), and an encoded plaintext's
+# coefficients are of order Delta |w| sqrt(nonzero slots) / N: at Delta alone
+# most of them would round to 0 and the weights would be attenuated.  Its
+# plaintexts are encoded at Delta * 2^CLASSIFIER_EXTRA_BITS; the output keeps
+# that factor in its (tracked) scale, which q_0 has room for.
+CLASSIFIER_EXTRA_BITS = 6
+
+
 class Planner:
     def __init__(self, primes_q: Sequence[int], log_n: int, log_scale: float, layout: str, alpha: int = 3,
-                 max_giant_blocks: int = 8, members: int = 1):
+                 max_giant_blocks: int = 8, members: int = 1, input_lambda: int = 1):
         self.members = members
+        self.input_lambda = input_lambda
         self.alpha = alpha
         self.max_giant_blocks = max_giant_blocks
         self.q = list(primes_q)
@@ -461,10 +472,11 @@ class Planner:
         ia = self.p.tensors[a]
         return self._emit(kind=F.STEP_ADD, src=a, src2=b, dst=self._t(ia.layout, ia.level, ia.scale))
 
-    def dense(self, src: int, node: Dict, ps: List[Dict]) -> int:
+    def dense(self, src: int, node: Dict, ps: List[Dict], last: bool = False) -> int:
         info = self.p.tensors[src]
         lin = info.layout
         cout = node["cout"]
+        wsc = self.delta * (2.0 ** CLASSIFIER_EXTRA_BITS if last else 1.0)
         if self.layout == "hw":
             # products in block k of ciphertext 0, then a sum over the block
             w = ps[0]["w"]
@@ -476,7 +488,7 @@ class Planner:
                     ct, base = _pick_copy(lin.copies[c], k * lin.block, self.n)
                     vec[base + offs] = w[k, c * len(offs):(c + 1) * len(offs)]
             part = SlotMap(1, [[(0, k * lin.block)] for k in range(cout)], 1, 1, 1, 1, lin.block)
-            t = self._bsgs_step(src, terms_of(diag), self.n, part, self.delta, self._bias_vecs([ps[0]["bias"]], part))
+            t = self._bsgs_step(src, terms_of(diag), self.n, part, wsc, self._bias_vecs([ps[0]["bias"]], part))
             t = self._rule(t)
             ti = self.p.tensors[t]
             steps = [lin.st << m for m in range(int(math.log2(lin.W)))] + \
@@ -485,20 +497,20 @@ class Planner:
             return self._emit(kind=F.STEP_ROTSUM, src=t, steps=steps,
                               dst=self._t(map_single(cout, lin.block, self.n), ti.level, ti.scale))
         if self.layout == "hw_ens":
-            return self._dense_ensemble(src, node, ps)
+            return self._dense_ensemble(src, node, ps, wsc)
         lout = map_single(cout, lin.block, self.n)
         terms = terms_of(diagonals(ps[0]["w"].reshape(cout, -1, 1, 1), 1, 0, lin, lout, self.n))
-        t = self._bsgs_step(src, terms, 8 * lin.block, lout, self.delta, self._bias_vecs([ps[0]["bias"]], lout))
+        t = self._bsgs_step(src, terms, 8 * lin.block, lout, wsc, self._bias_vecs([ps[0]["bias"]], lout))
         return self._rule(t)
 
-    def _dense_ensemble(self, src: int, node: Dict, ps: List[Dict]) -> int:
+    def _dense_ensemble(self, src: int, node: Dict, ps: List[Dict], wsc: float) -> int:
         """Dense layer of an ensemble in the HW layout, then the ensemble
         average (Sec. 5.3).  Input channel c (ciphertext c) holds member m's
         pooled feature at slot m*B; output k of member m goes to slot
         m*B + k, read at rotation r = -k, with weight w_m[k, c] / M; giant
         steps only (each partial sum sum_c d_(c,g) (.) in_c is rotated once).
-        Then the M blocks are summed by rotations of B, 2B, 4B, ..: the
-        averaged logit k ends in slot k of block 0."""
+        Then the M blocks are summed by rotations of B, 2B, 4B, .. (before
+        the rescale): the averaged logit k ends in slot k of block 0."""
         info = self.p.tensors[src]
         lin = info.layout
         cout, M, B = node["cout"], self.members, lin.block
@@ -523,14 +535,15 @@ class Planner:
         terms = Terms(o_idx, c_idx, (-k_idx) % self.n, inv.reshape(-1), vecs)
         part = SlotMap(1, [[(0, m * B + k) for m in range(M)] for k in range(cout)], 1, 1, 1, 1, B)
         bias = self._bias_vecs([p["bias"] / float(M) for p in ps], part)
-        t = self._bsgs_step(src, terms, 1, part, self.delta, bias)
-        t = self._rule(t)
+        t = self._bsgs_step(src, terms, 1, part, wsc, bias)
+        # the block sum runs before the rescale, on the product at the
+        # larger scale, where the rotations' noise is negligible
         ti = self.p.tensors[t]
         steps = [B << j for j in range(max(0, (M - 1).bit_length()))]
         self.p.rotations.update(steps)
-        return self._emit(kind=F.STEP_ROTSUM, src=t, steps=steps,
-                          dst=self._t(SlotMap(1, [[(0, k)] for k in range(cout)], 1, 1, 1, 1, B), ti.level,
-                                      ti.scale))
+        t = self._emit(kind=F.STEP_ROTSUM, src=t, steps=steps,
+                       dst=self._t(SlotMap(1, [[(0, k)] for k in range(cout)], 1, 1, 1, 1, B), ti.level, ti.scale))
+        return self._rule(t)
 
     def compile(self, net: List[Dict], prms: List[Dict]) -> Program:
         node_t: Dict[int, int] = {}
@@ -545,7 +558,7 @@ class Planner:
                     lay = map_hw_ensemble(node["c"], node["h"], node["w"], self.n, self.members)
                 else:
                     lay = map_packed(node["c"], node["h"], node["w"], 1, node["w"], node["h"] * node["w"], self.n)
-                node_t[idx] = self.p.input = self._t(lay, self.L, self.delta)
+                node_t[idx] = self.p.input = self._t(lay, self.L, self.delta ** self.input_lambda)
             elif kind == "conv":
                 if idx not in later:
                     node_t[idx] = self.conv(node_t[node["src"]], node, ps)
@@ -562,22 +575,31 @@ class Planner:
                     sc = self.shortcut_identity(node_t[b], ps, main)
                 node_t[idx] = self.add(node_t[a], sc)
             elif kind == "dense":
-                node_t[idx] = self.dense(node_t[node["src"]], node, ps)
+                node_t[idx] = self.dense(node_t[node["src"]], node, ps, last=idx == len(net) - 1)
         self.p.output = node_t[len(net) - 1]
         return self.p
 
 
 def compile_network(net, raw, primes_q, log_n, log_scale, layout, alpha: int = 3,
-                    max_giant_blocks: int = 8) -> Program:
+                    max_giant_blocks: int = 8, input_lambda: int = 1) -> Program:
     """raw: one model's raw parameters, or a list of them (an ensemble, laid
     out with layout "hw_ens": member m in block m of every ciphertext).
     alpha: digit width of key switching (for the baby-step / giant-step
-    cost model); max_giant_blocks = 1 keeps the giant step at one block."""
+    cost model); max_giant_blocks = 1 keeps the giant step at one block.
+    input_lambda: the client encodes the image at scale Delta^input_lambda
+    (the program's input tensor scale; 2 keeps every key switch of the
+    first layer at scale Delta^2)."""
     raws = raw if isinstance(raw, (list, tuple)) else [raw]
     if len(raws) > 1 and layout != "hw_ens":
         raise ValueError("an ensemble needs the hw_ens layout")
     prms = [prepare_params(net, r) for r in raws]
-    return Planner(primes_q, log_n, log_scale, layout, alpha, max_giant_blocks, len(raws)).compile(net, prms)
+    return Planner(primes_q, log_n, log_scale, layout, alpha, max_giant_blocks, len(raws),
+                   input_lambda).compile(net, prms)
+
+
+def input_scale(prog: Program) -> float:
+    """the scale at which the client encodes the program's input"""
+    return prog.tensors[prog.input].scale
 
 
 def giant_steps(prog: Program) -> List[int]:

@@ -18,8 +18,9 @@ workloads; no dataset items are reproduced):
                           2 + 100 m; the activation polynomial of a layer
                           (seed 3) is shared by the members
   clustered weights       per layer, joint k-means in R^M over the members'
-                          weight draws (k centroids, ``cluster_joint``);
-                          every weight is replaced by its centroid's entry
+                          weight draws (k centroids fitted on at most 10^5
+                          positions, ``cluster_joint``); every weight is
+                          replaced by its nearest centroid's entry
 """
 from __future__ import annotations
 
@@ -224,19 +225,26 @@ def kmeans(points: np.ndarray, k: int, iters: int = 100):
     return cent, assign
 
 
-def cluster_joint(raws: List[Dict[int, Dict[str, np.ndarray]]], net: List[Dict], k: int = 16):
+def cluster_joint(raws: List[Dict[int, Dict[str, np.ndarray]]], net: List[Dict], k: int = 16,
+                  fit_max: int = 100000):
     """Joint weight clustering of an ensemble: for every convolution and
     dense layer, the M members' weights at one position form a point of R^M;
-    k-means (``kmeans``) over all positions of the layer gives k centroid
-    vectors, and member m's weight becomes entry m of its position's
-    centroid.  Returns new parameter dicts (other entries shared)."""
+    k-means (``kmeans``) gives k centroid vectors -- fitted on every
+    ceil(n / fit_max)-th position when a layer has more than fit_max -- and
+    every position takes its nearest centroid (squared distance, ties to the
+    lower index): member m's weight becomes entry m of that centroid.
+    Returns new parameter dicts (other entries shared)."""
     out = [{i: dict(p) for i, p in r.items()} for r in raws]
     for i, nd in enumerate(net):
         if nd["op"] not in ("conv", "dense"):
             continue
         shape = raws[0][i]["w"].shape
         pts = np.stack([r[i]["w"].reshape(-1) for r in raws], axis=1)
-        cent, assign = kmeans(pts, k)
+        stride = -(-len(pts) // fit_max)
+        cent, assign = kmeans(pts[::stride], k)
+        if stride > 1:
+            d2 = (cent * cent).sum(axis=1)[None, :] - 2.0 * (pts @ cent.T)
+            assign = np.argmin(d2, axis=1)
         for m in range(len(raws)):
             out[m][i]["w"] = cent[assign, m].reshape(shape)
     return out
@@ -250,13 +258,22 @@ def enc_seed(image_index: int, ct_index: int) -> int:
 # CKKS parameter presets: ring degree 2^logn; q_1..q_L of q_bits, q_0 of
 # q0_bits, alpha special primes of p_bits (alpha is also the digit width of
 # hybrid key switching); default scale Delta = 2^log_scale.  The N = 2^16
-# networks use dnum = 3 digits at the top level: alpha = 7 special primes of
-# 58 bits (406 bits) cover a digit of seven 50-bit primes.
+# networks use dnum = 3 digits at the top level (alpha = 7 special primes of
+# 58 bits for digits of seven 58-bit primes; key switches there run on
+# ciphertexts at scale Delta^2 or more, where the digit/P noise term is
+# negligible), and Delta = 2^29 with q ~ 2^58 keeps one prime per rescale
+# (tower reuse, round(log_Delta q) = 2): measured ResNet-20 logit error
+# 8.3e-4 at N = 2^16 (2.5e-3 at Delta = 2^28, 6.8e-2 at Delta = 2^25).
+# scale of the client's input encoding, as a power of Delta, per preset: the
+# N = 2^16 networks encrypt at Delta^2 so that the first layer's rotations,
+# like all later key switches, act on a ciphertext at scale >= Delta^2
+INPUT_LAMBDA = {"vgg11": 2, "resnet20": 2, "resnet18": 2}
+
 PRESETS = {
     "tiny": dict(logn=13, L=4, q_bits=40, q0_bits=40, p_bits=40, alpha=1, log_scale=40),
     "resnet_mini": dict(logn=12, L=8, q_bits=50, q0_bits=40, p_bits=58, alpha=3, log_scale=25),
-    "vgg11": dict(logn=16, L=11, q_bits=50, q0_bits=40, p_bits=58, alpha=7, log_scale=25),
-    "resnet20": dict(logn=16, L=20, q_bits=50, q0_bits=40, p_bits=58, alpha=7, log_scale=25),
-    "resnet18": dict(logn=16, L=18, q_bits=50, q0_bits=40, p_bits=58, alpha=7, log_scale=25),
-    "resnet18_mini": dict(logn=12, L=18, q_bits=50, q0_bits=40, p_bits=58, alpha=7, log_scale=25),
+    "vgg11": dict(logn=16, L=11, q_bits=58, q0_bits=40, p_bits=58, alpha=7, log_scale=29),
+    "resnet20": dict(logn=16, L=20, q_bits=58, q0_bits=40, p_bits=58, alpha=7, log_scale=29),
+    "resnet18": dict(logn=16, L=18, q_bits=58, q0_bits=40, p_bits=58, alpha=7, log_scale=29),
+    "resnet18_mini": dict(logn=12, L=18, q_bits=58, q0_bits=40, p_bits=58, alpha=7, log_scale=29),
 }

@@ -1,0 +1,67 @@
+"""The networks at their full sizes (N = 2^16) on the GPU: one encrypted
+image through the whole network, decrypted logits within 1e-3 of the float64
+network with the same argmax (bit-level parity at these sizes is covered by
+the small-ring cases; here the property that holds at any size is checked)."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import cnn
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(arch, preset, layout, raw, ref_fn, img_shape):
+    from paper_2509_22857_gb300 import _lib as F
+    from paper_2509_22857_gb300 import model as M
+    pre = synth.PRESETS[preset]
+    N = 1 << pre["logn"]
+    net = synth.ARCHS[arch]()
+    ctx = F.fhe_ctx_create(pre["logn"], pre["L"], pre["q_bits"], pre["q0_bits"], pre["p_bits"], pre["alpha"],
+                           pre["log_scale"])
+    try:
+        prog = M.compile_network(net, raw, F.fhe_ctx_primes(ctx)[: pre["L"] + 1], pre["logn"], pre["log_scale"],
+                                 layout, pre["alpha"], input_lambda=synth.INPUT_LAMBDA[preset])
+        sk, evk = F.fhe_keygen(ctx, synth.SEED_KEYS, sorted(prog.rotations))
+        desc = M.ModelDesc(prog, N // 2)
+        model = F.fhe_model_load(ctx, desc.desc)
+        img = synth.image(0, *img_shape)
+        cts = []
+        for k, v in enumerate(M.input_slots(prog, img, N // 2)):
+            pt = F.fhe_encode(ctx, v, M.input_scale(prog), pre["L"])
+            cts.append(F.fhe_encrypt(ctx, sk, pt, synth.enc_seed(0, k)))
+            F.fhe_pt_free(pt)
+        n_out = prog.tensors[prog.output].layout.n_ct
+        outs = F.fhe_infer(ctx, model, evk, cts, 1, n_out)
+        y = []
+        for ct, slot in M.logit_slots(prog):
+            dec = F.fhe_decrypt(ctx, sk, outs[ct])
+            y.append(F.fhe_decode(ctx, dec, N // 2)[slot].real)
+            F.fhe_pt_free(dec)
+        y = np.array(y)
+        want = ref_fn(net, img)
+        for h in outs + cts:
+            F.fhe_ct_free(h)
+        F.fhe_model_free(model)
+        F.fhe_evk_free(evk)
+        F.fhe_sk_free(sk)
+    finally:
+        F.fhe_ctx_destroy(ctx)
+    return y, want
+
+
+def test_resnet20_full_size_logits():
+    net = synth.resnet20()
+    raw = synth.params(net)
+    y, want = _run("resnet20", "resnet20", "packed", raw, lambda n, img: cnn.forward_plain(n, raw, img), (3, 32, 32))
+    assert np.max(np.abs(y - want)) < 1e-3
+    assert np.argmax(y) == np.argmax(want)
+
+
+def test_resnet18_ensemble_full_size_logits():
+    net = synth.resnet18()
+    raws = synth.cluster_joint([synth.params(net, m) for m in range(3)], net, 16)
+    y, want = _run("resnet18", "resnet18", "hw_ens", raws, lambda n, img: cnn.forward_ensemble(n, raws, img),
+                   (3, 64, 64))
+    assert np.max(np.abs(y - want)) < 1e-3
+    assert np.argmax(y) == np.argmax(want)

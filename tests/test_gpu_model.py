@@ -10,7 +10,8 @@ from oracle import cnn
 
 pytestmark = pytest.mark.gpu
 
-CASES = {"tiny": ("tiny", "tiny", "hw"), "mini": ("resnet_mini", "resnet_mini", "packed"),
+# (arch, preset, layout[, input scale as a power of Delta])
+CASES = {"tiny": ("tiny", "tiny", "hw"), "mini": ("resnet_mini", "resnet_mini", "packed", 2),
          "vgg_mini": ("vgg_mini", "resnet_mini", "packed"),
          # ResNet-18's structure, an ensemble of 3 in the HW layout, weights
          # clustered jointly to 4 values per layer
@@ -22,7 +23,8 @@ class Setup:
     def __init__(self, case):
         from paper_2509_22857_gb300 import _lib as F
         from paper_2509_22857_gb300 import model as M
-        arch, preset, layout = CASES[case]
+        arch, preset, layout = CASES[case][:3]
+        lam = CASES[case][3] if len(CASES[case]) > 3 else 1
         self.F, self.M = F, M
         self.net = synth.ARCHS[arch]()
         if layout == "hw_ens":
@@ -40,10 +42,10 @@ class Setup:
         self.ctx = F.fhe_ctx_create(pre["logn"], pre["L"], pre["q_bits"], pre["q0_bits"], pre["p_bits"],
                                     pre["alpha"], pre["log_scale"])
         self.pm = M.compile_network(self.net, self.raw, F.fhe_ctx_primes(self.ctx)[: pre["L"] + 1], pre["logn"],
-                                    pre["log_scale"], layout, pre["alpha"])
+                                    pre["log_scale"], layout, pre["alpha"], input_lambda=lam)
         # the oracle evaluates the same diagonals with the package's baby-step / giant-step split
         self.po = cnn.compile_he(self.net, t, self.prm, layout, M.giant_steps(self.pm),
-                                 ENSEMBLE if layout == "hw_ens" else 1)
+                                 ENSEMBLE if layout == "hw_ens" else 1, lam)
         self._oracle_cache = {}
         self.keys = self.S.keygen(synth.SEED_KEYS, sorted(self.po.rot_steps))
         self.sk, self.evk = F.fhe_keygen(self.ctx, synth.SEED_KEYS, sorted(self.pm.rotations))
@@ -56,7 +58,7 @@ class Setup:
         img = synth.image(i, self.inp["c"], self.inp["h"], self.inp["w"])
         out = []
         for k, v in enumerate(M.input_slots(self.pm, img, self.prm.N // 2)):
-            pt = F.fhe_encode(self.ctx, v, self.prm.scale, self.prm.L)
+            pt = F.fhe_encode(self.ctx, v, M.input_scale(self.pm), self.prm.L)
             out.append(F.fhe_encrypt(self.ctx, self.sk, pt, synth.enc_seed(i, k)))
             F.fhe_pt_free(pt)
         return img, out
@@ -167,3 +169,25 @@ def test_per_layer_entry_points(setup):
             F.fhe_ct_free(h)
         for h in handles:
             F.fhe_ct_free(h)
+
+
+def test_chunked_linear_steps_change_nothing(setup):
+    """Linear steps split into chunks of few sources (rotated copies made and
+    consumed a chunk at a time, MAC outputs accumulated over chunks) give
+    the same ciphertexts as one chunk."""
+    s = setup
+    F = s.F
+    n_out = s.pm.tensors[s.pm.output].layout.n_ct
+    img, cts = s.encrypt(0)
+    whole = F.fhe_infer(s.ctx, s.model, s.evk, cts, 1, n_out)
+    F.fhe_ctx_set_linear_chunk(s.ctx, 5)
+    try:
+        parts = F.fhe_infer(s.ctx, s.model, s.evk, cts, 1, n_out)
+    finally:
+        F.fhe_ctx_set_linear_chunk(s.ctx, 160)
+    for a, b in zip(whole, parts):
+        assert np.array_equal(F.fhe_ct_export(a, s.prm.N)[0], F.fhe_ct_export(b, s.prm.N)[0])
+    for h in whole + parts + cts:
+        F.fhe_ct_free(h)
+    with pytest.raises(F.FheError):
+        F.fhe_ctx_set_linear_chunk(s.ctx, 1)

@@ -112,3 +112,24 @@ def test_clustered_ensemble_program_matches_oracle():
             assert len(st["vecs"]) <= 4 * 9
     # 18 levels along the network (Table 1, ResNet-18 P2FRT = 18): output on q_0
     assert pm.tensors[pm.output].level == 0
+
+
+def test_input_at_delta_squared_costs_no_level():
+    """Encrypting the image at Delta^2 (first-layer rotations at scale
+    Delta^2) leaves ResNet-20's plan at the same depth: output at level 0
+    after the same number of rescales, in both compilers."""
+    net = synth.resnet20()
+    raw = synth.params(net)
+    pre = synth.PRESETS["resnet20"]
+    prm = O.make_params(**dict(pre, logn=12))
+    plans = {}
+    for lam in (1, 2):
+        pm = M.compile_network(net, raw, prm.q, pre["logn"], pre["log_scale"], "packed", pre["alpha"],
+                               input_lambda=lam)
+        c = cnn.Compiler(prm, "packed", M.giant_steps(pm), 1, lam)
+        c.n = 1 << (pre["logn"] - 1)
+        po = c.compile(net, cnn.transform(net, raw))
+        _check(po, pm)
+        assert M.input_scale(pm) == po.tensors[po.input_tensor].scale == prm.scale ** lam
+        plans[lam] = (pm.tensors[pm.output].level, sum(1 for s in pm.steps if s["kind"] == 2))
+    assert plans[1] == plans[2] == (0, plans[1][1])
