@@ -118,6 +118,12 @@ def ks_weight(level, alpha):
 # products) = 2.01e12 modmul/s.
 ALU_PEAK_MODMUL = 152 * 64 * 2.07e9 / 10
 
+# DRAM bytes (read + write) of one top-level key switch of 4 polynomials with
+# the current kernels, summed over its kernels from one ncu capture
+# (profiles/ks_kernels_resnet20_level20.md); reported only for that
+# configuration (group of 4 at level 20, digit width 7).
+KS_TRAFFIC_L20_G4 = 1304410368
+
 
 def ks_modmuls(level, alpha, logn):
     """modular multiplications of one hybrid key switch at `level`"""
@@ -238,6 +244,18 @@ def run_ours(args, rank, world):
         torch.cuda.synchronize()
         barrier()
         return max_over_ranks(e0.elapsed_time(e1) / k, world)
+
+    if args.profile_uniform:
+        # one uniform batch in the profiled NVTX range (same kernels as a
+        # pipeline step, few enough launches for a serialised launch list)
+        infer(cts, B)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("bench_timed")
+        infer(cts, B)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        print(json.dumps({"profile_uniform": True, "batch": B}), flush=True)
+        return None
 
     # where the time goes: one uniform batch with events around every phase
     outs, phase_ms = F.fhe_infer_profiled(ctx, model, evk, cts, B, n_out, stream)
@@ -376,7 +394,8 @@ def run_ours(args, rank, world):
                      "achieved": round(alu_achieved / 1e9, 1), "peak": round(ALU_PEAK_MODMUL / 1e9, 1),
                      "unit": "Gmodmul/s", "peak_kind": "derived (152 SMs x 64 IMAD/clk x 2.07 GHz / 10 IMAD "
                                                        "per 64-bit modmul)",
-                     "frac": round(alu_achieved / ALU_PEAK_MODMUL, 4), "traffic": None,
+                     "frac": round(alu_achieved / ALU_PEAK_MODMUL, 4),
+                     "traffic": KS_TRAFFIC_L20_G4 if (g == 4 and lv == 20 and alpha == 7) else None,
                      "algorithmic_modmuls": int(ks_mm),
                      "hbm": {"achieved_gbs": round(achieved, 1), "peak_gbs": peak, "peak_kind": peak_kind,
                              "frac": round(achieved / peak, 4), "algorithmic_bytes": int(ks_bytes)},
@@ -628,6 +647,8 @@ def main():
     ap.add_argument("--workload", default="resnet20", choices=["resnet20", "resnet18_ensemble", "serving"],
                     help="resnet18_ensemble: one batch of the clustered ResNet-18 ensemble; serving: a Poisson "
                          "request stream through the server (neither is the bench line)")
+    ap.add_argument("--profile-uniform", action="store_true",
+                    help="run one uniform batch inside the NVTX range bench_timed and exit (for ncu launch lists)")
     ap.add_argument("--requests", type=int, default=1000, help="serving: number of requests")
     ap.add_argument("--rate", type=float, default=20.0, help="serving: mean arrivals per second")
     args = ap.parse_args()
@@ -651,7 +672,7 @@ def main():
         import torch
         torch.distributed.init_process_group("nccl")
     res = run_ours(args, rank, world)
-    if rank == 0:
+    if rank == 0 and res is not None:
         print(json.dumps(res), flush=True)
     if world > 1:
         import torch
