@@ -65,3 +65,51 @@ def test_resnet18_ensemble_full_size_logits():
                    (3, 64, 64))
     assert np.max(np.abs(y - want)) < 1e-3
     assert np.argmax(y) == np.argmax(want)
+
+
+def test_keyswitch_bit_exact_at_full_size():
+    """The bench's parameters (N = 2^16, 21 + 7 primes of the ResNet-20 chain,
+    digit width 7): a rotation and a relinearised square at the top level and
+    a rotation low in the chain, and a rescale, give limbs bit-identical to
+    the oracle's on the same seeded randomness."""
+    from oracle import ckks as O
+    from paper_2509_22857_gb300 import _lib as F
+    pre = synth.PRESETS["resnet20"]
+    prm = O.make_params(**pre)
+    S = O.CKKS(prm)
+    keys = S.keygen(synth.SEED_KEYS, [33])
+    ctx = F.fhe_ctx_create(pre["logn"], pre["L"], pre["q_bits"], pre["q0_bits"], pre["p_bits"], pre["alpha"],
+                           pre["log_scale"])
+    try:
+        sk, evk = F.fhe_keygen(ctx, synth.SEED_KEYS, [33])
+        z = np.random.default_rng(8).uniform(-1, 1, prm.N // 2)
+
+        def coef(ct):
+            return np.stack([np.stack([O.intt(ct.c[r, t], prm.primes[t], prm.psi[t]) for t in range(ct.level + 1)])
+                             for r in range(ct.c.shape[0])])
+
+        def same(ct_o, h):
+            buf, lv, sc = F.fhe_ct_export(h, prm.N)
+            assert lv == ct_o.level and sc == ct_o.scale
+            assert np.array_equal(buf, coef(ct_o))
+
+        for level in (pre["L"], 5):
+            ct_o = S.encrypt(keys, S.encode(z, prm.scale ** 2, level), 40 + level)
+            pt = F.fhe_encode(ctx, z, prm.scale ** 2, level)
+            ct_g = F.fhe_encrypt(ctx, sk, pt, 40 + level)
+            F.fhe_pt_free(pt)
+            r_g = F.fhe_rotate(ctx, evk, ct_g, 33)
+            same(S.rotate(ct_o, 33, keys), r_g)
+            if level == pre["L"]:
+                q_g = F.fhe_square(ctx, evk, ct_g)
+                q_o = S.relinearize(S.tensor_square(ct_o), keys)
+                same(q_o, q_g)
+                F.fhe_rescale(ctx, q_g)
+                same(S.rescale(q_o), q_g)
+                F.fhe_ct_free(q_g)
+            for h in (r_g, ct_g):
+                F.fhe_ct_free(h)
+        F.fhe_evk_free(evk)
+        F.fhe_sk_free(sk)
+    finally:
+        F.fhe_ctx_destroy(ctx)
