@@ -914,77 +914,85 @@ __global__ void k_decrypt(DevCtx c, const u64 *ct, const u64 *s, u64 *m, int lev
     }
 }
 
-// ---- pt-MAC.  A CTA owns `tc` consecutive coefficients of one limb for
-// 256/tc images (thread = coefficient x image; tc = 32 for 8 or more images,
-// up to 256 for one image, so no thread idles on small batches) and computes
-// every output group of the step: the rotated inputs it reads stay in L1
-// across groups, and the CTAs of the image tiles of one coefficient tile run
-// back to back so each plaintext tile is fetched from HBM once per batch.  Products are summed in
-// 128 bits and reduced only when the sum could leave Barrett's range: with
-// b = bitlen(q), K products of residues stay below K q^2 < 2^(b+62) for
-// K <= 2^(62-b) (4096 terms for 50-bit primes).
+// ---- pt-MAC.  A CTA owns 2 tc consecutive coefficients of one limb for
+// 256/tc images (thread = two adjacent coefficients x image, 16-byte loads;
+// tc = 32 for 8 or more images, up to 256 for one image, so no thread idles
+// on small batches) and computes every output group of the step: the
+// rotated inputs it reads stay in L1 across groups, and the CTAs of the image
+// tiles of one coefficient tile run back to back so each plaintext tile is
+// fetched from HBM once per batch.  Products are summed in 128 bits and
+// reduced only when the sum could leave Barrett's range: with b = bitlen(q),
+// K products of residues stay below K q^2 < 2^(b+62) for K <= 2^(62-b)
+// (16 terms for 58-bit primes).
 __global__ void __launch_bounds__(256) k_mac(DevCtx c, MacArgs a, int tc) {
+    // each thread owns two adjacent coefficients (16-byte loads)
     const int limb = blockIdx.z;
     const ModQ m = c.primes[limb].m;
     const long long N = 1ll << c.logN;
     const int cl = threadIdx.x % tc, il = threadIdx.x / tc;
     const int img = blockIdx.x * (256 / tc) + il;
     if (img >= a.n_items) return;
-    const long long off = (long long)limb * N + (long long)blockIdx.y * tc + cl;
+    const long long off = (long long)limb * N + (long long)blockIdx.y * 2 * tc + 2 * cl;
     const long long P = (long long)(a.level + 1) * N;
     // products summed before a reduction (one slot kept for the carried residue)
     const int kmax = (m.b >= 61 ? 2 : (1 << min(62 - m.b, 20))) - 1;
     for (int g = 0; g < a.n_groups; g++) {
         const MacGroup G = a.groups[g];
-        U128 acc0 = {0, 0}, acc1 = {0, 0};
+        U128 a00 = {0, 0}, a01 = {0, 0}, a10 = {0, 0}, a11 = {0, 0};   // [poly][coefficient]
         int cnt = 0;
         int t = G.term_begin;
-        // four terms per iteration: their loads are in flight together
-        for (; t + 4 <= G.term_end; t += 4) {
-            u64 p[4], x0[4], x1[4];
+        // two terms per iteration: their loads are in flight together
+        for (; t + 2 <= G.term_end; t += 2) {
+            ulonglong2 p[2], x0[2], x1[2];
 #pragma unroll
-            for (int k = 0; k < 4; k++) {
+            for (int k = 0; k < 2; k++) {
                 const MacTerm T = a.terms[t + k];
                 const MacSrc S = a.srcs[T.src];
                 const u64 *sp = S.base + (long long)img * S.item + off;
-                p[k] = __ldg(&T.pt[off]);
-                x0[k] = sp[0];
-                x1[k] = sp[P];
+                p[k] = __ldg(reinterpret_cast<const ulonglong2 *>(T.pt + off));
+                x0[k] = *reinterpret_cast<const ulonglong2 *>(sp);
+                x1[k] = *reinterpret_cast<const ulonglong2 *>(sp + P);
             }
 #pragma unroll
-            for (int k = 0; k < 4; k++) {
-                mac(acc0, p[k], x0[k]);
-                mac(acc1, p[k], x1[k]);
+            for (int k = 0; k < 2; k++) {
+                mac(a00, p[k].x, x0[k].x);
+                mac(a01, p[k].y, x0[k].y);
+                mac(a10, p[k].x, x1[k].x);
+                mac(a11, p[k].y, x1[k].y);
             }
-            cnt += 4;
-            if (cnt + 4 > kmax) {
-                acc0 = U128{barrett(acc0, m), 0};
-                acc1 = U128{barrett(acc1, m), 0};
+            cnt += 2;
+            if (cnt + 2 > kmax) {
+                a00 = U128{barrett(a00, m), 0};
+                a01 = U128{barrett(a01, m), 0};
+                a10 = U128{barrett(a10, m), 0};
+                a11 = U128{barrett(a11, m), 0};
                 cnt = 0;
             }
         }
-        for (; t < G.term_end; t++) {
+        if (t < G.term_end) {
             const MacTerm T = a.terms[t];
             const MacSrc S = a.srcs[T.src];
-            const u64 p = __ldg(&T.pt[off]);
             const u64 *sp = S.base + (long long)img * S.item + off;
-            mac(acc0, p, sp[0]);
-            mac(acc1, p, sp[P]);
-            if (++cnt == kmax) {
-                acc0 = U128{barrett(acc0, m), 0};
-                acc1 = U128{barrett(acc1, m), 0};
-                cnt = 0;
-            }
+            const ulonglong2 p = __ldg(reinterpret_cast<const ulonglong2 *>(T.pt + off));
+            const ulonglong2 x0 = *reinterpret_cast<const ulonglong2 *>(sp);
+            const ulonglong2 x1 = *reinterpret_cast<const ulonglong2 *>(sp + P);
+            mac(a00, p.x, x0.x);
+            mac(a01, p.y, x0.y);
+            mac(a10, p.x, x1.x);
+            mac(a11, p.y, x1.y);
         }
         u64 *o = G.out + (long long)img * G.out_item + off;
-        const u64 b = G.bias ? __ldg(&G.bias[off]) : 0;
-        u64 r0 = add_mod(barrett(acc0, m), b, m.q), r1 = barrett(acc1, m);
+        const ulonglong2 b = G.bias ? __ldg(reinterpret_cast<const ulonglong2 *>(G.bias + off)) : make_ulonglong2(0, 0);
+        ulonglong2 r0 = make_ulonglong2(add_mod(barrett(a00, m), b.x, m.q), add_mod(barrett(a01, m), b.y, m.q));
+        ulonglong2 r1 = make_ulonglong2(barrett(a10, m), barrett(a11, m));
         if (G.accumulate) {
-            r0 = add_mod(r0, o[0], m.q);
-            r1 = add_mod(r1, o[P], m.q);
+            const ulonglong2 o0 = *reinterpret_cast<const ulonglong2 *>(o);
+            const ulonglong2 o1 = *reinterpret_cast<const ulonglong2 *>(o + P);
+            r0 = make_ulonglong2(add_mod(r0.x, o0.x, m.q), add_mod(r0.y, o0.y, m.q));
+            r1 = make_ulonglong2(add_mod(r1.x, o1.x, m.q), add_mod(r1.y, o1.y, m.q));
         }
-        o[0] = r0;
-        o[P] = r1;
+        *reinterpret_cast<ulonglong2 *>(o) = r0;
+        *reinterpret_cast<ulonglong2 *>(o + P) = r1;
     }
 }
 
@@ -1287,9 +1295,9 @@ cudaError_t launch_mac(const DevCtx &c, const MacArgs &a, cudaStream_t s) {
     // images per CTA: the batch rounded up to a power of two, at most 8
     int ib = 1;
     while (ib < 8 && ib < a.n_items) ib *= 2;
-    const int tc = 256 / ib;
-    if ((1ll << c.logN) % tc) return cudaErrorInvalidValue;
-    dim3 g((a.n_items + ib - 1) / ib, (unsigned)((1ll << c.logN) / tc), a.level + 1);
+    const int tc = 256 / ib;   // threads per image, two coefficients each
+    if ((1ll << c.logN) % (2 * tc)) return cudaErrorInvalidValue;
+    dim3 g((a.n_items + ib - 1) / ib, (unsigned)((1ll << c.logN) / (2 * tc)), a.level + 1);
     COUNT_LAUNCH();
     k_mac<<<g, 256, 0, s>>>(c, a, tc);
     return cudaGetLastError();
