@@ -122,7 +122,7 @@ ALU_PEAK_MODMUL = 152 * 64 * 2.07e9 / 10
 # the current kernels, summed over its kernels from one ncu capture
 # (profiles/ks_kernels_resnet20_level20.md); reported only for that
 # configuration (group of 4 at level 20, digit width 7).
-KS_TRAFFIC_L20_G4 = 1304410368
+KS_TRAFFIC_L20_G4 = 1286310912
 
 
 def ks_modmuls(level, alpha, logn):

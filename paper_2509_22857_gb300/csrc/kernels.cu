@@ -477,53 +477,65 @@ __global__ void __launch_bounds__(NT, 3) k_ks_modup_row(DevCtx c, LevelTab lt, K
     for (int k = 0; k < 16; k++) p[tau + Gm::S * k] = reduce_fwd(x[k], P.m);
 }
 
-// (4b) inner product with the key, acc_k[t] = sum_j ext_j[t] * key_j[k][t].
-// One thread per coefficient; the items of the batch are looped inside so
-// each key coefficient is fetched from HBM once per batch.
+// (4b) inner product with the key, acc_k[t] = sum_j ext_j[t] * key_j[k][t],
+// for ND digits.  Each thread takes two adjacent NTT slots and loops over
+// the items of the batch, so each key coefficient is fetched from HBM once
+// per batch.
+// In the bit-reversed NTT order a Galois gather maps every aligned pair of
+// slots onto an aligned pair (in swapped order when the source index is odd),
+// so each operand pair is one 16-byte load.  ND sizes the key and operand
+// registers exactly, which keeps more loads in flight per SM than the scalar
+// kernel with one slot per thread and arrays for 7 digits, which was latency-bound.
+__device__ __forceinline__ ulonglong2 ld_pair(const u64 *p, bool swap) {
+    ulonglong2 v = *(const ulonglong2 *)p;
+    return swap ? make_ulonglong2(v.y, v.x) : v;
+}
+
+template <int ND>
 __global__ void __launch_bounds__(256) k_ks_ip(DevCtx c, LevelTab lt, KsArgs a, KsLayout ly) {
-    const int ext = lt.ext, nd = lt.n_digits;
+    const int ext = lt.ext;
     const int t = blockIdx.y;
     const int pi = ext_prime(t, a.level, c.L);
     const ModQ m = c.primes[pi].m;
     const long long N = 1ll << c.logN;
-    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    const int col = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     const long long key_limbs = c.L + 1 + c.alpha;
     const int jt = t <= a.level ? t / c.alpha : -1;   // digit that holds limb t itself
-    // hoisted rotation: sigma acts on every extended limb (NTT-domain gather)
     const int ip_col = galois_src(col, a.ip_galois, c.logN);
     const int src_col = jt >= 0 ? galois_src(ip_col, a.galois, c.logN) : ip_col;
-    // the key of this limb for every digit, kept in registers across the batch
-    u64 k0[7], k1[7];
+    const bool ip_sw = ip_col & 1, src_sw = src_col & 1;
+    ulonglong2 k0[ND], k1[ND];
 #pragma unroll
-    for (int j = 0; j < 7; j++) {
-        if (j < nd) {
-            const u64 *kb = a.key + ((long long)(j * 2) * key_limbs + pi) * N + col;
-            k0[j] = __ldg(kb);
-            k1[j] = __ldg(kb + key_limbs * N);
-        }
+    for (int j = 0; j < ND; j++) {
+        const u64 *kb = a.key + ((long long)(j * 2) * key_limbs + pi) * N + col;
+        k0[j] = __ldg((const ulonglong2 *)kb);
+        k1[j] = __ldg((const ulonglong2 *)(kb + key_limbs * N));
     }
     for (int item = 0; item < a.n_items; item++) {
-        const u64 *mu = a.ws + item * a.ws_item + ly.mu + (long long)t * N + ip_col;
-        u64 x[7];
+        const u64 *mu = a.ws + item * a.ws_item + ly.mu + (long long)t * N + (ip_col & ~1);
+        const u64 *dd = a.d + item * a.d_item + (long long)t * N + (src_col & ~1);
+        ulonglong2 x[ND];
 #pragma unroll
-        for (int j = 0; j < 7; j++)
-            if (j < nd) x[j] = (j == jt) ? a.d[item * a.d_item + (long long)t * N + src_col] : mu[(long long)j * ext * N];
-        U128 acc0 = {0, 0}, acc1 = {0, 0};
+        for (int j = 0; j < ND; j++) x[j] = (j == jt) ? ld_pair(dd, src_sw) : ld_pair(mu + (long long)j * ext * N, ip_sw);
+        U128 a00 = {0, 0}, a01 = {0, 0}, a10 = {0, 0}, a11 = {0, 0};
 #pragma unroll
-        for (int j = 0; j < 7; j++) {
-            if (j < nd) {
-                mac(acc0, x[j], k0[j]);
-                mac(acc1, x[j], k1[j]);
-            }
+        for (int j = 0; j < ND; j++) {
+            mac(a00, x[j].x, k0[j].x);
+            mac(a01, x[j].y, k0[j].y);
+            mac(a10, x[j].x, k1[j].x);
+            mac(a11, x[j].y, k1[j].y);
         }
-        u64 *o0 = a.ws + item * a.ws_item + ly.acc + (long long)t * N + col;
-        u64 r0 = barrett(acc0, m), r1 = barrett(acc1, m);
+        ulonglong2 *o0 = (ulonglong2 *)(a.ws + item * a.ws_item + ly.acc + (long long)t * N + col);
+        ulonglong2 *o1 = (ulonglong2 *)((u64 *)o0 + (long long)ext * N);
+        ulonglong2 r0 = make_ulonglong2(barrett(a00, m), barrett(a01, m));
+        ulonglong2 r1 = make_ulonglong2(barrett(a10, m), barrett(a11, m));
         if (a.ip_accumulate) {
-            r0 = add_mod(r0, o0[0], m.q);
-            r1 = add_mod(r1, o0[(long long)ext * N], m.q);
+            const ulonglong2 p0 = *o0, p1 = *o1;
+            r0 = make_ulonglong2(add_mod(r0.x, p0.x, m.q), add_mod(r0.y, p0.y, m.q));
+            r1 = make_ulonglong2(add_mod(r1.x, p1.x, m.q), add_mod(r1.y, p1.y, m.q));
         }
-        o0[0] = r0;
-        o0[(long long)ext * N] = r1;
+        *o0 = r0;
+        *o1 = r1;
     }
 }
 
@@ -1190,6 +1202,11 @@ cudaError_t launch_keyswitch(const DevCtx &c, const LevelTab &lt, const KsArgs &
     if (a.add_galois == 0) a.add_galois = a.galois;
     const int nl = a.level + 1, ext = lt.ext, nd = lt.n_digits, B = a.n_items;
     if (nd > 7) return cudaErrorInvalidValue;   // inner-product accumulator bound
+    // the inner product takes two slots per thread: 16-byte aligned operands and
+    // N >= 512 (always true of the library's own buffers, whose limbs start at
+    // multiples of N)
+    if (c.logN < 9 || ((uintptr_t)a.d | (uintptr_t)a.ws | (uintptr_t)a.key) % 16 != 0 || ((a.d_item | a.ws_item) & 1))
+        return cudaErrorMisalignedAddress;
     KsLayout ly = ks_layout(a.level, nd, c.alpha, c.logN);
     const int tc = tiles_col(c);
 #define KS_EV(i) \
@@ -1204,7 +1221,17 @@ cudaError_t launch_keyswitch(const DevCtx &c, const LevelTab &lt, const KsArgs &
     if (phases & KS_MODUP) DISPATCH_LOGR(c.logR2, k_ks_modup_row, dim3(tc, B * nd * ext), c, lt, a, ly);
     if (phases & KS_IP) {
         COUNT_LAUNCH();
-        k_ks_ip<<<dim3((unsigned)((1ll << c.logN) / 256), ext), 256, 0, s>>>(c, lt, a, ly);
+        const dim3 g2((unsigned)((1ll << c.logN) / 512), ext);
+        switch (nd) {
+        case 1: k_ks_ip<1><<<g2, 256, 0, s>>>(c, lt, a, ly); break;
+        case 2: k_ks_ip<2><<<g2, 256, 0, s>>>(c, lt, a, ly); break;
+        case 3: k_ks_ip<3><<<g2, 256, 0, s>>>(c, lt, a, ly); break;
+        case 4: k_ks_ip<4><<<g2, 256, 0, s>>>(c, lt, a, ly); break;
+        case 5: k_ks_ip<5><<<g2, 256, 0, s>>>(c, lt, a, ly); break;
+        case 6: k_ks_ip<6><<<g2, 256, 0, s>>>(c, lt, a, ly); break;
+        case 7: k_ks_ip<7><<<g2, 256, 0, s>>>(c, lt, a, ly); break;
+        default: return cudaErrorInvalidValue;
+        }
     }
     KS_EV(4);
     if (phases & KS_MODDOWN) DISPATCH_LOGR(c.logR2, k_ks_md_intt_row, dim3(tc, B * 2 * c.alpha), c, lt, a, ly);
