@@ -141,23 +141,9 @@ def ks_modmuls(level, alpha, logn):
 
 def program_ledger(prog, alpha):
     """key switches of one image and their weighted count (in top-level units)"""
-    n_ks, w = 0, 0.0
-    for st in prog.steps:
-        t_in = prog.tensors[st["src"]]
-        lv = t_in.level
-        if st["kind"] == 1:
-            babies = {(i, b) for i, b in zip(st["t_ct"], st["t_baby"]) if b}
-            giants = {(o, g) for o, g in zip(st["t_out"], st["t_giant"]) if g}
-            k = len(babies) + len(giants)
-        elif st["kind"] == 3:
-            k = t_in.layout.n_ct
-        elif st["kind"] == 4:
-            k = t_in.layout.n_ct * len(st["steps"])
-        else:
-            k = 0
-        n_ks += k
-        w += k * ks_weight(lv, alpha)
-    return n_ks, w
+    from paper_2509_22857_gb300 import model as M
+    census = M.keyswitch_census(prog)
+    return sum(census.values()), sum(k * ks_weight(lv, alpha) for lv, k in census.items())
 
 
 def plaintext_bytes(prog, N):
@@ -633,6 +619,34 @@ def run_ks_only(args):
     F.fhe_ctx_destroy(ctx)
 
 
+def run_autotune(args):
+    """Rank the admissible digit widths (dnum) for the ResNet-20 parameters by
+    measured key-switch time, weighted by how many key switches one image
+    performs at each level; print the table as one JSON line."""
+    from paper_2509_22857_gb300 import _lib as F
+    from paper_2509_22857_gb300 import autotune as A
+    from paper_2509_22857_gb300 import model as M
+    pre = dict(synth.PRESETS[PRESET])
+    ctx = F.fhe_ctx_create(pre["logn"], pre["L"], pre["q_bits"], pre["q0_bits"], pre["p_bits"], pre["alpha"],
+                           pre["log_scale"], 0)
+    primes = F.fhe_ctx_primes(ctx)[: pre["L"] + 1]
+    F.fhe_ctx_destroy(ctx)
+    net = synth.ARCHS[PRESET]()
+    prog = M.compile_network(net, synth.params(net), primes, pre["logn"], pre["log_scale"], "packed",
+                             pre["alpha"], input_lambda=synth.INPUT_LAMBDA[PRESET])
+    levels = A.keyswitch_levels(prog)
+    tuner = A.Tuner(args.autotune_cache)
+    t0 = time.time()
+    rec = A.tune_digit_width(tuner, pre["logn"], pre["L"], pre["q_bits"], pre["q0_bits"], pre["p_bits"],
+                             pre["log_scale"], candidates=range(1, 9), levels=levels, items=4, iters=5)
+    top = {a: v[str(pre["L"])] for a, v in rec["us"].items()}
+    print(json.dumps({"autotune": "digit_width", "preset": PRESET, "preset_alpha": pre["alpha"],
+                      "device": A.device_name(), "keyswitch_levels": levels, "best": rec["best"],
+                      "cost_us_per_img": rec["cost_us"], "top_level_us": top,
+                      "top_level_best": int(min(top, key=lambda a: top[a])), "tune_s": round(time.time() - t0, 1)}),
+          flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -651,7 +665,13 @@ def main():
                     help="run one uniform batch inside the NVTX range bench_timed and exit (for ncu launch lists)")
     ap.add_argument("--requests", type=int, default=1000, help="serving: number of requests")
     ap.add_argument("--rate", type=float, default=20.0, help="serving: mean arrivals per second")
+    ap.add_argument("--autotune", action="store_true",
+                    help="rank the admissible digit widths by measured, census-weighted key-switch time and exit")
+    ap.add_argument("--autotune-cache", default=None, help="--autotune: JSON cache file of the tuner")
     args = ap.parse_args()
+    if args.autotune:
+        run_autotune(args)
+        return
     if args.ks_only:
         run_ks_only(args)
         return

@@ -1,0 +1,187 @@
+"""Autotuner for the launch parameters the kernels leave open.
+
+Two knobs are measured on the device through the C ABI rather than fixed by
+hand, and the results are cached per device name and parameter set:
+
+* **Digit width** alpha of hybrid key switching: alpha special primes, and
+  dnum = ceil((l+1)/alpha) digits at level l.  The width changes the key's
+  shape and so the ciphertexts' bits: it is a parameter of the scheme, not a
+  free launch choice.  The tuner therefore only ranks the *admissible* widths
+  by measured key-switch time, weighted over the levels a network switches
+  at.  The chosen width goes into the parameter preset, and the parity
+  checks compute both sides with that same width.  A width is admissible when
+  the special modulus P (alpha primes of p_bits) is at least every digit's
+  modulus, so that the key-switching noise, about digit * e / P per digit
+  (Sec. 2.2, hybrid key switching with a special modulus), stays at the
+  level of a fresh encryption error; and when the key has at most 7 digits
+  (the inner product's 128-bit accumulator bound).
+* **Linear-step chunk size** (MAC sources per pass, `fhe_ctx_set_linear_chunk`):
+  bit-neutral.  The tuner checks that every candidate gives identical
+  ciphertexts and keeps the fastest.
+
+The NTT split (two passes of 2^ceil(logN/2) x 2^floor(logN/2)) and one limb
+per CTA row are compile-time choices of the kernels' templates and are not
+tuned here.
+"""
+from __future__ import annotations
+
+import json
+import os
+import time
+from dataclasses import dataclass, field
+from typing import Callable, Dict, Iterable, List, Optional, Sequence, Tuple
+
+MAX_DIGITS = 7
+
+
+def digit_bits(L: int, q_bits: int, q0_bits: int, alpha: int) -> List[int]:
+    """Bit size of each digit's modulus at the top level: digit j holds
+    primes q_{j alpha} .. q_{(j+1) alpha - 1} of q_0 (q0_bits), q_1..q_L (q_bits)."""
+    sizes = [q0_bits] + [q_bits] * L
+    return [sum(sizes[j:j + alpha]) for j in range(0, L + 1, alpha)]
+
+
+def admissible(L: int, q_bits: int, q0_bits: int, p_bits: int, alpha: int) -> bool:
+    """P = alpha primes of p_bits covers every digit, and at most 7 digits."""
+    if alpha < 1:
+        return False
+    d = digit_bits(L, q_bits, q0_bits, alpha)
+    return len(d) <= MAX_DIGITS and alpha * p_bits >= max(d)
+
+
+def admissible_widths(L: int, q_bits: int, q0_bits: int, p_bits: int,
+                      candidates: Iterable[int] = range(1, 9)) -> List[int]:
+    return [a for a in candidates if admissible(L, q_bits, q0_bits, p_bits, a)]
+
+
+def device_name() -> str:
+    import torch
+    return torch.cuda.get_device_name(torch.cuda.current_device())
+
+
+@dataclass
+class Tuner:
+    """Result cache: key -> record, optionally persisted as JSON at `path`."""
+    path: Optional[str] = None
+    records: Dict[str, dict] = field(default_factory=dict)
+
+    def __post_init__(self):
+        if self.path and os.path.exists(self.path):
+            with open(self.path) as f:
+                self.records = json.load(f)
+
+    def lookup(self, key: str) -> Optional[dict]:
+        return self.records.get(key)
+
+    def record(self, key: str, rec: dict) -> dict:
+        self.records[key] = rec
+        if self.path:
+            d = os.path.dirname(os.path.abspath(self.path))
+            os.makedirs(d, exist_ok=True)
+            tmp = self.path + ".tmp"
+            with open(tmp, "w") as f:
+                json.dump(self.records, f, indent=1, sort_keys=True)
+            os.replace(tmp, self.path)
+        return rec
+
+
+def _key(op: str, device: str, **kw) -> str:
+    return "|".join([op, device] + ["%s=%s" % (k, kw[k]) for k in sorted(kw)])
+
+
+def tune_digit_width(tuner: Tuner, logn: int, L: int, q_bits: int, q0_bits: int, p_bits: int,
+                     log_scale: float, candidates: Iterable[int] = range(1, 9),
+                     levels: Optional[Sequence[Tuple[int, float]]] = None, items: int = 4, iters: int = 5,
+                     F=None, device: Optional[str] = None, seed: int = 11) -> dict:
+    """Rank the admissible digit widths by measured key-switch time.
+
+    levels: (level, weight) pairs, e.g. the number of key switches a network
+    performs at each level; default: the top level alone.  The cost of a
+    width is sum(weight * microseconds per switched polynomial at level).
+    Returns {"best": alpha, "cost_us": {alpha: cost}, "us": {alpha: {level: us}}}.
+    """
+    if F is None:
+        from . import _lib as F
+    dev = device if device is not None else device_name()
+    levels = list(levels) if levels else [(L, 1.0)]
+    widths = admissible_widths(L, q_bits, q0_bits, p_bits, candidates)
+    if not widths:
+        raise ValueError("no admissible digit width among the candidates")
+    key = _key("digit_width", dev, logn=logn, L=L, q=q_bits, q0=q0_bits, p=p_bits, items=items,
+               levels=",".join("%d:%g" % lw for lw in levels), widths=",".join(map(str, widths)))
+    hit = tuner.lookup(key)
+    if hit is not None:
+        return hit
+    us: Dict[int, Dict[int, float]] = {}
+    for a in widths:
+        ctx = F.fhe_ctx_create(logn, L, q_bits, q0_bits, p_bits, a, log_scale)
+        try:
+            sk, evk = F.fhe_keygen(ctx, seed, [])
+            try:
+                us[a] = {}
+                for lv, _ in levels:
+                    ms = F.fhe_profile_keyswitch(ctx, evk, lv, items, iters)
+                    us[a][lv] = sum(ms) / items * 1e3
+            finally:
+                F.fhe_evk_free(evk)
+                F.fhe_sk_free(sk)
+        finally:
+            F.fhe_ctx_destroy(ctx)
+    cost = {a: sum(w * us[a][lv] for lv, w in levels) for a in widths}
+    best = min(widths, key=lambda a: (cost[a], a))
+    rec = {"best": best, "cost_us": {str(a): round(c, 3) for a, c in cost.items()},
+           "us": {str(a): {str(lv): round(t, 3) for lv, t in v.items()} for a, v in us.items()}}
+    return tuner.record(key, rec)
+
+
+def keyswitch_levels(prog) -> List[Tuple[int, float]]:
+    """(level, number of key switches of one image) of a compiled network
+    program, top level first: the weights for tune_digit_width."""
+    from . import model as M
+    return sorted(((lv, float(k)) for lv, k in M.keyswitch_census(prog).items()), reverse=True)
+
+
+def tune_linear_chunk(tuner: Tuner, ctx, model, evk, cts, n_img: int, n_out: int, N: int,
+                      candidates: Sequence[int] = (40, 80, 160, 320), reps: int = 2, F=None,
+                      device: Optional[str] = None, model_key: str = "", sync: Optional[Callable] = None) -> dict:
+    """Time fhe_infer with each chunk size (MAC sources per pass), check that
+    all candidates give identical ciphertexts, leave the fastest set in ctx.
+    Returns {"best": c, "ms": {c: ms}}."""
+    if F is None:
+        from . import _lib as F
+    if sync is None:
+        import torch
+        sync = torch.cuda.synchronize
+    dev = device if device is not None else device_name()
+    key = _key("linear_chunk", dev, model=model_key, n_img=n_img, cands=",".join(map(str, candidates)))
+    hit = tuner.lookup(key)
+    if hit is not None:
+        F.fhe_ctx_set_linear_chunk(ctx, hit["best"])
+        return hit
+    ref = None
+    ms: Dict[int, float] = {}
+    for c in candidates:
+        F.fhe_ctx_set_linear_chunk(ctx, c)
+        best_t = None
+        for r in range(reps + 1):          # first run warms up
+            sync()
+            t0 = time.perf_counter()
+            outs = F.fhe_infer(ctx, model, evk, cts, n_img, n_out)
+            sync()
+            t = (time.perf_counter() - t0) * 1e3
+            if r == 0:
+                got = [F.fhe_ct_export(h, N)[0] for h in outs]
+                if ref is None:
+                    ref = got
+                elif not all((a == b).all() for a, b in zip(ref, got)):
+                    for h in outs:
+                        F.fhe_ct_free(h)
+                    raise RuntimeError("chunk size %d changed the output ciphertexts" % c)
+            else:
+                best_t = t if best_t is None else min(best_t, t)
+            for h in outs:
+                F.fhe_ct_free(h)
+        ms[c] = best_t
+    best = min(candidates, key=lambda c: (ms[c], c))
+    F.fhe_ctx_set_linear_chunk(ctx, best)
+    return tuner.record(key, {"best": best, "ms": {str(c): round(t, 3) for c, t in ms.items()}})

@@ -607,6 +607,35 @@ def giant_steps(prog: Program) -> List[int]:
     return [st["giant"] for st in prog.steps if st["kind"] == F.STEP_LINEAR]
 
 
+def keyswitches_of_step(prog: Program, st: dict) -> int:
+    """Hybrid key switches one image's step performs, all at the level of its
+    source: the distinct baby rotations (input ciphertext, step) and giant
+    rotations (output, step) of a linear step, one relinearisation per
+    ciphertext of an activation, one rotation per ciphertext and step of a
+    rotate-and-sum."""
+    t_in = prog.tensors[st["src"]]
+    if st["kind"] == F.STEP_LINEAR:
+        babies = {(i, b) for i, b in zip(st["t_ct"], st["t_baby"]) if b}
+        giants = {(o, g) for o, g in zip(st["t_out"], st["t_giant"]) if g}
+        return len(babies) + len(giants)
+    if st["kind"] == F.STEP_ACT:
+        return t_in.layout.n_ct
+    if st["kind"] == F.STEP_ROTSUM:
+        return t_in.layout.n_ct * len(st["steps"])
+    return 0
+
+
+def keyswitch_census(prog: Program) -> Dict[int, int]:
+    """level -> number of hybrid key switches one image performs there"""
+    out: Dict[int, int] = {}
+    for st in prog.steps:
+        k = keyswitches_of_step(prog, st)
+        if k:
+            lv = prog.tensors[st["src"]].level
+            out[lv] = out.get(lv, 0) + k
+    return out
+
+
 # =========================================================== to the C ABI
 
 class ModelDesc:
