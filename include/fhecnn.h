@@ -100,6 +100,12 @@ int fhe_ctx_primes(const fhe_ctx *ctx, uint64_t *out, size_t cap, size_t *n);
  * HW-layout layer are made and consumed a chunk at a time.  Returns
  * FHE_E_INVAL for a value below 2. */
 int fhe_ctx_set_linear_chunk(fhe_ctx *ctx, int lin_chunk_srcs);
+/* Host-side fault injection (no counterpart in the paper): after `after`
+ * further device allocations through the context succeed, the next one is
+ * refused with FHE_E_OOM, as cudaMalloc's own refusal would be, and the
+ * injection turns itself off.  after < 0 turns it off at once.  The failing
+ * call frees what it allocated and leaves the context usable. */
+int fhe_ctx_inject_alloc_failure(fhe_ctx *ctx, int after);
 
 /* ---------------------------------------------------------------- client */
 
@@ -166,7 +172,9 @@ int fhe_square(fhe_ctx *ctx, const fhe_evk *evk, const fhe_ct *in, fhe_ct **out,
  * rounding, drop one level, scale /= q_level.  In place on the handle.
  * FHE_E_LEVEL at level 0. */
 int fhe_rescale(fhe_ctx *ctx, fhe_ct *ct, void *stream);
-/* out = a + b (same level; the result carries a's scale). */
+/* out = a + b.  Both operands must have the same level and the same scale
+ * (relative difference at most 1e-9), else FHE_E_LEVEL (Sec. 4.3: addends
+ * are brought to one level and scale before they are added). */
 int fhe_add(fhe_ctx *ctx, const fhe_ct *a, const fhe_ct *b, fhe_ct **out, void *stream);
 /* out = a * pt (slot-wise), scale multiplies. */
 int fhe_mul_plain(fhe_ctx *ctx, const fhe_ct *a, const fhe_pt *pt, fhe_ct **out, void *stream);
@@ -313,16 +321,22 @@ int fhe_pipeline_free(fhe_pipeline *pipe);
  * fhe_server_submit takes ownership of the model's n_in_ct input ciphertexts
  * of one image (they are freed once admitted) and returns a ticket.
  * fhe_server_poll returns the request's n_out_ct output ciphertexts (new
- * handles owned by the caller) once done (*n_out = 0 before; wait != 0
- * blocks until done) and its latency from submit to completion.
+ * handles owned by the caller) once done, and its latency from submit to
+ * completion; *n_out = 0 while it is not done.  timeout_ms = 0 returns at
+ * once, < 0 waits until done, > 0 waits at most that long and then returns
+ * FHE_E_TIMEOUT (the request stays queued and can be polled again).
+ * fhe_server_pause(server, 1) stops every worker before its next tick (a
+ * stalled host worker: queued and in-flight requests wait, nothing is lost);
+ * fhe_server_pause(server, 0) resumes them where they stopped.
  * fhe_server_stats: completed requests and the p50 / p99 of their latency.
  */
 int fhe_server_create(fhe_ctx *ctx, const fhe_evk *evk, fhe_server **out);
 int fhe_server_add_model(fhe_server *server, const fhe_model *model, int group, size_t reserve_bytes,
                          int *model_id);
 int fhe_server_submit(fhe_server *server, int model_id, fhe_ct *const *in, uint64_t *ticket);
-int fhe_server_poll(fhe_server *server, uint64_t ticket, int wait, fhe_ct **out, size_t cap, size_t *n_out,
+int fhe_server_poll(fhe_server *server, uint64_t ticket, int timeout_ms, fhe_ct **out, size_t cap, size_t *n_out,
                     double *latency_ms);
+int fhe_server_pause(fhe_server *server, int paused);
 int fhe_server_stats(fhe_server *server, uint64_t *completed, double *p50_ms, double *p99_ms);
 int fhe_server_destroy(fhe_server *server);
 

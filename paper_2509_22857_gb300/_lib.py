@@ -51,6 +51,10 @@ STEP_LINEAR, STEP_RESCALE, STEP_ACT, STEP_ROTSUM, STEP_CMUL, STEP_DROP, STEP_ADD
 _lib = None
 
 
+# error codes of include/fhecnn.h
+FHE_OK, FHE_E_INVAL, FHE_E_LEVEL, FHE_E_NOKEY, FHE_E_OOM, FHE_E_CUDA, FHE_E_TIMEOUT = 0, -1, -2, -3, -4, -5, -6
+
+
 class FheError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__("libfhecnn error %d: %s" % (code, msg))
@@ -71,6 +75,7 @@ def lib() -> ctypes.CDLL:
             "fhe_ctx_create": (c_int, [ctypes.POINTER(FheParams), PP]),
             "fhe_ctx_destroy": (c_int, [V]),
             "fhe_ctx_set_linear_chunk": (c_int, [V, c_int]),
+            "fhe_ctx_inject_alloc_failure": (c_int, [V, c_int]),
             "fhe_ctx_primes": (c_int, [V, P_U64, c_size, ctypes.POINTER(c_size)]),
             "fhe_keygen": (c_int, [V, c_u64, P_I32, c_size, PP, PP]),
             "fhe_sk_free": (c_int, [V]),
@@ -109,6 +114,7 @@ def lib() -> ctypes.CDLL:
             "fhe_server_submit": (c_int, [V, c_int, PP, ctypes.POINTER(c_u64)]),
             "fhe_server_poll": (c_int, [V, c_u64, c_int, PP, c_size, ctypes.POINTER(c_size), P_DBL]),
             "fhe_server_stats": (c_int, [V, ctypes.POINTER(c_u64), P_DBL, P_DBL]),
+            "fhe_server_pause": (c_int, [V, c_int]),
             "fhe_server_destroy": (c_int, [V]),
             "fhe_ntt_device": (c_int, [V, V, c_size, P_I32, c_int, V]),
             "fhe_evk_export": (c_int, [V, c_int, P_U64, c_size, ctypes.POINTER(c_size)]),
@@ -161,6 +167,10 @@ def fhe_ctx_destroy(ctx):
 
 def fhe_ctx_set_linear_chunk(ctx, lin_chunk_srcs: int):
     _check(lib().fhe_ctx_set_linear_chunk(ctx, int(lin_chunk_srcs)))
+
+
+def fhe_ctx_inject_alloc_failure(ctx, after: int):
+    _check(lib().fhe_ctx_inject_alloc_failure(ctx, int(after)))
 
 
 def fhe_ctx_primes(ctx) -> List[int]:
@@ -396,12 +406,19 @@ def fhe_server_submit(server, model_id: int, cts) -> int:
     return t.value
 
 
-def fhe_server_poll(server, ticket: int, wait: bool, cap: int) -> Tuple[List[int], float]:
-    """returns (output handles, latency ms); no handles while pending"""
+def fhe_server_poll(server, ticket: int, wait, cap: int) -> Tuple[List[int], float]:
+    """returns (output handles, latency ms); no handles while pending.
+    wait: True (until done), False (not at all) or a timeout in milliseconds,
+    after which FheError with code FHE_E_TIMEOUT is raised."""
+    timeout_ms = -1 if wait is True else 0 if wait is False else int(wait)
     out = (c_void * max(cap, 1))()
     n, lat = c_size(), c_double()
-    _check(lib().fhe_server_poll(server, ticket, int(wait), out, cap, ctypes.byref(n), ctypes.byref(lat)))
+    _check(lib().fhe_server_poll(server, ticket, timeout_ms, out, cap, ctypes.byref(n), ctypes.byref(lat)))
     return [out[i] for i in range(n.value)], lat.value
+
+
+def fhe_server_pause(server, paused: bool):
+    _check(lib().fhe_server_pause(server, int(bool(paused))))
 
 
 def fhe_server_stats(server) -> Tuple[int, float, float]:
@@ -442,7 +459,7 @@ def fhe_sk_export(sk, n_words: int) -> np.ndarray:
 
 
 EXPORTED = ["fhe_last_error", "fhe_kernel_launches", "fhe_ctx_create", "fhe_ctx_destroy", "fhe_ctx_primes",
-            "fhe_ctx_set_linear_chunk", "fhe_keygen",
+            "fhe_ctx_set_linear_chunk", "fhe_ctx_inject_alloc_failure", "fhe_keygen",
             "fhe_sk_free", "fhe_evk_free", "fhe_evk_galois", "fhe_encode", "fhe_pt_free", "fhe_encrypt",
             "fhe_decrypt", "fhe_decode", "fhe_ct_free", "fhe_ct_info", "fhe_ct_export", "fhe_ct_import",
             "fhe_rotate", "fhe_square", "fhe_rescale", "fhe_add", "fhe_mul_plain", "fhe_model_load",
@@ -450,4 +467,4 @@ EXPORTED = ["fhe_last_error", "fhe_kernel_launches", "fhe_ctx_create", "fhe_ctx_
             "fhe_ntt_device", "fhe_evk_export", "fhe_sk_export", "fhe_encode_coeffs",
             "fhe_profile_keyswitch", "fhe_rescale_noalloc", "fhe_infer_profiled", "fhe_pipeline_create", "fhe_pipeline_info",
             "fhe_pipeline_tick", "fhe_pipeline_free", "fhe_server_create", "fhe_server_add_model",
-            "fhe_server_submit", "fhe_server_poll", "fhe_server_stats", "fhe_server_destroy"]
+            "fhe_server_submit", "fhe_server_poll", "fhe_server_pause", "fhe_server_stats", "fhe_server_destroy"]

@@ -214,8 +214,9 @@ void Encoder::decode(const double *m, double scale, double *re, double *im, size
 // ================================================================ memory
 
 int dev_alloc(fhe_ctx *ctx, void **p, size_t bytes) {
-    (void)ctx;
     *p = nullptr;
+    if (ctx && ctx->fail_alloc_after.load() >= 0 && ctx->fail_alloc_after.fetch_sub(1) == 0)
+        return fhe_fail(FHE_E_OOM, "device allocation refused (injected failure)");
     if (bytes == 0) bytes = 8;
     cudaError_t e = cudaMalloc(p, bytes);
     if (e != cudaSuccess) {
@@ -466,6 +467,12 @@ extern "C" int fhe_ctx_destroy(fhe_ctx *ctx) {
     return FHE_OK;
 }
 
+extern "C" int fhe_ctx_inject_alloc_failure(fhe_ctx *ctx, int after) {
+    if (!ctx) return fhe_fail(FHE_E_INVAL, "null argument");
+    ctx->fail_alloc_after.store(after < 0 ? -1 : after);
+    return FHE_OK;
+}
+
 extern "C" int fhe_ctx_set_linear_chunk(fhe_ctx *ctx, int lin_chunk_srcs) {
     if (!ctx || lin_chunk_srcs < 2) return fhe_fail(FHE_E_INVAL, "linear chunk must be at least 2 sources");
     ctx->lin_chunk_srcs = lin_chunk_srcs;
@@ -708,7 +715,10 @@ extern "C" int fhe_encrypt(fhe_ctx *c, const fhe_sk *sk, const fhe_pt *pt, uint6
     FHE_TRY(dev_alloc(c, (void **)&ct->d, (size_t)2 * nl * N * 8));
     u64 *c0 = ct->d, *c1 = ct->d + (size_t)nl * N;
     long long *e;
-    FHE_TRY(dev_alloc(c, (void **)&e, N * 8));
+    if (dev_alloc(c, (void **)&e, N * 8) != FHE_OK) {
+        dev_free(ct->d);
+        return FHE_E_OOM;
+    }
     FHE_CU(launch_sample_uniform(c->dc, seed, DOM_ENC_A, 0, 0, 1, c1, nl, pidx.data(), 0));
     FHE_CU(launch_sample_small(c->dc, seed, DOM_ENC_E, 0, 0, 1, e, 0));
     FHE_CU(launch_signed_to_limbs(c->dc, e, c0, nl, pidx.data(), 0));
@@ -971,6 +981,8 @@ extern "C" int fhe_rescale(fhe_ctx *c, fhe_ct *ct, void *stream) {
 extern "C" int fhe_add(fhe_ctx *c, const fhe_ct *a, const fhe_ct *b, fhe_ct **out, void *stream) {
     if (!c || !a || !b || !out) return fhe_fail(FHE_E_INVAL, "null argument");
     if (a->level != b->level || a->n_poly != b->n_poly) return fhe_fail(FHE_E_LEVEL, "operands differ in level");
+    if (std::fabs(a->scale - b->scale) > 1e-9 * std::fmax(std::fabs(a->scale), std::fabs(b->scale)))
+        return fhe_fail(FHE_E_LEVEL, "operands differ in scale");
     FHE_CU(cudaSetDevice(c->dev));
     fhe_ct *o;
     FHE_TRY(new_ct(c, a->level, a->n_poly, a->scale, &o));

@@ -1,6 +1,7 @@
 // Host-side internals shared by the library's translation units.
 #pragma once
 #include <cstdint>
+#include <atomic>
 #include <map>
 #include <string>
 #include <vector>
@@ -71,6 +72,7 @@ struct fhe_ctx {
     size_t rs_ws_words = 0;
     int dev = 0;
     int lin_chunk_srcs = 160;         // MAC sources per chunk of a linear step
+    std::atomic<int> fail_alloc_after{-1};   // injected failure: allocations left before one is refused
 };
 
 struct fhe_ct {

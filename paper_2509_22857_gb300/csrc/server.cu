@@ -55,6 +55,7 @@ struct fhe_server {
     std::mutex mu;
     std::condition_variable cv;
     bool stop = false;
+    bool paused = false;      // workers run no tick while set (a stalled host worker)
     uint64_t next_ticket = 1;
     std::vector<std::unique_ptr<ModelSlot>> models;
     std::unordered_map<uint64_t, Result> results;
@@ -70,7 +71,9 @@ static void worker_loop(fhe_server *sv, ModelSlot *ms) {
         std::vector<Request> admit;
         {
             std::unique_lock<std::mutex> lk(sv->mu);
-            sv->cv.wait(lk, [&] { return sv->stop || !ms->queue.empty() || !ms->in_flight.empty(); });
+            sv->cv.wait(lk, [&] {
+                return sv->stop || (!sv->paused && (!ms->queue.empty() || !ms->in_flight.empty()));
+            });
             if (sv->stop) return;
             while (!ms->queue.empty() && (int)admit.size() < ms->group) {
                 admit.push_back(std::move(ms->queue.front()));
@@ -169,15 +172,32 @@ extern "C" int fhe_server_submit(fhe_server *sv, int model_id, fhe_ct *const *in
     return FHE_OK;
 }
 
-extern "C" int fhe_server_poll(fhe_server *sv, uint64_t ticket, int wait, fhe_ct **out, size_t cap, size_t *n_out,
-                               double *latency_ms) {
+extern "C" int fhe_server_pause(fhe_server *sv, int paused) {
+    if (!sv) return fhe_fail(FHE_E_INVAL, "null argument");
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->paused = paused != 0;
+    }
+    sv->cv.notify_all();
+    return FHE_OK;
+}
+
+extern "C" int fhe_server_poll(fhe_server *sv, uint64_t ticket, int timeout_ms, fhe_ct **out, size_t cap,
+                               size_t *n_out, double *latency_ms) {
     if (!sv || !n_out) return fhe_fail(FHE_E_INVAL, "null argument");
+    *n_out = 0;
     std::unique_lock<std::mutex> lk(sv->mu);
     auto it = sv->results.find(ticket);
     if (it == sv->results.end()) return fhe_fail(FHE_E_INVAL, "unknown ticket");
-    if (wait) sv->cv.wait(lk, [&] { return sv->results[ticket].done; });
+    // the entry stays in the map until it is returned, so the reference is stable under the lock
+    const auto done = [&] { return sv->results[ticket].done; };
+    if (timeout_ms < 0) {
+        sv->cv.wait(lk, done);
+    } else if (timeout_ms > 0 && !sv->cv.wait_for(lk, std::chrono::milliseconds(timeout_ms), done)) {
+        return fhe_fail(FHE_E_TIMEOUT, "request " + std::to_string(ticket) + " not done within " +
+                                           std::to_string(timeout_ms) + " ms");
+    }
     Result &r = sv->results[ticket];
-    *n_out = 0;
     if (!r.done) return FHE_OK;
     if (r.error != FHE_OK) {
         const int e = r.error;

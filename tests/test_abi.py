@@ -48,3 +48,13 @@ def test_product_never_imports_the_oracle():
             if f.endswith((".py", ".cu", ".h", ".cuh", ".cpp")):
                 text = open(os.path.join(dirpath, f)).read()
                 assert "oracle" not in re.sub(r"#.*|//.*", "", text).lower(), f
+
+
+def test_binding_error_codes_match_the_header():
+    from paper_2509_22857_gb300 import _lib
+    src = open(os.path.join(ROOT, "include", "fhecnn.h")).read()
+    codes = {m.group(1): int(m.group(2)) for m in re.finditer(r"#define\s+(FHE_(?:OK|E_[A-Z]+))\s+(-?\d+)", src)}
+    assert set(codes) == {"FHE_OK", "FHE_E_INVAL", "FHE_E_LEVEL", "FHE_E_NOKEY", "FHE_E_OOM", "FHE_E_CUDA",
+                          "FHE_E_TIMEOUT"}
+    for name, v in codes.items():
+        assert getattr(_lib, name) == v, name

@@ -206,3 +206,49 @@ def test_import_export_roundtrip(pair):
     bad[0, 1, 5] = prm.primes[1]
     with pytest.raises(F.FheError):
         F.fhe_ct_import(ctx, bad, 2, 1.0)
+
+
+def test_add_rejects_a_scale_mismatch(pair):
+    F, ctx, prm, S, keys, sk, evk = pair
+    z = np.random.default_rng(8).uniform(-1, 1, prm.N // 2)
+    pa = F.fhe_encode(ctx, z, prm.scale, 2)
+    pb = F.fhe_encode(ctx, z, 2 * prm.scale, 2)
+    a, b = F.fhe_encrypt(ctx, sk, pa, 61), F.fhe_encrypt(ctx, sk, pb, 62)
+    with pytest.raises(F.FheError) as e:
+        F.fhe_add(ctx, a, b)
+    assert e.value.code == F.FHE_E_LEVEL
+    for h in (a, b):
+        F.fhe_ct_free(h)
+    for h in (pa, pb):
+        F.fhe_pt_free(h)
+
+
+def test_injected_allocation_failure_leaves_the_context_usable(pair):
+    """A refused device allocation (host-side injection) fails the call with
+    FHE_E_OOM; the same calls afterwards give the same bits as before."""
+    F, ctx, prm, S, keys, sk, evk = pair
+    z = np.random.default_rng(9).uniform(-1, 1, prm.N // 2)
+    pt = F.fhe_encode(ctx, z, prm.scale, prm.L)
+    ct = F.fhe_encrypt(ctx, sk, pt, 70)
+    rot = F.fhe_rotate(ctx, evk, ct, 1)
+    want_ct, want_rot = F.fhe_ct_export(ct, prm.N)[0], F.fhe_ct_export(rot, prm.N)[0]
+    for after in (0, 1):            # the ciphertext buffer, then the error polynomial
+        F.fhe_ctx_inject_alloc_failure(ctx, after)
+        with pytest.raises(F.FheError) as e:
+            F.fhe_encrypt(ctx, sk, pt, 70)
+        assert e.value.code == F.FHE_E_OOM and "injected" in str(e.value)
+    F.fhe_ctx_inject_alloc_failure(ctx, 0)
+    with pytest.raises(F.FheError) as e:
+        F.fhe_rotate(ctx, evk, ct, 1)
+    assert e.value.code == F.FHE_E_OOM
+    # the injection turned itself off
+    ct2 = F.fhe_encrypt(ctx, sk, pt, 70)
+    rot2 = F.fhe_rotate(ctx, evk, ct2, 1)
+    assert np.array_equal(F.fhe_ct_export(ct2, prm.N)[0], want_ct)
+    assert np.array_equal(F.fhe_ct_export(rot2, prm.N)[0], want_rot)
+    F.fhe_ctx_inject_alloc_failure(ctx, 5)
+    F.fhe_ctx_inject_alloc_failure(ctx, -1)   # armed, then off: nothing is refused
+    rot3 = F.fhe_rotate(ctx, evk, ct2, 1)
+    for h in (ct, rot, ct2, rot2, rot3):
+        F.fhe_ct_free(h)
+    F.fhe_pt_free(pt)
