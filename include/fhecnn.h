@@ -129,6 +129,21 @@ int fhe_sk_free(fhe_sk *sk);
 int fhe_evk_free(fhe_evk *evk);
 /* Galois elements present in the key set (test hook): out[cap], *n = count. */
 int fhe_evk_galois(const fhe_evk *evk, int32_t *out, size_t cap, size_t *n);
+/* Key transport between client and server (Sec. 2.2: the server holds only
+ * the public evaluation keys).  Layouts are those of fhe_sk_export and
+ * fhe_evk_export: NTT domain, limb t reduced mod prime t (q_0..q_L, then
+ * p_0..p_{alpha-1}).
+ * fhe_sk_import: (L+1+alpha)*N words.
+ * fhe_evk_import: n_keys host buffers of words_per_key =
+ * dnum*2*(L+1+alpha)*N words each (dnum = ceil((L+1)/alpha)), keys[i] the
+ * key of Galois element galois[i], galois 0 = the relinearisation key
+ * (exactly one).  Galois elements are odd, in [3, 2N), and distinct.
+ * Buffers are caller-owned and read during the call only.  FHE_E_INVAL for
+ * a wrong size, element or count, or a residue not below its prime; nothing
+ * is allocated then. */
+int fhe_sk_import(fhe_ctx *ctx, const uint64_t *buf, size_t n_words, fhe_sk **out);
+int fhe_evk_import(fhe_ctx *ctx, const int32_t *galois, size_t n_keys, const uint64_t *const *keys,
+                   size_t words_per_key, fhe_evk **out);
 
 /*
  * Encoding (Sec. 2.2): n <= N/2 complex slots (re[i], im[i]; im may be NULL

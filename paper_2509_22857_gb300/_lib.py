@@ -119,6 +119,8 @@ def lib() -> ctypes.CDLL:
             "fhe_ntt_device": (c_int, [V, V, c_size, P_I32, c_int, V]),
             "fhe_evk_export": (c_int, [V, c_int, P_U64, c_size, ctypes.POINTER(c_size)]),
             "fhe_sk_export": (c_int, [V, P_U64, c_size]),
+            "fhe_sk_import": (c_int, [V, P_U64, c_size, PP]),
+            "fhe_evk_import": (c_int, [V, P_I32, c_size, ctypes.POINTER(P_U64), c_size, PP]),
             "fhe_profile_keyswitch": (c_int, [V, V, c_int, c_int, c_int, ctypes.POINTER(ctypes.c_float), V]),
             "fhe_encode_coeffs": (c_int, [V, P_DBL, P_DBL, c_size, c_double, P_DBL]),
         }
@@ -204,6 +206,29 @@ def fhe_evk_galois(evk) -> List[int]:
     out = np.zeros(max(n.value, 1), dtype=np.int32)
     _check(lib().fhe_evk_galois(evk, _ptr(out, P_I32), n.value, ctypes.byref(n)))
     return [int(x) for x in out[: n.value]]
+
+
+def fhe_sk_import(ctx, words: np.ndarray) -> int:
+    """secret key from the words of fhe_sk_export"""
+    w = np.ascontiguousarray(words, dtype=np.uint64)
+    h = c_void()
+    _check(lib().fhe_sk_import(ctx, _ptr(w, P_U64), w.size, ctypes.byref(h)))
+    return h.value
+
+
+def fhe_evk_import(ctx, keys) -> int:
+    """evaluation key set from {galois element: words of fhe_evk_export}
+    (element 0: the relinearisation key)"""
+    items = sorted(keys.items())
+    arrs = [np.ascontiguousarray(v, dtype=np.uint64) for _, v in items]
+    words = arrs[0].size if arrs else 0
+    if any(a.size != words for a in arrs):
+        raise ValueError("keys of different sizes")
+    gal = np.ascontiguousarray([g for g, _ in items] or [0], dtype=np.int32)
+    ptrs = (P_U64 * max(len(arrs), 1))(*[_ptr(a, P_U64) for a in arrs])
+    h = c_void()
+    _check(lib().fhe_evk_import(ctx, _ptr(gal, P_I32), len(arrs), ptrs, words, ctypes.byref(h)))
+    return h.value
 
 
 def fhe_encode(ctx, z, scale: float, level: int) -> int:
@@ -467,4 +492,4 @@ EXPORTED = ["fhe_last_error", "fhe_kernel_launches", "fhe_ctx_create", "fhe_ctx_
             "fhe_ntt_device", "fhe_evk_export", "fhe_sk_export", "fhe_encode_coeffs",
             "fhe_profile_keyswitch", "fhe_rescale_noalloc", "fhe_infer_profiled", "fhe_pipeline_create", "fhe_pipeline_info",
             "fhe_pipeline_tick", "fhe_pipeline_free", "fhe_server_create", "fhe_server_add_model",
-            "fhe_server_submit", "fhe_server_poll", "fhe_server_pause", "fhe_server_stats", "fhe_server_destroy"]
+            "fhe_sk_import", "fhe_evk_import", "fhe_server_submit", "fhe_server_poll", "fhe_server_pause", "fhe_server_stats", "fhe_server_destroy"]

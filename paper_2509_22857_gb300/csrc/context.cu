@@ -651,6 +651,83 @@ extern "C" int fhe_evk_free(fhe_evk *evk) {
     return FHE_OK;
 }
 
+// every residue of n_blocks blocks laid out [block][L+1+alpha][N] below its prime
+static bool limbs_in_range(const fhe_ctx *c, const uint64_t *buf, size_t n_blocks) {
+    for (size_t b = 0; b < n_blocks; b++)
+        for (int t = 0; t < c->n_primes; t++) {
+            const u64 q = c->primes[t];
+            const uint64_t *p = buf + (b * c->n_primes + t) * (size_t)c->N;
+            for (long long i = 0; i < c->N; i++)
+                if (p[i] >= q) return false;
+        }
+    return true;
+}
+
+extern "C" int fhe_sk_import(fhe_ctx *c, const uint64_t *buf, size_t n_words, fhe_sk **out) {
+    if (!c || !buf || !out) return fhe_fail(FHE_E_INVAL, "null argument");
+    const size_t w = (size_t)c->n_primes * c->N;
+    if (n_words != w) return fhe_fail(FHE_E_INVAL, "a secret key has (L+1+alpha)*N words");
+    if (!limbs_in_range(c, buf, 1)) return fhe_fail(FHE_E_INVAL, "secret key residue not below its prime");
+    FHE_CU(cudaSetDevice(c->dev));
+    std::unique_ptr<fhe_sk> sk(new fhe_sk());
+    sk->ctx = c;
+    FHE_TRY(dev_alloc(c, (void **)&sk->s_ntt, w * 8));
+    const cudaError_t e = cudaMemcpy(sk->s_ntt, buf, w * 8, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        dev_free(sk->s_ntt);
+        return fhe_fail(FHE_E_CUDA, std::string("cudaMemcpy: ") + cudaGetErrorString(e));
+    }
+    *out = sk.release();
+    return FHE_OK;
+}
+
+extern "C" int fhe_evk_import(fhe_ctx *c, const int32_t *galois, size_t n_keys, const uint64_t *const *keys,
+                              size_t words_per_key, fhe_evk **out) {
+    if (!c || !out || (n_keys && (!galois || !keys))) return fhe_fail(FHE_E_INVAL, "null argument");
+    const size_t kw = key_words(c);
+    if (words_per_key != kw) return fhe_fail(FHE_E_INVAL, "key size does not match the context");
+    const int digits = (c->L + c->alpha) / c->alpha;
+    int n_relin = 0;
+    std::map<int, size_t> seen;
+    for (size_t i = 0; i < n_keys; i++) {
+        const int k = galois[i];
+        if (!keys[i]) return fhe_fail(FHE_E_INVAL, "null key buffer");
+        if (k == 0) {
+            n_relin++;
+            continue;
+        }
+        if (k < 3 || (long long)k >= 2 * c->N || (k & 1) == 0)
+            return fhe_fail(FHE_E_INVAL, "not a Galois element of this ring: " + std::to_string(k));
+        if (!seen.emplace(k, i).second) return fhe_fail(FHE_E_INVAL, "duplicate Galois element " + std::to_string(k));
+    }
+    if (n_relin != 1) return fhe_fail(FHE_E_INVAL, "exactly one relinearisation key (galois 0) is required");
+    for (size_t i = 0; i < n_keys; i++)
+        if (!limbs_in_range(c, keys[i], (size_t)digits * 2))
+            return fhe_fail(FHE_E_INVAL, "key " + std::to_string(i) + ": residue not below its prime");
+    FHE_CU(cudaSetDevice(c->dev));
+    fhe_evk *evk = new fhe_evk();
+    evk->ctx = c;
+    evk->digits = digits;
+    int rc = FHE_OK;
+    for (size_t i = 0; i < n_keys && rc == FHE_OK; i++) {
+        u64 *d = nullptr;
+        rc = dev_alloc(c, (void **)&d, kw * 8);
+        if (rc != FHE_OK) break;
+        if (galois[i] == 0)
+            evk->relin = d;
+        else
+            evk->galois[galois[i]] = d;
+        const cudaError_t e = cudaMemcpy(d, keys[i], kw * 8, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) rc = fhe_fail(FHE_E_CUDA, std::string("cudaMemcpy: ") + cudaGetErrorString(e));
+    }
+    if (rc != FHE_OK) {
+        fhe_evk_free(evk);
+        return rc;
+    }
+    *out = evk;
+    return FHE_OK;
+}
+
 extern "C" int fhe_evk_galois(const fhe_evk *evk, int32_t *out, size_t cap, size_t *n) {
     if (!evk || !n) return fhe_fail(FHE_E_INVAL, "null argument");
     *n = evk->galois.size();
