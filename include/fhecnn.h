@@ -68,8 +68,14 @@ typedef struct fhe_server fhe_server;
  * L primes q_1..q_L of q_bits, then q_0 of q0_bits, then the alpha special
  * primes of p_bits, each skipping primes already taken.  alpha is also the
  * number of consecutive primes per key-switching digit.
- * Limits: 12 <= log_n <= 16; prime sizes 31..58 bits; 1 <= alpha <= 8;
- * L + 1 + alpha <= 64.
+ * Or `primes` gives the chain explicitly (the appendix on FHE parameters
+ * prints the paper's chains): L+1+alpha values, q_0..q_L then
+ * p_0..p_{alpha-1}, each prime, = 1 mod 2N, distinct and of 20..58 bits;
+ * the *_bits fields are then ignored.
+ * Limits: 12 <= log_n <= 16; generated primes 31..58 bits; 1 <= alpha <= 8;
+ * L + 1 + alpha <= 64; at most 2^(62 - b) digits ceil((L+1)/alpha) for the
+ * largest prime's size b (the key inner product sums one 2b-bit product per
+ * digit below Barrett's 2^(b+62) bound).
  */
 typedef struct {
     int log_n;
@@ -80,6 +86,7 @@ typedef struct {
     int alpha;
     double log_scale;   /* Delta = 2^log_scale */
     int device;         /* CUDA device ordinal */
+    const uint64_t *primes;   /* explicit chain, or NULL */
 } fhe_params;
 
 const char *fhe_last_error(void);

@@ -26,7 +26,8 @@ PP = ctypes.POINTER(ctypes.c_void_p)
 
 class FheParams(ctypes.Structure):
     _fields_ = [("log_n", c_int), ("L", c_int), ("q_bits", c_int), ("q0_bits", c_int),
-                ("p_bits", c_int), ("alpha", c_int), ("log_scale", c_double), ("device", c_int)]
+                ("p_bits", c_int), ("alpha", c_int), ("log_scale", c_double), ("device", c_int),
+                ("primes", P_U64)]
 
 
 class FheStepDesc(ctypes.Structure):
@@ -156,8 +157,16 @@ def fhe_kernel_launches() -> int:
     return int(lib().fhe_kernel_launches())
 
 
-def fhe_ctx_create(log_n, L, q_bits, q0_bits, p_bits, alpha, log_scale, device=0) -> int:
-    p = FheParams(log_n, L, q_bits, q0_bits, p_bits, alpha, float(log_scale), device)
+def fhe_ctx_create(log_n, L, q_bits, q0_bits, p_bits, alpha, log_scale, device=0, primes=None) -> int:
+    """primes: optional explicit chain q_0..q_L, p_0..p_{alpha-1} (the bit
+    sizes are then ignored)"""
+    arr = None
+    if primes is not None:
+        arr = np.ascontiguousarray(np.array([int(x) for x in primes], dtype=np.uint64))
+        if arr.size != L + 1 + alpha:
+            raise ValueError("an explicit chain has L + 1 + alpha primes")
+    p = FheParams(log_n, L, q_bits, q0_bits, p_bits, alpha, float(log_scale), device,
+                  _ptr(arr, P_U64) if arr is not None else None)
     h = c_void()
     _check(lib().fhe_ctx_create(ctypes.byref(p), ctypes.byref(h)))
     return h.value

@@ -414,13 +414,34 @@ extern "C" int fhe_ctx_create(const fhe_params *p, fhe_ctx **out) {
     if (p->log_n < 12 || p->log_n > 16) return fhe_fail(FHE_E_INVAL, "log_n must be in [12, 16]");
     if (p->alpha < 1 || p->alpha > 8) return fhe_fail(FHE_E_INVAL, "alpha must be in [1, 8]");
     if (p->L < 0 || p->L + 1 + p->alpha > FHE_MAX_LIMBS) return fhe_fail(FHE_E_INVAL, "too many primes");
-    // 58: lazy NTT values stay below 2^61 and Barrett's constants fit 64 bits;
-    // 31: a 64-bit word (sampling) or a 58-bit residue reduces in one Barrett step
-    if (p->q_bits > 58 || p->q0_bits > 58 || p->p_bits > 58 || p->q_bits < 31 || p->q0_bits < 31 ||
-        p->p_bits < 31)
-        return fhe_fail(FHE_E_INVAL, "prime sizes must be in [31, 58] bits");
+    const u64 two_n = 2ull << p->log_n;
+    const int n_primes = p->L + 1 + p->alpha;
+    int max_bits = 0;
+    if (p->primes) {
+        // 58: lazy NTT values stay below 2^61 and Barrett's constants fit 64 bits
+        for (int i = 0; i < n_primes; i++) {
+            const u64 q = p->primes[i];
+            const int b = q ? 64 - __builtin_clzll(q) : 0;
+            if (b < 20 || b > 58) return fhe_fail(FHE_E_INVAL, "explicit primes must have 20..58 bits");
+            if (q % two_n != 1) return fhe_fail(FHE_E_INVAL, "explicit prime not = 1 mod 2N: " + std::to_string(q));
+            if (!h_is_prime(q)) return fhe_fail(FHE_E_INVAL, "explicit chain value is not prime: " + std::to_string(q));
+            for (int j = 0; j < i; j++)
+                if (p->primes[j] == q) return fhe_fail(FHE_E_INVAL, "explicit chain repeats a prime");
+            max_bits = std::max(max_bits, b);
+        }
+    } else {
+        // 31..58 bits for generated chains
+        if (p->q_bits > 58 || p->q0_bits > 58 || p->p_bits > 58 || p->q_bits < 31 || p->q0_bits < 31 ||
+            p->p_bits < 31)
+            return fhe_fail(FHE_E_INVAL, "prime sizes must be in [31, 58] bits");
+        max_bits = std::max(std::max(p->q_bits, p->q0_bits), p->p_bits);
+    }
+    // the key inner product sums one product below 2^(2b) per digit; Barrett
+    // reduction takes sums below 2^(b+62)
     const int digits_top = (p->L + p->alpha) / p->alpha;
-    if (digits_top > 7) return fhe_fail(FHE_E_INVAL, "more than 7 key-switching digits");
+    if ((long long)digits_top > (1ll << (62 - max_bits)))
+        return fhe_fail(FHE_E_INVAL, std::to_string(digits_top) + " key-switching digits exceed 2^(62 - " +
+                                         std::to_string(max_bits) + ")");
     int ndev = 0;
     FHE_CU(cudaGetDeviceCount(&ndev));
     if (p->device < 0 || p->device >= ndev) return fhe_fail(FHE_E_INVAL, "no such CUDA device");
@@ -434,18 +455,22 @@ extern "C" int fhe_ctx_create(const fhe_params *p, fhe_ctx **out) {
     c->alpha = p->alpha;
     c->n_primes = p->L + 1 + p->alpha;
     c->scale = std::pow(2.0, p->log_scale);
-    const u64 two_n = 2 * (u64)c->N;
-    std::vector<u64> rest = p->L > 0 ? h_gen_primes(p->q_bits, p->L, two_n, {}) : std::vector<u64>();
-    if ((int)rest.size() != p->L) return fhe_fail(FHE_E_INVAL, "not enough q primes");
-    std::vector<u64> q0 = h_gen_primes(p->q0_bits, 1, two_n, rest);
-    if (q0.size() != 1) return fhe_fail(FHE_E_INVAL, "no q0 prime");
-    std::vector<u64> taken = rest;
-    taken.push_back(q0[0]);
-    std::vector<u64> sp = h_gen_primes(p->p_bits, p->alpha, two_n, taken);
-    if ((int)sp.size() != p->alpha) return fhe_fail(FHE_E_INVAL, "not enough special primes");
-    c->primes.push_back(q0[0]);
-    for (u64 x : rest) c->primes.push_back(x);
-    for (u64 x : sp) c->primes.push_back(x);
+    c->prm.primes = nullptr;   // the caller's array is read during this call only
+    if (p->primes) {
+        c->primes.assign(p->primes, p->primes + n_primes);
+    } else {
+        std::vector<u64> rest = p->L > 0 ? h_gen_primes(p->q_bits, p->L, two_n, {}) : std::vector<u64>();
+        if ((int)rest.size() != p->L) return fhe_fail(FHE_E_INVAL, "not enough q primes");
+        std::vector<u64> q0 = h_gen_primes(p->q0_bits, 1, two_n, rest);
+        if (q0.size() != 1) return fhe_fail(FHE_E_INVAL, "no q0 prime");
+        std::vector<u64> taken = rest;
+        taken.push_back(q0[0]);
+        std::vector<u64> sp = h_gen_primes(p->p_bits, p->alpha, two_n, taken);
+        if ((int)sp.size() != p->alpha) return fhe_fail(FHE_E_INVAL, "not enough special primes");
+        c->primes.push_back(q0[0]);
+        for (u64 x : rest) c->primes.push_back(x);
+        for (u64 x : sp) c->primes.push_back(x);
+    }
     c->enc.init(c->logN);
     int r = build_tables(c.get());
     if (r != FHE_OK) {

@@ -539,6 +539,50 @@ __global__ void __launch_bounds__(256) k_ks_ip(DevCtx c, LevelTab lt, KsArgs a, 
     }
 }
 
+// Inner product for more than 7 digits (one special prime per digit, as in
+// the paper's own parameter sets): the digits are a loop and the key pairs
+// are loaded per item, since they no longer fit in registers.  Same layout,
+// gathers and arithmetic as k_ks_ip.
+__global__ void __launch_bounds__(256) k_ks_ip_n(DevCtx c, LevelTab lt, KsArgs a, KsLayout ly) {
+    const int ext = lt.ext, nd = lt.n_digits;
+    const int t = blockIdx.y;
+    const int pi = ext_prime(t, a.level, c.L);
+    const ModQ m = c.primes[pi].m;
+    const long long N = 1ll << c.logN;
+    const int col = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const long long key_limbs = c.L + 1 + c.alpha;
+    const int jt = t <= a.level ? t / c.alpha : -1;
+    const int ip_col = galois_src(col, a.ip_galois, c.logN);
+    const int src_col = jt >= 0 ? galois_src(ip_col, a.galois, c.logN) : ip_col;
+    const bool ip_sw = ip_col & 1, src_sw = src_col & 1;
+    for (int item = 0; item < a.n_items; item++) {
+        const u64 *mu = a.ws + item * a.ws_item + ly.mu + (long long)t * N + (ip_col & ~1);
+        const u64 *dd = a.d + item * a.d_item + (long long)t * N + (src_col & ~1);
+        U128 a00 = {0, 0}, a01 = {0, 0}, a10 = {0, 0}, a11 = {0, 0};
+        for (int j = 0; j < nd; j++) {
+            const ulonglong2 x = (j == jt) ? ld_pair(dd, src_sw) : ld_pair(mu + (long long)j * ext * N, ip_sw);
+            const u64 *kb = a.key + ((long long)(j * 2) * key_limbs + pi) * N + col;
+            const ulonglong2 k0 = __ldg((const ulonglong2 *)kb);
+            const ulonglong2 k1 = __ldg((const ulonglong2 *)(kb + key_limbs * N));
+            mac(a00, x.x, k0.x);
+            mac(a01, x.y, k0.y);
+            mac(a10, x.x, k1.x);
+            mac(a11, x.y, k1.y);
+        }
+        ulonglong2 *o0 = (ulonglong2 *)(a.ws + item * a.ws_item + ly.acc + (long long)t * N + col);
+        ulonglong2 *o1 = (ulonglong2 *)((u64 *)o0 + (long long)ext * N);
+        ulonglong2 r0 = make_ulonglong2(barrett(a00, m), barrett(a01, m));
+        ulonglong2 r1 = make_ulonglong2(barrett(a10, m), barrett(a11, m));
+        if (a.ip_accumulate) {
+            const ulonglong2 p0 = *o0, p1 = *o1;
+            r0 = make_ulonglong2(add_mod(r0.x, p0.x, m.q), add_mod(r0.y, p0.y, m.q));
+            r1 = make_ulonglong2(add_mod(r1.x, p1.x, m.q), add_mod(r1.y, p1.y, m.q));
+        }
+        *o0 = r0;
+        *o1 = r1;
+    }
+}
+
 // out[i][t] (+)= in[i][t] gathered by sigma_galois, limbs 0..level
 __global__ void k_gather_acc(DevCtx c, const u64 *in, long long in_item, u64 *out, long long out_item, int level,
                              int galois, int accumulate) {
@@ -1201,7 +1245,7 @@ cudaError_t launch_keyswitch(const DevCtx &c, const LevelTab &lt, const KsArgs &
     if (a.ip_galois == 0) a.ip_galois = 1;
     if (a.add_galois == 0) a.add_galois = a.galois;
     const int nl = a.level + 1, ext = lt.ext, nd = lt.n_digits, B = a.n_items;
-    if (nd > 7) return cudaErrorInvalidValue;   // inner-product accumulator bound
+    if (nd > 64) return cudaErrorInvalidValue;   // the context bounds digits by the primes' sizes
     // the inner product takes two slots per thread: 16-byte aligned operands and
     // N >= 512 (always true of the library's own buffers, whose limbs start at
     // multiples of N)
@@ -1230,7 +1274,7 @@ cudaError_t launch_keyswitch(const DevCtx &c, const LevelTab &lt, const KsArgs &
         case 5: k_ks_ip<5><<<g2, 256, 0, s>>>(c, lt, a, ly); break;
         case 6: k_ks_ip<6><<<g2, 256, 0, s>>>(c, lt, a, ly); break;
         case 7: k_ks_ip<7><<<g2, 256, 0, s>>>(c, lt, a, ly); break;
-        default: return cudaErrorInvalidValue;
+        default: k_ks_ip_n<<<g2, 256, 0, s>>>(c, lt, a, ly);
         }
     }
     KS_EV(4);

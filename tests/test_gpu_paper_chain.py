@@ -1,0 +1,87 @@
+"""The paper's own parameter set for ResNet-32 (its printed chain: q_0 of 28
+bits, 32 primes of ~52 bits, one 54-bit special prime, so 33 key-switching
+digits) on the device, at N = 2^12 (the primes are = 1 mod 2^17): rotation,
+relinearised square and rescales bit-equal to the oracle's; chains the
+library must refuse."""
+import numpy as np
+import pytest
+
+import paper_chains
+from oracle import ckks as O
+
+pytestmark = pytest.mark.gpu
+
+LOGN = 12
+
+
+@pytest.fixture(scope="module")
+def paper():
+    from paper_2509_22857_gb300 import _lib as F
+    _, d, q, p = paper_chains.chain("ResNet-32")
+    prm = O.Params(LOGN, q, p, 1, 2.0 ** d)
+    ctx = F.fhe_ctx_create(LOGN, prm.L, 0, 0, 0, 1, d, primes=q + p)
+    S = O.CKKS(prm)
+    steps = [1, -1, 5]
+    keys = S.keygen(11, steps)
+    sk, evk = F.fhe_keygen(ctx, 11, steps)
+    yield F, ctx, prm, S, keys, sk, evk
+    F.fhe_evk_free(evk)
+    F.fhe_sk_free(sk)
+    F.fhe_ctx_destroy(ctx)
+
+
+def _same(F, S, ct_o, ct_g):
+    prm = S.prm
+    buf, lv, sc = F.fhe_ct_export(ct_g, prm.N)
+    ref = np.stack([np.stack([O.intt(ct_o.c[r, t], prm.primes[t], prm.psi[t]) for t in range(ct_o.level + 1)])
+                    for r in range(ct_o.c.shape[0])])
+    assert lv == ct_o.level and sc == ct_o.scale and np.array_equal(buf, ref)
+
+
+def test_chain_is_taken_as_given(paper):
+    F, ctx, prm, S, keys, sk, evk = paper
+    assert F.fhe_ctx_primes(ctx) == prm.primes
+    assert len(prm.digits(prm.L)) == 33
+
+
+def test_keyswitching_with_33_digits_bit_exact(paper):
+    F, ctx, prm, S, keys, sk, evk = paper
+    z = np.random.default_rng(2).uniform(-1, 1, prm.N // 2)
+    scale = prm.scale ** 3
+    ct_o = S.encrypt(keys, S.encode(z, scale, prm.L), 21)
+    pt = F.fhe_encode(ctx, z, scale, prm.L)
+    ct_g = F.fhe_encrypt(ctx, sk, pt, 21)
+    F.fhe_pt_free(pt)
+    _same(F, S, ct_o, ct_g)
+    for step in (1, -1, 5):
+        r = F.fhe_rotate(ctx, evk, ct_g, step)
+        _same(F, S, S.rotate(ct_o, step, keys), r)
+        F.fhe_ct_free(r)
+    sq_o = S.relinearize(S.tensor_square(ct_o), keys)
+    sq_g = F.fhe_square(ctx, evk, ct_g)
+    _same(F, S, sq_o, sq_g)
+    # rescales down the chain, the last onto the 28-bit q_0
+    for _ in range(prm.L):
+        sq_o = S.rescale(sq_o)
+        F.fhe_rescale(ctx, sq_g)
+    _same(F, S, sq_o, sq_g)
+    for h in (sq_g, ct_g):
+        F.fhe_ct_free(h)
+
+
+def test_bad_explicit_chains_are_refused():
+    from paper_2509_22857_gb300 import _lib as F
+    _, d, q, p = paper_chains.chain("ResNet-32")
+    composite = q[3] + 2 * 8192
+    assert composite % 8192 == 1 and not O.is_prime(composite)
+    bad = [q[:3] + [q[1]] + p,                 # a repeated prime
+           q[:3] + [composite] + p,            # = 1 mod 2N, not prime
+           q[:3] + [2 ** 31 - 1] + p]          # prime, not = 1 mod 2N
+    for chain in bad:
+        with pytest.raises(F.FheError) as e:
+            F.fhe_ctx_create(LOGN, 3, 0, 0, 0, 1, d, primes=chain)
+        assert e.value.code == F.FHE_E_INVAL
+    # more digits than Barrett's bound allows for 58-bit primes: 17 > 2^(62-58)
+    with pytest.raises(F.FheError) as e:
+        F.fhe_ctx_create(LOGN, 16, 58, 40, 58, 1, 29)
+    assert e.value.code == F.FHE_E_INVAL

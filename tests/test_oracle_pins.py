@@ -11,6 +11,7 @@ import os
 import numpy as np
 import pytest
 
+import paper_chains
 from oracle import ckks as C
 from oracle import planner
 
@@ -20,15 +21,7 @@ GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 # ------------------------------------------------------------------ primes
 
 def _paper_chains():
-    rows = []
-    for line in open(os.path.join(GOLDEN, "paper_primes.txt")):
-        if line.startswith("#") or not line.strip():
-            continue
-        head, qs, p = [x.strip() for x in line.split("|")]
-        name, logn, d, L, lq, lp = head.split()
-        rows.append((name, int(logn), int(d), int(L), int(lq), int(lp),
-                     [int(x, 16) for x in qs.split()], int(p, 16)))
-    return rows
+    return paper_chains.rows()
 
 
 def test_paper_prime_chains_are_ntt_primes():
@@ -469,3 +462,32 @@ def test_lazy_rotation_sum_decrypts_to_the_sum(small):
     out = S.rotate_sum_lazy([(cts[1], 1), (cts[2], 5)], keys, cts[0])
     want = zs[0] + np.roll(zs[1], -1) + np.roll(zs[2], -5)
     assert np.max(np.abs(S.decrypt_decode(keys, out).real - want)) < 1e-6
+
+
+def test_oracle_with_the_paper_resnet32_chain():
+    """The paper's ResNet-32 chain (q_0 of 28 bits, 32 primes of ~52 bits, one
+    54-bit special prime, so one prime per digit: 33 digits at the top) at
+    N = 2^10: the key switch of a uniform d is d*s^2 plus noise of a fresh
+    error's size; a rotation decrypts to the rotated slots; a rescale from
+    Delta^3 leaves Delta and the values."""
+    logn, d, q, p = paper_chains.chain("ResNet-32")
+    prm = C.Params(10, q, p, 1, 2.0 ** d)
+    assert len(prm.digits(prm.L)) == 33 and q[0].bit_length() == 28
+    S = C.CKKS(prm)
+    keys = S.keygen(11, [1])
+    lv = prm.L
+    rng = np.random.default_rng(3)
+    dd = np.stack([rng.integers(0, prm.q[t], prm.N, dtype=np.uint64) for t in range(lv + 1)])
+    got = S.crt(S.decrypt_residues(keys, C.Ciphertext(S.key_switch(dd, lv, keys.relin), lv, 1.0)))
+    s2 = np.stack([C.vmul(keys.s_ntt[t], keys.s_ntt[t], prm.q[t]) for t in range(lv + 1)])
+    want = S.crt(np.stack([C.intt(C.vmul(dd[t], s2[t], prm.q[t]), prm.q[t], prm.psi[t]) for t in range(lv + 1)]))
+    Q = math.prod(prm.q)
+    assert max(abs(((g - w + Q // 2) % Q) - Q // 2) for g, w in zip(got, want)) < 2 ** 20
+    z = rng.uniform(-1, 1, prm.N // 2)
+    ct = S.encrypt(keys, S.encode(z, 2.0 ** (3 * d), lv), 8)
+    assert np.max(np.abs(S.decrypt_decode(keys, S.rotate(ct, 1, keys)) - np.roll(z, -1))) < 1e-6
+    r = S.rescale(ct)
+    assert r.level == lv - 1 and abs(math.log2(r.scale) - d) < 0.01
+    # the rescale's rounding (1/2 per coefficient, times s) decodes to about
+    # sqrt(N) * 13 / Delta ~ 1e-5 in the slots at Delta = 2^26, N = 2^10
+    assert np.max(np.abs(S.decrypt_decode(keys, r) - z)) < 1e-4
