@@ -100,6 +100,12 @@ def resnet20(num_classes: int = 10) -> List[Dict]:
     return resnet((16, 32, 64), 3, 32, num_classes)
 
 
+def resnet32(num_classes: int = 10) -> List[Dict]:
+    """ResNet-32 for 32x32x3: three stages of five basic blocks with
+    16/32/64 channels (the paper's N = 2^16 workload, Table 4)."""
+    return resnet((16, 32, 64), 5, 32, num_classes)
+
+
 def resnet_mini() -> List[Dict]:
     """A ResNet with the same structure at a small size (8x8x3 input,
     4/8/16 channels, one block per stage) for full-network parity tests."""
@@ -162,8 +168,8 @@ def vgg_mini() -> List[Dict]:
     return vgg(cfg=(4, "M", 8, "M", "M"), in_hw=8, fc=(8,), num_classes=10)
 
 
-ARCHS = {"tiny": tiny, "resnet20": resnet20, "resnet_mini": resnet_mini, "vgg11": vgg11, "vgg_mini": vgg_mini,
-         "resnet18": resnet18, "resnet18_mini": resnet18_mini}
+ARCHS = {"tiny": tiny, "resnet20": resnet20, "resnet32": resnet32, "resnet_mini": resnet_mini, "vgg11": vgg11,
+         "vgg_mini": vgg_mini, "resnet18": resnet18, "resnet18_mini": resnet18_mini}
 
 
 # ------------------------------------------------------------- parameters
@@ -276,4 +282,24 @@ PRESETS = {
     "resnet20": dict(logn=16, L=20, q_bits=58, q0_bits=40, p_bits=58, alpha=7, log_scale=29),
     "resnet18": dict(logn=16, L=18, q_bits=58, q0_bits=40, p_bits=58, alpha=7, log_scale=29),
     "resnet18_mini": dict(logn=12, L=18, q_bits=58, q0_bits=40, p_bits=58, alpha=7, log_scale=29),
+}
+
+
+# The paper's own parameter sets, with the prime chains its appendix on FHE
+# parameters prints (q_0, the small output prime printed last there, first
+# here; then q_1..q_L in printed order; then P).  One special prime, so one
+# prime per key-switching digit.
+PAPER_PARAMS = {
+    "resnet32": dict(
+        logn=16, L=32, alpha=1, log_scale=26,
+        q=[
+          0x8020001, 0x10000000060001, 0xffffffff00001, 0x10000000180001, 0xfffffffe40001,
+          0x10000000200001, 0xfffffffe20001, 0x100000003e0001, 0xfffffffbe0001, 0x10000000500001,
+          0xfffffffa60001, 0x100000006e0001, 0xfffffff820001, 0x100000007e0001, 0xfffffff480001,
+          0x10000000960001, 0xfffffff280001, 0x10000000c80001, 0x10000000d80001, 0xffffffed60001,
+          0x10000000ec0001, 0xffffffec40001, 0x10000000fc0001, 0xffffffeb00001, 0x100000010e0001,
+          0xffffffe9e0001, 0x10000001380001, 0xffffffe9a0001, 0x100000016a0001, 0xffffffe940001,
+          0x10000001bc0001, 0xffffffe6a0001, 0x10000001be0001,
+        ],
+        p=[0x3fffffffd60001]),
 }

@@ -1,6 +1,8 @@
 """The package's host-side model lowering (parameter transforms, slot layouts,
 diagonals, levels, scales, constants) produces exactly the oracle's program:
 same steps, same rotation set, bit-identical diagonal and bias vectors."""
+import os
+
 import numpy as np
 import pytest
 
@@ -133,3 +135,19 @@ def test_input_at_delta_squared_costs_no_level():
         assert M.input_scale(pm) == po.tensors[po.input_tensor].scale == prm.scale ** lam
         plans[lam] = (pm.tensors[pm.output].level, sum(1 for s in pm.steps if s["kind"] == 2))
     assert plans[1] == plans[2] == (0, plans[1][1])
+
+
+@pytest.mark.slow
+def test_resnet32_on_the_papers_chain_uses_table1_levels():
+    """ResNet-32 compiled on the paper's own chain (Delta = 2^26, 52-bit
+    primes, tower reuse) enters at level L = 32 and leaves at level 0: the
+    32 levels of Table 1's P2FRT column for ResNet-32."""
+    pp = synth.PAPER_PARAMS["resnet32"]
+    levels = {r.split()[0]: int(r.split()[-1]) for r in open(os.path.join(os.path.dirname(__file__), "golden",
+                                                                          "table1_levels.txt"))
+              if r.strip() and not r.startswith("#")}
+    net = synth.resnet32()
+    prog = M.compile_network(net, synth.params(net), pp["q"], pp["logn"], pp["log_scale"], "packed", pp["alpha"],
+                             input_lambda=2)
+    assert prog.tensors[prog.input].level == pp["L"] == levels["ResNet-32"]
+    assert prog.tensors[prog.output].level == 0

@@ -53,3 +53,13 @@ def test_cluster_joint_shares_one_codebook_per_layer():
     # members differ before clustering
     i = next(i for i, nd in enumerate(net) if nd["op"] == "conv")
     assert not np.array_equal(raws[0][i]["w"], raws[1][i]["w"])
+
+
+def test_paper_parameter_sets_match_the_printed_chains():
+    """synth's copy of the paper's ResNet-32 chain equals the appendix's
+    printed chain (tests/golden/paper_primes.txt), q_0 first."""
+    import paper_chains
+    logn, d, q, p = paper_chains.chain("ResNet-32")
+    pp = synth.PAPER_PARAMS["resnet32"]
+    assert (pp["logn"], pp["log_scale"], pp["L"]) == (logn, d, len(q) - 1)
+    assert pp["q"] == q and pp["p"] == p and pp["alpha"] == len(p)
