@@ -15,7 +15,6 @@ exchange between ranks.
 """
 import argparse
 import json
-import math
 import os
 import subprocess
 import sys
