@@ -491,3 +491,31 @@ def test_oracle_with_the_paper_resnet32_chain():
     # the rescale's rounding (1/2 per coefficient, times s) decodes to about
     # sqrt(N) * 13 / Delta ~ 1e-5 in the slots at Delta = 2^26, N = 2^10
     assert np.max(np.abs(S.decrypt_decode(keys, r) - z)) < 1e-4
+
+
+def test_rotation_steps_repeat_with_period_half_n(small):
+    """5 has multiplicative order exactly N/2 modulo 2N (the slot rotations
+    form a cyclic group of order N/2), so rotations by r and r + N/2 are one
+    automorphism and a rotation by N/2 leaves the slots unchanged."""
+    prm, S, keys = small
+    for logn in (5, 10, 12, 16):
+        N = 1 << logn
+        assert pow(5, N // 2, 2 * N) == 1 and pow(5, N // 4, 2 * N) != 1
+    N = prm.N
+    z = np.random.default_rng(11).uniform(-1, 1, N // 2)
+    ct = S.encrypt(keys, S.encode(z, prm.scale, prm.L), 12)
+    assert np.array_equal(S.rotate(ct, 1 + N // 2, keys).c, S.rotate(ct, 1, keys).c)
+    assert np.array_equal(S.rotate(ct, N // 2, keys).c, ct.c)
+    assert np.max(np.abs(S.decrypt_decode(keys, S.rotate(ct, -N // 2, keys)) - z)) < 1e-6
+
+
+def test_degenerate_inputs(small):
+    """An empty slot vector encodes to the zero plaintext; a ciphertext on
+    q_0 alone still decrypts; there is no rescale below level 0."""
+    prm, S, keys = small
+    assert not S.encode(np.zeros(0), prm.scale, prm.L).m.any()
+    z = np.random.default_rng(12).uniform(-1, 1, prm.N // 2)
+    ct0 = S.encrypt(keys, S.encode(z, prm.scale, 0), 13)
+    assert ct0.level == 0 and np.max(np.abs(S.decrypt_decode(keys, ct0) - z)) < 1e-6
+    with pytest.raises(AssertionError):
+        S.rescale(ct0)
