@@ -374,7 +374,7 @@ def run_ours(args, rank, world):
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
         "roofline": {"bound": "alu",
-                     "kernel": "hybrid key switch (9 kernels: ModUp, key inner product, ModDown), level %d, "
+                     "kernel": "hybrid key switch (10 kernels: ModUp, key inner product, exact ModDown), level %d, "
                                "%d polynomials (one group of the pipeline)" % (lv, g),
                      "achieved": round(alu_achieved / 1e9, 1), "peak": round(ALU_PEAK_MODMUL / 1e9, 1),
                      "unit": "Gmodmul/s", "peak_kind": "derived (152 SMs x 64 IMAD/clk x 2.07 GHz / 10 IMAD "
