@@ -1,7 +1,10 @@
 // Host check of the library's modular arithmetic (compiled with g++ by
 // tests/test_modarith_host.py): Barrett reduction of sums of up to eight
 // products and Shoup multiplication against 128-bit '%', for primes of
-// 31..58 bits (the library's limits).  Prints "ok" or the first failure.
+// 20..58 bits (the library's limits for explicit chains); and the key inner
+// product's sums of one product per digit at the context's digit cap
+// min(2^(62 - b), 64), worst case and random.  Prints "ok" or the first
+// failure.
 #include <cstdio>
 #include <random>
 #include "../paper_2509_22857_gb300/csrc/modarith.cuh"
@@ -28,7 +31,7 @@ static bool is_prime(u64 n) {
 
 int main() {
     std::mt19937_64 g(12345);
-    for (int bits = 31; bits <= 58; bits++) {
+    for (int bits = 20; bits <= 58; bits++) {
         for (int rep = 0; rep < 3; rep++) {
             u64 q = ((1ull << bits) - 1) - (g() % (1ull << (bits - 2)));
             q |= 1;
@@ -63,6 +66,19 @@ int main() {
                 if (barrett(acc2, m) != (u64)(ref2 % q)) { printf("wide-sum fail q=%llu\n", q); return 1; }
                 u64 word = g();
                 if (barrett(U128{word, 0}, m) != word % q) { printf("word reduction fail\n"); return 1; }
+            }
+            // key inner product: one product of two residues per digit, as many
+            // digits as the context admits for this prime size
+            const int dmax = bits >= 56 ? (1 << (62 - bits)) : 64;
+            for (int it = 0; it < 500; it++) {
+                U128 acc = {0, 0};
+                u128 ref = 0;
+                for (int t = 0; t < dmax; t++) {
+                    const u64 a = it == 0 ? q - 1 : g() % q, b = it == 0 ? q - 1 : g() % q;
+                    mac(acc, a, b);
+                    ref += (u128)a * b;
+                }
+                if (barrett(acc, m) != (u64)(ref % q)) { printf("digit-sum fail q=%llu digits=%d\n", q, dmax); return 1; }
             }
         }
     }
