@@ -13,8 +13,10 @@ hand, and the results are cached per device name and parameter set:
   the special modulus P (alpha primes of p_bits) is at least every digit's
   modulus, so that the key-switching noise, about digit * e / P per digit
   (Sec. 2.2, hybrid key switching with a special modulus), stays at the
-  level of a fresh encryption error; and when the key has at most 7 digits
-  (the inner product's 128-bit accumulator bound).
+  level of a fresh encryption error; and when the key has no more digits
+  than the library admits, min(2^(62 - b), 64) for the largest prime of b
+  bits (the inner product sums one product below 2^(2b) per digit, and
+  Barrett reduction takes sums below 2^(b+62)).
 * **Linear-step chunk size** (MAC sources per pass, `fhe_ctx_set_linear_chunk`):
   bit-neutral.  The tuner checks that every candidate gives identical
   ciphertexts and keeps the fastest.
@@ -31,7 +33,12 @@ import time
 from dataclasses import dataclass, field
 from typing import Callable, Dict, Iterable, List, Optional, Sequence, Tuple
 
-MAX_DIGITS = 7
+MAX_LIMBS = 64
+
+
+def max_digits(max_bits: int) -> int:
+    """most key-switching digits the library admits with primes of at most max_bits"""
+    return min(1 << (62 - max_bits), MAX_LIMBS)
 
 
 def digit_bits(L: int, q_bits: int, q0_bits: int, alpha: int) -> List[int]:
@@ -42,11 +49,12 @@ def digit_bits(L: int, q_bits: int, q0_bits: int, alpha: int) -> List[int]:
 
 
 def admissible(L: int, q_bits: int, q0_bits: int, p_bits: int, alpha: int) -> bool:
-    """P = alpha primes of p_bits covers every digit, and at most 7 digits."""
+    """P = alpha primes of p_bits covers every digit, and the library admits
+    the digit count."""
     if alpha < 1:
         return False
     d = digit_bits(L, q_bits, q0_bits, alpha)
-    return len(d) <= MAX_DIGITS and alpha * p_bits >= max(d)
+    return len(d) <= max_digits(max(q_bits, q0_bits, p_bits)) and alpha * p_bits >= max(d)
 
 
 def admissible_widths(L: int, q_bits: int, q0_bits: int, p_bits: int,

@@ -17,8 +17,10 @@ def test_digit_bits_and_rule_at_resnet20_parameters():
     pre = synth.PRESETS["resnet20"]
     assert A.digit_bits(20, 58, 40, 7) == [40 + 6 * 58, 7 * 58, 7 * 58]
     assert A.digit_bits(20, 58, 40, 3)[-1] == 3 * 58 and len(A.digit_bits(20, 58, 40, 3)) == 7
-    # 1 and 2 give more than 7 digits; every width from 3 on covers its digits with 58-bit P primes
-    assert A.admissible_widths(pre["L"], pre["q_bits"], pre["q0_bits"], pre["p_bits"]) == [3, 4, 5, 6, 7, 8]
+    # width 1 gives 21 digits, above the 16 that 58-bit primes admit (2^(62-58));
+    # every width from 2 on covers its digits with 58-bit P primes
+    assert A.max_digits(58) == 16 and A.max_digits(54) == 64
+    assert A.admissible_widths(pre["L"], pre["q_bits"], pre["q0_bits"], pre["p_bits"]) == [2, 3, 4, 5, 6, 7, 8]
     # P smaller than a digit is rejected
     assert not A.admissible(4, 50, 40, 30, 2)
     assert A.admissible(4, 50, 40, 50, 2)
@@ -129,12 +131,12 @@ class FakeLib:
 
 
 def test_digit_width_tuner_weights_levels_and_caches():
-    # width 3 is faster at the low level, 4 at the top: the weights decide
-    us = {(3, 20): 50.0, (3, 2): 10.0, (4, 20): 40.0, (4, 2): 30.0, (2, 20): 1.0, (2, 2): 1.0}
+    # width 3 is faster at the low level, 4 at the top: the weights decide; L = 20
+    # gives width 1 twenty-one digits (more than 2^(62-58) = 16): never measured
+    us = {(3, 20): 50.0, (3, 2): 10.0, (4, 20): 40.0, (4, 2): 30.0, (1, 20): 1.0, (1, 2): 1.0}
     F = FakeLib(ks_us=us)
     t = A.Tuner()
-    # L = 20 gives width 2 eleven digits (more than 7): never measured
-    kw = dict(logn=12, L=20, q_bits=50, q0_bits=40, p_bits=58, log_scale=25, candidates=(2, 3, 4), F=F,
+    kw = dict(logn=12, L=20, q_bits=50, q0_bits=40, p_bits=58, log_scale=25, candidates=(1, 3, 4), F=F,
               device="fake")
     top = A.tune_digit_width(t, levels=[(20, 1.0)], **kw)
     assert top["best"] == 4 and set(top["cost_us"]) == {"3", "4"}
@@ -145,7 +147,7 @@ def test_digit_width_tuner_weights_levels_and_caches():
     n = F.calls
     assert A.tune_digit_width(t, levels=[(20, 1.0), (2, 5.0)], **kw) == low and F.calls == n   # cached
     with pytest.raises(ValueError):
-        A.tune_digit_width(t, levels=None, **dict(kw, candidates=(2,)))
+        A.tune_digit_width(t, levels=None, **dict(kw, candidates=(1,)))
 
 
 def test_linear_chunk_tuner_picks_fastest_and_checks_outputs():
