@@ -151,3 +151,26 @@ def test_resnet32_on_the_papers_chain_uses_table1_levels():
                              input_lambda=2)
     assert prog.tensors[prog.input].level == pp["L"] == levels["ResNet-32"]
     assert prog.tensors[prog.output].level == 0
+
+
+def test_ensemble_work_is_flat_in_members():
+    """Sec. 5.3 (ensembles share ciphertexts): with the members in the blocks
+    of one HW layout, the homomorphic work of an image does not grow with M
+    -- the same input ciphertexts, levels and plaintext-MAC terms for
+    M = 1..4 -- except ceil(log2 M) rotations that sum the members' blocks
+    before the output (the structural reason the paper's ensemble time is
+    flat in M)."""
+    pre = synth.PRESETS["resnet18_mini"]
+    prm = O.make_params(**pre)
+    net = synth.resnet18_mini()
+    base = None
+    for members in (1, 2, 3, 4):
+        raws = synth.cluster_joint([synth.params(net, m) for m in range(members)], net, 4)
+        prog = M.compile_network(net, raws, prm.q, pre["logn"], pre["log_scale"], "hw_ens", pre["alpha"])
+        got = (prog.tensors[prog.input].layout.n_ct, prog.tensors[prog.input].level,
+               prog.tensors[prog.output].level, sum(len(st["t_out"]) for st in prog.steps if st["kind"] == 1))
+        ks = sum(M.keyswitch_census(prog).values())
+        if base is None:
+            base = (got, ks)
+        assert got == base[0], (members, got, base[0])
+        assert ks == base[1] + (members - 1).bit_length(), (members, ks, base[1])
