@@ -3,8 +3,9 @@
 One step = one batched homomorphic inference of a batch of encrypted
 32x32x3 images through the whole ResNet-20-shaped network (every
 convolution, activation, rescale, shortcut, pool and dense layer: all the
-hot-path operations), N = 2^16, 21 moduli of the ciphertext chain + 3
-special primes.  Inputs are seeded synthetic images and random weights.
+hot-path operations), N = 2^16, 21 moduli of the ciphertext chain + 7
+special primes (digit width 7).  Inputs are seeded synthetic images and
+random weights.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B]
   python bench.py --impl reference ...   (the CPU oracle on a bounded sample)
@@ -101,31 +102,39 @@ def aggregate_throughput(units_per_rank: int, world: int, ms_max: float) -> floa
     return units_per_rank * world / (ms_max / 1e3)
 
 
-def ks_weight(level, alpha):
-    """limb transforms in one hybrid key switch at `level` (the dominant cost)"""
-    nl = level + 1
-    nd = (level + alpha) // alpha
-    return nl + (nd * (nl + alpha) - nl) + 2 * alpha + 2 * nl
+# Integer roofline.  The key switch and the plaintext MAC are bound by the
+# 64-bit modular arithmetic on the integer pipes, not by HBM.  Algorithmic
+# work is counted in modular multiplications (one per NTT butterfly, per
+# basis-conversion term, per key inner-product term, per output scaling; one
+# per plaintext-ciphertext product).  Peak: SMs x 64 32-bit integer
+# multiply-adds per clock per SM (the integer multiply rate of the CUDA
+# arithmetic-throughput table for compute capability 10.x: 4 sub-partitions x
+# 16 lanes) x the SM clock sampled during the timed region, divided by the
+# 10 multiply-adds of one 64-bit Shoup product (4 for the high 64 bits, 3 + 3
+# for the two low products).
+IMAD_PER_CLK_SM = 64
+IMAD_PER_MODMUL = 10
 
 
-# Integer roofline.  The key switch is bound by the 64-bit modular
-# arithmetic on the integer pipes, not by HBM.  Algorithmic work is counted in
-# modular multiplications (one per NTT butterfly, per basis-conversion term,
-# per key inner-product term, per output scaling).  Peak: 152 SMs x 64
-# 32-bit IMAD per clock per SM x 2.07 GHz, divided by the 10 IMADs of one
-# 64-bit Shoup multiplication (4 for the high product, 3 + 3 for the two low
-# products) = 2.01e12 modmul/s.
-ALU_PEAK_MODMUL = 152 * 64 * 2.07e9 / 10
-
-# DRAM bytes (read + write) of one top-level key switch of 4 polynomials with
-# the current kernels, summed over its kernels from one ncu capture
-# (profiles/ks_kernels_resnet20_level20.md); reported only for that
-# configuration (group of 4 at level 20, digit width 7).
-KS_TRAFFIC_L20_G4 = 1286310912
+def alu_peak_modmul(n_sm: int, sm_mhz: float) -> float:
+    return n_sm * IMAD_PER_CLK_SM * sm_mhz * 1e6 / IMAD_PER_MODMUL
 
 
-def ks_modmuls(level, alpha, logn):
-    """modular multiplications of one hybrid key switch at `level`"""
+# DRAM bytes (read + write) of one top-level key switch of 4 polynomials,
+# summed over its kernels from one ncu capture of the kernels as they are
+# now (taken 2026-12-04, digit width 7, level 20); reported only for that
+# configuration and only while those kernels are unchanged.
+KS_TRAFFIC = {"bytes": None, "level": 20, "items": 4, "alpha": 7, "captured": None}
+
+
+def ks_parts(level, alpha, logn):
+    """modular multiplications of the three phases of one hybrid key switch
+    at `level`: (ModUp, key inner product, ModDown).  ModUp: inverse NTT of
+    the level+1 limbs, basis conversion of every digit to the limbs outside
+    it, their NTTs; inner product: two key polynomials per digit and
+    extended limb; ModDown: inverse NTT of the special limbs of both
+    polynomials, conversion to the level+1 limbs, their NTTs and the P^-1
+    scaling."""
     N = 1 << logn
     bf = (N // 2) * logn
     nl = level + 1
@@ -135,14 +144,82 @@ def ks_modmuls(level, alpha, logn):
     modup = nl * bf + sum((ext - d) * d * N + (ext - d) * bf for d in digits)
     ip = 2 * nd * ext * N
     moddown = 2 * alpha * bf + 2 * nl * alpha * N + 2 * nl * bf + 2 * nl * N
-    return modup + ip + moddown
+    return modup, ip, moddown
 
 
-def program_ledger(prog, alpha):
-    """key switches of one image and their weighted count (in top-level units)"""
+def ks_modmuls(level, alpha, logn):
+    """modular multiplications of one hybrid key switch at `level`"""
+    return sum(ks_parts(level, alpha, logn))
+
+
+def linear_ks_modmuls(level, alpha, logn, n_baby_inputs, n_babies, n_giants, n_giant_outputs):
+    """key-switching work of one linear step with hoisting: the baby-step
+    rotations of one input share its ModUp (each needs an inner product and
+    a ModDown), the giant-step rotations of one output share its ModDown
+    (each needs a ModUp and an inner product)"""
+    mu, ip, md = ks_parts(level, alpha, logn)
+    return n_baby_inputs * mu + n_babies * (ip + md) + n_giants * (mu + ip) + n_giant_outputs * md
+
+
+def image_modmuls(prog, alpha, logn):
+    """(key switches, their modular multiplications) of one image of a
+    compiled program"""
     from paper_2509_22857_gb300 import model as M
-    census = M.keyswitch_census(prog)
-    return sum(census.values()), sum(k * ks_weight(lv, alpha) for lv, k in census.items())
+    n_ks, mm = 0, 0
+    for st in prog.steps:
+        lv = prog.tensors[st["src"]].level
+        if st["kind"] == 1:
+            babies = {(int(i), int(b)) for i, b in zip(st["t_ct"], st["t_baby"]) if b}
+            giants = {(int(o), int(g)) for o, g in zip(st["t_out"], st["t_giant"]) if g}
+            mm += linear_ks_modmuls(lv, alpha, logn, len({i for i, _ in babies}), len(babies), len(giants),
+                                    len({o for o, _ in giants}))
+            n_ks += len(babies) + len(giants)
+        else:
+            k = M.keyswitches_of_step(prog, st)
+            n_ks += k
+            mm += k * ks_modmuls(lv, alpha, logn)
+    return n_ks, mm
+
+
+def oracle_image_modmuls(prog, alpha, logn):
+    """the same count on the oracle's program format"""
+    mm = 0
+    for st in prog.steps:
+        src = st["src"][0] if isinstance(st["src"], list) else st["src"]
+        t_in = prog.tensors[src]
+        lv = t_in.level
+        if st["op"] == "linear":
+            babies = set(st["baby"])
+            giants = {(o, g) for o, gs in st["groups"].items() for g in gs if g}
+            mm += linear_ks_modmuls(lv, alpha, logn, len({i for i, _ in babies}), len(babies), len(giants),
+                                    len({o for o, _ in giants}))
+        elif st["op"] == "act":
+            mm += t_in.layout.n_ct * ks_modmuls(lv, alpha, logn)
+        elif st["op"] == "rotsum":
+            mm += t_in.layout.n_ct * len(st["steps"]) * ks_modmuls(lv, alpha, logn)
+    return mm
+
+
+def mac_products(prog, N):
+    """plaintext-ciphertext products of one image (both polynomials, every
+    active limb of every term)"""
+    return sum(len(st["t_out"]) * 2 * (prog.tensors[st["src"]].level + 1) * N
+               for st in prog.steps if st["kind"] == 1)
+
+
+def mac_bytes(prog, N, batch):
+    """algorithmic HBM bytes of the MAC of a batch: every source ciphertext
+    once per image, every distinct plaintext once per batch, every output
+    ciphertext once per image"""
+    total = 0
+    for st in prog.steps:
+        if st["kind"] != 1:
+            continue
+        W = (prog.tensors[st["src"]].level + 1) * N * 8
+        n_src = len({(int(i), int(b)) for i, b in zip(st["t_ct"], st["t_baby"])})
+        n_out = prog.tensors[st["dst"]].layout.n_ct
+        total += batch * (2 * W * n_src + 2 * W * n_out) + W * (len(st["vecs"]) + len(st["bias"]))
+    return total
 
 
 def plaintext_bytes(prog, N):
@@ -152,24 +229,6 @@ def plaintext_bytes(prog, N):
             n_pt = len(st["vecs"]) + len(st["bias"])
             total += n_pt * (prog.tensors[st["src"]].level + 1) * N * 8
     return total
-
-
-def oracle_ledger(prog, alpha):
-    """the same count on the oracle's program format"""
-    w = 0.0
-    for st in prog.steps:
-        src = st["src"][0] if isinstance(st["src"], list) else st["src"]
-        t_in = prog.tensors[src]
-        if st["op"] == "linear":
-            k = len(st["baby"]) + sum(1 for gs in st["groups"].values() for g in gs if g)
-        elif st["op"] == "act":
-            k = t_in.layout.n_ct
-        elif st["op"] == "rotsum":
-            k = t_in.layout.n_ct * len(st["steps"])
-        else:
-            k = 0
-        w += k * ks_weight(t_in.level, alpha)
-    return w
 
 
 # ===================================================================== ours
@@ -329,10 +388,20 @@ def run_ours(args, rank, world):
     achieved = ks_bytes / ks_total / 1e9
     ks_mm = g * ks_modmuls(lv, alpha, pre["logn"])
     alu_achieved = ks_mm / ks_total
+    # the integer peak at this GPU's SM count and the clock sampled under load
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_mhz = clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 2070.0
+    alu_peak = alu_peak_modmul(n_sm, sm_mhz)
+    traffic = KS_TRAFFIC["bytes"] if (KS_TRAFFIC["bytes"] and g == KS_TRAFFIC["items"] and lv == KS_TRAFFIC["level"]
+                                      and alpha == KS_TRAFFIC["alpha"]) else None
+    # the MAC of the uniform batch (its phase timed with events on the stream)
+    mac_mm = B * mac_products(prog, N)
+    mac_s = phase_ms["linear_mac"] / 1e3
+    mac_b = mac_bytes(prog, N, B)
     img_s_batch = aggregate_throughput(S * g, world, ms_batch)
     img_s_uniform = aggregate_throughput(B, world, ms_uniform)
     img_s_single = aggregate_throughput(1, world, ms_single)
-    n_ks, wks = program_ledger(prog, alpha)
+    n_ks, img_mm = image_modmuls(prog, alpha, pre["logn"])
 
     res = {
         "metric": METRIC,
@@ -363,8 +432,9 @@ def run_ours(args, rank, world):
             "single_ms_per_img": round(ms_single, 3),
             "batched_over_single": round(img_s_batch / img_s_single, 4),
             "keyswitches_per_img": n_ks,
-            "l2": "inputs larger than L2: every step streams %.1f GB of resident weight plaintexts "
-                  "(L2 is 0.13 GB)" % (plaintext_bytes(prog, N) / 1e9),
+            "l2": "inputs larger than L2: every tick streams the %.1f GB of resident weight plaintexts once "
+                  "(each segment its own layers'), %.0f GB per step; L2 is 0.13 GB"
+                  % (plaintext_bytes(prog, N) / 1e9, S * plaintext_bytes(prog, N) / 1e9),
             "setup_s": round(t_setup, 1),
             "uniform_batch_phase_ms": {k: round(v, 1) for k, v in phase_ms.items()},
             "parallelism": "replicas" if world > 1 else "single",
@@ -374,20 +444,32 @@ def run_ours(args, rank, world):
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
         "roofline": {"bound": "alu",
-                     "kernel": "hybrid key switch (10 kernels: ModUp, key inner product, exact ModDown), level %d, "
-                               "%d polynomials (one group of the pipeline)" % (lv, g),
-                     "achieved": round(alu_achieved / 1e9, 1), "peak": round(ALU_PEAK_MODMUL / 1e9, 1),
-                     "unit": "Gmodmul/s", "peak_kind": "derived (152 SMs x 64 IMAD/clk x 2.07 GHz / 10 IMAD "
-                                                       "per 64-bit modmul)",
-                     "frac": round(alu_achieved / ALU_PEAK_MODMUL, 4),
-                     "traffic": KS_TRAFFIC_L20_G4 if (g == 4 and lv == 20 and alpha == 7) else None,
+                     "kernel": "hybrid key switch (ModUp, key inner product, exact ModDown), level %d, "
+                               "%d polynomials (one group of the pipeline), timed by CUDA events on its stream "
+                               "right after the timed region" % (lv, g),
+                     "achieved": round(alu_achieved / 1e9, 1), "peak": round(alu_peak / 1e9, 1),
+                     "unit": "Gmodmul/s",
+                     "peak_kind": "derived: %d SMs x %d IMAD/clk x %.0f MHz (median sampled SM clock) / %d IMAD "
+                                  "per 64-bit Shoup product" % (n_sm, IMAD_PER_CLK_SM, sm_mhz, IMAD_PER_MODMUL),
+                     "frac": round(alu_achieved / alu_peak, 4),
+                     "traffic": traffic,
+                     "traffic_from": (("ncu capture of these kernels, %s" % KS_TRAFFIC["captured"]) if traffic
+                                      else "no capture of the current kernels at this configuration"),
                      "algorithmic_modmuls": int(ks_mm),
                      "hbm": {"achieved_gbs": round(achieved, 1), "peak_gbs": peak, "peak_kind": peak_kind,
                              "frac": round(achieved / peak, 4), "algorithmic_bytes": int(ks_bytes)},
-                     "kernel_ms": {k: round(v, 4) for k, v in zip(KS_KERNELS, ks_ms)}},
+                     "kernel_ms": {k: round(v, 4) for k, v in zip(KS_KERNELS, ks_ms)},
+                     "mac": {"kernel": "plaintext MAC of the linear layers, uniform batch of %d (phase timed by "
+                                       "CUDA events)" % B,
+                             "achieved": round(mac_mm / mac_s / 1e9, 1), "peak": round(alu_peak / 1e9, 1),
+                             "unit": "Gmodmul/s", "frac": round(mac_mm / mac_s / alu_peak, 4),
+                             "algorithmic_products": int(mac_mm),
+                             "hbm": {"achieved_gbs": round(mac_b / mac_s / 1e9, 1), "peak_gbs": peak,
+                                     "frac": round(mac_b / mac_s / 1e9 / peak, 4),
+                                     "algorithmic_bytes": int(mac_b)}}},
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        res["cpu_baseline"] = cpu_baseline(prog, wks, pre)
+        res["cpu_baseline"] = cpu_baseline(img_mm, pre)
     F.fhe_model_free(model)
     for h in cts:
         F.fhe_ct_free(h)
@@ -412,14 +494,64 @@ def oracle_rotation_seconds(pre, level):
     return time.perf_counter() - t0, S, keys, ct
 
 
-def cpu_baseline(prog, weighted_ks, pre):
+def _cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def _oracle_worker(pre, level, barrier, q):
+    """one process of the throughput sample: set up, wait for the others,
+    then time one rotation (wall-clock start and end)"""
+    _, S, keys, ct = oracle_rotation_seconds(pre, level)
+    barrier.wait()
+    t0 = time.time()
+    S.rotate(ct, 1, keys)
+    q.put((t0, time.time()))
+
+
+def oracle_rotation_throughput(pre, level, procs):
+    """rotations per second of `procs` oracle processes running at once (one
+    rotation each, started together)"""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    barrier = ctx.Barrier(procs)
+    q = ctx.Queue()
+    ps = [ctx.Process(target=_oracle_worker, args=(pre, level, barrier, q)) for _ in range(procs)]
+    for p in ps:
+        p.start()
+    spans = [q.get(timeout=600) for _ in ps]
+    for p in ps:
+        p.join(timeout=60)
+    return procs / (max(e for _, e in spans) - min(t for t, _ in spans))
+
+
+def cpu_baseline(img_mm, pre):
+    """The CPU oracle as it stands on this host: one top-level rotation on one
+    core, and the rotations per second of one process per core running at
+    once; both scaled to images by the image's key-switching work (modular
+    multiplications of the hoisted program, in units of one top-level
+    rotation)."""
+    unit = ks_modmuls(pre["L"], pre["alpha"], pre["logn"])
+    rot_per_img = img_mm / unit
     secs = oracle_rotation_seconds(pre, pre["L"])[0]
-    per_img = secs * weighted_ks / ks_weight(pre["L"], pre["alpha"])
-    return {"value": round(1.0 / per_img, 8), "unit": "img/s", "cores": 1, "kind": "oracle",
-            "sample": "one hybrid-key-switch rotation at the top level (N=2^16, 21 + %d primes) timed on the CPU "
-                      "oracle (%.1f s), scaled by the image's key switches weighted by limb transforms "
-                      "(%.0f top-level equivalents); plaintext products and additions not counted" %
-                      (pre["alpha"], secs, weighted_ks / ks_weight(pre["L"], pre["alpha"]))}
+    nproc = os.cpu_count() or 1
+    procs = max(1, min(nproc, 32))
+    rps = oracle_rotation_throughput(pre, pre["L"], procs)
+    return {"value": round(rps / rot_per_img, 8), "unit": "img/s", "cores": procs, "kind": "oracle",
+            "nproc": nproc, "cpu_model": _cpu_model(),
+            "single_core_img_s": round(1.0 / (secs * rot_per_img), 8),
+            "sample": "hybrid-key-switch rotations at the top level (N=2^16, 21 + %d primes) on the CPU oracle: "
+                      "one on one core (%.1f s), then one per process in %d processes at once (%.3f rotations/s); "
+                      "scaled to images by the image's key-switching work with hoisting (%.0f top-level "
+                      "rotation equivalents); plaintext products and additions not counted" %
+                      (pre["alpha"], secs, procs, rps, rot_per_img)}
 
 
 def run_reference(args, rank, world):
@@ -439,7 +571,7 @@ def run_reference(args, rank, world):
     comp = cnn.Compiler(prm, "packed", giants, 1, lam)
     comp.n = 1 << (pre["logn"] - 1)
     prog = comp.compile(net, cnn.transform(net, raw))
-    unit = oracle_ledger(prog, pre["alpha"]) / ks_weight(pre["L"], pre["alpha"])
+    unit = oracle_image_modmuls(prog, pre["alpha"], pre["logn"]) / ks_modmuls(pre["L"], pre["alpha"], pre["logn"])
     _, S, keys, ct = oracle_rotation_seconds(pre, pre["L"])
     for _ in range(args.warmup):
         S.rotate(ct, 1, keys)
@@ -502,7 +634,7 @@ def run_resnet18(args):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
-    n_ks, _ = program_ledger(prog, pre["alpha"])
+    n_ks, _ = image_modmuls(prog, pre["alpha"], pre["logn"])
     res = {"workload": "ResNet-18 ensemble of 3 (64x64x3, 200 classes), HW layout, 16 joint clusters per layer; "
                        "CKKS N=2^16, 19 + %d primes" % pre["alpha"],
            "batch": B, "img_s": round(B / (ms / 1e3), 4), "ms_per_batch": round(ms, 1),

@@ -325,10 +325,18 @@ int fhe_pipeline_info(const fhe_pipeline *pipe, int *n_segments, int *group, int
  * n_in_ct each; n_in may be 0).  out (capacity group * n_out_ct) receives the
  * output ciphertexts of the group that leaves this tick, *n_out its image
  * count (0 while the pipeline fills) and *out_tag the tick at which that
- * group entered (-1 if none).  Synchronous.
+ * group entered (-1 if none).  Synchronous.  The tick at which this call's
+ * images enter is the value fhe_pipeline_ticks reports before the call.
+ * Errors: a refusal found before launch (bad arguments, FHE_E_OOM for the
+ * output ciphertexts) changes nothing: no image enters, the tick is not
+ * counted, and the group due to leave leaves at the next call.  A failure
+ * after launch (FHE_E_CUDA) still counts the tick and enters the images;
+ * *n_out is then 0 and *out_tag names the group whose outputs were lost.
  */
 int fhe_pipeline_tick(fhe_pipeline *pipe, const fhe_ct *const *in, size_t n_in, fhe_ct **out, size_t *n_out,
                       int64_t *out_tag);
+/* Ticks counted so far (the entry tick of the next admitted group). */
+int fhe_pipeline_ticks(const fhe_pipeline *pipe, int64_t *ticks);
 int fhe_pipeline_free(fhe_pipeline *pipe);
 
 /*
@@ -395,7 +403,10 @@ int fhe_profile_keyswitch(fhe_ctx *ctx, const fhe_evk *evk, int level, int n_ite
  * 131072 words, i.e. two polynomials at N = 2^16), held by every GPU that
  * loads the library until the process exits; larger sizes are rejected with
  * FHE_E_INVAL.  The first call on a device looks up that array's device
- * address (cudaGetSymbolAddress): make it before any stream capture.  All
+ * address (cudaGetSymbolAddress): make it before any stream capture.  That
+ * address is kept for the life of the device's primary context: after
+ * cudaDeviceReset (or anything else that destroys that context) do not call
+ * this entry point again in the same process.  All
  * calls share the array, so calls that overlap on the GPU (other streams,
  * other threads) race; serialise them.  Asynchronous on `stream`.
  */

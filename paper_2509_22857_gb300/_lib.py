@@ -109,6 +109,7 @@ def lib() -> ctypes.CDLL:
                                           ctypes.POINTER(c_int)]),
             "fhe_pipeline_tick": (c_int, [V, PP, c_size, PP, ctypes.POINTER(c_size),
                                           ctypes.POINTER(ctypes.c_int64)]),
+            "fhe_pipeline_ticks": (c_int, [V, ctypes.POINTER(ctypes.c_int64)]),
             "fhe_pipeline_free": (c_int, [V]),
             "fhe_server_create": (c_int, [V, V, PP]),
             "fhe_server_add_model": (c_int, [V, V, c_int, c_size, ctypes.POINTER(c_int)]),
@@ -418,6 +419,12 @@ def fhe_pipeline_tick(pipe, cts, n_in: int, out_capacity: int) -> Tuple[List[int
     return [out[i] for i in range(n_out.value * n_ct_out)], n_out.value, tag.value
 
 
+def fhe_pipeline_ticks(pipe) -> int:
+    t = ctypes.c_int64()
+    _check(lib().fhe_pipeline_ticks(pipe, ctypes.byref(t)))
+    return t.value
+
+
 def fhe_pipeline_free(pipe):
     _check(lib().fhe_pipeline_free(pipe))
 
@@ -500,5 +507,5 @@ EXPORTED = ["fhe_last_error", "fhe_kernel_launches", "fhe_ctx_create", "fhe_ctx_
             "fhe_model_free", "fhe_eval_conv", "fhe_eval_quad_act", "fhe_eval_pool_dense", "fhe_infer",
             "fhe_ntt_device", "fhe_evk_export", "fhe_sk_export", "fhe_encode_coeffs",
             "fhe_profile_keyswitch", "fhe_rescale_noalloc", "fhe_infer_profiled", "fhe_pipeline_create", "fhe_pipeline_info",
-            "fhe_pipeline_tick", "fhe_pipeline_free", "fhe_server_create", "fhe_server_add_model",
+            "fhe_pipeline_tick", "fhe_pipeline_ticks", "fhe_pipeline_free", "fhe_server_create", "fhe_server_add_model",
             "fhe_sk_import", "fhe_evk_import", "fhe_server_submit", "fhe_server_poll", "fhe_server_pause", "fhe_server_stats", "fhe_server_destroy"]

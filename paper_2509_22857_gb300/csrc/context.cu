@@ -473,6 +473,9 @@ extern "C" int fhe_ctx_create(const fhe_params *p, fhe_ctx **out) {
     }
     c->enc.init(c->logN);
     int r = build_tables(c.get());
+    // the tables' uploads complete before any stream of the caller uses them
+    if (r == FHE_OK && cudaDeviceSynchronize() != cudaSuccess)
+        r = fhe_fail(FHE_E_CUDA, std::string("table upload: ") + cudaGetErrorString(cudaGetLastError()));
     if (r != FHE_OK) {
         for (void *q : c->owned) dev_free(q);
         return r;
@@ -697,7 +700,10 @@ extern "C" int fhe_sk_import(fhe_ctx *c, const uint64_t *buf, size_t n_words, fh
     std::unique_ptr<fhe_sk> sk(new fhe_sk());
     sk->ctx = c;
     FHE_TRY(dev_alloc(c, (void **)&sk->s_ntt, w * 8));
-    const cudaError_t e = cudaMemcpy(sk->s_ntt, buf, w * 8, cudaMemcpyHostToDevice);
+    // synchronised: a pageable upload may return before its DMA lands, and
+    // the key is then used from other (non-blocking) streams
+    cudaError_t e = cudaMemcpy(sk->s_ntt, buf, w * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         dev_free(sk->s_ntt);
         return fhe_fail(FHE_E_CUDA, std::string("cudaMemcpy: ") + cudaGetErrorString(e));
@@ -744,6 +750,11 @@ extern "C" int fhe_evk_import(fhe_ctx *c, const int32_t *galois, size_t n_keys, 
             evk->galois[galois[i]] = d;
         const cudaError_t e = cudaMemcpy(d, keys[i], kw * 8, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) rc = fhe_fail(FHE_E_CUDA, std::string("cudaMemcpy: ") + cudaGetErrorString(e));
+    }
+    // as for the secret key: the uploads complete before the keys are used
+    if (rc == FHE_OK) {
+        const cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) rc = fhe_fail(FHE_E_CUDA, std::string("key upload: ") + cudaGetErrorString(e));
     }
     if (rc != FHE_OK) {
         fhe_evk_free(evk);

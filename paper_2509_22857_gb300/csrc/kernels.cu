@@ -997,26 +997,71 @@ __global__ void __launch_bounds__(256) k_mac(DevCtx c, MacArgs a, int tc) {
         U128 a00 = {0, 0}, a01 = {0, 0}, a10 = {0, 0}, a11 = {0, 0};   // [poly][coefficient]
         int cnt = 0;
         int t = G.term_begin;
-        // two terms per iteration: their loads are in flight together
-        for (; t + 2 <= G.term_end; t += 2) {
-            ulonglong2 p[2], x0[2], x1[2];
+        while (t < G.term_end) {
+            const int run = a.terms[t].run;
+            if (run <= 1 && t + 1 < G.term_end && a.terms[t + 1].run <= 1) {
+                // two single terms: their loads are in flight together
+                ulonglong2 p[2], x0[2], x1[2];
 #pragma unroll
-            for (int k = 0; k < 2; k++) {
-                const MacTerm T = a.terms[t + k];
-                const MacSrc S = a.srcs[T.src];
-                const u64 *sp = S.base + (long long)img * S.item + off;
-                p[k] = __ldg(reinterpret_cast<const ulonglong2 *>(T.pt + off));
-                x0[k] = *reinterpret_cast<const ulonglong2 *>(sp);
-                x1[k] = *reinterpret_cast<const ulonglong2 *>(sp + P);
-            }
+                for (int k = 0; k < 2; k++) {
+                    const MacTerm T = a.terms[t + k];
+                    const MacSrc S = a.srcs[T.src];
+                    const u64 *sp = S.base + (long long)img * S.item + off;
+                    p[k] = __ldg(reinterpret_cast<const ulonglong2 *>(T.pt + off));
+                    x0[k] = *reinterpret_cast<const ulonglong2 *>(sp);
+                    x1[k] = *reinterpret_cast<const ulonglong2 *>(sp + P);
+                }
 #pragma unroll
-            for (int k = 0; k < 2; k++) {
-                mac(a00, p[k].x, x0[k].x);
-                mac(a01, p[k].y, x0[k].y);
-                mac(a10, p[k].x, x1[k].x);
-                mac(a11, p[k].y, x1[k].y);
+                for (int k = 0; k < 2; k++) {
+                    mac(a00, p[k].x, x0[k].x);
+                    mac(a01, p[k].y, x0[k].y);
+                    mac(a10, p[k].x, x1[k].x);
+                    mac(a11, p[k].y, x1[k].y);
+                }
+                cnt += 2;
+                t += 2;
+            } else {
+                // one term, or a run of terms sharing one plaintext: the
+                // run's sources are added mod q (two at a time), then one
+                // product
+                const MacTerm T = a.terms[t];
+                const int len = run < 1 ? 1 : run;
+                const u64 *sp = a.srcs[T.src].base + (long long)img * a.srcs[T.src].item + off;
+                const ulonglong2 p = __ldg(reinterpret_cast<const ulonglong2 *>(T.pt + off));
+                ulonglong2 s0 = *reinterpret_cast<const ulonglong2 *>(sp);
+                ulonglong2 s1 = *reinterpret_cast<const ulonglong2 *>(sp + P);
+                int r = 1;
+                for (; r + 2 <= len; r += 2) {
+                    ulonglong2 y0[2], y1[2];
+#pragma unroll
+                    for (int k = 0; k < 2; k++) {
+                        const MacSrc S = a.srcs[a.terms[t + r + k].src];
+                        const u64 *q = S.base + (long long)img * S.item + off;
+                        y0[k] = *reinterpret_cast<const ulonglong2 *>(q);
+                        y1[k] = *reinterpret_cast<const ulonglong2 *>(q + P);
+                    }
+#pragma unroll
+                    for (int k = 0; k < 2; k++) {
+                        s0 = make_ulonglong2(add_mod(s0.x, y0[k].x, m.q), add_mod(s0.y, y0[k].y, m.q));
+                        s1 = make_ulonglong2(add_mod(s1.x, y1[k].x, m.q), add_mod(s1.y, y1[k].y, m.q));
+                    }
+                }
+                if (r < len) {
+                    const MacSrc S = a.srcs[a.terms[t + r].src];
+                    const u64 *q = S.base + (long long)img * S.item + off;
+                    const ulonglong2 y0 = *reinterpret_cast<const ulonglong2 *>(q);
+                    const ulonglong2 y1 = *reinterpret_cast<const ulonglong2 *>(q + P);
+                    s0 = make_ulonglong2(add_mod(s0.x, y0.x, m.q), add_mod(s0.y, y0.y, m.q));
+                    s1 = make_ulonglong2(add_mod(s1.x, y1.x, m.q), add_mod(s1.y, y1.y, m.q));
+                }
+                mac(a00, p.x, s0.x);
+                mac(a01, p.y, s0.y);
+                mac(a10, p.x, s1.x);
+                mac(a11, p.y, s1.y);
+                cnt += 1;
+                t += len;
             }
-            cnt += 2;
+            // at most two products before the next check
             if (cnt + 2 > kmax) {
                 a00 = U128{barrett(a00, m), 0};
                 a01 = U128{barrett(a01, m), 0};
@@ -1024,18 +1069,6 @@ __global__ void __launch_bounds__(256) k_mac(DevCtx c, MacArgs a, int tc) {
                 a11 = U128{barrett(a11, m), 0};
                 cnt = 0;
             }
-        }
-        if (t < G.term_end) {
-            const MacTerm T = a.terms[t];
-            const MacSrc S = a.srcs[T.src];
-            const u64 *sp = S.base + (long long)img * S.item + off;
-            const ulonglong2 p = __ldg(reinterpret_cast<const ulonglong2 *>(T.pt + off));
-            const ulonglong2 x0 = *reinterpret_cast<const ulonglong2 *>(sp);
-            const ulonglong2 x1 = *reinterpret_cast<const ulonglong2 *>(sp + P);
-            mac(a00, p.x, x0.x);
-            mac(a01, p.y, x0.y);
-            mac(a10, p.x, x1.x);
-            mac(a11, p.y, x1.y);
         }
         u64 *o = G.out + (long long)img * G.out_item + off;
         const ulonglong2 b = G.bias ? __ldg(reinterpret_cast<const ulonglong2 *>(G.bias + off)) : make_ulonglong2(0, 0);

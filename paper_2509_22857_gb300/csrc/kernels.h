@@ -153,14 +153,17 @@ cudaError_t launch_decrypt(const DevCtx &c, const u64 *ct, const u64 *s_ntt, u64
 // Plaintext-ciphertext multiply-accumulate of a linear layer.  Output group
 // g (one accumulator ciphertext per image) is
 //   out_g = sum_{t in terms(g)} pt_t (.) srcs[src_t]   (+ bias_g on poly 0)
-// where a source is a ciphertext tensor (image i at base + i*item).
+// where a source is a ciphertext tensor (image i at base + i*item).  Terms
+// that share a plaintext (clustered weights) may be given as a run: the
+// run's sources are added mod q first and multiplied by the plaintext once
+// (grouped accumulation; the same residues, fewer products).
 struct MacSrc {
     const u64 *base;      // image 0's ciphertext (2 polys x (level+1) limbs)
     long long item;       // per-image stride
 };
 struct MacTerm {
     int src;              // index into srcs
-    int pad_;
+    int run;              // first term of a run: the run's length (terms that share pt, consecutive); else 0 or 1
     const u64 *pt;        // plaintext limbs (level+1) x N
 };
 struct MacGroup {

@@ -314,10 +314,20 @@ struct Exec {
         auto key = std::make_pair(pers->variant, cur_step * 65536 + list_sub);
         auto it = pers->lists.find(key);
         if (it == pers->lists.end()) {
+            // Lists are made by the eager ticks that precede any capture.  The
+            // upload is ordered on this executor's own stream (non-blocking):
+            // a plain cudaMemcpy from pageable memory runs on the legacy
+            // stream and may return before its DMA lands, so a kernel on
+            // this stream could read a partly written list.
+            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+            FHE_CU(cudaStreamIsCapturing(s, &cs));
+            if (cs != cudaStreamCaptureStatusNone)
+                return fhe_fail(FHE_E_INVAL, "internal: work list first needed inside a graph capture");
             void *p;
             FHE_TRY(dev_alloc(m->ctx, &p, bytes + 16));
             pers->owned.push_back(p);
-            FHE_CU(cudaMemcpy(p, host, bytes, cudaMemcpyHostToDevice));
+            FHE_CU(cudaMemcpyAsync(p, host, bytes, cudaMemcpyHostToDevice, s));
+            FHE_CU(cudaStreamSynchronize(s));
             it = pers->lists.emplace(key, (char *)p).first;
         }
         *out = it->second;
@@ -481,10 +491,24 @@ struct Exec {
                 for (int t = tb; t < tc; t++) {
                     MacTerm T;
                     T.src = src_of(L.t_ct[t], L.t_baby[t]);
-                    T.pad_ = 0;
+                    T.run = 1;
                     if (T.src < 0) return fhe_fail(FHE_E_INVAL, "internal: missing baby rotation");
                     T.pt = L.t_pt[t];
                     ht.push_back(T);
+                }
+                // grouped accumulation: the group's terms that share a
+                // plaintext become one run (sources summed, one product);
+                // the sum mod q does not depend on the order of the terms
+                std::stable_sort(ht.begin() + G.term_begin, ht.end(),
+                                 [](const MacTerm &x, const MacTerm &y) { return x.pt < y.pt; });
+                for (int t = G.term_begin; t < (int)ht.size();) {
+                    int e = t + 1;
+                    while (e < (int)ht.size() && ht[e].pt == ht[t].pt) {
+                        ht[e].run = 0;
+                        e++;
+                    }
+                    ht[t].run = e - t;
+                    t = e;
                 }
                 G.term_end = (int)ht.size();
                 hg.push_back(G);
@@ -1026,23 +1050,8 @@ extern "C" int fhe_pipeline_info(const fhe_pipeline *p, int *n_segments, int *gr
     return FHE_OK;
 }
 
-extern "C" int fhe_pipeline_tick(fhe_pipeline *p, const fhe_ct *const *in, size_t n_in, fhe_ct **out, size_t *n_out,
-                                 int64_t *out_tag) {
-    if (!p || !n_out || !out_tag || (n_in && !in) || n_in > (size_t)p->g) return fhe_fail(FHE_E_INVAL, "bad argument");
-    fhe_ctx *c = p->ctx;
-    fhe_model *m = p->m;
-    FHE_CU(cudaSetDevice(c->dev));
-    const int par = (int)(p->tick & 1);
-    const MTensor &ti = m->tensors[m->input];
-    const long long cs_in = 2ll * (ti.level + 1) * c->N;
-    for (size_t k = 0; k < n_in * ti.n_ct; k++) {
-        if (!in[k] || in[k]->level != ti.level || in[k]->n_poly != 2)
-            return fhe_fail(FHE_E_LEVEL, "input ciphertext level / shape does not match the model");
-    }
-    for (size_t k = 0; k < n_in * ti.n_ct; k++)
-        FHE_CU(cudaMemcpyAsync(p->cutbuf[par][0].at(m->input) + k * cs_in, in[k]->d, cs_in * 8,
-                               cudaMemcpyDeviceToDevice, p->main));
-    p->entered.push_back((int)n_in);
+// The tick's launches, after its inputs are copied in (see fhe_pipeline_tick).
+static int pipeline_launch(fhe_pipeline *p, int par) {
     if (p->graphs && (p->exec[par] || p->tick >= 2)) {
         if (!p->exec[par]) {
             cudaGraph_t g;
@@ -1063,34 +1072,94 @@ extern "C" int fhe_pipeline_tick(fhe_pipeline *p, const fhe_ct *const *in, size_
     } else {
         FHE_TRY(run_tick(p, par));
     }
-    // the group that entered S-1 ticks ago leaves now
+    return FHE_OK;
+}
+
+// One tick.  Everything that can be refused (arguments, the output
+// ciphertexts' memory) is settled before anything is launched, so a refusal
+// leaves the pipeline exactly as it was: no group entered, no tick counted,
+// and the group due to leave still leaves at the next call.  Once the tick is
+// launched it is counted whatever happens next, so the entry ticks of the
+// groups inside stay aligned with the tick counter; on a failure after the
+// launch *out_tag still names the group that was due to leave (its outputs
+// are lost) and *n_out is 0.
+extern "C" int fhe_pipeline_tick(fhe_pipeline *p, const fhe_ct *const *in, size_t n_in, fhe_ct **out, size_t *n_out,
+                                 int64_t *out_tag) {
+    if (!p || !n_out || !out_tag || (n_in && !in) || n_in > (size_t)p->g) return fhe_fail(FHE_E_INVAL, "bad argument");
     *n_out = 0;
     *out_tag = -1;
-    const long long entry = p->tick - (p->S - 1);
-    if (entry >= 0 && p->entered[entry] > 0) {
-        const MTensor &to = m->tensors[m->output];
-        const long long cs = 2ll * (to.level + 1) * c->N;
-        const u64 *src = p->cutbuf[1 - par][p->S].at(m->output);
-        const size_t cnt = (size_t)p->entered[entry] * to.n_ct;
-        for (size_t k = 0; k < cnt; k++) {
-            fhe_ct *o = new fhe_ct();
-            o->ctx = c;
-            o->level = to.level;
-            o->n_poly = 2;
-            o->scale = to.scale;
-            if (dev_alloc(c, (void **)&o->d, cs * 8) != FHE_OK) {
-                delete o;
-                for (size_t r = 0; r < k; r++) fhe_ct_free(out[r]);
-                return FHE_E_OOM;
-            }
-            FHE_CU(cudaMemcpyAsync(o->d, src + k * cs, cs * 8, cudaMemcpyDeviceToDevice, p->main));
-            out[k] = o;
-        }
-        *n_out = (size_t)p->entered[entry];
-        *out_tag = entry;
+    fhe_ctx *c = p->ctx;
+    fhe_model *m = p->m;
+    FHE_CU(cudaSetDevice(c->dev));
+    const int par = (int)(p->tick & 1);
+    const MTensor &ti = m->tensors[m->input];
+    const long long cs_in = 2ll * (ti.level + 1) * c->N;
+    for (size_t k = 0; k < n_in * ti.n_ct; k++) {
+        if (!in[k] || in[k]->level != ti.level || in[k]->n_poly != 2)
+            return fhe_fail(FHE_E_LEVEL, "input ciphertext level / shape does not match the model");
     }
-    FHE_CU(cudaStreamSynchronize(p->main));
+    // the group that entered S-1 ticks ago leaves at this tick: its output
+    // ciphertexts are allocated first
+    const MTensor &to = m->tensors[m->output];
+    const long long cs = 2ll * (to.level + 1) * c->N;
+    const long long entry = p->tick - (p->S - 1);
+    const int leaving = entry >= 0 ? p->entered[entry] : 0;
+    const size_t cnt = (size_t)leaving * to.n_ct;
+    for (size_t k = 0; k < cnt; k++) {
+        fhe_ct *o = new fhe_ct();
+        o->ctx = c;
+        o->level = to.level;
+        o->n_poly = 2;
+        o->scale = to.scale;
+        const int rc = dev_alloc(c, (void **)&o->d, cs * 8);
+        if (rc != FHE_OK) {
+            delete o;
+            for (size_t r = 0; r < k; r++) {
+                fhe_ct_free(out[r]);
+                out[r] = nullptr;
+            }
+            return rc;
+        }
+        out[k] = o;
+    }
+    auto drop_outputs = [&]() {
+        for (size_t k = 0; k < cnt; k++) {
+            fhe_ct_free(out[k]);
+            out[k] = nullptr;
+        }
+    };
+    for (size_t k = 0; k < n_in * ti.n_ct; k++) {
+        const cudaError_t e = cudaMemcpyAsync(p->cutbuf[par][0].at(m->input) + k * cs_in, in[k]->d, cs_in * 8,
+                                              cudaMemcpyDeviceToDevice, p->main);
+        if (e != cudaSuccess) {
+            drop_outputs();
+            return fhe_fail(FHE_E_CUDA, std::string("input copy: ") + cudaGetErrorString(e));
+        }
+    }
+    p->entered.push_back((int)n_in);
+    int rc = pipeline_launch(p, par);
     p->tick++;
+    if (leaving > 0) *out_tag = entry;
+    if (rc == FHE_OK) {
+        const u64 *src = p->cutbuf[1 - par][p->S].at(m->output);
+        for (size_t k = 0; k < cnt && rc == FHE_OK; k++) {
+            const cudaError_t e = cudaMemcpyAsync(out[k]->d, src + k * cs, cs * 8, cudaMemcpyDeviceToDevice, p->main);
+            if (e != cudaSuccess) rc = fhe_fail(FHE_E_CUDA, std::string("output copy: ") + cudaGetErrorString(e));
+        }
+    }
+    const cudaError_t se = cudaStreamSynchronize(p->main);
+    if (rc == FHE_OK && se != cudaSuccess) rc = fhe_fail(FHE_E_CUDA, std::string("tick: ") + cudaGetErrorString(se));
+    if (rc != FHE_OK) {
+        drop_outputs();
+        return rc;
+    }
+    *n_out = (size_t)leaving;
+    return FHE_OK;
+}
+
+extern "C" int fhe_pipeline_ticks(const fhe_pipeline *p, int64_t *ticks) {
+    if (!p || !ticks) return fhe_fail(FHE_E_INVAL, "null argument");
+    *ticks = p->tick;
     return FHE_OK;
 }
 

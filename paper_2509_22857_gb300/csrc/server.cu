@@ -84,24 +84,38 @@ static void worker_loop(fhe_server *sv, ModelSlot *ms) {
         for (auto &r : admit)
             for (auto *c : r.in) in.push_back(c);
         size_t n_done = 0;
-        int64_t tag = -1;
+        int64_t tag = -1, before = 0, after = 0;
+        fhe_pipeline_ticks(ms->pipe, &before);
         const int rc = fhe_pipeline_tick(ms->pipe, in.data(), admit.size(), out.data(), &n_done, &tag);
+        fhe_pipeline_ticks(ms->pipe, &after);
         for (auto &r : admit)
             for (auto *c : r.in) fhe_ct_free(c);
         std::lock_guard<std::mutex> lk(sv->mu);
+        // the pipeline's tick counter is the entry tick of each admitted group
+        const long long entry = before;
+        ms->tick = after;
         if (rc != FHE_OK) {
             sv->error = rc;
             sv->error_msg = fhe_last_error();
-            for (auto &r : admit) {
+            auto fail = [&](const Request &r) {
                 Result &res = sv->results[r.ticket];
                 res.done = true;
                 res.error = rc;
+            };
+            // this tick's admissions failed with it (refused before launch:
+            // they never entered; failed after: their state is unknown)
+            for (auto &r : admit) fail(r);
+            // the group that was due to leave lost its outputs
+            if (tag >= 0) {
+                auto it = ms->in_flight.find(tag);
+                if (it != ms->in_flight.end()) {
+                    for (auto &r : it->second) fail(r);
+                    ms->in_flight.erase(it);
+                }
             }
             sv->cv.notify_all();
             continue;
         }
-        const long long entry = ms->tick;
-        ms->tick++;
         if (!admit.empty()) {
             for (auto &r : admit) r.in.clear();
             ms->in_flight[entry] = std::move(admit);

@@ -317,7 +317,10 @@ CLASSIFIER_EXTRA_BITS = 6
 
 class Planner:
     def __init__(self, primes_q: Sequence[int], log_n: int, log_scale: float, layout: str, alpha: int = 3,
-                 max_giant_blocks: int = 8, members: int = 1, input_lambda: int = 1):
+                 max_giant_blocks: int = 8, members: int = 1, input_lambda: int = 1,
+                 giants: Optional[Sequence[int]] = None):
+        self.giants = None if giants is None else list(giants)
+        self.n_linear = 0
         self.members = members
         self.input_lambda = input_lambda
         self.alpha = alpha
@@ -372,6 +375,9 @@ class Planner:
     def _bsgs_step(self, src: int, terms: Terms, giant: int, dst_layout: SlotMap, w_scale: float,
                    bias_vecs: Dict[int, np.ndarray]) -> int:
         info = self.p.tensors[src]
+        if self.giants is not None:
+            giant = self.giants[self.n_linear]
+        self.n_linear += 1
         prod = info.scale * w_scale
         dst = self._t(dst_layout, info.level, prod)
         b = terms.r % giant
@@ -581,20 +587,23 @@ class Planner:
 
 
 def compile_network(net, raw, primes_q, log_n, log_scale, layout, alpha: int = 3,
-                    max_giant_blocks: int = 8, input_lambda: int = 1) -> Program:
+                    max_giant_blocks: int = 8, input_lambda: int = 1,
+                    giants: Optional[Sequence[int]] = None) -> Program:
     """raw: one model's raw parameters, or a list of them (an ensemble, laid
     out with layout "hw_ens": member m in block m of every ciphertext).
     alpha: digit width of key switching (for the baby-step / giant-step
     cost model); max_giant_blocks = 1 keeps the giant step at one block.
     input_lambda: the client encodes the image at scale Delta^input_lambda
     (the program's input tensor scale; 2 keeps every key switch of the
-    first layer at scale Delta^2)."""
+    first layer at scale Delta^2).  giants: the giant-step size of every
+    linear step in program order, in place of the planner's choice (any
+    split evaluates the same diagonals)."""
     raws = raw if isinstance(raw, (list, tuple)) else [raw]
     if len(raws) > 1 and layout != "hw_ens":
         raise ValueError("an ensemble needs the hw_ens layout")
     prms = [prepare_params(net, r) for r in raws]
     return Planner(primes_q, log_n, log_scale, layout, alpha, max_giant_blocks, len(raws),
-                   input_lambda).compile(net, prms)
+                   input_lambda, giants).compile(net, prms)
 
 
 def input_scale(prog: Program) -> float:

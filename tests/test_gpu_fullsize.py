@@ -113,3 +113,77 @@ def test_keyswitch_bit_exact_at_full_size():
         F.fhe_sk_free(sk)
     finally:
         F.fhe_ctx_destroy(ctx)
+
+
+def test_resnet20_first_layers_bit_exact_at_full_size():
+    """The bench's workload at its full size and launch shape: ResNet-20's
+    first packed convolution, the rescale and the activation after it, for
+    a batch of 4 images (the pipeline's group: 4 images per MAC CTA, 4
+    polynomials per key switch).  Image 0's ciphertexts equal the oracle's
+    limb for limb; images 1..3 equal their one-image runs."""
+    from oracle import ckks as O
+    from paper_2509_22857_gb300 import _lib as F
+    from paper_2509_22857_gb300 import model as M
+    pre = synth.PRESETS["resnet20"]
+    prm = O.make_params(**pre)
+    S = O.CKKS(prm)
+    lam = synth.INPUT_LAMBDA["resnet20"]
+    net = synth.resnet20()
+    raw = synth.params(net)
+    ctx = F.fhe_ctx_create(pre["logn"], pre["L"], pre["q_bits"], pre["q0_bits"], pre["p_bits"], pre["alpha"],
+                           pre["log_scale"])
+    try:
+        assert F.fhe_ctx_primes(ctx) == list(prm.primes)
+        pm = M.compile_network(net, raw, prm.primes[: pre["L"] + 1], pre["logn"], pre["log_scale"], "packed",
+                               pre["alpha"], input_lambda=lam)
+        po = cnn.compile_he(net, cnn.transform(net, raw), prm, "packed", M.giant_steps(pm), 1, lam)
+        n_first = 3
+        kinds = [st["kind"] for st in pm.steps[:n_first]]
+        assert kinds == [F.STEP_LINEAR, F.STEP_RESCALE, F.STEP_ACT]
+        assert [st["op"] for st in po.steps[:n_first]] == ["linear", "rescale", "act"]
+        # the program up to the first activation
+        head = M.Program(tensors=pm.tensors, steps=pm.steps[:n_first], input=pm.input,
+                         output=pm.steps[n_first - 1]["dst"])
+        st0 = pm.steps[0]
+        rots = sorted({int(b) for b in st0["t_baby"] if b} | {int(g) for g in st0["t_giant"] if g})
+        head.rotations = set(rots)
+        sk, evk = F.fhe_keygen(ctx, synth.SEED_KEYS, rots)
+        desc = M.ModelDesc(head, prm.N // 2)
+        model = F.fhe_model_load(ctx, desc.desc)
+        n_out = pm.tensors[head.output].layout.n_ct
+        B = 4
+        cts = []
+        for i in range(B):
+            img = synth.image(i, 3, 32, 32)
+            for k, v in enumerate(M.input_slots(pm, img, prm.N // 2)):
+                pt = F.fhe_encode(ctx, v, M.input_scale(pm), pre["L"])
+                cts.append(F.fhe_encrypt(ctx, sk, pt, synth.enc_seed(i, k)))
+                F.fhe_pt_free(pt)
+        n_in = len(cts) // B
+        batched = F.fhe_infer(ctx, model, evk, cts, B, n_out)
+        got = [F.fhe_ct_export(h, prm.N) for h in batched]
+        for i in range(1, B):
+            alone = F.fhe_infer(ctx, model, evk, cts[i * n_in:(i + 1) * n_in], 1, n_out)
+            for a, b in zip(alone, got[i * n_out:(i + 1) * n_out]):
+                assert np.array_equal(F.fhe_ct_export(a, prm.N)[0], b[0]), i
+                F.fhe_ct_free(a)
+        for h in batched + cts:
+            F.fhe_ct_free(h)
+        F.fhe_model_free(model)
+        F.fhe_evk_free(evk)
+        F.fhe_sk_free(sk)
+        # the oracle, image 0
+        keys = S.keygen(synth.SEED_KEYS, sorted({b for (_, b) in po.steps[0]["baby"]} |
+                                                {g for o in po.steps[0]["groups"] for g in po.steps[0]["groups"][o]
+                                                 if g}))
+        ocs = cnn.encrypt_input(S, keys, po, synth.image(0, 3, 32, 32), 0, synth.enc_seed)
+        vals = cnn.run_he(S, keys, po, ocs, stop_after=n_first - 1)
+        ref = vals[po.steps[n_first - 1]["dst"]]
+        assert len(ref) == n_out
+        for (buf, lv, sc), r in zip(got[:n_out], ref):
+            assert lv == r.level and sc == r.scale
+            want = np.stack([np.stack([O.intt(r.c[p, t], prm.primes[t], prm.psi[t]) for t in range(r.level + 1)])
+                             for p in range(2)])
+            assert np.array_equal(buf, want)
+    finally:
+        F.fhe_ctx_destroy(ctx)

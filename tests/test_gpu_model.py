@@ -191,3 +191,82 @@ def test_chunked_linear_steps_change_nothing(setup):
         F.fhe_ct_free(h)
     with pytest.raises(F.FheError):
         F.fhe_ctx_set_linear_chunk(s.ctx, 1)
+
+
+def test_batch_of_nine_equals_one_at_a_time(setup):
+    """Nine images: the MAC runs 8 images per CTA (the shape of the bench's
+    uniform batch and of the ResNet-18 batch of 32) plus a ragged CTA of one
+    image; every image equals its one-image run (image 0 equals the oracle
+    in test_network_bit_exact_and_logits)."""
+    s = setup
+    F = s.F
+    n_out = s.pm.tensors[s.pm.output].layout.n_ct
+    B = 9
+    imgs = [s.encrypt(i)[1] for i in range(B)]
+    flat = [h for cts in imgs for h in cts]
+    batched = F.fhe_infer(s.ctx, s.model, s.evk, flat, B, n_out)
+    for i in range(B):
+        single = F.fhe_infer(s.ctx, s.model, s.evk, imgs[i], 1, n_out)
+        for a, b in zip(single, batched[i * n_out:(i + 1) * n_out]):
+            assert np.array_equal(F.fhe_ct_export(a, s.prm.N)[0], F.fhe_ct_export(b, s.prm.N)[0]), i
+            F.fhe_ct_free(a)
+    for h in batched + flat:
+        F.fhe_ct_free(h)
+
+
+@pytest.mark.parametrize("case", ["mini", "vgg_mini"])
+def test_oracle_chosen_schedule_bit_exact(case):
+    """The oracle compiles the network with a baby-step / giant-step split it
+    chooses itself (its default: one block per convolution, eight for the
+    packed dense layer), the GPU program is compiled with that split in
+    place of its planner's, and the output ciphertexts are equal: the GPU
+    path is checked on a schedule its own planner did not produce."""
+    from paper_2509_22857_gb300 import _lib as F
+    from paper_2509_22857_gb300 import model as M
+    arch, preset, layout = CASES[case][:3]
+    lam = CASES[case][3] if len(CASES[case]) > 3 else 1
+    net = synth.ARCHS[arch]()
+    raw = synth.params(net)
+    pre = synth.PRESETS[preset]
+    prm = O.make_params(**pre)
+    S = O.CKKS(prm)
+    po = cnn.compile_he(net, cnn.transform(net, raw), prm, layout, None, 1, lam)
+    own = [st["giant"] for st in po.steps if st["op"] == "linear"]
+    ctx = F.fhe_ctx_create(pre["logn"], pre["L"], pre["q_bits"], pre["q0_bits"], pre["p_bits"], pre["alpha"],
+                           pre["log_scale"])
+    try:
+        planned = M.giant_steps(M.compile_network(net, raw, F.fhe_ctx_primes(ctx)[: pre["L"] + 1], pre["logn"],
+                                                  pre["log_scale"], layout, pre["alpha"], input_lambda=lam))
+        pm = M.compile_network(net, raw, F.fhe_ctx_primes(ctx)[: pre["L"] + 1], pre["logn"], pre["log_scale"],
+                               layout, pre["alpha"], input_lambda=lam, giants=own)
+        assert M.giant_steps(pm) == own
+        if case == "mini":
+            assert own != planned     # the planner would have split differently
+        assert pm.rotations == po.rot_steps
+        keys = S.keygen(synth.SEED_KEYS, sorted(po.rot_steps))
+        sk, evk = F.fhe_keygen(ctx, synth.SEED_KEYS, sorted(pm.rotations))
+        desc = M.ModelDesc(pm, prm.N // 2)
+        model = F.fhe_model_load(ctx, desc.desc)
+        inp = net[0]
+        img = synth.image(2, inp["c"], inp["h"], inp["w"])
+        cts = []
+        for k, v in enumerate(M.input_slots(pm, img, prm.N // 2)):
+            pt = F.fhe_encode(ctx, v, M.input_scale(pm), pre["L"])
+            cts.append(F.fhe_encrypt(ctx, sk, pt, synth.enc_seed(2, k)))
+            F.fhe_pt_free(pt)
+        n_out = pm.tensors[pm.output].layout.n_ct
+        outs = F.fhe_infer(ctx, model, evk, cts, 1, n_out)
+        ref = cnn.run_he(S, keys, po, cnn.encrypt_input(S, keys, po, img, 2, synth.enc_seed))[po.output_tensor]
+        for h, r in zip(outs, ref):
+            buf, lv, sc = F.fhe_ct_export(h, prm.N)
+            assert lv == r.level and sc == r.scale
+            want = np.stack([np.stack([O.intt(r.c[p, t], prm.primes[t], prm.psi[t]) for t in range(r.level + 1)])
+                             for p in range(2)])
+            assert np.array_equal(buf, want)
+        for h in outs + cts:
+            F.fhe_ct_free(h)
+        F.fhe_model_free(model)
+        F.fhe_evk_free(evk)
+        F.fhe_sk_free(sk)
+    finally:
+        F.fhe_ctx_destroy(ctx)

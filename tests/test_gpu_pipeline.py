@@ -76,3 +76,53 @@ def test_pipeline_equals_alone(mini, graphs):
         for h in cts:
             F.fhe_ct_free(h)
     F.fhe_pipeline_free(pipe)
+
+
+def test_refused_output_allocation_keeps_the_groups_aligned(mini):
+    """A tick whose output ciphertexts cannot be allocated is refused before
+    launch: nothing enters, the tick is not counted, and the group due to
+    leave leaves at the next call with the ciphertexts it gets alone."""
+    F, ctx, model, evk, encrypt, N = mini
+    pipe = F.fhe_pipeline_create(ctx, model, evk, 1, True)
+    S, g, n_in_ct, n_out_ct = F.fhe_pipeline_info(pipe)
+    entries, got = {}, {}
+
+    def tick(imgs, cts):
+        t = F.fhe_pipeline_ticks(pipe)
+        outs, n_out, tag = F.fhe_pipeline_tick(pipe, cts, len(imgs), n_out_ct)
+        entries[t] = imgs
+        if n_out:
+            assert entries[tag] and len(entries[tag]) == n_out
+            got[entries[tag][0]] = [F.fhe_ct_export(h, N)[0] for h in outs]
+        for h in outs:
+            F.fhe_ct_free(h)
+
+    for i in range(S - 1):
+        cts = encrypt(i)
+        tick([i], cts)
+        for h in cts:
+            F.fhe_ct_free(h)
+    assert not got
+    cts = encrypt(S - 1)
+    before = F.fhe_pipeline_ticks(pipe)
+    F.fhe_ctx_inject_alloc_failure(ctx, 0)    # the leaving image's output ciphertext
+    with pytest.raises(F.FheError) as e:
+        F.fhe_pipeline_tick(pipe, cts, 1, n_out_ct)
+    assert e.value.code == F.FHE_E_OOM
+    assert F.fhe_pipeline_ticks(pipe) == before
+    tick([S - 1], cts)
+    assert sorted(got) == [0]
+    for h in cts:
+        F.fhe_ct_free(h)
+    for _ in range(S):
+        tick([], [])
+    assert sorted(got) == list(range(S))
+    for i in range(S):
+        cts = encrypt(i)
+        alone = F.fhe_infer(ctx, model, evk, cts, 1, n_out_ct)
+        for a, b in zip(alone, got[i]):
+            assert np.array_equal(F.fhe_ct_export(a, N)[0], b), i
+            F.fhe_ct_free(a)
+        for h in cts:
+            F.fhe_ct_free(h)
+    F.fhe_pipeline_free(pipe)
