@@ -124,7 +124,7 @@ def alu_peak_modmul(n_sm: int, sm_mhz: float) -> float:
 # summed over its kernels from one ncu capture of the kernels as they are
 # now (taken 2026-12-04, digit width 7, level 20); reported only for that
 # configuration and only while those kernels are unchanged.
-KS_TRAFFIC = {"bytes": None, "level": 20, "items": 4, "alpha": 7, "captured": None}
+KS_TRAFFIC = {"bytes": 2721573888, "level": 20, "items": 8, "alpha": 7, "captured": "2026-12-04"}
 
 
 def ks_parts(level, alpha, logn):
@@ -322,7 +322,17 @@ def run_ours(args, rank, world):
     probe = F.fhe_pipeline_create(ctx, model, evk, 1, False)
     S = F.fhe_pipeline_info(probe)[0]
     F.fhe_pipeline_free(probe)
-    g = max(1, -(-B // S))
+    group_tuning = None
+    if args.tune_group:
+        from paper_2509_22857_gb300 import autotune as A
+        images = [cts[i * n_in:(i + 1) * n_in] for i in range(B)]
+        group_tuning = A.tune_pipeline_group(A.Tuner(args.autotune_cache), ctx, model, evk, images, n_out, N,
+                                             candidates=(2, 4, 8), model_key=PRESET)
+        g = group_tuning["best"]
+    elif args.group:
+        g = args.group
+    else:
+        g = max(1, -(-B // S))
     pipe = F.fhe_pipeline_create(ctx, model, evk, g, True)
     state = {"next": 0}
 
@@ -334,11 +344,15 @@ def run_ours(args, rank, world):
         for h in outs:
             F.fhe_ct_free(h)
 
+    # one step = T ticks; a group of g images leaves per tick once the
+    # pipeline is full (every tick runs every segment, full or not)
+    T = args.ticks if args.ticks > 0 else S
+
     def pipe_step():
-        for _ in range(S):
+        for _ in range(T):
             tick(lambda i: cts[i * n_in:(i + 1) * n_in])
 
-    for _ in range(max(1, args.warmup)):
+    for _ in range(max(args.warmup, -(-S // T))):     # at least one fill of the pipeline
         pipe_step()
     clk = Clocks(dev)
     clk.start()
@@ -356,7 +370,7 @@ def run_ours(args, rank, world):
     lvl_in, sc_in = pre["L"], M.input_scale(prog)
 
     def e2e_step():
-        for _ in range(S):
+        for _ in range(T):
             i0 = state["next"] % B
             hs = [F.fhe_ct_import(ctx, host_in[((i0 + i) % B) * n_in + k], lvl_in, sc_in)
                   for i in range(g) for k in range(n_in)]
@@ -371,8 +385,8 @@ def run_ours(args, rank, world):
     ms_e2e = timed(e2e_step, max(1, args.steps))
     F.fhe_pipeline_free(pipe)
     out_level = prog.tensors[prog.output].level
-    h2d = S * g * n_in * 2 * (pre["L"] + 1) * N * 8
-    d2h = S * g * n_out * 2 * (out_level + 1) * N * 8
+    h2d = T * g * n_in * 2 * (pre["L"] + 1) * N * 8
+    d2h = T * g * n_out * 2 * (out_level + 1) * N * 8
 
     # key-switch roofline at the top level, batch of B (the pipeline that
     # dominates the step): algorithmic bytes per switched polynomial =
@@ -398,7 +412,7 @@ def run_ours(args, rank, world):
     mac_mm = B * mac_products(prog, N)
     mac_s = phase_ms["linear_mac"] / 1e3
     mac_b = mac_bytes(prog, N, B)
-    img_s_batch = aggregate_throughput(S * g, world, ms_batch)
+    img_s_batch = aggregate_throughput(T * g, world, ms_batch)
     img_s_uniform = aggregate_throughput(B, world, ms_uniform)
     img_s_single = aggregate_throughput(1, world, ms_single)
     n_ks, img_mm = image_modmuls(prog, alpha, pre["logn"])
@@ -422,10 +436,13 @@ def run_ours(args, rank, world):
                         "special primes, digit width %d (dnum %d); channel-packed layout"
                         % (pre["log_scale"], pre["q0_bits"], pre["L"], pre["q_bits"], pre["alpha"], pre["p_bits"],
                            pre["alpha"], -(-(pre["L"] + 1) // pre["alpha"])),
-            "batch": S * g,
+            "batch": T * g,
+            "in_flight": S * g,
             "mixed_levels": True,
-            "pipeline": "%d segments (cut after each activation), a group of %d images enters per tick; "
-                        "segments run on concurrent streams, each tick replayed from a CUDA graph" % (S, g),
+            "pipeline": "%d segments (cut after each activation), a group of %d images enters per tick, %d ticks "
+                        "per step; segments run on concurrent streams, each tick replayed from a CUDA graph"
+                        % (S, g, T),
+            "group_tuning": group_tuning,
             "uniform_batch": B,
             "uniform_batch_img_s": round(img_s_uniform, 4),
             "single_img_s": round(img_s_single, 4),
@@ -434,13 +451,13 @@ def run_ours(args, rank, world):
             "keyswitches_per_img": n_ks,
             "l2": "inputs larger than L2: every tick streams the %.1f GB of resident weight plaintexts once "
                   "(each segment its own layers'), %.0f GB per step; L2 is 0.13 GB"
-                  % (plaintext_bytes(prog, N) / 1e9, S * plaintext_bytes(prog, N) / 1e9),
+                  % (plaintext_bytes(prog, N) / 1e9, T * plaintext_bytes(prog, N) / 1e9),
             "setup_s": round(t_setup, 1),
             "uniform_batch_phase_ms": {k: round(v, 1) for k, v in phase_ms.items()},
             "parallelism": "replicas" if world > 1 else "single",
         },
         "clocks": clocks,
-        "e2e": {"value": round(aggregate_throughput(S * g, world, ms_e2e), 4), "unit": "img/s",
+        "e2e": {"value": round(aggregate_throughput(T * g, world, ms_e2e), 4), "unit": "img/s",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
         "roofline": {"bound": "alu",
@@ -607,7 +624,8 @@ def run_resnet18(args):
     ctx = F.fhe_ctx_create(pre["logn"], pre["L"], pre["q_bits"], pre["q0_bits"], pre["p_bits"], pre["alpha"],
                            pre["log_scale"], 0)
     net = synth.resnet18()
-    raws = synth.cluster_joint([synth.params(net, m) for m in range(3)], net, 16)
+    M_members = args.members
+    raws = synth.cluster_joint([synth.params(net, m) for m in range(M_members)], net, 16)
     prog = M.compile_network(net, raws, F.fhe_ctx_primes(ctx)[: pre["L"] + 1], pre["logn"], pre["log_scale"],
                              "hw_ens", pre["alpha"], input_lambda=synth.INPUT_LAMBDA["resnet18"])
     sk, evk = F.fhe_keygen(ctx, synth.SEED_KEYS, sorted(prog.rotations))
@@ -635,8 +653,9 @@ def run_resnet18(args):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     n_ks, _ = image_modmuls(prog, pre["alpha"], pre["logn"])
-    res = {"workload": "ResNet-18 ensemble of 3 (64x64x3, 200 classes), HW layout, 16 joint clusters per layer; "
-                       "CKKS N=2^16, 19 + %d primes" % pre["alpha"],
+    res = {"workload": "ResNet-18 ensemble of %d (64x64x3, 200 classes), HW layout, 16 joint clusters per layer; "
+                       "CKKS N=2^16, 19 + %d primes" % (M_members, pre["alpha"]),
+           "members": M_members,
            "batch": B, "img_s": round(B / (ms / 1e3), 4), "ms_per_batch": round(ms, 1),
            "phase_ms": {k: round(v, 1) for k, v in phase_ms.items()}, "setup_s": round(t_setup, 1),
            "keyswitches_per_img": n_ks, "distinct_plaintexts": sum(len(st["vecs"]) for st in prog.steps
@@ -650,33 +669,169 @@ def run_resnet18(args):
     F.fhe_ctx_destroy(ctx)
 
 
+def run_vgg11(args):
+    """VGG-11 (configuration A: 8 convolutions, 5 average pools, 3 dense
+    layers) on 32x32x3 images, channel-packed, N = 2^16: the packed
+    convolutions' plaintexts (239K rows, about 0.86 TB if encoded at once)
+    are encoded on the device each time their layer runs; the dense layers'
+    plaintexts stay resident.  One uniform batch through the whole network
+    (fhe_infer) and its phase split (its logits are checked against the
+    float64 network in tests/test_gpu_fullsize.py)."""
+    import torch
+    from paper_2509_22857_gb300 import _lib as F
+    from paper_2509_22857_gb300 import model as M
+    pre = synth.PRESETS["vgg11"]
+    N = 1 << pre["logn"]
+    B = args.batch
+    t0 = time.time()
+    ctx = F.fhe_ctx_create(pre["logn"], pre["L"], pre["q_bits"], pre["q0_bits"], pre["p_bits"], pre["alpha"],
+                           pre["log_scale"], 0)
+    net = synth.vgg11()
+    raw = synth.params(net)
+    prog = M.compile_network(net, raw, F.fhe_ctx_primes(ctx)[: pre["L"] + 1], pre["logn"], pre["log_scale"],
+                             "packed", pre["alpha"], input_lambda=synth.INPUT_LAMBDA["vgg11"], on_demand=True)
+    t_compile = time.time() - t0
+    sk, evk = F.fhe_keygen(ctx, synth.SEED_KEYS, sorted(prog.rotations))
+    desc = M.ModelDesc(prog, N // 2)
+    model = F.fhe_model_load(ctx, desc.desc)
+    t_setup = time.time() - t0
+    n_out = prog.tensors[prog.output].layout.n_ct
+    cts = []
+    for i in range(B):
+        img = synth.image(i, 3, 32, 32)
+        for k, v in enumerate(M.input_slots(prog, img, N // 2)):
+            pt = F.fhe_encode(ctx, v, M.input_scale(prog), pre["L"])
+            cts.append(F.fhe_encrypt(ctx, sk, pt, synth.enc_seed(i, k)))
+            F.fhe_pt_free(pt)
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    outs, phase_ms = F.fhe_infer_profiled(ctx, model, evk, cts, B, n_out, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    n_ks, _ = image_modmuls(prog, pre["alpha"], pre["logn"])
+    rows = sum(len(st["vecs"]) for st in prog.steps if st["kind"] == 1 and st["vecs"]
+               and isinstance(st["vecs"][0], M.SparseVec))
+    res = {"workload": "VGG-11 (config A, 8 conv + 3 dense, 32x32x3, 10 classes), channel-packed; CKKS N=2^16, "
+                       "%d + %d primes; packed convolutions' plaintexts encoded on demand" % (pre["L"] + 1,
+                                                                                            pre["alpha"]),
+           "batch": B, "img_s": round(B / (ms / 1e3), 4), "ms_per_batch": round(ms, 1),
+           "phase_ms": {k: round(v, 1) for k, v in phase_ms.items()}, "compile_s": round(t_compile, 1),
+           "setup_s": round(t_setup, 1), "keyswitches_per_img": n_ks, "rows_encoded_on_demand": rows,
+           "resident_plaintext_gb": round(plaintext_bytes(prog, N) / 1e9 - sum(
+               len(st["vecs"]) * (prog.tensors[st["src"]].level + 1) * N * 8 for st in prog.steps
+               if st["kind"] == 1 and st["vecs"] and isinstance(st["vecs"][0], M.SparseVec)) / 1e9, 2)}
+    print(json.dumps(res), flush=True)
+    for h in outs + cts:
+        F.fhe_ct_free(h)
+    F.fhe_model_free(model)
+    F.fhe_evk_free(evk)
+    F.fhe_sk_free(sk)
+    F.fhe_ctx_destroy(ctx)
+
+
+def run_resnet32(args):
+    """ResNet-32 (3 stages x 5 basic blocks) on 32x32x3 images on the
+    paper's own parameter set for it (appendix "Details on FHE Parameters",
+    Table 4: N = 2^16, Delta = 2^26, a 27-bit q_0 and 32 primes of ~52 bits,
+    one 54-bit special prime, so every prime is its own key-switching digit:
+    33 digits at the top level), channel-packed: one uniform batch through the
+    whole network (fhe_infer) and its phase split."""
+    import torch
+    from paper_2509_22857_gb300 import _lib as F
+    from paper_2509_22857_gb300 import model as M
+    pp = synth.PAPER_PARAMS["resnet32"]
+    N = 1 << pp["logn"]
+    B = args.batch
+    t0 = time.time()
+    ctx = F.fhe_ctx_create(pp["logn"], pp["L"], 0, 0, 0, pp["alpha"], pp["log_scale"], 0, primes=pp["q"] + pp["p"])
+    net = synth.resnet32()
+    raw = synth.params(net)
+    prog = M.compile_network(net, raw, pp["q"], pp["logn"], pp["log_scale"], "packed", pp["alpha"], input_lambda=2)
+    sk, evk = F.fhe_keygen(ctx, synth.SEED_KEYS, sorted(prog.rotations))
+    desc = M.ModelDesc(prog, N // 2)
+    model = F.fhe_model_load(ctx, desc.desc)
+    t_setup = time.time() - t0
+    n_out = prog.tensors[prog.output].layout.n_ct
+    cts = []
+    for i in range(B):
+        img = synth.image(i, 3, 32, 32)
+        for k, v in enumerate(M.input_slots(prog, img, N // 2)):
+            pt = F.fhe_encode(ctx, v, M.input_scale(prog), pp["L"])
+            cts.append(F.fhe_encrypt(ctx, sk, pt, synth.enc_seed(i, k)))
+            F.fhe_pt_free(pt)
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    outs, phase_ms = F.fhe_infer_profiled(ctx, model, evk, cts, B, n_out, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    n_ks, _ = image_modmuls(prog, pp["alpha"], pp["logn"])
+    res = {"workload": "ResNet-32 (16/32/64, 3x5 blocks), 32x32x3, 10 classes, channel-packed, on the paper's "
+                       "ResNet-32 parameter set: N=2^16, Delta=2^26, 27-bit q0 + 32 x ~52-bit, one 54-bit P "
+                       "(33 digits)",
+           "batch": B, "img_s": round(B / (ms / 1e3), 5), "s_per_img": round(ms / 1e3 / B, 3),
+           "ms_per_batch": round(ms, 1), "phase_ms": {k: round(v, 1) for k, v in phase_ms.items()},
+           "setup_s": round(t_setup, 1), "keyswitches_per_img": n_ks,
+           "plaintext_gb": round(plaintext_bytes(prog, N) / 1e9, 1),
+           "paper_cpu_s_per_img": {"value": 1833, "note": "ResNet-32 / CIFAR-10, slice clustering k=64, "
+                                                          "2x AMD EPYC 64-core, SEAL 4.1 (context only)"}}
+    print(json.dumps(res), flush=True)
+    for h in outs + cts:
+        F.fhe_ct_free(h)
+    F.fhe_model_free(model)
+    F.fhe_evk_free(evk)
+    F.fhe_sk_free(sk)
+    F.fhe_ctx_destroy(ctx)
+
+
 def run_serving(args):
     """Serving stream: Poisson arrivals (rate args.rate) of single-image
     requests drawn 50/30/20 from VGG-, ResNet-20- and ResNet-18-ensemble-
-    shaped models (their small forms, one ring N = 2^12 and one key set),
-    submitted to the continuous-batching server at their arrival times;
-    reports p50 / p99 latency and the images per second completed."""
+    shaped models, submitted to the continuous-batching server at their
+    arrival times; reports p50 / p99 latency and the images per second
+    completed.  --serving-size small: their small forms (one ring N = 2^12);
+    full: the full-size models at N = 2^16 in one context (ResNet-20's
+    21-prime chain; VGG-11 and the ResNet-18 ensemble are compiled on its
+    first 12 and 19 primes, VGG-11 with its convolutions' plaintexts encoded
+    on demand)."""
     from paper_2509_22857_gb300 import _lib as F
     from paper_2509_22857_gb300 import model as M
-    pre = synth.PRESETS["resnet18_mini"]
+    full = args.serving_size == "full"
+    pre = synth.PRESETS["resnet20" if full else "resnet18_mini"]
     N = 1 << pre["logn"]
     ctx = F.fhe_ctx_create(pre["logn"], pre["L"], pre["q_bits"], pre["q0_bits"], pre["p_bits"], pre["alpha"],
                            pre["log_scale"], 0)
-    primes = F.fhe_ctx_primes(ctx)[: pre["L"] + 1]
-    specs = [("vgg_mini", "packed", None), ("resnet_mini", "packed", None), ("resnet18_mini", "hw_ens", 3)]
+    chain = F.fhe_ctx_primes(ctx)
+    if full:
+        # every pipeline segment keeps its own encode scratch (1 GiB each)
+        # and its rotated copies (chunks of 40 sources; bit-neutral)
+        F.fhe_ctx_set_encode_scratch(ctx, 1 << 30)
+        F.fhe_ctx_set_linear_chunk(ctx, 40)
+        # (arch, layout, members, levels, on demand, clusters)
+        specs = [("vgg11", "packed", None, synth.PRESETS["vgg11"]["L"], True, 0),
+                 ("resnet20", "packed", None, pre["L"], False, 0),
+                 ("resnet18", "hw_ens", 3, synth.PRESETS["resnet18"]["L"], False, 16)]
+    else:
+        specs = [("vgg_mini", "packed", None, pre["L"], False, 0), ("resnet_mini", "packed", None, pre["L"], False, 0),
+                 ("resnet18_mini", "hw_ens", 3, pre["L"], False, 4)]
     progs, rots = [], set()
-    for arch, layout, members in specs:
+    for arch, layout, members, lv, od, k in specs:
         net = synth.ARCHS[arch]()
-        raw = synth.cluster_joint([synth.params(net, m) for m in range(members)], net, 4) if members else \
+        raw = synth.cluster_joint([synth.params(net, m) for m in range(members)], net, k) if members else \
             synth.params(net)
-        progs.append((net, M.compile_network(net, raw, primes, pre["logn"], pre["log_scale"], layout,
-                                             pre["alpha"])))
+        progs.append((net, M.compile_network(net, raw, chain[: lv + 1], pre["logn"], pre["log_scale"], layout,
+                                             pre["alpha"], input_lambda=2 if full else 1, on_demand=od)))
         rots |= progs[-1][1].rotations
     sk, evk = F.fhe_keygen(ctx, synth.SEED_KEYS, sorted(rots))
     descs = [M.ModelDesc(p, N // 2) for _, p in progs]
     models = [F.fhe_model_load(ctx, d.desc) for d in descs]
     server = F.fhe_server_create(ctx, evk)
-    mids = [F.fhe_server_add_model(server, m, 4) for m in models]
+    mids = [F.fhe_server_add_model(server, m, 1 if full else 4) for m in models]
     rng = np.random.default_rng(5)
     n_req = args.requests
     which = rng.choice(3, size=n_req, p=[0.5, 0.3, 0.2])
@@ -689,7 +844,7 @@ def run_serving(args):
         img = synth.image(r, inp["c"], inp["h"], inp["w"])
         cts = []
         for k, v in enumerate(M.input_slots(prog, img, N // 2)):
-            pt = F.fhe_encode(ctx, v, M.input_scale(prog), pre["L"])
+            pt = F.fhe_encode(ctx, v, M.input_scale(prog), prog.tensors[prog.input].level)
             cts.append(F.fhe_encrypt(ctx, sk, pt, synth.enc_seed(r, k)))
             F.fhe_pt_free(pt)
         reqs.append(cts)
@@ -711,13 +866,16 @@ def run_serving(args):
             F.fhe_ct_free(h)
     t_end = time.perf_counter()
     done, p50, p99 = F.fhe_server_stats(server)
-    per_model = {specs[k][0]: {"requests": int((which == k).sum()),
-                               "p50_ms": round(float(np.percentile([l for l, w in zip(lat, which) if w == k], 50)), 2),
-                               "p99_ms": round(float(np.percentile([l for l, w in zip(lat, which) if w == k], 99)), 2)}
+    def pct(k, q):
+        v = [l for l, w in zip(lat, which) if w == k]
+        return round(float(np.percentile(v, q)), 2) if v else None
+
+    per_model = {specs[k][0]: {"requests": int((which == k).sum()), "p50_ms": pct(k, 50), "p99_ms": pct(k, 99)}
                  for k in range(3)}
-    print(json.dumps({"workload": "serving: Poisson %.1f req/s, %d single-image requests, 50/30/20 VGG / ResNet-20 / "
-                                  "ResNet-18-ensemble shapes (small forms, N=2^12, %d primes)"
-                                  % (args.rate, n_req, pre["L"] + 1 + pre["alpha"]),
+    print(json.dumps({"workload": "serving: Poisson %.2f req/s, %d single-image requests, 50/30/20 VGG / ResNet-20 / "
+                                  "ResNet-18-ensemble shapes (%s, N=2^%d, %d primes)"
+                                  % (args.rate, n_req, "full size" if full else "small forms", pre["logn"],
+                                     pre["L"] + 1 + pre["alpha"]),
                       "completed": done, "p50_ms": round(p50, 2), "p99_ms": round(p99, 2),
                       "img_s": round(done / (t_end - t0), 3), "per_model": per_model}), flush=True)
     F.fhe_server_destroy(server)
@@ -789,16 +947,27 @@ def main():
     ap.add_argument("--ks-only", action="store_true", help="time only the top-level key switch")
     ap.add_argument("--ks-level", type=int, default=None)
     ap.add_argument("--alpha", type=int, default=None, help="--ks-only: digit width (special primes)")
-    ap.add_argument("--workload", default="resnet20", choices=["resnet20", "resnet18_ensemble", "serving"],
+    ap.add_argument("--workload", default="resnet20", choices=["resnet20", "resnet18_ensemble", "vgg11", "resnet32", "serving"],
                     help="resnet18_ensemble: one batch of the clustered ResNet-18 ensemble; serving: a Poisson "
                          "request stream through the server (neither is the bench line)")
     ap.add_argument("--profile-uniform", action="store_true",
                     help="run one uniform batch inside the NVTX range bench_timed and exit (for ncu launch lists)")
+    ap.add_argument("--members", type=int, default=3, help="resnet18_ensemble: ensemble members (1..8)")
     ap.add_argument("--requests", type=int, default=1000, help="serving: number of requests")
     ap.add_argument("--rate", type=float, default=20.0, help="serving: mean arrivals per second")
+    ap.add_argument("--serving-size", default="small", choices=["small", "full"],
+                    help="serving: the models' small forms (N=2^12) or full size (N=2^16)")
     ap.add_argument("--autotune", action="store_true",
                     help="rank the admissible digit widths by measured, census-weighted key-switch time and exit")
     ap.add_argument("--autotune-cache", default=None, help="--autotune: JSON cache file of the tuner")
+    ap.add_argument("--group", type=int, default=8,
+                    help="images per pipeline tick (8: the best of 2, 4, 8 measured by --tune-group on GB300; "
+                         "0: the uniform batch spread over the segments)")
+    ap.add_argument("--ticks", type=int, default=5,
+                    help="pipeline ticks per timed step (every tick runs every segment, i.e. the whole network, "
+                         "for the group at each level; a group of images leaves per tick)")
+    ap.add_argument("--tune-group", action="store_true",
+                    help="pick the pipeline's images per tick by measurement (2, 4, 8) before the timed run")
     args = ap.parse_args()
     if args.autotune:
         run_autotune(args)
@@ -808,6 +977,12 @@ def main():
         return
     if args.workload == "resnet18_ensemble":
         run_resnet18(args)
+        return
+    if args.workload == "vgg11":
+        run_vgg11(args)
+        return
+    if args.workload == "resnet32":
+        run_resnet32(args)
         return
     if args.workload == "serving":
         run_serving(args)

@@ -107,6 +107,12 @@ int fhe_ctx_primes(const fhe_ctx *ctx, uint64_t *out, size_t cap, size_t *n);
  * HW-layout layer are made and consumed a chunk at a time.  Returns
  * FHE_E_INVAL for a value below 2. */
 int fhe_ctx_set_linear_chunk(fhe_ctx *ctx, int lin_chunk_srcs);
+/* Device scratch, in bytes, for the plaintexts of a linear step encoded on
+ * demand (fhe_step_desc.sparse_vec_begin): each row takes N doubles of FFT
+ * buffer plus its limbs, and a step runs its output groups in batches whose
+ * distinct rows fit (at least one group per batch; default 4 GiB).
+ * Bit-neutral. */
+int fhe_ctx_set_encode_scratch(fhe_ctx *ctx, size_t bytes);
 /* Host-side fault injection (no counterpart in the paper): after `after`
  * further device allocations through the context succeed, the next one is
  * refused with FHE_E_OOM, as cudaMalloc's own refusal would be, and the
@@ -257,6 +263,22 @@ typedef struct {
     const int32_t *steps;
     /* DROP */
     int level;
+    /*
+     * LINEAR, encoded on demand (the paper's "Standard" evaluation, Sec. 5.2
+     * and its appendix tables, where plaintext encoding is part of the
+     * layer's cost): when sparse_vec_begin is non-null, vecs is unused and
+     * row v of the term vectors is given by its nonzero entries
+     * sparse_slot / sparse_val[sparse_vec_begin[v] .. sparse_vec_begin[v+1])
+     * (slots < n_slots).  Nothing of these rows is encoded at load: each
+     * time the step runs, the library encodes the plaintexts of a batch of
+     * output groups on the device (the host encoder's operations in its
+     * order, so the plaintexts are bit-identical to a resident encoding),
+     * multiplies, and reuses the buffer for the next batch.  For layers
+     * whose encoded plaintexts would not fit in device memory.
+     */
+    const int64_t *sparse_vec_begin; /* [n_vecs + 1] */
+    const int32_t *sparse_slot;      /* [nnz] */
+    const double *sparse_val;        /* [nnz] */
 } fhe_step_desc;
 
 typedef struct {

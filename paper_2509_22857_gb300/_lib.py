@@ -21,6 +21,7 @@ c_int, c_size, c_u64, c_double, c_void = (ctypes.c_int, ctypes.c_size_t, ctypes.
 P_U64 = ctypes.POINTER(ctypes.c_uint64)
 P_I32 = ctypes.POINTER(ctypes.c_int32)
 P_DBL = ctypes.POINTER(ctypes.c_double)
+P_I64 = ctypes.POINTER(ctypes.c_int64)
 PP = ctypes.POINTER(ctypes.c_void_p)
 
 
@@ -38,7 +39,8 @@ class FheStepDesc(ctypes.Structure):
                 ("term_vec_id", P_I32), ("n_vecs", c_int), ("vecs", P_DBL),
                 ("n_bias", c_int), ("bias_out", P_I32), ("bias_vec", P_DBL),
                 ("c1", c_double), ("c0", c_double), ("value", c_double),
-                ("n_steps", c_int), ("steps", P_I32), ("level", c_int)]
+                ("n_steps", c_int), ("steps", P_I32), ("level", c_int),
+                ("sparse_vec_begin", P_I64), ("sparse_slot", P_I32), ("sparse_val", P_DBL)]
 
 
 class FheModelDesc(ctypes.Structure):
@@ -75,6 +77,7 @@ def lib() -> ctypes.CDLL:
             "fhe_kernel_launches": (ctypes.c_uint64, []),
             "fhe_ctx_create": (c_int, [ctypes.POINTER(FheParams), PP]),
             "fhe_ctx_destroy": (c_int, [V]),
+            "fhe_ctx_set_encode_scratch": (c_int, [V, c_size]),
             "fhe_ctx_set_linear_chunk": (c_int, [V, c_int]),
             "fhe_ctx_inject_alloc_failure": (c_int, [V, c_int]),
             "fhe_ctx_primes": (c_int, [V, P_U64, c_size, ctypes.POINTER(c_size)]),
@@ -183,6 +186,10 @@ def fhe_ctx_set_linear_chunk(ctx, lin_chunk_srcs: int):
 
 def fhe_ctx_inject_alloc_failure(ctx, after: int):
     _check(lib().fhe_ctx_inject_alloc_failure(ctx, int(after)))
+
+
+def fhe_ctx_set_encode_scratch(ctx, n_bytes: int):
+    _check(lib().fhe_ctx_set_encode_scratch(ctx, int(n_bytes)))
 
 
 def fhe_ctx_primes(ctx) -> List[int]:
@@ -387,7 +394,8 @@ def fhe_infer(ctx, model, evk, cts, n_img: int, n_out_per_img: int, stream=None)
 
 
 PHASES = {2: "rescale", 3: "activation", 4: "rotsum", 5: "cmul", 6: "drop", 7: "add",
-          10: "linear_baby_rotations", 11: "linear_mac", 12: "linear_giant_rotations"}
+          10: "linear_baby_rotations", 11: "linear_mac", 12: "linear_giant_rotations",
+          13: "linear_encode_on_demand"}
 
 
 def fhe_infer_profiled(ctx, model, evk, cts, n_img: int, n_out_per_img: int, stream=None):
@@ -500,7 +508,7 @@ def fhe_sk_export(sk, n_words: int) -> np.ndarray:
 
 
 EXPORTED = ["fhe_last_error", "fhe_kernel_launches", "fhe_ctx_create", "fhe_ctx_destroy", "fhe_ctx_primes",
-            "fhe_ctx_set_linear_chunk", "fhe_ctx_inject_alloc_failure", "fhe_keygen",
+            "fhe_ctx_set_linear_chunk", "fhe_ctx_set_encode_scratch", "fhe_ctx_inject_alloc_failure", "fhe_keygen",
             "fhe_sk_free", "fhe_evk_free", "fhe_evk_galois", "fhe_encode", "fhe_pt_free", "fhe_encrypt",
             "fhe_decrypt", "fhe_decode", "fhe_ct_free", "fhe_ct_info", "fhe_ct_export", "fhe_ct_import",
             "fhe_rotate", "fhe_square", "fhe_rescale", "fhe_add", "fhe_mul_plain", "fhe_model_load",

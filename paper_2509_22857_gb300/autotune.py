@@ -20,6 +20,9 @@ hand, and the results are cached per device name and parameter set:
 * **Linear-step chunk size** (MAC sources per pass, `fhe_ctx_set_linear_chunk`):
   bit-neutral.  The tuner checks that every candidate gives identical
   ciphertexts and keeps the fastest.
+* **Pipeline group size** (images entering the mixed-level pipeline per
+  tick): bit-neutral; measured as images leaving per second, one pipeline
+  alive at a time.
 
 The NTT split (two passes of 2^ceil(logN/2) x 2^floor(logN/2)) and one limb
 per CTA row are compile-time choices of the kernels' templates and are not
@@ -193,3 +196,61 @@ def tune_linear_chunk(tuner: Tuner, ctx, model, evk, cts, n_img: int, n_out: int
     best = min(candidates, key=lambda c: (ms[c], c))
     F.fhe_ctx_set_linear_chunk(ctx, best)
     return tuner.record(key, {"best": best, "ms": {str(c): round(t, 3) for c, t in ms.items()}})
+
+
+def tune_pipeline_group(tuner: Tuner, ctx, model, evk, image_cts: Sequence[Sequence[int]], n_out: int, N: int,
+                        candidates: Sequence[int] = (2, 4, 8), steps: int = 1, F=None,
+                        device: Optional[str] = None, model_key: str = "",
+                        sync: Optional[Callable] = None) -> dict:
+    """Images per tick of the mixed-level pipeline (fhe_pipeline_*): for each
+    candidate group g, one pipeline (only one alive at a time) is filled,
+    then `steps` x S ticks of g images each are timed; throughput is the
+    images that leave per second.  Bit-neutral: the first image's outputs
+    must be identical for every candidate.  image_cts: the input ciphertext
+    handles of each image (reused cyclically).  Returns {"best": g,
+    "img_s": {g: img/s}}."""
+    if F is None:
+        from . import _lib as F
+    if sync is None:
+        import torch
+        sync = torch.cuda.synchronize
+    dev = device if device is not None else device_name()
+    key = _key("pipeline_group", dev, model=model_key, cands=",".join(map(str, candidates)), steps=steps)
+    hit = tuner.lookup(key)
+    if hit is not None:
+        return hit
+    n_img = len(image_cts)
+    ref = None
+    rate: Dict[int, float] = {}
+    for g in candidates:
+        pipe = F.fhe_pipeline_create(ctx, model, evk, g, True)
+        try:
+            S = F.fhe_pipeline_info(pipe)[0]
+            state = {"next": 0, "first": None}
+
+            def tick():
+                i0 = state["next"]
+                grp = [h for i in range(g) for h in image_cts[(i0 + i) % n_img]]
+                state["next"] += g
+                outs, n_done, tag = F.fhe_pipeline_tick(pipe, grp, g, g * n_out)
+                if n_done and tag == 0 and state["first"] is None:
+                    state["first"] = [F.fhe_ct_export(h, N)[0] for h in outs[:n_out]]
+                for h in outs:
+                    F.fhe_ct_free(h)
+
+            for _ in range(S):          # fill: the first group leaves at the last of these ticks
+                tick()
+            sync()
+            t0 = time.perf_counter()
+            for _ in range(steps * S):
+                tick()
+            sync()
+            rate[g] = steps * S * g / (time.perf_counter() - t0)
+        finally:
+            F.fhe_pipeline_free(pipe)
+        if ref is None:
+            ref = state["first"]
+        elif state["first"] is None or not all((a == b).all() for a, b in zip(ref, state["first"])):
+            raise RuntimeError("group size %d changed the output ciphertexts" % g)
+    best = max(candidates, key=lambda c: (rate[c], -c))
+    return tuner.record(key, {"best": best, "img_s": {str(g): round(r, 4) for g, r in rate.items()}})

@@ -507,6 +507,12 @@ extern "C" int fhe_ctx_set_linear_chunk(fhe_ctx *ctx, int lin_chunk_srcs) {
     return FHE_OK;
 }
 
+extern "C" int fhe_ctx_set_encode_scratch(fhe_ctx *ctx, size_t bytes) {
+    if (!ctx || bytes == 0) return fhe_fail(FHE_E_INVAL, "bad argument");
+    ctx->on_demand_bytes = bytes;
+    return FHE_OK;
+}
+
 extern "C" int fhe_ctx_primes(const fhe_ctx *ctx, uint64_t *out, size_t cap, size_t *n) {
     if (!ctx || !n) return fhe_fail(FHE_E_INVAL, "null argument");
     *n = ctx->primes.size();
@@ -562,6 +568,33 @@ int op_rescale(fhe_ctx *ctx, const u64 *in, long long in_item, u64 *out, long lo
     a.level = level;
     a.ws = ws;
     FHE_CU(launch_rescale(ctx->dc, ctx->lt[level], a, s));
+    return FHE_OK;
+}
+
+int enc_tables(fhe_ctx *ctx, const EncTab **out) {
+    if (!ctx->enc_dev_ready) {
+        const Encoder &E = ctx->enc;
+        EncTab t;
+        memset(&t, 0, sizeof(t));
+        void *d;
+        FHE_TRY(upload(ctx, E.fft_re.data(), E.fft_re.size() * sizeof(double), &d));
+        t.fft_re = (const double *)d;
+        FHE_TRY(upload(ctx, E.fft_im.data(), E.fft_im.size() * sizeof(double), &d));
+        t.fft_im = (const double *)d;
+        for (size_t st = 0; st < E.fft_off.size() && st < 24; st++) t.off[st] = (long long)E.fft_off[st];
+        FHE_TRY(upload(ctx, E.tw_c.data(), E.tw_c.size() * sizeof(double), &d));
+        t.tw_c = (const double *)d;
+        FHE_TRY(upload(ctx, E.tw_s.data(), E.tw_s.size() * sizeof(double), &d));
+        t.tw_s = (const double *)d;
+        std::vector<unsigned> perm(E.n);
+        for (size_t j = 0; j < E.n; j++) perm[j] = E.brv[E.slot_pos[j]];
+        FHE_TRY(upload(ctx, perm.data(), perm.size() * sizeof(unsigned), &d));
+        t.perm = (const unsigned *)d;
+        FHE_CU(cudaDeviceSynchronize());
+        ctx->enc_dev = t;
+        ctx->enc_dev_ready = true;
+    }
+    *out = &ctx->enc_dev;
     return FHE_OK;
 }
 

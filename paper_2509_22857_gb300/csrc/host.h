@@ -72,7 +72,10 @@ struct fhe_ctx {
     size_t rs_ws_words = 0;
     int dev = 0;
     int lin_chunk_srcs = 160;         // MAC sources per chunk of a linear step
+    size_t on_demand_bytes = 4ull << 30;   // scratch of plaintexts encoded on demand (per linear step)
     std::atomic<int> fail_alloc_after{-1};   // injected failure: allocations left before one is refused
+    EncTab enc_dev;                   // device copy of the encoder's tables (on first use)
+    bool enc_dev_ready = false;
 };
 
 struct fhe_ct {
@@ -118,5 +121,7 @@ int op_rescale(fhe_ctx *ctx, const u64 *in, long long in_item, u64 *out, long lo
                int n_poly, int level, cudaStream_t s, u64 *ws = nullptr);
 int op_ntt(fhe_ctx *ctx, const u64 *src, u64 *dst, long long item, int n_items, int n_limbs,
            const unsigned char *pidx, bool inverse, cudaStream_t s);
+// the encoder's tables on the device, uploaded on the first call
+int enc_tables(fhe_ctx *ctx, const EncTab **out);
 // encode integral doubles into NTT-domain limbs 0..level (device)
 int op_encode_to(fhe_ctx *ctx, const double *m_host, int level, u64 *dst, cudaStream_t s);

@@ -14,7 +14,9 @@
 // Galois gathers) fused into the loads and stores.
 #include "kernels.h"
 
+#include <algorithm>
 #include <atomic>
+#include <cstring>
 
 #define NT 256
 
@@ -980,7 +982,7 @@ __global__ void k_decrypt(DevCtx c, const u64 *ct, const u64 *s, u64 *m, int lev
 // reduced only when the sum could leave Barrett's range: with b = bitlen(q),
 // K products of residues stay below K q^2 < 2^(b+62) for K <= 2^(62-b)
 // (16 terms for 58-bit primes).
-__global__ void __launch_bounds__(256) k_mac(DevCtx c, MacArgs a, int tc) {
+__global__ void __launch_bounds__(256, 3) k_mac(DevCtx c, MacArgs a, int tc) {
     // each thread owns two adjacent coefficients (16-byte loads)
     const int limb = blockIdx.z;
     const ModQ m = c.primes[limb].m;
@@ -1082,6 +1084,56 @@ __global__ void __launch_bounds__(256) k_mac(DevCtx c, MacArgs a, int tc) {
         }
         *reinterpret_cast<ulonglong2 *>(o) = r0;
         *reinterpret_cast<ulonglong2 *>(o + P) = r1;
+    }
+}
+
+// ---- on-demand slot encoding (the host encoder's operations, in its order;
+// the double-precision intrinsics are never contracted into FMAs)
+// row vids[v]'s nonzeros into the bit-reversed FFT input of vector v
+// (real parts; the buffer is zeroed first)
+__global__ void k_enc_scatter(int n, const int *vids, const long long *begin, const int *slot, const double *val,
+                              const unsigned *perm, double *buf) {
+    const int v = blockIdx.y;
+    const int row = vids[v];
+    double *ar = buf + (long long)v * 2 * n;
+    for (long long e = begin[row] + blockIdx.x * (long long)blockDim.x + threadIdx.x; e < begin[row + 1];
+         e += (long long)gridDim.x * blockDim.x)
+        ar[perm[slot[e]]] = val[e];
+}
+
+// one radix-2 decimation-in-time stage of length 2^s on every vector
+__global__ void k_enc_fft_stage(int n, int s, const double *cr, const double *ci, double *buf) {
+    const int v = blockIdx.y;
+    double *ar = buf + (long long)v * 2 * n, *ai = ar + n;
+    const int half = 1 << (s - 1);
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n / 2; t += gridDim.x * blockDim.x) {
+        const int k = t & (half - 1);
+        const int j = ((t >> (s - 1)) << s) + k;
+        const double wr = cr[k], wi = -ci[k];
+        const double br = ar[j + half], bi = ai[j + half];
+        const double vr = __dsub_rn(__dmul_rn(br, wr), __dmul_rn(bi, wi));
+        const double vi = __dadd_rn(__dmul_rn(br, wi), __dmul_rn(bi, wr));
+        const double ur = ar[j], ui = ai[j];
+        ar[j] = __dadd_rn(ur, vr);
+        ai[j] = __dadd_rn(ui, vi);
+        ar[j + half] = __dsub_rn(ur, vr);
+        ai[j + half] = __dsub_rn(ui, vi);
+    }
+}
+
+// twist by exp(-i pi k / N), times scale / n, rounded half away from zero:
+// m[k] and m[k + n] overwrite the real and imaginary parts in place
+__global__ void k_enc_twist(int n, const double *tc, const double *ts, double f, double *buf) {
+    const int v = blockIdx.y;
+    double *ar = buf + (long long)v * 2 * n, *ai = ar + n;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const double c = tc[k], sn = ts[k];
+        double r = __dadd_rn(__dmul_rn(ar[k], c), __dmul_rn(ai[k], sn));
+        double i = __dsub_rn(__dmul_rn(ai[k], c), __dmul_rn(ar[k], sn));
+        r = __dmul_rn(r, f);
+        i = __dmul_rn(i, f);
+        ar[k] = round(r);
+        ai[k] = round(i);
     }
 }
 
@@ -1218,6 +1270,9 @@ __device__ u64 pow2_mod(int e, const ModQ &m) {
 __global__ void k_double_to_limbs(DevCtx c, const double *v, u64 *out) {
     const long long N = 1ll << c.logN;
     const int limb = blockIdx.y;
+    // vector blockIdx.z: N doubles in, gridDim.y limbs out
+    v += (long long)blockIdx.z * N;
+    out += (long long)blockIdx.z * gridDim.y * N;
     const ModQ m = c.primes[limb].m;
     for (long long j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += (long long)gridDim.x * blockDim.x) {
         const double x = v[j];
@@ -1272,8 +1327,36 @@ cudaError_t launch_ntt(const DevCtx &c, const NttArgs &a, bool inverse, cudaStre
     return cudaGetLastError();
 }
 
+static cudaError_t launch_keyswitch_part(const DevCtx &c, const LevelTab &lt, const KsArgs &args, cudaStream_t s,
+                                         cudaEvent_t *ev, int phases);
+
+// Grids put items x (rows per item) on grid.y (at most 65535): a batch whose
+// ModUp rows (digits x extended limbs per item) exceed that is launched in
+// parts of consecutive items (every per-item pointer advanced by its stride).
 cudaError_t launch_keyswitch(const DevCtx &c, const LevelTab &lt, const KsArgs &args, cudaStream_t s,
                              cudaEvent_t *ev, int phases) {
+    const int nl = args.level + 1;
+    const int rows = std::max(std::max(lt.n_digits * lt.ext, 2 * nl), 2 * c.alpha);
+    const int per = 65535 / rows;
+    if (per < 1) return cudaErrorInvalidValue;
+    if (args.n_items <= per) return launch_keyswitch_part(c, lt, args, s, ev, phases);
+    for (int i0 = 0; i0 < args.n_items; i0 += per) {
+        KsArgs a = args;
+        a.n_items = std::min(per, args.n_items - i0);
+        a.d = args.d + (long long)i0 * args.d_item;
+        if (a.add0) a.add0 = args.add0 + (long long)i0 * args.add_item;
+        if (a.add1) a.add1 = args.add1 + (long long)i0 * args.add_item;
+        if (a.base) a.base = args.base + (long long)i0 * args.base_item;
+        a.out = args.out + (long long)i0 * args.out_item;
+        a.ws = args.ws + (long long)i0 * args.ws_item;
+        const cudaError_t e = launch_keyswitch_part(c, lt, a, s, i0 == 0 ? ev : nullptr, phases);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+static cudaError_t launch_keyswitch_part(const DevCtx &c, const LevelTab &lt, const KsArgs &args, cudaStream_t s,
+                                         cudaEvent_t *ev, int phases) {
     KsArgs a = args;
     if (a.ip_galois == 0) a.ip_galois = 1;
     if (a.add_galois == 0) a.add_galois = a.galois;
@@ -1454,6 +1537,36 @@ cudaError_t launch_double_to_limbs(const DevCtx &c, const double *v, u64 *out, i
     COUNT_LAUNCH();
     k_double_to_limbs<<<ew_grid(c, n_limbs, 1), 256, 0, s>>>(c, v, out);
     return cudaGetLastError();
+}
+
+cudaError_t launch_encode_sparse(const DevCtx &c, const EncTab &e, int V, const int *vids, const long long *begin,
+                                 const int *slot, const double *val, double scale, int level, double *buf, u64 *pt,
+                                 cudaStream_t s) {
+    if (V <= 0) return cudaSuccess;
+    if (V > 65535 || level + 1 > 65535) return cudaErrorInvalidValue;
+    const int n = 1 << (c.logN - 1);
+    cudaError_t r = cudaMemsetAsync(buf, 0, (size_t)V * 2 * n * sizeof(double), s);
+    if (r != cudaSuccess) return r;
+    COUNT_LAUNCH();
+    k_enc_scatter<<<dim3(4, V), 256, 0, s>>>(n, vids, begin, slot, val, e.perm, buf);
+    const int bx = std::min(n / 2 / 256 > 0 ? n / 2 / 256 : 1, 64);
+    for (int st = 1; (1 << st) <= n; st++) {
+        COUNT_LAUNCH();
+        k_enc_fft_stage<<<dim3(bx, V), 256, 0, s>>>(n, st, e.fft_re + e.off[st], e.fft_im + e.off[st], buf);
+    }
+    COUNT_LAUNCH();
+    k_enc_twist<<<dim3(bx, V), 256, 0, s>>>(n, e.tw_c, e.tw_s, scale / (double)n, buf);
+    COUNT_LAUNCH();
+    k_double_to_limbs<<<dim3(std::min((int)((1ll << c.logN) / 256), 64), level + 1, V), 256, 0, s>>>(c, buf, pt);
+    NttArgs a;
+    memset(&a, 0, sizeof(a));
+    a.src = pt;
+    a.dst = pt;
+    a.src_item = a.dst_item = (long long)(level + 1) << c.logN;
+    a.n_items = V;
+    a.n_limbs = level + 1;
+    for (int l = 0; l <= level; l++) a.pidx[l] = (unsigned char)l;
+    return launch_ntt(c, a, false, s);
 }
 
 cudaError_t launch_automorphism(const DevCtx &c, const u64 *in, u64 *out, int n_limbs, int galois, cudaStream_t s) {

@@ -184,6 +184,25 @@ struct MacArgs {
 };
 cudaError_t launch_mac(const DevCtx &c, const MacArgs &a, cudaStream_t s);
 
+// Device copy of the slot encoder's tables (the host encoder's own values):
+// FFT twiddles of the stage of length 2^s at re/im + off[s] (2^(s-1)
+// entries), the twist cos / sin(pi k / N), and perm[j] = brv(slot_pos[j]),
+// where slot j lands before the first butterfly stage.
+struct EncTab {
+    const double *fft_re, *fft_im;
+    long long off[24];
+    const double *tw_c, *tw_s;
+    const unsigned *perm;
+};
+// On-demand encoding of V term vectors given sparsely (row vids[v] of
+// begin/slot/val) at `scale`, into NTT-domain limbs 0..level at
+// pt + v * (level+1) * N.  buf: V * N doubles of scratch.  The operations are
+// the host encoder's in its order (no contraction), so the limbs equal a
+// resident encoding of the same dense vector.
+cudaError_t launch_encode_sparse(const DevCtx &c, const EncTab &e, int V, const int *vids, const long long *begin,
+                                 const int *slot, const double *val, double scale, int level, double *buf, u64 *pt,
+                                 cudaStream_t s);
+
 // ChaCha20-based samplers (the stream of one (seed, domain, id0, id1)).
 // uniform residues written directly as NTT-domain limbs
 cudaError_t launch_sample_uniform(const DevCtx &c, uint64_t seed, uint32_t domain, uint32_t id0,

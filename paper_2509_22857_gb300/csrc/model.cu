@@ -22,8 +22,16 @@ struct MLinear {
     std::vector<int> baby_ct, baby_step;           // distinct (ct, b != 0)
     std::vector<int> g_out, g_giant, g_tb, g_te;   // groups
     std::vector<int> t_ct, t_baby;
-    std::vector<u64 *> t_pt;
+    std::vector<u64 *> t_pt;                       // resident plaintext of each term
     std::vector<u64 *> bias_pt;                    // per output ct (nullable)
+    // encoded on demand: the term rows stay sparse on the device
+    bool on_demand = false;
+    double w_scale = 0;
+    int n_rows = 0;
+    long long *d_begin = nullptr;
+    int *d_slot = nullptr;
+    double *d_val = nullptr;
+    std::vector<int> t_vid;                        // row of each term
 };
 
 struct MStep {
@@ -82,7 +90,8 @@ static int load_linear(fhe_model *m, const fhe_step_desc &sd, MStep &st) {
     if (sd.n_groups < 0 || (sd.n_groups > 0 && (!sd.group_out || !sd.group_giant || !sd.group_term_begin)))
         return fhe_fail(FHE_E_INVAL, "linear step: missing group arrays");
     const int n_terms = sd.n_groups > 0 ? sd.group_term_begin[sd.n_groups] : 0;
-    if (n_terms > 0 && (!sd.term_ct || !sd.term_baby || !sd.term_vec_id || !sd.vecs || sd.n_vecs < 1))
+    if (n_terms > 0 && (!sd.term_ct || !sd.term_baby || !sd.term_vec_id || (!sd.vecs && !sd.sparse_vec_begin) ||
+                        sd.n_vecs < 1))
         return fhe_fail(FHE_E_INVAL, "linear step: missing term arrays");
     // every distinct vector is encoded once; its terms share the plaintext
     std::vector<u64 *> vec_pt(n_terms > 0 ? sd.n_vecs : 0, nullptr);
@@ -105,6 +114,36 @@ static int load_linear(fhe_model *m, const fhe_step_desc &sd, MStep &st) {
             L.g_tb.push_back(n_terms);
             L.g_te.push_back(n_terms);
         }
+    if (n_terms > 0 && sd.sparse_vec_begin) {
+        // encoded on demand: rows checked and copied to the device as given
+        const int64_t *bg = sd.sparse_vec_begin;
+        if (!sd.sparse_slot || !sd.sparse_val || bg[0] != 0)
+            return fhe_fail(FHE_E_INVAL, "linear step: sparse rows");
+        for (int v = 0; v < sd.n_vecs; v++)
+            if (bg[v + 1] < bg[v]) return fhe_fail(FHE_E_INVAL, "linear step: sparse row offsets");
+        const long long nnz = bg[sd.n_vecs];
+        for (long long e = 0; e < nnz; e++)
+            if (sd.sparse_slot[e] < 0 || (size_t)sd.sparse_slot[e] >= ns)
+                return fhe_fail(FHE_E_INVAL, "linear step: sparse slot index");
+        const EncTab *et;
+        FHE_TRY(enc_tables(c, &et));
+        void *d;
+        FHE_TRY(dev_alloc(c, &d, (size_t)(sd.n_vecs + 1) * 8));
+        m->owned.push_back(d);
+        FHE_CU(cudaMemcpy(d, bg, (size_t)(sd.n_vecs + 1) * 8, cudaMemcpyHostToDevice));
+        L.d_begin = (long long *)d;
+        FHE_TRY(dev_alloc(c, &d, (size_t)nnz * 4));
+        m->owned.push_back(d);
+        FHE_CU(cudaMemcpy(d, sd.sparse_slot, (size_t)nnz * 4, cudaMemcpyHostToDevice));
+        L.d_slot = (int *)d;
+        FHE_TRY(dev_alloc(c, &d, (size_t)nnz * 8));
+        m->owned.push_back(d);
+        FHE_CU(cudaMemcpy(d, sd.sparse_val, (size_t)nnz * 8, cudaMemcpyHostToDevice));
+        L.d_val = (double *)d;
+        L.on_demand = true;
+        L.w_scale = sd.w_scale;
+        L.n_rows = sd.n_vecs;
+    }
     for (int t = 0; t < n_terms; t++) {
         const int ct = sd.term_ct[t], b = sd.term_baby[t];
         if (ct < 0 || ct >= tin.n_ct) return fhe_fail(FHE_E_INVAL, "linear step: input index");
@@ -113,6 +152,11 @@ static int load_linear(fhe_model *m, const fhe_step_desc &sd, MStep &st) {
         if (galois_of_step(c, b) != 1) baby.insert({ct, b});
         const int v = sd.term_vec_id[t];
         if (v < 0 || v >= sd.n_vecs) return fhe_fail(FHE_E_INVAL, "linear step: vector index");
+        L.t_vid.push_back(v);
+        if (L.on_demand) {
+            L.t_pt.push_back(nullptr);
+            continue;
+        }
         if (!vec_pt[v]) FHE_TRY(encode_vec(m, sd.vecs + (size_t)v * ns, sd.w_scale, L.level, &vec_pt[v]));
         L.t_pt.push_back(vec_pt[v]);
     }
@@ -230,7 +274,7 @@ namespace {
 // in a CUDA graph).
 struct Persist {
     std::map<std::pair<int, int>, u64 *> tmp;      // (step, index) -> device buffer
-    std::map<std::pair<int, int>, char *> lists;   // (variant, step) -> device work list
+    std::map<std::pair<int, long long>, char *> lists;   // (variant, step and sub-list) -> device work list
     std::vector<void *> owned;
     int variant = 0;                               // which set of work lists (pipeline parity)
     u64 *ks_ws = nullptr;                          // this executor's key-switch workspace
@@ -250,7 +294,7 @@ struct Exec {
     std::vector<std::vector<char>> host_stage;
     Persist *pers = nullptr;              // non-null: pipeline mode
     int cur_step = -1;
-    int list_sub = 0;                     // which work list of the current step
+    long long list_sub = 0;               // which work list of the current step
     // optional timing: events bracketing each phase, summed per phase kind
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> *prof = nullptr;
     void mark(int kind, bool begin) {
@@ -311,7 +355,7 @@ struct Exec {
             FHE_CU(cudaMemcpyAsync(*out, host_stage.back().data(), bytes, cudaMemcpyHostToDevice, s));
             return FHE_OK;
         }
-        auto key = std::make_pair(pers->variant, cur_step * 65536 + list_sub);
+        auto key = std::make_pair(pers->variant, ((long long)cur_step << 40) + list_sub);
         auto it = pers->lists.find(key);
         if (it == pers->lists.end()) {
             // Lists are made by the eager ticks that precede any capture.  The
@@ -422,6 +466,21 @@ struct Exec {
         std::vector<u64 *> acc(ng, nullptr);
         for (int g = 0; g < ng; g++)
             if (galois_of_step(c, L.g_giant[g]) != 1) FHE_TRY(tmp(ti++, (size_t)B * cs * 8, &acc[g]));
+        // scratch of the plaintexts encoded on demand: rows of one batch of
+        // groups (FFT buffer N doubles + (lv+1) limbs per row, at most the
+        // context's on_demand_bytes)
+        int od_rows = 0;
+        double *od_buf = nullptr;
+        u64 *od_pt = nullptr;
+        const EncTab *enc = nullptr;
+        if (L.on_demand) {
+            FHE_TRY(enc_tables(c, &enc));
+            const size_t per_row = (size_t)(lv + 2) * c->N * 8;
+            od_rows = (int)std::min<size_t>((size_t)L.n_rows, std::max<size_t>(1, c->on_demand_bytes / per_row));
+            od_rows = std::min(od_rows, 65535);
+            FHE_TRY(tmp(ti++, (size_t)od_rows * c->N * 8, (u64 **)&od_buf));
+            FHE_TRY(tmp(ti++, (size_t)od_rows * nlN * 8, &od_pt));
+        }
         for (size_t ch = 0; ch + 1 < cut.size(); ch++) {
             const int lo = cut[ch], hi = cut[ch + 1];
             // baby-step rotations of this chunk's inputs: the rotations of one
@@ -466,8 +525,11 @@ struct Exec {
                     if (L.baby_step[kk] == b) return n_in + (kk - first_baby[lo]);
                 return -1;
             };
-            std::vector<MacGroup> hg;
-            std::vector<MacTerm> ht;
+            // the groups of this chunk with their term ranges
+            struct CG {
+                int g, tb, tc;
+            };
+            std::vector<CG> cg;
             for (int g = 0; g < ng; g++) {
                 // the group's terms of this chunk (terms are ordered by input ct)
                 int tb = L.g_tb[g], te = L.g_te[g];
@@ -475,67 +537,129 @@ struct Exec {
                 int tc = tb;
                 while (tc < te && L.t_ct[tc] < hi) tc++;
                 if (ch > 0 && tc == tb) continue;
-                const int o = L.g_out[g];
-                MacGroup G;
-                if (!acc[g]) {
-                    G.out = out + o * cs;
-                    G.out_item = out_item;
-                    G.bias = ch == 0 ? L.bias_pt[o] : nullptr;
-                } else {
-                    G.out = acc[g];
-                    G.out_item = cs;
-                    G.bias = nullptr;
-                }
-                G.accumulate = ch > 0 ? 1 : 0;
-                G.term_begin = (int)ht.size();
-                for (int t = tb; t < tc; t++) {
-                    MacTerm T;
-                    T.src = src_of(L.t_ct[t], L.t_baby[t]);
-                    T.run = 1;
-                    if (T.src < 0) return fhe_fail(FHE_E_INVAL, "internal: missing baby rotation");
-                    T.pt = L.t_pt[t];
-                    ht.push_back(T);
-                }
-                // grouped accumulation: the group's terms that share a
-                // plaintext become one run (sources summed, one product);
-                // the sum mod q does not depend on the order of the terms
-                std::stable_sort(ht.begin() + G.term_begin, ht.end(),
-                                 [](const MacTerm &x, const MacTerm &y) { return x.pt < y.pt; });
-                for (int t = G.term_begin; t < (int)ht.size();) {
-                    int e = t + 1;
-                    while (e < (int)ht.size() && ht[e].pt == ht[t].pt) {
-                        ht[e].run = 0;
-                        e++;
-                    }
-                    ht[t].run = e - t;
-                    t = e;
-                }
-                G.term_end = (int)ht.size();
-                hg.push_back(G);
+                cg.push_back(CG{g, tb, tc});
             }
-            if (hg.empty()) continue;
-            const size_t gb = hg.size() * sizeof(MacGroup), tb_ = ht.size() * sizeof(MacTerm),
-                         sb = hs.size() * sizeof(MacSrc);
-            std::vector<char> lst(gb + tb_ + sb);
-            memcpy(lst.data(), hg.data(), gb);
-            if (tb_) memcpy(lst.data() + gb, ht.data(), tb_);
-            memcpy(lst.data() + gb + tb_, hs.data(), sb);
-            char *dw;
-            list_sub = (int)ch;
-            FHE_TRY(work_list(lst.data(), lst.size(), &dw));
-            list_sub = 0;
-            MacArgs ma;
-            ma.groups = (const MacGroup *)dw;
-            ma.terms = (const MacTerm *)(dw + gb);
-            ma.srcs = (const MacSrc *)(dw + gb + tb_);
-            ma.n_groups = (int)hg.size();
-            ma.n_srcs = (int)hs.size();
-            ma.n_items = B;
-            ma.level = lv;
-            mark(11, true);
-            FHE_CU(launch_mac(c->dc, ma, s));
-            mark(11, false);
-            if (!pers) cudaFreeAsync(dw, s);
+            // pieces of groups (term ranges), batched: all at once, or
+            // (plaintexts encoded on demand) as many as keep their distinct
+            // rows within the encoding scratch; a group may end one batch and
+            // continue in the next (its later pieces accumulate)
+            struct Piece {
+                int g, tb, tc;
+                bool cont;
+            };
+            std::vector<std::vector<Piece>> batches(1);
+            std::vector<std::vector<int>> batch_rows(1);
+            {
+                std::map<int, int> seen;
+                for (const CG &x : cg) {
+                    int t0 = x.tb;
+                    bool cont = false;
+                    if (!L.on_demand || x.tb == x.tc) {
+                        batches.back().push_back(Piece{x.g, x.tb, x.tc, false});
+                        continue;
+                    }
+                    for (int t = x.tb; t < x.tc; t++) {
+                        const int v = L.t_vid[t];
+                        if (seen.count(v)) continue;
+                        if ((int)seen.size() == od_rows) {
+                            if (t > t0) {
+                                batches.back().push_back(Piece{x.g, t0, t, cont});
+                                cont = true;
+                                t0 = t;
+                            }
+                            batches.emplace_back();
+                            batch_rows.emplace_back();
+                            seen.clear();
+                        }
+                        seen[v] = (int)batch_rows.back().size();
+                        batch_rows.back().push_back(v);
+                    }
+                    batches.back().push_back(Piece{x.g, t0, x.tc, cont});
+                }
+            }
+            for (size_t bi = 0; bi < batches.size(); bi++) {
+                const std::vector<Piece> &pcs = batches[bi];
+                const std::vector<int> &rows = batch_rows[bi];
+                std::map<int, int> row_slot;
+                for (size_t k = 0; k < rows.size(); k++) row_slot[rows[k]] = (int)k;
+                if (L.on_demand && !rows.empty()) {
+                    // encode this batch's rows
+                    char *dv;
+                    list_sub = ((long long)ch << 20) + 2 * (long long)bi + 1;
+                    FHE_TRY(work_list((const char *)rows.data(), rows.size() * sizeof(int), &dv));
+                    list_sub = 0;
+                    mark(13, true);
+                    FHE_CU(launch_encode_sparse(c->dc, *enc, (int)rows.size(), (const int *)dv, L.d_begin, L.d_slot,
+                                                L.d_val, L.w_scale, lv, od_buf, od_pt, s));
+                    mark(13, false);
+                    if (!pers) cudaFreeAsync(dv, s);
+                }
+                std::vector<MacGroup> hg;
+                std::vector<MacTerm> ht;
+                for (const Piece &pc : pcs) {
+                    const int g = pc.g, tb = pc.tb, tc = pc.tc;
+                    const int o = L.g_out[g];
+                    MacGroup G;
+                    if (!acc[g]) {
+                        G.out = out + o * cs;
+                        G.out_item = out_item;
+                        G.bias = (ch == 0 && !pc.cont) ? L.bias_pt[o] : nullptr;
+                    } else {
+                        G.out = acc[g];
+                        G.out_item = cs;
+                        G.bias = nullptr;
+                    }
+                    G.accumulate = (ch > 0 || pc.cont) ? 1 : 0;
+                    G.term_begin = (int)ht.size();
+                    for (int t = tb; t < tc; t++) {
+                        MacTerm T;
+                        T.src = src_of(L.t_ct[t], L.t_baby[t]);
+                        T.run = 1;
+                        if (T.src < 0) return fhe_fail(FHE_E_INVAL, "internal: missing baby rotation");
+                        T.pt = L.on_demand ? od_pt + (long long)row_slot[L.t_vid[t]] * nlN : L.t_pt[t];
+                        ht.push_back(T);
+                    }
+                    // grouped accumulation: the group's terms that share a
+                    // plaintext become one run (sources summed, one product);
+                    // the sum mod q does not depend on the order of the terms
+                    std::stable_sort(ht.begin() + G.term_begin, ht.end(),
+                                     [](const MacTerm &x, const MacTerm &y) { return x.pt < y.pt; });
+                    for (int t = G.term_begin; t < (int)ht.size();) {
+                        int e = t + 1;
+                        while (e < (int)ht.size() && ht[e].pt == ht[t].pt) {
+                            ht[e].run = 0;
+                            e++;
+                        }
+                        ht[t].run = e - t;
+                        t = e;
+                    }
+                    G.term_end = (int)ht.size();
+                    hg.push_back(G);
+                }
+                if (hg.empty()) continue;
+                const size_t gb = hg.size() * sizeof(MacGroup), tb_ = ht.size() * sizeof(MacTerm),
+                             sb = hs.size() * sizeof(MacSrc);
+                std::vector<char> lst(gb + tb_ + sb);
+                memcpy(lst.data(), hg.data(), gb);
+                if (tb_) memcpy(lst.data() + gb, ht.data(), tb_);
+                memcpy(lst.data() + gb + tb_, hs.data(), sb);
+                char *dw;
+                list_sub = ((long long)ch << 20) + 2 * (long long)bi;
+                FHE_TRY(work_list(lst.data(), lst.size(), &dw));
+                list_sub = 0;
+                MacArgs ma;
+                ma.groups = (const MacGroup *)dw;
+                ma.terms = (const MacTerm *)(dw + gb);
+                ma.srcs = (const MacSrc *)(dw + gb + tb_);
+                ma.n_groups = (int)hg.size();
+                ma.n_srcs = (int)hs.size();
+                ma.n_items = B;
+                ma.level = lv;
+                mark(11, true);
+                FHE_CU(launch_mac(c->dc, ma, s));
+                mark(11, false);
+                if (!pers) cudaFreeAsync(dw, s);
+            }
         }
         mark(12, true);
         // giant steps: out_o += sum_g rot(acc_{o,g}, g) with one ModDown per
@@ -582,6 +706,8 @@ struct Exec {
         mark(12, false);
         for (auto p : rb) tmp_free(p);
         for (auto p : acc) tmp_free(p);
+        tmp_free(od_buf);
+        tmp_free(od_pt);
         return FHE_OK;
     }
 
@@ -857,6 +983,8 @@ struct Segment {
     cudaEvent_t done = nullptr;
     Persist pers;
     std::map<int, u64 *> ibuf;
+    cudaGraphExec_t exec[2] = {nullptr, nullptr};   // this segment alone, per parity
+    long long captured[2] = {0, 0};
 };
 
 }  // namespace
@@ -878,12 +1006,15 @@ struct fhe_pipeline {
     long long tick = 0;
     std::vector<int> entered;   // images entered at each tick
     std::vector<void *> owned;
+    bool creating = false;      // the creation ticks run (and capture) every segment
 
     ~fhe_pipeline() {
         if (main) cudaStreamSynchronize(main);
         for (auto &e : exec)
             if (e) cudaGraphExecDestroy(e);
         for (auto &sg : seg) {
+            for (auto &e : sg->exec)
+                if (e) cudaGraphExecDestroy(e);
             if (sg->st) cudaStreamDestroy(sg->st);
             if (sg->done) cudaEventDestroy(sg->done);
         }
@@ -928,15 +1059,36 @@ int run_segment(fhe_pipeline *p, int k, int parity) {
     return FHE_OK;
 }
 
-// all segments of one tick: fork from the main stream, join back into it
-int run_tick(fhe_pipeline *p, int parity) {
+// the segments of one tick (occupied[k]: run segment k): fork from the main
+// stream, join back into it
+int run_tick(fhe_pipeline *p, int parity, const std::vector<char> &occupied) {
     FHE_CU(cudaEventRecord(p->fork, p->main));
     for (int k = 0; k < p->S; k++) {
+        if (!occupied[k]) continue;
         FHE_CU(cudaStreamWaitEvent(p->seg[k]->st, p->fork, 0));
         FHE_TRY(run_segment(p, k, parity));
         FHE_CU(cudaEventRecord(p->seg[k]->done, p->seg[k]->st));
     }
-    for (int k = 0; k < p->S; k++) FHE_CU(cudaStreamWaitEvent(p->main, p->seg[k]->done, 0));
+    for (int k = 0; k < p->S; k++)
+        if (occupied[k]) FHE_CU(cudaStreamWaitEvent(p->main, p->seg[k]->done, 0));
+    return FHE_OK;
+}
+
+// one segment's launches captured alone on its own stream (per parity)
+int capture_segment(fhe_pipeline *p, int k, int parity) {
+    Segment &sg = *p->seg[k];
+    cudaGraph_t g;
+    const unsigned long long l0 = fhe_launch_counter();
+    FHE_CU(cudaStreamBeginCapture(sg.st, cudaStreamCaptureModeRelaxed));
+    int rc = run_segment(p, k, parity);
+    cudaError_t ce = cudaStreamEndCapture(sg.st, &g);
+    sg.captured[parity] = (long long)(fhe_launch_counter() - l0);
+    fhe_launch_counter_add(-sg.captured[parity]);
+    if (rc != FHE_OK) return rc;
+    if (ce != cudaSuccess) return fhe_fail(FHE_E_CUDA, std::string("segment capture: ") + cudaGetErrorString(ce));
+    ce = cudaGraphInstantiate(&sg.exec[parity], g, 0);
+    cudaGraphDestroy(g);
+    if (ce != cudaSuccess) return fhe_fail(FHE_E_CUDA, std::string("instantiate: ") + cudaGetErrorString(ce));
     return FHE_OK;
 }
 
@@ -1028,12 +1180,19 @@ extern "C" int fhe_pipeline_create(fhe_ctx *c, const fhe_model *mc, const fhe_ev
     FHE_CU(cudaDeviceSynchronize());
     if (p->graphs) {
         // capture both parities' graphs now, on an empty pipeline, so that no
-        // capture happens later while other threads use the device
+        // capture happens later while other threads use the device: the
+        // whole tick's, then every segment's alone
+        p->creating = true;
         for (int k = 0; k < 4; k++) {
             size_t n_done = 0;
             int64_t tag = -1;
-            FHE_TRY(fhe_pipeline_tick(p.get(), nullptr, 0, nullptr, &n_done, &tag));
+            const int rc = fhe_pipeline_tick(p.get(), nullptr, 0, nullptr, &n_done, &tag);
+            if (rc != FHE_OK) return rc;
         }
+        p->creating = false;
+        for (int par = 0; par < 2; par++)
+            for (int k = 0; k < p->S; k++) FHE_TRY(capture_segment(p.get(), k, par));
+        FHE_CU(cudaDeviceSynchronize());
         p->tick = 0;
         p->entered.clear();
     }
@@ -1051,13 +1210,42 @@ extern "C" int fhe_pipeline_info(const fhe_pipeline *p, int *n_segments, int *gr
 }
 
 // The tick's launches, after its inputs are copied in (see fhe_pipeline_tick).
+// Segment k holds the group that entered k ticks ago; segments whose group
+// is empty are skipped (a partly filled pipeline, as at low load in
+// serving, then costs only its occupied segments).  A full tick replays one
+// graph of all segments; a partial one replays the occupied segments' own
+// graphs.
 static int pipeline_launch(fhe_pipeline *p, int par) {
+    std::vector<char> occupied(p->S, 1);
+    int n_occ = p->S;
+    if (!p->creating) {
+        n_occ = 0;
+        for (int k = 0; k < p->S; k++) {
+            occupied[k] = p->tick - k >= 0 && p->entered[p->tick - k] > 0;
+            n_occ += occupied[k];
+        }
+    }
+    if (n_occ == 0) return FHE_OK;
+    if (p->graphs && n_occ < p->S && p->seg[0]->exec[par]) {
+        FHE_CU(cudaEventRecord(p->fork, p->main));
+        for (int k = 0; k < p->S; k++) {
+            if (!occupied[k]) continue;
+            Segment &sg = *p->seg[k];
+            FHE_CU(cudaStreamWaitEvent(sg.st, p->fork, 0));
+            FHE_CU(cudaGraphLaunch(sg.exec[par], sg.st));
+            fhe_launch_counter_add(sg.captured[par]);
+            FHE_CU(cudaEventRecord(sg.done, sg.st));
+        }
+        for (int k = 0; k < p->S; k++)
+            if (occupied[k]) FHE_CU(cudaStreamWaitEvent(p->main, p->seg[k]->done, 0));
+        return FHE_OK;
+    }
     if (p->graphs && (p->exec[par] || p->tick >= 2)) {
         if (!p->exec[par]) {
             cudaGraph_t g;
             const unsigned long long l0 = fhe_launch_counter();
             FHE_CU(cudaStreamBeginCapture(p->main, cudaStreamCaptureModeRelaxed));
-            int rc = run_tick(p, par);
+            int rc = run_tick(p, par, occupied);
             cudaError_t ce = cudaStreamEndCapture(p->main, &g);
             p->captured[par] = (long long)(fhe_launch_counter() - l0);
             fhe_launch_counter_add(-p->captured[par]);
@@ -1070,7 +1258,7 @@ static int pipeline_launch(fhe_pipeline *p, int par) {
         FHE_CU(cudaGraphLaunch(p->exec[par], p->main));
         fhe_launch_counter_add(p->captured[par]);
     } else {
-        FHE_TRY(run_tick(p, par));
+        FHE_TRY(run_tick(p, par, occupied));
     }
     return FHE_OK;
 }

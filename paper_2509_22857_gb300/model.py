@@ -133,30 +133,69 @@ def _pick_copy(copies, out_base, n_slots):
     return best[1], best[2]
 
 
-def diagonals(w: np.ndarray, stride: int, pad: int, src: SlotMap, dst: SlotMap, n_slots: int):
-    """{(out ct, in ct, r): vector} such that out[s] = sum_r vec[s]*in[s + r]."""
+class SparseVec:
+    """A slot vector given by its nonzero entries (slots ascending): the form
+    in which weight vectors of a step encoded on demand are kept (a dense
+    vector of a 512-channel packed convolution is N/2 doubles, of which a
+    few hundred are nonzero)."""
+
+    __slots__ = ("slots", "vals")
+
+    def __init__(self, slots, vals):
+        order = np.argsort(slots, kind="stable")
+        self.slots = np.asarray(slots, dtype=np.int64)[order]
+        self.vals = np.asarray(vals, dtype=np.float64)[order]
+
+    def roll(self, g: int, n_slots: int) -> "SparseVec":
+        """np.roll of the dense vector by g"""
+        return SparseVec((self.slots + g) % n_slots, self.vals)
+
+    def key(self) -> bytes:
+        return self.slots.tobytes() + b"|" + self.vals.tobytes()
+
+    def dense(self, n_slots: int) -> np.ndarray:
+        v = np.zeros(n_slots)
+        v[self.slots] = self.vals
+        return v
+
+    def __len__(self):
+        return len(self.slots)
+
+
+def diagonals(w: np.ndarray, stride: int, pad: int, src: SlotMap, dst: SlotMap, n_slots: int,
+              sparse: bool = False):
+    """{(out ct, in ct, r): vector} such that out[s] = sum_r vec[s]*in[s + r]
+    (vectors as SparseVec with sparse=True)."""
     cout, cin, k, _ = w.shape
     oh = np.repeat(np.arange(dst.H), dst.W)
     ow = np.tile(np.arange(dst.W), dst.H)
+    # kernel offsets: the valid output positions and their input offsets
+    # (the same for every channel pair)
+    offs = []
+    for dh in range(k):
+        ih = oh * stride + dh - pad
+        for dw in range(k):
+            iw = ow * stride + dw - pad
+            ok = (ih >= 0) & (ih < src.H) & (iw >= 0) & (iw < src.W)
+            if ok.any():
+                offs.append((dh, dw, ok, ih[ok] * src.st * src.row + iw[ok] * src.st))
     rows = {"oc": [], "ic": [], "r": [], "so": [], "v": []}
     for o in range(cout):
         for oct_, obase in dst.copies[o]:
             so = obase + oh * dst.st * dst.row + ow * dst.st
-            for i in range(cin):
-                ict, ibase = _pick_copy(src.copies[i], obase, n_slots)
-                for dh in range(k):
-                    ih = oh * stride + dh - pad
-                    for dw in range(k):
-                        iw = ow * stride + dw - pad
-                        ok = (ih >= 0) & (ih < src.H) & (iw >= 0) & (iw < src.W)
-                        if not ok.any():
-                            continue
-                        si = ibase + ih[ok] * src.st * src.row + iw[ok] * src.st
-                        rows["oc"].append(np.full(ok.sum(), oct_))
-                        rows["ic"].append(np.full(ok.sum(), ict))
-                        rows["r"].append((si - so[ok]) % n_slots)
-                        rows["so"].append(so[ok])
-                        rows["v"].append(np.full(ok.sum(), w[o, i, dh, dw]))
+            picks = [_pick_copy(src.copies[i], obase, n_slots) for i in range(cin)]
+            ict = np.array([p_[0] for p_ in picks], dtype=np.int64)
+            ibase = np.array([p_[1] for p_ in picks], dtype=np.int64)
+            for dh, dw, ok, si_off in offs:
+                so_ok = so[ok]
+                n_ok = len(so_ok)
+                # all input channels at once: [cin, n_ok]
+                si = ibase[:, None] + si_off[None, :]
+                rows["oc"].append(np.full(cin * n_ok, oct_))
+                rows["ic"].append(np.repeat(ict, n_ok))
+                rows["r"].append(((si - so_ok[None, :]) % n_slots).reshape(-1))
+                rows["so"].append(np.tile(so_ok, cin))
+                rows["v"].append(np.repeat(w[o, :, dh, dw], n_ok))
     oc = np.concatenate(rows["oc"])
     ic = np.concatenate(rows["ic"])
     r = np.concatenate(rows["r"])
@@ -171,8 +210,11 @@ def diagonals(w: np.ndarray, stride: int, pad: int, src: SlotMap, dst: SlotMap, 
         seg_so = so[lo:hi]
         if np.any(seg_so[1:] == seg_so[:-1]):
             raise ValueError("two weights land on one diagonal slot")
-        vec = np.zeros(n_slots)
-        vec[seg_so] = v[lo:hi]
+        if sparse:
+            vec = SparseVec(seg_so, v[lo:hi])
+        else:
+            vec = np.zeros(n_slots)
+            vec[seg_so] = v[lo:hi]
         out[(int(oc[lo]), int(ic[lo]), int(r[lo]))] = vec
     return out
 
@@ -318,7 +360,8 @@ CLASSIFIER_EXTRA_BITS = 6
 class Planner:
     def __init__(self, primes_q: Sequence[int], log_n: int, log_scale: float, layout: str, alpha: int = 3,
                  max_giant_blocks: int = 8, members: int = 1, input_lambda: int = 1,
-                 giants: Optional[Sequence[int]] = None):
+                 giants: Optional[Sequence[int]] = None, on_demand: bool = False):
+        self.on_demand = on_demand
         self.giants = None if giants is None else list(giants)
         self.n_linear = 0
         self.members = members
@@ -388,8 +431,13 @@ class Planner:
         vecs: List[np.ndarray] = []
         remap = np.empty(len(pairs), dtype=np.int64)
         for j, (v, gg) in enumerate(pairs):
-            rolled = np.roll(terms.vecs[v], gg) if gg else terms.vecs[v]
-            key = rolled.tobytes()
+            vec = terms.vecs[v]
+            if isinstance(vec, SparseVec):
+                rolled = vec.roll(int(gg), self.n) if gg else vec
+                key = rolled.key()
+            else:
+                rolled = np.roll(vec, gg) if gg else vec
+                key = rolled.tobytes()
             if key not in table:
                 table[key] = len(vecs)
                 vecs.append(rolled)
@@ -436,7 +484,8 @@ class Planner:
             bias = self._bias_vecs([ps[k if self.layout == "hw_ens" else 0]["bias"] for k in range(reps)], lout)
         else:
             lout = map_packed(node["cout"], ho, wo, st, lin.row, lin.block, self.n)
-            terms = terms_of(diagonals(ps[0]["w"], node["stride"], node["pad"], lin, lout, self.n))
+            terms = terms_of(diagonals(ps[0]["w"], node["stride"], node["pad"], lin, lout, self.n,
+                                       sparse=self.on_demand))
             giant = self._pick_giant(terms, lin.block, info.level)
             bias = self._bias_vecs([ps[0]["bias"]], lout)
         ws_scale = self.delta if target is None else self._shortcut_scale(info, target)
@@ -588,7 +637,7 @@ class Planner:
 
 def compile_network(net, raw, primes_q, log_n, log_scale, layout, alpha: int = 3,
                     max_giant_blocks: int = 8, input_lambda: int = 1,
-                    giants: Optional[Sequence[int]] = None) -> Program:
+                    giants: Optional[Sequence[int]] = None, on_demand: bool = False) -> Program:
     """raw: one model's raw parameters, or a list of them (an ensemble, laid
     out with layout "hw_ens": member m in block m of every ciphertext).
     alpha: digit width of key switching (for the baby-step / giant-step
@@ -597,13 +646,16 @@ def compile_network(net, raw, primes_q, log_n, log_scale, layout, alpha: int = 3
     (the program's input tensor scale; 2 keeps every key switch of the
     first layer at scale Delta^2).  giants: the giant-step size of every
     linear step in program order, in place of the planner's choice (any
-    split evaluates the same diagonals)."""
+    split evaluates the same diagonals).  on_demand: the weight vectors of
+    the packed convolutions are kept sparse and encoded on the device each
+    time their step runs, instead of being encoded once and held in HBM
+    (for layers whose plaintexts do not fit)."""
     raws = raw if isinstance(raw, (list, tuple)) else [raw]
     if len(raws) > 1 and layout != "hw_ens":
         raise ValueError("an ensemble needs the hw_ens layout")
     prms = [prepare_params(net, r) for r in raws]
     return Planner(primes_q, log_n, log_scale, layout, alpha, max_giant_blocks, len(raws),
-                   input_lambda, giants).compile(net, prms)
+                   input_lambda, giants, on_demand).compile(net, prms)
 
 
 def input_scale(prog: Program) -> float:
@@ -693,7 +745,16 @@ class ModelDesc:
                 d.term_baby = p32(arr(st["t_baby"] if n_t else [0], np.int32))
                 d.term_vec_id = p32(arr(st["t_vid"] if n_t else [0], np.int32))
                 d.n_vecs = len(st["vecs"])
-                d.vecs = pd(arr(np.stack(st["vecs"]) if st["vecs"] else np.zeros((1, n_slots)), np.float64))
+                if st["vecs"] and isinstance(st["vecs"][0], SparseVec):
+                    # encoded on the device when the step runs
+                    lens = np.array([len(v) for v in st["vecs"]], dtype=np.int64)
+                    d.vecs = None
+                    d.sparse_vec_begin = arr(np.concatenate([[0], np.cumsum(lens)]), np.int64).ctypes.data_as(
+                        F.P_I64)
+                    d.sparse_slot = p32(arr(np.concatenate([v.slots for v in st["vecs"]]), np.int32))
+                    d.sparse_val = pd(arr(np.concatenate([v.vals for v in st["vecs"]]), np.float64))
+                else:
+                    d.vecs = pd(arr(np.stack(st["vecs"]) if st["vecs"] else np.zeros((1, n_slots)), np.float64))
                 bo = sorted(st["bias"])
                 d.n_bias = len(bo)
                 d.bias_out = p32(arr(bo or [0], np.int32))

@@ -1,6 +1,7 @@
 """The autotuner on the device: every admissible digit width timed and
-ranked, the cache answering a second tuner; the linear chunk size tuned on a
-small network with identical outputs across candidates."""
+ranked, the cache answering a second tuner; the linear chunk size and the
+pipeline's group size tuned on a small network with identical outputs across
+candidates."""
 import pytest
 
 import synth
@@ -56,6 +57,12 @@ def test_linear_chunk_tuning_keeps_outputs():
         rec = A.tune_linear_chunk(A.Tuner(), ctx, model, evk, cts, 2, n_out, N, candidates=(4, 160), reps=1,
                                   model_key="resnet_mini")
         assert rec["best"] in (4, 160) and all(t > 0 for t in rec["ms"].values())
+        # the pipeline's group size: raises if a group size changes image 0's outputs
+        n_in = len(cts) // 2
+        images = [cts[i * n_in:(i + 1) * n_in] for i in range(2)]
+        rec = A.tune_pipeline_group(A.Tuner(), ctx, model, evk, images, n_out, N, candidates=(1, 2, 4),
+                                    model_key="resnet_mini")
+        assert rec["best"] in (1, 2, 4) and all(r > 0 for r in rec["img_s"].values())
     finally:
         for h in cts:
             F.fhe_ct_free(h)

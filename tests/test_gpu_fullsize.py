@@ -11,7 +11,7 @@ from oracle import cnn
 pytestmark = pytest.mark.gpu
 
 
-def _run(arch, preset, layout, raw, ref_fn, img_shape):
+def _run(arch, preset, layout, raw, ref_fn, img_shape, on_demand=False):
     from paper_2509_22857_gb300 import _lib as F
     from paper_2509_22857_gb300 import model as M
     pre = synth.PRESETS[preset]
@@ -21,7 +21,8 @@ def _run(arch, preset, layout, raw, ref_fn, img_shape):
                            pre["log_scale"])
     try:
         prog = M.compile_network(net, raw, F.fhe_ctx_primes(ctx)[: pre["L"] + 1], pre["logn"], pre["log_scale"],
-                                 layout, pre["alpha"], input_lambda=synth.INPUT_LAMBDA[preset])
+                                 layout, pre["alpha"], input_lambda=synth.INPUT_LAMBDA[preset],
+                                 on_demand=on_demand)
         sk, evk = F.fhe_keygen(ctx, synth.SEED_KEYS, sorted(prog.rotations))
         desc = M.ModelDesc(prog, N // 2)
         model = F.fhe_model_load(ctx, desc.desc)
@@ -63,6 +64,19 @@ def test_resnet18_ensemble_full_size_logits():
     raws = synth.cluster_joint([synth.params(net, m) for m in range(3)], net, 16)
     y, want = _run("resnet18", "resnet18", "hw_ens", raws, lambda n, img: cnn.forward_ensemble(n, raws, img),
                    (3, 64, 64))
+    assert np.max(np.abs(y - want)) < 1e-3
+    assert np.argmax(y) == np.argmax(want)
+
+
+def test_vgg11_full_size_logits_with_on_demand_encoding():
+    """VGG-11 channel-packed at N = 2^16: its packed convolutions' plaintexts
+    (239K rows, far beyond device memory if encoded at once) are encoded on
+    the device each time their layer runs; decrypted logits within 1e-3 of
+    the float64 network, same argmax."""
+    net = synth.vgg11()
+    raw = synth.params(net)
+    y, want = _run("vgg11", "vgg11", "packed", raw, lambda n, img: cnn.forward_plain(n, raw, img), (3, 32, 32),
+                   on_demand=True)
     assert np.max(np.abs(y - want)) < 1e-3
     assert np.argmax(y) == np.argmax(want)
 

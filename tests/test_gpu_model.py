@@ -270,3 +270,70 @@ def test_oracle_chosen_schedule_bit_exact(case):
         F.fhe_sk_free(sk)
     finally:
         F.fhe_ctx_destroy(ctx)
+
+
+@pytest.mark.parametrize("case", ["mini", "vgg_mini"])
+def test_on_demand_encoding_equals_resident(case):
+    """The same network with its packed convolutions' plaintexts encoded on
+    the device each time a step runs (sparse rows, host encoder's operation
+    order) gives the ciphertexts of the resident program, with a scratch so
+    small that every step runs its output groups in several batches, and
+    through the graph-replayed pipeline as well."""
+    from paper_2509_22857_gb300 import _lib as F
+    from paper_2509_22857_gb300 import model as M
+    arch, preset, layout = CASES[case][:3]
+    lam = CASES[case][3] if len(CASES[case]) > 3 else 1
+    net = synth.ARCHS[arch]()
+    raw = synth.params(net)
+    pre = synth.PRESETS[preset]
+    N = 1 << pre["logn"]
+    ctx = F.fhe_ctx_create(pre["logn"], pre["L"], pre["q_bits"], pre["q0_bits"], pre["p_bits"], pre["alpha"],
+                           pre["log_scale"])
+    try:
+        primes = F.fhe_ctx_primes(ctx)[: pre["L"] + 1]
+        pm = M.compile_network(net, raw, primes, pre["logn"], pre["log_scale"], layout, pre["alpha"],
+                               input_lambda=lam)
+        po = M.compile_network(net, raw, primes, pre["logn"], pre["log_scale"], layout, pre["alpha"],
+                               input_lambda=lam, on_demand=True)
+        assert any(st["kind"] == 1 and isinstance(st["vecs"][0], M.SparseVec) for st in po.steps)
+        sk, evk = F.fhe_keygen(ctx, synth.SEED_KEYS, sorted(pm.rotations))
+        dm, do = M.ModelDesc(pm, N // 2), M.ModelDesc(po, N // 2)
+        m_res, m_od = F.fhe_model_load(ctx, dm.desc), F.fhe_model_load(ctx, do.desc)
+        inp = net[0]
+        cts = []
+        for i in range(2):
+            img = synth.image(i, inp["c"], inp["h"], inp["w"])
+            for k, v in enumerate(M.input_slots(pm, img, N // 2)):
+                pt = F.fhe_encode(ctx, v, M.input_scale(pm), pre["L"])
+                cts.append(F.fhe_encrypt(ctx, sk, pt, synth.enc_seed(i, k)))
+                F.fhe_pt_free(pt)
+        n_out = pm.tensors[pm.output].layout.n_ct
+        n_in = len(cts) // 2
+        want_h = F.fhe_infer(ctx, m_res, evk, cts, 2, n_out)
+        want = [F.fhe_ct_export(h, N)[0] for h in want_h]
+        # a few rows per batch: (lv + 2) N words of scratch per row
+        F.fhe_ctx_set_encode_scratch(ctx, 5 * (pre["L"] + 2) * N * 8)
+        got_h = F.fhe_infer(ctx, m_od, evk, cts, 2, n_out)
+        got = [F.fhe_ct_export(h, N)[0] for h in got_h]
+        assert all(np.array_equal(a, b) for a, b in zip(want, got))
+        pipe = F.fhe_pipeline_create(ctx, m_od, evk, 1, True)
+        S = F.fhe_pipeline_info(pipe)[0]
+        outs = []
+        for t in range(S + 1):
+            grp = cts[:n_in] if t == 0 else []
+            o, n_done, tag = F.fhe_pipeline_tick(pipe, grp, len(grp) // n_in, n_out)
+            if n_done:
+                assert tag == 0
+                outs = [F.fhe_ct_export(h, N)[0] for h in o]
+            for h in o:
+                F.fhe_ct_free(h)
+        F.fhe_pipeline_free(pipe)
+        assert outs and all(np.array_equal(a, b) for a, b in zip(want[:n_out], outs))
+        for h in got_h + want_h + cts:
+            F.fhe_ct_free(h)
+        F.fhe_model_free(m_res)
+        F.fhe_model_free(m_od)
+        F.fhe_evk_free(evk)
+        F.fhe_sk_free(sk)
+    finally:
+        F.fhe_ctx_destroy(ctx)

@@ -85,3 +85,34 @@ def test_bad_explicit_chains_are_refused():
     with pytest.raises(F.FheError) as e:
         F.fhe_ctx_create(LOGN, 16, 58, 40, 58, 1, 29)
     assert e.value.code == F.FHE_E_INVAL
+
+
+def test_batch_beyond_one_launch_of_33_digit_modup(paper):
+    """64 ciphertexts key-switched together at the top of the 33-digit chain:
+    33 digits x 34 extended limbs per item put at most 58 items on one
+    launch's grid, so the batch is launched in two parts.  Each image's
+    relinearised square equals the one-image fhe_square."""
+    from types import SimpleNamespace
+    from paper_2509_22857_gb300 import model as M
+    F, ctx, prm, S, keys, sk, evk = paper
+    lay = SimpleNamespace(n_ct=1)
+    scale = prm.scale ** 3
+    prog = M.Program(tensors=[M.TInfo(lay, prm.L, scale), M.TInfo(lay, prm.L, scale * scale)],
+                     steps=[{"kind": F.STEP_ACT, "src": 0, "dst": 1, "c1": 0.0, "c0": 0.0}], input=0, output=1)
+    desc = M.ModelDesc(prog, prm.N // 2)
+    model = F.fhe_model_load(ctx, desc.desc)
+    B = 64
+    cts = []
+    for i in range(B):
+        z = np.random.default_rng(100 + i).uniform(-1, 1, prm.N // 2)
+        pt = F.fhe_encode(ctx, z, scale, prm.L)
+        cts.append(F.fhe_encrypt(ctx, sk, pt, 300 + i))
+        F.fhe_pt_free(pt)
+    outs = F.fhe_infer(ctx, model, evk, cts, B, 1)
+    for i in (0, 57, 58, 63):
+        one = F.fhe_square(ctx, evk, cts[i])
+        assert np.array_equal(F.fhe_ct_export(outs[i], prm.N)[0], F.fhe_ct_export(one, prm.N)[0]), i
+        F.fhe_ct_free(one)
+    for h in outs + cts:
+        F.fhe_ct_free(h)
+    F.fhe_model_free(model)

@@ -174,3 +174,33 @@ def test_ensemble_work_is_flat_in_members():
             base = (got, ks)
         assert got == base[0], (members, got, base[0])
         assert ks == base[1] + (members - 1).bit_length(), (members, ks, base[1])
+
+
+@pytest.mark.parametrize("arch,layout", [("vgg_mini", "packed"), ("resnet_mini", "packed")])
+def test_on_demand_program_describes_the_resident_one(arch, layout):
+    """A program compiled for on-demand encoding keeps its convolution rows
+    sparse; term for term it is the resident program (same outputs, giant
+    and baby steps, inputs), and every sparse row is the resident vector."""
+    pre = synth.PRESETS["resnet_mini"]
+    prm = O.make_params(**pre)
+    net = synth.ARCHS[arch]()
+    raw = synth.params(net)
+    dense = M.compile_network(net, raw, prm.q, pre["logn"], pre["log_scale"], layout, pre["alpha"])
+    od = M.compile_network(net, raw, prm.q, pre["logn"], pre["log_scale"], layout, pre["alpha"], on_demand=True)
+    assert len(dense.steps) == len(od.steps) and dense.rotations == od.rotations
+    n = prm.N // 2
+    n_sparse = 0
+    for a, b in zip(dense.steps, od.steps):
+        assert a["kind"] == b["kind"]
+        if a["kind"] != 1:
+            continue
+        for k in ("t_out", "t_giant", "t_ct", "t_baby"):
+            assert np.array_equal(a[k], b[k]), k
+        sparse = isinstance(b["vecs"][0], M.SparseVec)
+        n_sparse += sparse
+        for t in range(len(a["t_out"])):
+            va, vb = a["vecs"][a["t_vid"][t]], b["vecs"][b["t_vid"][t]]
+            assert np.array_equal(va, vb.dense(n) if sparse else vb)
+            if sparse:
+                assert np.count_nonzero(va) == len(vb)
+    assert n_sparse >= 2     # the packed convolutions
