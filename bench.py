@@ -631,6 +631,11 @@ def run_resnet18(args):
     sk, evk = F.fhe_keygen(ctx, synth.SEED_KEYS, sorted(prog.rotations))
     desc = M.ModelDesc(prog, N // 2)
     model = F.fhe_model_load(ctx, desc.desc)
+    if args.chunk:
+        F.fhe_ctx_set_linear_chunk(ctx, args.chunk)
+    # whole key switches of a step (an activation of B x 64 channel
+    # ciphertexts) in launches of 64 items: the workspace stays 6.4 GB
+    F.fhe_ctx_set_keyswitch_batch(ctx, 64)
     t_setup = time.time() - t0
     n_out = prog.tensors[prog.output].layout.n_ct
     cts = []
@@ -641,14 +646,12 @@ def run_resnet18(args):
             cts.append(F.fhe_encrypt(ctx, sk, pt, synth.enc_seed(i, k)))
             F.fhe_pt_free(pt)
     stream = torch.cuda.current_stream()
-    outs, phase_ms = F.fhe_infer_profiled(ctx, model, evk, cts, B, n_out, stream)
-    torch.cuda.synchronize()
-    for h in outs:
-        F.fhe_ct_free(h)
+    # one batch, timed by events on the stream (the phase split comes from
+    # events around each phase of the same run)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    outs = F.fhe_infer(ctx, model, evk, cts, B, n_out, stream)
+    outs, phase_ms = F.fhe_infer_profiled(ctx, model, evk, cts, B, n_out, stream)
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
@@ -658,6 +661,7 @@ def run_resnet18(args):
            "members": M_members,
            "batch": B, "img_s": round(B / (ms / 1e3), 4), "ms_per_batch": round(ms, 1),
            "phase_ms": {k: round(v, 1) for k, v in phase_ms.items()}, "setup_s": round(t_setup, 1),
+           "linear_chunk_sources": args.chunk or 160,
            "keyswitches_per_img": n_ks, "distinct_plaintexts": sum(len(st["vecs"]) for st in prog.steps
                                                                   if st["kind"] == 1)}
     print(json.dumps(res), flush=True)
@@ -812,6 +816,8 @@ def run_serving(args):
         # and its rotated copies (chunks of 40 sources; bit-neutral)
         F.fhe_ctx_set_encode_scratch(ctx, 1 << 30)
         F.fhe_ctx_set_linear_chunk(ctx, 40)
+        # and its key-switch workspace (8 items per launch)
+        F.fhe_ctx_set_keyswitch_batch(ctx, 8)
         # (arch, layout, members, levels, on demand, clusters)
         specs = [("vgg11", "packed", None, synth.PRESETS["vgg11"]["L"], True, 0),
                  ("resnet20", "packed", None, pre["L"], False, 0),
@@ -831,10 +837,21 @@ def run_serving(args):
     descs = [M.ModelDesc(p, N // 2) for _, p in progs]
     models = [F.fhe_model_load(ctx, d.desc) for d in descs]
     server = F.fhe_server_create(ctx, evk)
-    mids = [F.fhe_server_add_model(server, m, 1 if full else 4) for m in models]
+    # admission by device memory: a model whose pipeline does not fit is
+    # refused (FHE_E_OOM) and the stream is served by the admitted ones
+    mids, refused = [], []
+    for k, m in enumerate(models):
+        try:
+            mids.append(F.fhe_server_add_model(server, m, 1 if full else 4))
+        except F.FheError as e:
+            if e.code != F.FHE_E_OOM:
+                raise
+            mids.append(None)
+            refused.append({"model": specs[k][0], "error": str(e)})
+    mix = np.array([0.5, 0.3, 0.2]) * np.array([mid is not None for mid in mids])
     rng = np.random.default_rng(5)
     n_req = args.requests
-    which = rng.choice(3, size=n_req, p=[0.5, 0.3, 0.2])
+    which = rng.choice(3, size=n_req, p=mix / mix.sum())
     gaps = rng.exponential(1.0 / args.rate, size=n_req)
     # client side: every request's image encrypted before the stream starts
     reqs = []
@@ -876,6 +893,7 @@ def run_serving(args):
                                   "ResNet-18-ensemble shapes (%s, N=2^%d, %d primes)"
                                   % (args.rate, n_req, "full size" if full else "small forms", pre["logn"],
                                      pre["L"] + 1 + pre["alpha"]),
+                      "refused_models": refused,
                       "completed": done, "p50_ms": round(p50, 2), "p99_ms": round(p99, 2),
                       "img_s": round(done / (t_end - t0), 3), "per_model": per_model}), flush=True)
     F.fhe_server_destroy(server)
@@ -953,6 +971,8 @@ def main():
     ap.add_argument("--profile-uniform", action="store_true",
                     help="run one uniform batch inside the NVTX range bench_timed and exit (for ncu launch lists)")
     ap.add_argument("--members", type=int, default=3, help="resnet18_ensemble: ensemble members (1..8)")
+    ap.add_argument("--chunk", type=int, default=0,
+                    help="resnet18_ensemble: MAC sources per linear chunk (0: the library's default, 160)")
     ap.add_argument("--requests", type=int, default=1000, help="serving: number of requests")
     ap.add_argument("--rate", type=float, default=20.0, help="serving: mean arrivals per second")
     ap.add_argument("--serving-size", default="small", choices=["small", "full"],

@@ -113,6 +113,11 @@ int fhe_ctx_set_linear_chunk(fhe_ctx *ctx, int lin_chunk_srcs);
  * distinct rows fit (at least one group per batch; default 4 GiB).
  * Bit-neutral. */
 int fhe_ctx_set_encode_scratch(fhe_ctx *ctx, size_t bytes);
+/* At most max_items items per launch of a whole key switch of a network
+ * step (activations, rotate-and-sum), so that its workspace is sized for
+ * max_items (0, the default: any number).  Pipelines size their per-segment
+ * workspaces by it when they are created.  Bit-neutral. */
+int fhe_ctx_set_keyswitch_batch(fhe_ctx *ctx, int max_items);
 /* Host-side fault injection (no counterpart in the paper): after `after`
  * further device allocations through the context succeed, the next one is
  * refused with FHE_E_OOM, as cudaMalloc's own refusal would be, and the

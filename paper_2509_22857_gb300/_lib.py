@@ -78,6 +78,7 @@ def lib() -> ctypes.CDLL:
             "fhe_ctx_create": (c_int, [ctypes.POINTER(FheParams), PP]),
             "fhe_ctx_destroy": (c_int, [V]),
             "fhe_ctx_set_encode_scratch": (c_int, [V, c_size]),
+            "fhe_ctx_set_keyswitch_batch": (c_int, [V, c_int]),
             "fhe_ctx_set_linear_chunk": (c_int, [V, c_int]),
             "fhe_ctx_inject_alloc_failure": (c_int, [V, c_int]),
             "fhe_ctx_primes": (c_int, [V, P_U64, c_size, ctypes.POINTER(c_size)]),
@@ -190,6 +191,10 @@ def fhe_ctx_inject_alloc_failure(ctx, after: int):
 
 def fhe_ctx_set_encode_scratch(ctx, n_bytes: int):
     _check(lib().fhe_ctx_set_encode_scratch(ctx, int(n_bytes)))
+
+
+def fhe_ctx_set_keyswitch_batch(ctx, max_items: int):
+    _check(lib().fhe_ctx_set_keyswitch_batch(ctx, int(max_items)))
 
 
 def fhe_ctx_primes(ctx) -> List[int]:
@@ -508,7 +513,8 @@ def fhe_sk_export(sk, n_words: int) -> np.ndarray:
 
 
 EXPORTED = ["fhe_last_error", "fhe_kernel_launches", "fhe_ctx_create", "fhe_ctx_destroy", "fhe_ctx_primes",
-            "fhe_ctx_set_linear_chunk", "fhe_ctx_set_encode_scratch", "fhe_ctx_inject_alloc_failure", "fhe_keygen",
+            "fhe_ctx_set_linear_chunk", "fhe_ctx_set_encode_scratch", "fhe_ctx_set_keyswitch_batch",
+            "fhe_ctx_inject_alloc_failure", "fhe_keygen",
             "fhe_sk_free", "fhe_evk_free", "fhe_evk_galois", "fhe_encode", "fhe_pt_free", "fhe_encrypt",
             "fhe_decrypt", "fhe_decode", "fhe_ct_free", "fhe_ct_info", "fhe_ct_export", "fhe_ct_import",
             "fhe_rotate", "fhe_square", "fhe_rescale", "fhe_add", "fhe_mul_plain", "fhe_model_load",

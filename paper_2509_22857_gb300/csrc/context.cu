@@ -513,6 +513,12 @@ extern "C" int fhe_ctx_set_encode_scratch(fhe_ctx *ctx, size_t bytes) {
     return FHE_OK;
 }
 
+extern "C" int fhe_ctx_set_keyswitch_batch(fhe_ctx *ctx, int max_items) {
+    if (!ctx || max_items < 0) return fhe_fail(FHE_E_INVAL, "bad argument");
+    ctx->ks_item_cap = max_items;
+    return FHE_OK;
+}
+
 extern "C" int fhe_ctx_primes(const fhe_ctx *ctx, uint64_t *out, size_t cap, size_t *n) {
     if (!ctx || !n) return fhe_fail(FHE_E_INVAL, "null argument");
     *n = ctx->primes.size();

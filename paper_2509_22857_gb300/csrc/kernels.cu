@@ -982,7 +982,13 @@ __global__ void k_decrypt(DevCtx c, const u64 *ct, const u64 *s, u64 *m, int lev
 // reduced only when the sum could leave Barrett's range: with b = bitlen(q),
 // K products of residues stay below K q^2 < 2^(b+62) for K <= 2^(62-b)
 // (16 terms for 58-bit primes).
-__global__ void __launch_bounds__(256, 3) k_mac(DevCtx c, MacArgs a, int tc) {
+#ifndef MAC_U
+#define MAC_U 2          // single terms whose loads are issued together
+#endif
+#ifndef MAC_MINB
+#define MAC_MINB 3
+#endif
+__global__ void __launch_bounds__(256, MAC_MINB) k_mac(DevCtx c, MacArgs a, int tc) {
     // each thread owns two adjacent coefficients (16-byte loads)
     const int limb = blockIdx.z;
     const ModQ m = c.primes[limb].m;
@@ -1001,11 +1007,14 @@ __global__ void __launch_bounds__(256, 3) k_mac(DevCtx c, MacArgs a, int tc) {
         int t = G.term_begin;
         while (t < G.term_end) {
             const int run = a.terms[t].run;
-            if (run <= 1 && t + 1 < G.term_end && a.terms[t + 1].run <= 1) {
-                // two single terms: their loads are in flight together
-                ulonglong2 p[2], x0[2], x1[2];
+            bool singles = run <= 1 && t + MAC_U - 1 < G.term_end;
 #pragma unroll
-                for (int k = 0; k < 2; k++) {
+            for (int k = 1; k < MAC_U; k++) singles = singles && a.terms[t + min(k, G.term_end - 1 - t)].run <= 1;
+            if (singles) {
+                // MAC_U single terms: their loads are in flight together
+                ulonglong2 p[MAC_U], x0[MAC_U], x1[MAC_U];
+#pragma unroll
+                for (int k = 0; k < MAC_U; k++) {
                     const MacTerm T = a.terms[t + k];
                     const MacSrc S = a.srcs[T.src];
                     const u64 *sp = S.base + (long long)img * S.item + off;
@@ -1014,14 +1023,14 @@ __global__ void __launch_bounds__(256, 3) k_mac(DevCtx c, MacArgs a, int tc) {
                     x1[k] = *reinterpret_cast<const ulonglong2 *>(sp + P);
                 }
 #pragma unroll
-                for (int k = 0; k < 2; k++) {
+                for (int k = 0; k < MAC_U; k++) {
                     mac(a00, p[k].x, x0[k].x);
                     mac(a01, p[k].y, x0[k].y);
                     mac(a10, p[k].x, x1[k].x);
                     mac(a11, p[k].y, x1[k].y);
                 }
-                cnt += 2;
-                t += 2;
+                cnt += MAC_U;
+                t += MAC_U;
             } else {
                 // one term, or a run of terms sharing one plaintext: the
                 // run's sources are added mod q (two at a time), then one
@@ -1063,8 +1072,8 @@ __global__ void __launch_bounds__(256, 3) k_mac(DevCtx c, MacArgs a, int tc) {
                 cnt += 1;
                 t += len;
             }
-            // at most two products before the next check
-            if (cnt + 2 > kmax) {
+            // at most MAC_U products before the next check
+            if (cnt + MAC_U > kmax) {
                 a00 = U128{barrett(a00, m), 0};
                 a01 = U128{barrett(a01, m), 0};
                 a10 = U128{barrett(a10, m), 0};
@@ -1410,7 +1419,27 @@ static cudaError_t launch_keyswitch_part(const DevCtx &c, const LevelTab &lt, co
     return cudaGetLastError();
 }
 
-cudaError_t launch_rescale(const DevCtx &c, const LevelTab &lt, const RescaleArgs &a, cudaStream_t s) {
+static cudaError_t launch_rescale_part(const DevCtx &c, const LevelTab &lt, const RescaleArgs &a, cudaStream_t s);
+
+// Grids put items x polys x limbs on grid.y (at most 65535): larger batches
+// are launched in parts of consecutive items.
+cudaError_t launch_rescale(const DevCtx &c, const LevelTab &lt, const RescaleArgs &args, cudaStream_t s) {
+    if (args.level < 1 || args.n_poly < 1) return cudaErrorInvalidValue;
+    const int per = 65535 / (args.n_poly * args.level);
+    if (per < 1) return cudaErrorInvalidValue;
+    for (int i0 = 0; i0 < args.n_items; i0 += per) {
+        RescaleArgs a = args;
+        a.n_items = std::min(per, args.n_items - i0);
+        a.in = args.in + (long long)i0 * args.in_item;
+        a.out = args.out + (long long)i0 * args.out_item;
+        a.ws = args.ws + ((long long)i0 * args.n_poly << c.logN);
+        const cudaError_t e = launch_rescale_part(c, lt, a, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+static cudaError_t launch_rescale_part(const DevCtx &c, const LevelTab &lt, const RescaleArgs &a, cudaStream_t s) {
     const int tc = tiles_col(c), B = a.n_items, lv = a.level;
     if (lv < 1) return cudaErrorInvalidValue;
     DISPATCH_LOGR(c.logR2, k_rs_intt_row, dim3(tc, B * a.n_poly), c, a);

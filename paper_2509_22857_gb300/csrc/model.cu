@@ -387,8 +387,24 @@ struct Exec {
         *err = FHE_OK;
         return it->second;
     }
+    // A whole key switch of many items runs in launches of at most the
+    // context's ks_item_cap items (its workspace is then sized for the cap);
+    // the phases of a split key switch carry state and run whole.
     int keyswitch(const KsArgs &a, int phases = KS_ALL) {
-        return op_keyswitch(m->ctx, a, s, pers ? pers->ks_ws : nullptr, phases);
+        const int cap = m->ctx->ks_item_cap;
+        if (phases != KS_ALL || cap <= 0 || a.n_items <= cap)
+            return op_keyswitch(m->ctx, a, s, pers ? pers->ks_ws : nullptr, phases);
+        for (int i0 = 0; i0 < a.n_items; i0 += cap) {
+            KsArgs b = a;
+            b.n_items = std::min(cap, a.n_items - i0);
+            b.d = a.d + (long long)i0 * a.d_item;
+            if (a.add0) b.add0 = a.add0 + (long long)i0 * a.add_item;
+            if (a.add1) b.add1 = a.add1 + (long long)i0 * a.add_item;
+            if (a.base) b.base = a.base + (long long)i0 * a.base_item;
+            b.out = a.out + (long long)i0 * a.out_item;
+            FHE_TRY(op_keyswitch(m->ctx, b, s, pers ? pers->ks_ws : nullptr, phases));
+        }
+        return FHE_OK;
     }
 
     // out = base + rot(x, step) for n items of one tensor-like layout
@@ -1167,7 +1183,10 @@ extern "C" int fhe_pipeline_create(fhe_ctx *c, const fhe_model *mc, const fhe_ev
             }
             int items = 0;
             if (st.kind == FHE_STEP_LINEAR) items = group;
-            if (st.kind == FHE_STEP_ACT || st.kind == FHE_STEP_ROTSUM) items = group * ti.n_ct;
+            if (st.kind == FHE_STEP_ACT || st.kind == FHE_STEP_ROTSUM) {
+                items = group * ti.n_ct;
+                if (c->ks_item_cap > 0) items = std::min(items, c->ks_item_cap);
+            }
             ks_words = std::max(ks_words, (size_t)items * ks_workspace_words(c->dc, ti.level));
             if (st.kind == FHE_STEP_RESCALE) rs_words = std::max(rs_words, (size_t)group * ti.n_ct * 2 * (size_t)c->N);
         }

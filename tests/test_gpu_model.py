@@ -171,6 +171,26 @@ def test_per_layer_entry_points(setup):
             F.fhe_ct_free(h)
 
 
+def test_keyswitch_item_cap_changes_nothing(setup):
+    """Whole key switches of a step (activations, rotate-and-sum) split into
+    launches of at most 2 items give the ciphertexts of one launch."""
+    s = setup
+    F = s.F
+    n_out = s.pm.tensors[s.pm.output].layout.n_ct
+    imgs = [s.encrypt(i)[1] for i in range(3)]
+    flat = [h for cts in imgs for h in cts]
+    whole = F.fhe_infer(s.ctx, s.model, s.evk, flat, 3, n_out)
+    F.fhe_ctx_set_keyswitch_batch(s.ctx, 2)
+    try:
+        parts = F.fhe_infer(s.ctx, s.model, s.evk, flat, 3, n_out)
+    finally:
+        F.fhe_ctx_set_keyswitch_batch(s.ctx, 0)
+    for a, b in zip(whole, parts):
+        assert np.array_equal(F.fhe_ct_export(a, s.prm.N)[0], F.fhe_ct_export(b, s.prm.N)[0])
+    for h in whole + parts + flat:
+        F.fhe_ct_free(h)
+
+
 def test_chunked_linear_steps_change_nothing(setup):
     """Linear steps split into chunks of few sources (rotated copies made and
     consumed a chunk at a time, MAC outputs accumulated over chunks) give

@@ -116,3 +116,32 @@ def test_batch_beyond_one_launch_of_33_digit_modup(paper):
     for h in outs + cts:
         F.fhe_ct_free(h)
     F.fhe_model_free(model)
+
+
+def test_rescale_batch_beyond_one_launch(paper):
+    """1100 ciphertexts rescaled together at level 32 (2 polynomials x 32
+    limbs per item: one launch's grid takes 1023 items, so the batch runs in
+    two parts); each equals its one-ciphertext fhe_rescale."""
+    from types import SimpleNamespace
+    from paper_2509_22857_gb300 import model as M
+    F, ctx, prm, S, keys, sk, evk = paper
+    lay = SimpleNamespace(n_ct=1)
+    scale = prm.scale ** 3
+    prog = M.Program(tensors=[M.TInfo(lay, prm.L, scale), M.TInfo(lay, prm.L - 1, scale / prm.q[prm.L])],
+                     steps=[{"kind": F.STEP_RESCALE, "src": 0, "dst": 1}], input=0, output=1)
+    desc = M.ModelDesc(prog, prm.N // 2)
+    model = F.fhe_model_load(ctx, desc.desc)
+    z = np.random.default_rng(5).uniform(-1, 1, prm.N // 2)
+    pt = F.fhe_encode(ctx, z, scale, prm.L)
+    B = 1100
+    cts = [F.fhe_encrypt(ctx, sk, pt, 500 + i) for i in range(B)]
+    F.fhe_pt_free(pt)
+    outs = F.fhe_infer(ctx, model, evk, cts, B, 1)
+    for i in (0, 1022, 1023, 1099):
+        one = F.fhe_ct_import(ctx, F.fhe_ct_export(cts[i], prm.N)[0], prm.L, scale)
+        F.fhe_rescale(ctx, one)
+        assert np.array_equal(F.fhe_ct_export(outs[i], prm.N)[0], F.fhe_ct_export(one, prm.N)[0]), i
+        F.fhe_ct_free(one)
+    for h in outs + cts:
+        F.fhe_ct_free(h)
+    F.fhe_model_free(model)
