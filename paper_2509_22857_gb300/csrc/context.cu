@@ -606,7 +606,7 @@ int enc_tables(fhe_ctx *ctx, const EncTab **out) {
 
 int op_encode_to(fhe_ctx *ctx, const double *m_host, int level, u64 *dst, cudaStream_t s) {
     double *dm;
-    FHE_CU(cudaMallocAsync((void **)&dm, ctx->N * sizeof(double), s));
+    FHE_ALLOC_ASYNC(&dm, ctx->N * sizeof(double), s);
     FHE_CU(cudaMemcpyAsync(dm, m_host, ctx->N * sizeof(double), cudaMemcpyHostToDevice, s));
     FHE_CU(launch_double_to_limbs(ctx->dc, dm, dst, level + 1, s));
     FHE_CU(cudaFreeAsync(dm, s));
@@ -1084,7 +1084,7 @@ extern "C" int fhe_square(fhe_ctx *c, const fhe_evk *evk, const fhe_ct *in, fhe_
     const int nl = in->level + 1;
     const long long N = c->N;
     u64 *t3;
-    FHE_CU(cudaMallocAsync((void **)&t3, (size_t)3 * nl * N * 8, s));
+    FHE_ALLOC_ASYNC(&t3, (size_t)3 * nl * N * 8, s);
     FHE_CU(launch_square_act(c->dc, in->d, 0, nullptr, nullptr, t3, 0, 1, in->level, s));
     fhe_ct *o;
     FHE_TRY(new_ct(c, in->level, 2, in->scale * in->scale, &o));

@@ -19,6 +19,17 @@ int fhe_fail(int code, const std::string &msg);
         if (e_ != cudaSuccess) return fhe_fail(FHE_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
     } while (0)
 
+// a stream-ordered allocation: refusal is FHE_E_OOM, as for dev_alloc
+#define FHE_ALLOC_ASYNC(ptr, bytes, stream)                                                        \
+    do {                                                                                           \
+        cudaError_t e_ = cudaMallocAsync((void **)(ptr), (bytes), (stream));                       \
+        if (e_ == cudaErrorMemoryAllocation) {                                                     \
+            cudaGetLastError();                                                                    \
+            return fhe_fail(FHE_E_OOM, "cudaMallocAsync(" + std::to_string((size_t)(bytes)) + "): out of memory"); \
+        }                                                                                          \
+        if (e_ != cudaSuccess) return fhe_fail(FHE_E_CUDA, std::string("cudaMallocAsync: ") + cudaGetErrorString(e_)); \
+    } while (0)
+
 #define FHE_TRY(call)              \
     do {                           \
         int r_ = (call);           \

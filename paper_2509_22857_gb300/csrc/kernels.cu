@@ -222,9 +222,13 @@ __device__ __forceinline__ void xchg_row_BA(u64 (&x)[16], u64 *sm, int tau, int 
 }
 
 constexpr int SMEM_WORDS = 4096 + 256;
-// elements per thread whose basis-conversion sums are accumulated together
+// elements per thread whose basis-conversion sums are accumulated together,
+// and the conversion kernels' blocks per SM (register bound)
 #ifndef CONV_CHUNK
 #define CONV_CHUNK 4
+#endif
+#ifndef CONV_MINB
+#define CONV_MINB 3
 #endif
 
 // ================================================================ plain NTT
@@ -400,7 +404,7 @@ __global__ void __launch_bounds__(NT) k_ks_intt_col(DevCtx c, LevelTab lt, KsArg
 
 // (3) ModUp: basis conversion of digit j to ext limb t fused with NTT columns
 template <int LOGR>
-__global__ void __launch_bounds__(NT, 3) k_ks_modup_col(DevCtx c, LevelTab lt, KsArgs a, KsLayout ly) {
+__global__ void __launch_bounds__(NT, CONV_MINB) k_ks_modup_col(DevCtx c, LevelTab lt, KsArgs a, KsLayout ly) {
     using Gm = Geo<LOGR>;
     __shared__ u64 sm[SMEM_WORDS];
     const int ext = lt.ext, nd = lt.n_digits;
@@ -679,7 +683,7 @@ __global__ void k_ks_md_overflow(DevCtx c, KsArgs a, KsLayout ly) {
 
 // (7) ModDown: basis conversion P -> q_i (minus floor(P/2)) fused with NTT columns
 template <int LOGR>
-__global__ void __launch_bounds__(NT, 3) k_ks_md_conv_col(DevCtx c, LevelTab lt, KsArgs a, KsLayout ly) {
+__global__ void __launch_bounds__(NT, CONV_MINB) k_ks_md_conv_col(DevCtx c, LevelTab lt, KsArgs a, KsLayout ly) {
     using Gm = Geo<LOGR>;
     __shared__ u64 sm[SMEM_WORDS];
     const int al = c.alpha;

@@ -317,7 +317,7 @@ struct Exec {
         if (buf[t]) return FHE_OK;
         if (pers) return fhe_fail(FHE_E_INVAL, "internal: tensor without a buffer in pipeline mode");
         const size_t bytes = (size_t)B * item(t) * 8;
-        FHE_CU(cudaMallocAsync((void **)&buf[t], bytes, s));
+        FHE_ALLOC_ASYNC(&buf[t], bytes, s);
         return FHE_OK;
     }
     void release(int t) {
@@ -330,7 +330,7 @@ struct Exec {
     // a temporary of the current step (index idx): stream-ordered, or persistent
     int tmp(int idx, size_t bytes, u64 **out) {
         if (!pers) {
-            FHE_CU(cudaMallocAsync((void **)out, bytes, s));
+            FHE_ALLOC_ASYNC(out, bytes, s);
             return FHE_OK;
         }
         auto key = std::make_pair(cur_step, idx);
@@ -351,7 +351,7 @@ struct Exec {
     int work_list(const char *host, size_t bytes, char **out) {
         if (!pers) {
             host_stage.emplace_back(host, host + bytes);
-            FHE_CU(cudaMallocAsync((void **)out, bytes + 16, s));
+            FHE_ALLOC_ASYNC(out, bytes + 16, s);
             FHE_CU(cudaMemcpyAsync(*out, host_stage.back().data(), bytes, cudaMemcpyHostToDevice, s));
             return FHE_OK;
         }
