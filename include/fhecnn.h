@@ -284,6 +284,17 @@ typedef struct {
     const int64_t *sparse_vec_begin; /* [n_vecs + 1] */
     const int32_t *sparse_slot;      /* [nnz] */
     const double *sparse_val;        /* [nnz] */
+    /*
+     * ACT with one coefficient pair per channel (node fusing Case 1, Sec. 4.1:
+     * a batch norm fused into the activation): when act_c1_vecs is non-null,
+     * c1 and c0 are unused and ciphertext k of the tensor computes
+     * x^2 + v1_k (.) x + v0_k, with v1_k = act_c1_vecs[k] encoded at
+     * act_c1_scale and v0_k = act_c0_vecs[k] at act_c0_scale (slot vectors,
+     * [n_ct][n_slots]; encoded once at load, at the tensor's level).
+     */
+    const double *act_c1_vecs;
+    const double *act_c0_vecs;
+    double act_c1_scale, act_c0_scale;
 } fhe_step_desc;
 
 typedef struct {

@@ -77,6 +77,11 @@ def forward_plain(net: List[Dict], raw: Dict, img: np.ndarray) -> np.ndarray:
             y = p["gamma"][:, None, None] * (y - p["mu"][:, None, None]) / p["sigma"][:, None, None] \
                 + p["beta"][:, None, None]
             vals[i] = y
+        elif op == "bn":
+            p = raw[i]
+            x = vals[nd["src"]]
+            vals[i] = p["gamma"][:, None, None] * (x - p["mu"][:, None, None]) / p["sigma"][:, None, None] \
+                + p["beta"][:, None, None]
         elif op == "act":
             p = raw[i]
             x = vals[nd["src"]]
@@ -91,12 +96,59 @@ def forward_plain(net: List[Dict], raw: Dict, img: np.ndarray) -> np.ndarray:
     return vals[len(net) - 1]
 
 
+# ------------------------------------------------------------ node fusing
+# Sec. 4.1, with batch norm written B(x) = b1 x + b0 (b1 = gamma / sigma,
+# b0 = beta - b1 mu) and the activation P(x) = c2 x^2 + c1 x + c0.
+
+def bn_linear(p: Dict) -> Tuple[np.ndarray, np.ndarray]:
+    """(b1, b0) of a batch norm"""
+    b1 = p["gamma"] / p["sigma"]
+    return b1, p["beta"] - b1 * p["mu"]
+
+
+def fuse_bn_act(b1, b0, c2, c1, c0):
+    """Case 1, P(B(x)) = p2 x^2 + p1 x + p0 (the appendix's derivation):
+    p2 = b1^2 c2, p1 = b1 (2 b0 c2 + c1), p0 = b0^2 c2 + b0 c1 + c0."""
+    return b1 * b1 * c2, b1 * (2.0 * b0 * c2 + c1), b0 * b0 * c2 + b0 * c1 + c0
+
+
+def fuse_bn_bn_add_act(bx1, bx0, by1, by0, c2, c1, c0):
+    """Case 3, P(B_X(x) + B_Y(y)) = S(x, y) = dx2 x^2 + dy2 y^2 + dxy x y +
+    dx x + dy y + d0, with s = bx0 + by0: dx2 = c2 bx1^2, dy2 = c2 by1^2,
+    dxy = 2 c2 bx1 by1, dx = bx1 (2 c2 s + c1), dy = by1 (2 c2 s + c1),
+    d0 = c2 s^2 + c1 s + c0.  Returns (dx2, dy2, dxy, dx, dy, d0)."""
+    s = bx0 + by0
+    return (c2 * bx1 * bx1, c2 * by1 * by1, 2.0 * c2 * bx1 * by1, bx1 * (2.0 * c2 * s + c1),
+            by1 * (2.0 * c2 * s + c1), c2 * s * s + c1 * s + c0)
+
+
+def fuse_bn_add_act(bx1, bx0, c2, c1, c0):
+    """Case 4 (identity shortcut), P(B_X(x) + y) = S(x, y): dx2 = c2 bx1^2,
+    dy2 = c2, dxy = 2 c2 bx1, dx = bx1 (2 c2 bx0 + c1), dy = 2 c2 bx0 + c1,
+    d0 = c2 bx0^2 + c1 bx0 + c0.  Returns (dx2, dy2, dxy, dx, dy, d0)."""
+    return (c2 * bx1 * bx1, c2 * np.ones_like(bx1), 2.0 * c2 * bx1, bx1 * (2.0 * c2 * bx0 + c1),
+            2.0 * c2 * bx0 + c1, c2 * bx0 * bx0 + c1 * bx0 + c0)
+
+
+def _scale_in(u, w: np.ndarray) -> np.ndarray:
+    """multiply the input channels of weights w [cout, cin, ...] by u (a
+    scalar or one value per input channel)"""
+    if np.ndim(u) == 0:
+        return w * u
+    return w * np.reshape(u, (1, -1) + (1,) * (w.ndim - 2))
+
+
 def transform(net: List[Dict], raw: Dict) -> Dict:
     """Folded and redistributed parameters.  Operation order (fixed):
     b1 = gamma / sigma; b0 = beta - b1 * mu; omega = (w * b1[o]) * u_in;
     alpha = bias * b1 + b0; act: c1 = b / a, c0 = c / a, u = a;
     pool: u = u_in / float(k*k); dense: w = w * u_in; identity shortcut:
-    multiply by u of the shortcut's source."""
+    multiply by u of the shortcut's source.  A batch norm that is a node of
+    its own (not after a convolution) must feed an activation: the two fuse
+    (Case 1, with b1 taken times the u of the batch norm's input) into
+    p2 x^2 + p1 x + p0 per channel, made monic: c1 = p1 / p2, c0 = p0 / p2,
+    u = p2 (one value per channel, taken up by the next convolution's or
+    dense layer's input channels)."""
     t: Dict = {}
     ups: Dict[int, float] = {}
     for i, nd in enumerate(net):
@@ -107,10 +159,26 @@ def transform(net: List[Dict], raw: Dict) -> Dict:
             p = raw[i]
             b1 = p["gamma"] / p["sigma"]
             b0 = p["beta"] - b1 * p["mu"]
-            omega = (p["w"] * b1[:, None, None, None]) * ups[nd["src"]]
+            omega = _scale_in(ups[nd["src"]], p["w"] * b1[:, None, None, None])
             alpha = p["bias"] * b1 + b0
             t[i] = {"w": omega, "bias": alpha}
             ups[i] = 1.0
+        elif op == "bn":
+            users = [j for j, m in enumerate(net) if m.get("src") == i or (isinstance(m.get("src"), list)
+                                                                            and i in m["src"])]
+            if [net[j]["op"] for j in users] != ["act"]:
+                raise ValueError("a batch norm of its own must feed one activation (node fusing Case 1)")
+            t[i] = {"fused_into": users[0]}
+            ups[i] = None
+        elif op == "act" and net[nd["src"]]["op"] == "bn":
+            # Case 1 on the batch norm's computed input x' = x / u: B(x) =
+            # (b1 u) x' + b0
+            p = raw[i]
+            bn_node = net[nd["src"]]
+            b1, b0 = bn_linear(raw[nd["src"]])
+            p2, p1, p0 = fuse_bn_act(b1 * ups[bn_node["src"]], b0, p["a"], p["b"], p["c"])
+            t[i] = {"c1": p1 / p2, "c0": p0 / p2}
+            ups[i] = p2
         elif op == "act":
             p = raw[i]
             t[i] = {"c1": p["b"] / p["a"], "c0": p["c"] / p["a"]}
@@ -119,12 +187,17 @@ def transform(net: List[Dict], raw: Dict) -> Dict:
             ups[i] = ups[nd["src"]] / float(nd["k"] * nd["k"])
         elif op == "dense":
             p = raw[i]
-            t[i] = {"w": p["w"] * ups[nd["src"]], "bias": p["bias"]}
+            u = ups[nd["src"]]
+            if np.ndim(u) != 0:
+                u = np.repeat(u, p["w"].shape[1] // len(u))   # inputs are channel-major
+            t[i] = {"w": p["w"] * u, "bias": p["bias"]}
             ups[i] = 1.0
         elif op == "add":
             a, b = nd["src"]
             # the main branch is a convolution (upsilon 1); an identity
             # shortcut from an activation carries that activation's upsilon
+            if net[b]["op"] != "conv" and np.ndim(ups[b]) != 0:
+                raise ValueError("an identity shortcut needs one upsilon for all channels")
             t[i] = {"shortcut_const": ups[b] if net[b]["op"] != "conv" else None}
             ups[i] = 1.0
     return t
@@ -139,9 +212,14 @@ def forward_transformed(net: List[Dict], t: Dict, img: np.ndarray) -> np.ndarray
         elif op == "conv":
             vals[i] = conv2d(vals[nd["src"]], t[i]["w"], nd["stride"], nd["pad"]) \
                 + t[i]["bias"][:, None, None]
+        elif op == "bn":
+            vals[i] = vals[nd["src"]]          # fused into the activation that follows
         elif op == "act":
             x = vals[nd["src"]]
-            vals[i] = x * x + t[i]["c1"] * x + t[i]["c0"]
+            c1, c0 = t[i]["c1"], t[i]["c0"]
+            if np.ndim(c1):
+                c1, c0 = c1[:, None, None], c0[:, None, None]
+            vals[i] = x * x + c1 * x + c0
         elif op == "pool":
             c, H, W = vals[nd["src"]].shape
             k = nd["k"]
@@ -220,6 +298,18 @@ def single_layout(c: int, B: int, n_slots: int) -> Layout:
 
 
 # =================================================================== program
+
+def channel_vectors(L: Layout, values: np.ndarray, n_slots: int) -> List[np.ndarray]:
+    """One slot vector per ciphertext of layout L holding values[c] at every
+    position of every replica of channel c (zero elsewhere)."""
+    vecs = [np.zeros(n_slots) for _ in range(L.n_ct)]
+    for ch, reps in enumerate(L.rep):
+        for ct, base in reps:
+            for h in range(L.H):
+                for w in range(L.W):
+                    vecs[ct][L.slot(base, h, w)] = values[ch]
+    return vecs
+
 
 def round_exact(v: float) -> int:
     """round half away from zero, exactly, for any finite double."""
@@ -416,16 +506,26 @@ class Compiler:
                 if i in shortcut_convs:
                     continue
                 node_t[i] = self._conv(node_t[nd["src"]], nd, [x[i] for x in ts], None)
+            elif op == "bn":
+                node_t[i] = node_t[nd["src"]]      # fused into the activation (Case 1)
             elif op == "act":
                 src = node_t[nd["src"]]
                 info = self.prog.tensors[src]
                 s = info.scale
                 s2 = s * s
                 out = self.prog.new(TensorInfo(info.layout, info.level, s2))
-                # constants: c1 at scale s (so c1*x is at s*s), c0 at scale s*s
-                self.prog.steps.append({"op": "act", "src": src, "dst": out,
-                                        "c1": round_exact(t[i]["c1"] * s),
-                                        "c0": round_exact(t[i]["c0"] * s2)})
+                if np.ndim(t[i]["c1"]):
+                    # per-channel coefficients (Case 1): slot vectors, c1
+                    # encoded at scale s (c1 (.) x is at s*s), c0 at s*s
+                    self.prog.steps.append({"op": "act", "src": src, "dst": out,
+                                            "c1_vecs": channel_vectors(info.layout, t[i]["c1"], n),
+                                            "c0_vecs": channel_vectors(info.layout, t[i]["c0"], n),
+                                            "c1_scale": s, "c0_scale": s2})
+                else:
+                    # constants: c1 at scale s (so c1*x is at s*s), c0 at scale s*s
+                    self.prog.steps.append({"op": "act", "src": src, "dst": out,
+                                            "c1": round_exact(t[i]["c1"] * s),
+                                            "c0": round_exact(t[i]["c0"] * s2)})
                 node_t[i] = self._maybe_rescale(out)
             elif op == "pool":
                 src = node_t[nd["src"]]
@@ -675,10 +775,15 @@ def run_he(S: C.CKKS, keys: C.Keys, prog: Program, cts: List[C.Ciphertext],
             vals[st["dst"]] = [S.rescale(x) for x in vals[st["src"]]]
         elif op == "act":
             outs = []
-            for x in vals[st["src"]]:
+            for k, x in enumerate(vals[st["src"]]):
                 y = S.relinearize(S.tensor_square(x), keys)
-                y = S.add(y, S.mul_const(x, st["c1"], x.scale))
-                y = S.add_const(y, st["c0"])
+                if "c1_vecs" in st:
+                    # per-channel coefficients: plaintext product and sum
+                    y = S.add(y, S.mul_plain(x, S.encode(st["c1_vecs"][k], st["c1_scale"], x.level)))
+                    y = S.add_plain(y, S.encode(st["c0_vecs"][k], st["c0_scale"], x.level))
+                else:
+                    y = S.add(y, S.mul_const(x, st["c1"], x.scale))
+                    y = S.add_const(y, st["c0"])
                 y.scale = dst_info.scale
                 outs.append(y)
             vals[st["dst"]] = outs

@@ -40,7 +40,9 @@ class FheStepDesc(ctypes.Structure):
                 ("n_bias", c_int), ("bias_out", P_I32), ("bias_vec", P_DBL),
                 ("c1", c_double), ("c0", c_double), ("value", c_double),
                 ("n_steps", c_int), ("steps", P_I32), ("level", c_int),
-                ("sparse_vec_begin", P_I64), ("sparse_slot", P_I32), ("sparse_val", P_DBL)]
+                ("sparse_vec_begin", P_I64), ("sparse_slot", P_I32), ("sparse_val", P_DBL),
+                ("act_c1_vecs", P_DBL), ("act_c0_vecs", P_DBL), ("act_c1_scale", c_double),
+                ("act_c0_scale", c_double)]
 
 
 class FheModelDesc(ctypes.Structure):

@@ -929,16 +929,19 @@ __global__ void k_add_const(DevCtx c, const u64 *a, long long a_item, const u64 
 }
 
 __global__ void k_square_act(DevCtx c, const u64 *in, long long in_item, const u64 *c1, const u64 *c0,
-                             u64 *out, long long out_item, int level) {
+                             u64 *out, long long out_item, int level, const u64 *c1v, const u64 *c0v, int n_ct) {
     const long long N = 1ll << c.logN;
     const int item = blockIdx.z;
     const int limb = blockIdx.y;
     const ModQ m = c.primes[limb].m;
     const long long P = (long long)(level + 1) * N;
-    const u64 w1 = c1 ? c1[limb] : 0, w0 = c0 ? c0[limb] : 0;
+    const u64 s1 = c1 ? c1[limb] : 0, s0 = c0 ? c0[limb] : 0;
+    // per-channel coefficients: this ciphertext's plaintexts, limb `limb`
+    const long long voff = (long long)(item % n_ct) * P + (long long)limb * N;
     const u64 *x = in + item * in_item + (long long)limb * N;
     u64 *o = out + item * out_item + (long long)limb * N;
     for (long long j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += (long long)gridDim.x * blockDim.x) {
+        const u64 w1 = c1v ? c1v[voff + j] : s1, w0 = c1v ? c0v[voff + j] : s0;
         const u64 a = x[j], b = x[P + j];
         U128 t0 = mul_wide(a, a);
         mac(t0, w1, a);
@@ -1490,9 +1493,12 @@ cudaError_t launch_add_const(const DevCtx &c, const u64 *a, long long a_item, co
 }
 
 cudaError_t launch_square_act(const DevCtx &c, const u64 *in, long long in_item, const u64 *c1, const u64 *c0,
-                              u64 *out, long long out_item, int n_items, int level, cudaStream_t s) {
+                              u64 *out, long long out_item, int n_items, int level, cudaStream_t s, const u64 *c1v,
+                              const u64 *c0v, int n_ct) {
+    if ((c1v == nullptr) != (c0v == nullptr) || n_ct < 1) return cudaErrorInvalidValue;
     COUNT_LAUNCH();
-    k_square_act<<<ew_grid(c, level + 1, n_items), 256, 0, s>>>(c, in, in_item, c1, c0, out, out_item, level);
+    k_square_act<<<ew_grid(c, level + 1, n_items), 256, 0, s>>>(c, in, in_item, c1, c0, out, out_item, level, c1v,
+                                                                 c0v, n_ct);
     return cudaGetLastError();
 }
 

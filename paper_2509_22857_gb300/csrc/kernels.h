@@ -140,9 +140,12 @@ cudaError_t launch_add_const(const DevCtx &c, const u64 *a, long long a_item, co
                              u64 *out, long long out_item, int n_items, int level, cudaStream_t s);
 // Tensor square with the activation's lower terms folded in:
 //   d0 = c0^2 + C1 c0 + C0, d1 = 2 c0 c1 + C1 c1, d2 = c1^2
+// with C1, C0 either one residue per limb (c1[l], c0[l]; nullable) or, when
+// c1v is non-null, NTT-domain plaintexts per ciphertext of the tensor: item
+// i uses c1v / c0v + (i % n_ct) * (level+1) * N (per-channel coefficients).
 cudaError_t launch_square_act(const DevCtx &c, const u64 *in, long long in_item, const u64 *c1,
                               const u64 *c0, u64 *out, long long out_item, int n_items, int level,
-                              cudaStream_t s);
+                              cudaStream_t s, const u64 *c1v = nullptr, const u64 *c0v = nullptr, int n_ct = 1);
 // copy limbs 0..new_level of every poly (mod-drop)
 cudaError_t launch_drop(const DevCtx &c, const u64 *in, long long in_item, int in_level, u64 *out,
                         long long out_item, int new_level, int n_items, int n_poly, cudaStream_t s);

@@ -38,6 +38,7 @@ struct MStep {
     int kind = 0, src = -1, src2 = -1, dst = -1;
     MLinear lin;
     u64 *c1 = nullptr, *c0 = nullptr, *cval = nullptr;   // per-limb residues
+    u64 *c1v = nullptr, *c0v = nullptr;                   // ACT per channel: [n_ct] plaintexts
     std::vector<int> rot;
     int level = 0;
 };
@@ -77,6 +78,28 @@ static int encode_vec(fhe_model *m, const double *vec, double scale, int level, 
     m->pt_bytes += bytes;
     FHE_TRY(op_encode_to(c, coef.data(), level, (u64 *)d, 0));
     *out = (u64 *)d;
+    return FHE_OK;
+}
+
+// per-channel activation coefficients: each ciphertext's two slot vectors
+// encoded at their scales and the tensor's level, contiguous per set
+static int encode_act_vecs(fhe_model *m, const fhe_step_desc &sd, const MTensor &ti, MStep *st) {
+    fhe_ctx *c = m->ctx;
+    const size_t ns = (size_t)c->N / 2;
+    const long long P = (long long)(ti.level + 1) * c->N;
+    for (int set = 0; set < 2; set++) {
+        void *d;
+        FHE_TRY(dev_alloc(c, &d, (size_t)ti.n_ct * P * 8));
+        m->owned.push_back(d);
+        const double *vecs = set ? sd.act_c0_vecs : sd.act_c1_vecs;
+        const double scale = set ? sd.act_c0_scale : sd.act_c1_scale;
+        std::vector<double> coef(c->N);
+        for (int k = 0; k < ti.n_ct; k++) {
+            c->enc.encode(vecs + (size_t)k * ns, nullptr, ns, scale, coef.data());
+            FHE_TRY(op_encode_to(c, coef.data(), ti.level, (u64 *)d + k * P, 0));
+        }
+        (set ? st->c0v : st->c1v) = (u64 *)d;
+    }
     return FHE_OK;
 }
 
@@ -216,6 +239,9 @@ extern "C" int fhe_model_load(fhe_ctx *c, const fhe_model_desc *d, fhe_model **o
             if (to.level != ti.level || to.n_ct != ti.n_ct) rc = fhe_fail(FHE_E_LEVEL, "act step levels");
             if (rc == FHE_OK) rc = residues_of(m.get(), sd.c1, ti.level, &st.c1);
             if (rc == FHE_OK) rc = residues_of(m.get(), sd.c0, ti.level, &st.c0);
+            if (rc == FHE_OK && (sd.act_c1_vecs != nullptr) != (sd.act_c0_vecs != nullptr))
+                rc = fhe_fail(FHE_E_INVAL, "act step: both per-channel vector sets or neither");
+            if (rc == FHE_OK && sd.act_c1_vecs) rc = encode_act_vecs(m.get(), sd, ti, &st);
             break;
         case FHE_STEP_CMUL:
             if (to.level != ti.level || to.n_ct != ti.n_ct) rc = fhe_fail(FHE_E_LEVEL, "cmul step levels");
@@ -734,7 +760,8 @@ struct Exec {
         const int n = B * m->tensors[st.src].n_ct;
         u64 *t3;
         FHE_TRY(tmp(0, (size_t)n * 3 * nlN * 8, &t3));
-        FHE_CU(launch_square_act(c->dc, buf[st.src], 2 * nlN, st.c1, st.c0, t3, 3 * nlN, n, lv, s));
+        FHE_CU(launch_square_act(c->dc, buf[st.src], 2 * nlN, st.c1, st.c0, t3, 3 * nlN, n, lv, s, st.c1v, st.c0v,
+                                 m->tensors[st.src].n_ct));
         KsArgs a;
         memset(&a, 0, sizeof(a));
         a.d = t3 + 2 * nlN;

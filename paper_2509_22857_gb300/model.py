@@ -38,11 +38,29 @@ from . import _lib as F
 
 # =========================================================== transforms
 
+def _by_input_channel(u, w: np.ndarray) -> np.ndarray:
+    """w [cout, cin, ...] times u (a scalar, or one value per input channel)"""
+    if np.ndim(u) == 0:
+        return w * u
+    return w * np.reshape(u, (1, -1) + (1,) * (w.ndim - 2))
+
+
+def fuse_bn_act(b1, b0, c2, c1, c0):
+    """Node fusing Case 1 (Sec. 4.1): P(B(x)) with B(x) = b1 x + b0 and
+    P(x) = c2 x^2 + c1 x + c0 is p2 x^2 + p1 x + p0 with p2 = b1^2 c2,
+    p1 = b1 (2 b0 c2 + c1), p0 = b0^2 c2 + b0 c1 + c0."""
+    return b1 * b1 * c2, b1 * (2.0 * b0 * c2 + c1), b0 * b0 * c2 + b0 * c1 + c0
+
+
 def prepare_params(net: List[Dict], raw: Dict) -> Dict[int, Dict]:
     """Folded, redistributed parameters per node.  Operation order:
     b1 = gamma/sigma; b0 = beta - b1*mu; w' = (w*b1[o])*u_in;
     bias' = bias*b1 + b0; activation c1 = b/a, c0 = c/a (u = a);
-    pool u = u_in/float(k*k); dense w' = w*u_in; identity shortcut times u."""
+    pool u = u_in/float(k*k); dense w' = w*u_in; identity shortcut times u.
+    A batch norm of its own (a "bn" node, not after a convolution) feeds one
+    activation and fuses into it (Case 1, b1 times the u of its input):
+    p2 x^2 + p1 x + p0 per channel, monic c1 = p1/p2, c0 = p0/p2, u = p2
+    per channel (taken up by the next layer's input channels)."""
     u: Dict[int, float] = {}
     out: Dict[int, Dict] = {}
     for idx, node in enumerate(net):
@@ -54,8 +72,22 @@ def prepare_params(net: List[Dict], raw: Dict) -> Dict[int, Dict]:
             p = raw[idx]
             b1 = p["gamma"] / p["sigma"]
             b0 = p["beta"] - b1 * p["mu"]
-            out[idx] = dict(w=(p["w"] * b1.reshape(-1, 1, 1, 1)) * u[node["src"]], bias=p["bias"] * b1 + b0)
+            out[idx] = dict(w=_by_input_channel(u[node["src"]], p["w"] * b1.reshape(-1, 1, 1, 1)),
+                            bias=p["bias"] * b1 + b0)
             u[idx] = 1.0
+        elif kind == "bn":
+            users = [n["op"] for n in net if n.get("src") == idx or
+                     (isinstance(n.get("src"), list) and idx in n["src"])]
+            if users != ["act"]:
+                raise ValueError("a batch norm of its own must feed one activation (node fusing Case 1)")
+            u[idx] = None
+        elif kind == "act" and net[node["src"]]["op"] == "bn":
+            p, q = raw[idx], raw[node["src"]]
+            b1 = q["gamma"] / q["sigma"]
+            b0 = q["beta"] - b1 * q["mu"]
+            p2, p1, p0 = fuse_bn_act(b1 * u[net[node["src"]]["src"]], b0, p["a"], p["b"], p["c"])
+            out[idx] = dict(c1=p1 / p2, c0=p0 / p2)
+            u[idx] = p2
         elif kind == "act":
             p = raw[idx]
             out[idx] = dict(c1=p["b"] / p["a"], c0=p["c"] / p["a"])
@@ -64,10 +96,15 @@ def prepare_params(net: List[Dict], raw: Dict) -> Dict[int, Dict]:
             u[idx] = u[node["src"]] / float(node["k"] * node["k"])
         elif kind == "dense":
             p = raw[idx]
-            out[idx] = dict(w=p["w"] * u[node["src"]], bias=p["bias"])
+            ud = u[node["src"]]
+            if np.ndim(ud) != 0:
+                ud = np.repeat(ud, p["w"].shape[1] // len(ud))   # inputs are channel-major
+            out[idx] = dict(w=p["w"] * ud, bias=p["bias"])
             u[idx] = 1.0
         elif kind == "add":
             sc = node["src"][1]
+            if net[sc]["op"] != "conv" and np.ndim(u[sc]) != 0:
+                raise ValueError("an identity shortcut needs one upsilon for all channels")
             out[idx] = dict(shortcut=None if net[sc]["op"] == "conv" else u[sc])
             u[idx] = 1.0
     return out
@@ -495,14 +532,32 @@ class Planner:
 
     def act(self, src: int, ps: List[Dict]) -> int:
         prm = ps[0]
-        if any(p["c1"] != prm["c1"] or p["c0"] != prm["c0"] for p in ps):
+        if any(np.any(p["c1"] != prm["c1"]) or np.any(p["c0"] != prm["c0"]) for p in ps):
             raise ValueError("ensemble members must share the activation polynomial")
         info = self.p.tensors[src]
         s = info.scale
         s2 = s * s
         dst = self._t(info.layout, info.level, s2)
-        self._emit(kind=F.STEP_ACT, src=src, dst=dst, c1=_round_int(prm["c1"] * s), c0=_round_int(prm["c0"] * s2))
+        if np.ndim(prm["c1"]):
+            # per-channel coefficients (Case 1): slot vectors, c1 encoded at
+            # scale s (so c1 (.) x is at s*s) and c0 at s*s
+            self._emit(kind=F.STEP_ACT, src=src, dst=dst, c1=0.0, c0=0.0,
+                       c1_vecs=self._channel_vecs(info.layout, prm["c1"]),
+                       c0_vecs=self._channel_vecs(info.layout, prm["c0"]), c1_scale=s, c0_scale=s2)
+        else:
+            self._emit(kind=F.STEP_ACT, src=src, dst=dst, c1=_round_int(prm["c1"] * s),
+                       c0=_round_int(prm["c0"] * s2))
         return self._rule(dst)
+
+    def _channel_vecs(self, layout: SlotMap, values: np.ndarray) -> List[np.ndarray]:
+        """one slot vector per ciphertext with values[c] at every position of
+        every copy of channel c"""
+        vecs = [np.zeros(self.n) for _ in range(layout.n_ct)]
+        offs = layout.offsets()
+        for ch, copies in enumerate(layout.copies):
+            for ct, base in copies:
+                vecs[ct][base + offs] = values[ch]
+        return vecs
 
     def pool(self, src: int, k: int) -> int:
         info = self.p.tensors[src]
@@ -617,6 +672,8 @@ class Planner:
             elif kind == "conv":
                 if idx not in later:
                     node_t[idx] = self.conv(node_t[node["src"]], node, ps)
+            elif kind == "bn":
+                node_t[idx] = node_t[node["src"]]     # fused into the activation that follows
             elif kind == "act":
                 node_t[idx] = self.act(node_t[node["src"]], ps)
             elif kind == "pool":
@@ -763,6 +820,11 @@ class ModelDesc:
             elif st["kind"] == F.STEP_ACT:
                 d.c1 = st["c1"]
                 d.c0 = st["c0"]
+                if "c1_vecs" in st:
+                    d.act_c1_vecs = pd(arr(np.stack(st["c1_vecs"]), np.float64))
+                    d.act_c0_vecs = pd(arr(np.stack(st["c0_vecs"]), np.float64))
+                    d.act_c1_scale = st["c1_scale"]
+                    d.act_c0_scale = st["c0_scale"]
             elif st["kind"] == F.STEP_CMUL:
                 d.value = st["value"]
             elif st["kind"] == F.STEP_ROTSUM:

@@ -168,8 +168,39 @@ def vgg_mini() -> List[Dict]:
     return vgg(cfg=(4, "M", 8, "M", "M"), in_hw=8, fc=(8,), num_classes=10)
 
 
+def preact_mini() -> List[Dict]:
+    """A pre-activation residual network at a small size (8x8x3, 4 channels,
+    10 classes): 3x3 stem convolution and activation, two blocks x -> BN ->
+    act -> conv -> act -> conv, + x, then BN -> act -> 8x8 average pool ->
+    dense.  Each
+    block's batch norm follows an addition, not a convolution: it is a node
+    of its own, and the activation after it takes the fused per-channel
+    polynomial of Sec. 4.1 Case 1.  The inner convolutions carry their own
+    batch norm (folded, Case 2); the second has none (pre-activation)."""
+    net = [{"op": "input", "c": 3, "h": 8, "w": 8}]
+
+    def add(node):
+        net.append(node)
+        return len(net) - 1
+
+    x = add(_conv(0, 3, 4, 3, 1, 1, "stem"))
+    x = add({"op": "act", "src": x})
+    for b in range(2):
+        n = add({"op": "bn", "src": x, "c": 4})
+        a = add({"op": "act", "src": n})
+        c1 = add(_conv(a, 4, 4, 3, 1, 1, "b%d_conv1" % b))
+        a2 = add({"op": "act", "src": c1})
+        c2 = add(_conv(a2, 4, 4, 3, 1, 1, "b%d_conv2" % b, bn=False))
+        x = add({"op": "add", "src": [c2, x]})
+    n = add({"op": "bn", "src": x, "c": 4})
+    a = add({"op": "act", "src": n})
+    p = add({"op": "pool", "src": a, "k": 8})
+    add({"op": "dense", "src": p, "cin": 4, "cout": 10, "name": "fc"})
+    return net
+
+
 ARCHS = {"tiny": tiny, "resnet20": resnet20, "resnet32": resnet32, "resnet_mini": resnet_mini, "vgg11": vgg11,
-         "vgg_mini": vgg_mini, "resnet18": resnet18, "resnet18_mini": resnet18_mini}
+         "vgg_mini": vgg_mini, "resnet18": resnet18, "resnet18_mini": resnet18_mini, "preact_mini": preact_mini}
 
 
 # ------------------------------------------------------------- parameters
@@ -200,6 +231,10 @@ def params(net: List[Dict], model: int = 0) -> Dict[int, Dict[str, np.ndarray]]:
         elif nd["op"] == "act":
             out[i] = {"a": ra.normal(0.1, 0.02), "b": ra.normal(0.5, 0.05),
                       "c": ra.normal(0.0, 0.01)}
+        elif nd["op"] == "bn":
+            c = nd["c"]
+            out[i] = {"gamma": rb.uniform(0.5, 1.5, c), "beta": rb.normal(0.0, 0.1, c),
+                      "mu": rb.normal(0.0, 0.1, c), "sigma": rb.uniform(0.5, 1.5, c)}
     return out
 
 

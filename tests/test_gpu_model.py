@@ -13,6 +13,9 @@ pytestmark = pytest.mark.gpu
 # (arch, preset, layout[, input scale as a power of Delta])
 CASES = {"tiny": ("tiny", "tiny", "hw"), "mini": ("resnet_mini", "resnet_mini", "packed", 2),
          "vgg_mini": ("vgg_mini", "resnet_mini", "packed"),
+         # pre-activation blocks: batch norm fused into the activation after
+         # it, per-channel quadratic coefficients (node fusing Case 1)
+         "preact": ("preact_mini", "resnet_mini", "packed"),
          # ResNet-18's structure, an ensemble of 3 in the HW layout, weights
          # clustered jointly to 4 values per layer
          "ens": ("resnet18_mini", "resnet18_mini", "hw_ens")}
@@ -147,9 +150,11 @@ def test_per_layer_entry_points(setup):
     F = s.F
     ref = s.oracle_outputs(0)
     kinds = [st["kind"] for st in s.pm.steps]
-    # first linear step (a convolution), the first activation, the first rotsum
+    # first linear step (a convolution), the first activation (the first
+    # with per-channel coefficients where the network has one), the first rotsum
+    vec_act = [i for i, st in enumerate(s.pm.steps) if st["kind"] == 3 and "c1_vecs" in st]
     for kind, call in ((1, "conv"), (3, "act"), (4, "pool")):
-        i = kinds.index(kind)
+        i = vec_act[0] if kind == 3 and vec_act else kinds.index(kind)
         st = s.pm.steps[i]
         so = s.po.steps[i]
         ins = ref[so["src"]]
@@ -292,7 +297,7 @@ def test_oracle_chosen_schedule_bit_exact(case):
         F.fhe_ctx_destroy(ctx)
 
 
-@pytest.mark.parametrize("case", ["mini", "vgg_mini"])
+@pytest.mark.parametrize("case", ["mini", "vgg_mini", "preact"])
 def test_on_demand_encoding_equals_resident(case):
     """The same network with its packed convolutions' plaintexts encoded on
     the device each time a step runs (sparse rows, host encoder's operation

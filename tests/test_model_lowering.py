@@ -42,9 +42,17 @@ def _check(po, pm):
         assert ga == gb
         assert a["w_scale"] == b["w_scale"] and a["bias_scale"] == b["bias_scale"]
         assert {k: v.tobytes() for k, v in a["bias"].items()} == {k: v.tobytes() for k, v in b["bias"].items()}
-    co = [float(s[k]) for s in po.steps if s["op"] in ("act", "cmul") for k in ("c1", "c0", "value") if k in s]
-    cm = [s[k] for s in pm.steps if s["kind"] in (3, 5) for k in ("c1", "c0", "value") if k in s]
+    co = [float(s[k]) for s in po.steps if s["op"] in ("act", "cmul") and "c1_vecs" not in s
+          for k in ("c1", "c0", "value") if k in s]
+    cm = [s[k] for s in pm.steps if s["kind"] in (3, 5) and "c1_vecs" not in s
+          for k in ("c1", "c0", "value") if k in s]
     assert co == cm
+    # per-channel activations (node fusing Case 1): the same slot vectors and scales
+    vo = [(np.stack(s["c1_vecs"]).tobytes(), np.stack(s["c0_vecs"]).tobytes(), s["c1_scale"], s["c0_scale"])
+          for s in po.steps if s["op"] == "act" and "c1_vecs" in s]
+    vm = [(np.stack(s["c1_vecs"]).tobytes(), np.stack(s["c0_vecs"]).tobytes(), s["c1_scale"], s["c0_scale"])
+          for s in pm.steps if s["kind"] == 3 and "c1_vecs" in s]
+    assert vo == vm
     assert [s["steps"] for s in po.steps if s["op"] == "rotsum"] == \
         [s["steps"] for s in pm.steps if s["kind"] == 4]
 
@@ -59,6 +67,15 @@ def test_mini_resnet_program_matches_oracle():
 
 def test_mini_vgg_program_matches_oracle():
     _check(*_both("vgg_mini", "resnet_mini", "packed"))
+
+
+def test_mini_preact_program_matches_oracle():
+    """Pre-activation blocks: each block's batch norm fused into its
+    activation (Case 1), per-channel coefficients, per-channel upsilon taken
+    up by the next convolution and the dense layer."""
+    po, pm = _both("preact_mini", "resnet_mini", "packed")
+    assert sum(1 for s in pm.steps if s["kind"] == 3 and "c1_vecs" in s) == 3
+    _check(po, pm)
 
 
 @pytest.mark.slow

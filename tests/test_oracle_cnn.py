@@ -28,10 +28,12 @@ def test_avgpool_by_hand():
     assert p[0, 0, 0] == (0 + 1 + 4 + 5) / 4 and p[1, 1, 1] == (26 + 27 + 30 + 31) / 4
 
 
-@pytest.mark.parametrize("arch", ["tiny", "resnet20"])
+@pytest.mark.parametrize("arch", ["tiny", "resnet20", "preact_mini"])
 def test_transforms_preserve_the_function(arch):
-    """Batch-norm folding (Case 2) and forward weight redistribution give the
-    same network output (Sec. 4.1-4.2: functional equivalence)."""
+    """Batch-norm folding (Case 2), batch norm fused into the activation that
+    follows it (Case 1, the pre-activation network) and forward weight
+    redistribution give the same network output (Sec. 4.1-4.2: functional
+    equivalence)."""
     net = synth.ARCHS[arch]()
     raw = synth.params(net)
     t = cnn.transform(net, raw)
@@ -41,6 +43,65 @@ def test_transforms_preserve_the_function(arch):
         y0 = cnn.forward_plain(net, raw, img)
         y1 = cnn.forward_transformed(net, t, img)
         assert np.allclose(y0, y1, rtol=1e-9, atol=1e-12)
+
+
+def _poly(c2, c1, c0, x):
+    return c2 * x * x + c1 * x + c0
+
+
+def _bivariate(d, x, y):
+    dx2, dy2, dxy, dx, dy, d0 = d
+    return dx2 * x * x + dy2 * y * y + dxy * x * y + dx * x + dy * y + d0
+
+
+def test_node_fusing_closed_forms_equal_the_composition():
+    """Sec. 4.1 Cases 1, 3 and 4: each closed form evaluated at random points
+    equals the composition it replaces, P(B(x)), P(B_X(x) + B_Y(y)) and
+    P(B_X(x) + y), written out as separate affine and quadratic steps.
+    Every coefficient is exercised: a dropped term, a wrong sign or a swapped
+    operand changes the value at some of the points."""
+    rng = np.random.default_rng(7)
+    k = 64
+    bx1, bx0, by1, by0 = (rng.normal(size=k) for _ in range(4))
+    c2, c1, c0 = rng.normal(size=3)
+    x, y = rng.normal(size=k), rng.normal(size=k)
+    p = cnn.fuse_bn_act(bx1, bx0, c2, c1, c0)
+    assert np.allclose(_poly(*p, x), _poly(c2, c1, c0, bx1 * x + bx0), rtol=1e-12, atol=1e-12)
+    d3 = cnn.fuse_bn_bn_add_act(bx1, bx0, by1, by0, c2, c1, c0)
+    ref3 = _poly(c2, c1, c0, (bx1 * x + bx0) + (by1 * y + by0))
+    assert np.allclose(_bivariate(d3, x, y), ref3, rtol=1e-12, atol=1e-12)
+    d4 = cnn.fuse_bn_add_act(bx1, bx0, c2, c1, c0)
+    ref4 = _poly(c2, c1, c0, (bx1 * x + bx0) + y)
+    assert np.allclose(_bivariate(d4, x, y), ref4, rtol=1e-12, atol=1e-12)
+    # Case 4 is Case 3 with the shortcut's batch norm the identity
+    d3i = cnn.fuse_bn_bn_add_act(bx1, bx0, np.ones(k), np.zeros(k), c2, c1, c0)
+    for a, b in zip(d3i, d4):
+        assert np.allclose(a, b, rtol=1e-14, atol=1e-14)
+    # Case 1 with the identity batch norm is the activation itself
+    q = cnn.fuse_bn_act(np.ones(k), np.zeros(k), c2, c1, c0)
+    assert np.allclose(q[0], c2) and np.allclose(q[1], c1) and np.allclose(q[2], c0)
+    # the batch norm's affine form (b1, b0) reproduces (x - mu) gamma / sigma + beta
+    prm = {k2: rng.uniform(0.5, 1.5, size=k) for k2 in ("gamma", "sigma")}
+    prm.update(mu=rng.normal(size=k), beta=rng.normal(size=k))
+    b1, b0 = cnn.bn_linear(prm)
+    assert np.allclose(b1 * x + b0, (x - prm["mu"]) * prm["gamma"] / prm["sigma"] + prm["beta"])
+
+
+def test_case1_fusion_changes_function_if_coefficient_dropped():
+    """Sanity of the fused-activation check on a whole network: zeroing the
+    linear term of one fused activation changes the pre-activation network's
+    output."""
+    net = synth.preact_mini()
+    raw = synth.params(net)
+    t = cnn.transform(net, raw)
+    acts = [i for i, nd in enumerate(net) if nd["op"] == "act" and np.ndim(t[i]["c1"]) > 0]
+    assert len(acts) == 3
+    img = synth.image(0, net[0]["c"], net[0]["h"], net[0]["w"])
+    y0 = cnn.forward_plain(net, raw, img)
+    assert np.allclose(y0, cnn.forward_transformed(net, t, img), rtol=1e-9, atol=1e-12)
+    i = acts[1]
+    t[i] = dict(t[i], c1=np.zeros_like(t[i]["c1"]))
+    assert not np.allclose(y0, cnn.forward_transformed(net, t, img), rtol=1e-6)
 
 
 def test_transform_changes_function_if_receiver_not_updated():
@@ -102,6 +163,29 @@ def test_tiny_network_under_ckks_matches_float64():
     assert np.argmax(y) == np.argmax(ref)
     # three rescales (conv, activation, dense): output on q_0, q_1
     assert prog.tensors[prog.output_tensor].level == 1
+
+
+@pytest.mark.slow
+def test_preact_network_under_ckks_matches_float64():
+    """The pre-activation network homomorphically, its three batch norms
+    fused into per-channel activations (Case 1): decrypted logits within 1e-3
+    of the float64 network with separate batch norms, and the same argmax."""
+    net = synth.preact_mini()
+    raw = synth.params(net)
+    t = cnn.transform(net, raw)
+    prm = C.make_params(**synth.PRESETS["resnet_mini"])
+    prog = cnn.compile_he(net, t, prm, "packed")
+    assert sum(1 for s in prog.steps if s["op"] == "act" and "c1_vecs" in s) == 3
+    S = C.CKKS(prm)
+    keys = S.keygen(synth.SEED_KEYS, sorted(prog.rot_steps))
+    hwc = net[0]
+    img = synth.image(0, hwc["c"], hwc["h"], hwc["w"])
+    cts = cnn.encrypt_input(S, keys, prog, img, 0, synth.enc_seed)
+    vals = cnn.run_he(S, keys, prog, cts)
+    y = cnn.decrypt_logits(S, keys, prog, vals[prog.output_tensor])
+    ref = cnn.forward_plain(net, raw, img)
+    assert np.max(np.abs(y - ref)) < 1e-3
+    assert np.argmax(y) == np.argmax(ref)
 
 
 def test_resnet20_program_levels_follow_tower_reuse():
