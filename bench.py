@@ -301,6 +301,20 @@ def run_ours(args, rank, world):
         print(json.dumps({"profile_uniform": True, "batch": B}), flush=True)
         return None
 
+    knob_tuning = None
+    if args.tune_knobs:
+        # images per MAC block and key-switch batch, timed on one pipeline
+        # group's worth of images through the whole network (bit-neutral:
+        # the tuner checks every value gives the same ciphertexts)
+        from paper_2509_22857_gb300 import autotune as A
+        tuner = A.Tuner(args.autotune_cache)
+        nb = min(B, 8)
+        knob_tuning = {
+            "mac_images": A.tune_mac_images(tuner, ctx, model, evk, cts[:nb * n_in], nb, n_out, N,
+                                            candidates=(0, 1, 2, 4, 8), reps=1, model_key=PRESET),
+            "keyswitch_batch": A.tune_keyswitch_batch(tuner, ctx, model, evk, cts[:nb * n_in], nb, n_out, N,
+                                                      candidates=(8, 4, 2), reps=1, model_key=PRESET)}
+
     # where the time goes: one uniform batch with events around every phase
     outs, phase_ms = F.fhe_infer_profiled(ctx, model, evk, cts, B, n_out, stream)
     for h in outs:
@@ -443,6 +457,7 @@ def run_ours(args, rank, world):
                         "per step; segments run on concurrent streams, each tick replayed from a CUDA graph"
                         % (S, g, T),
             "group_tuning": group_tuning,
+            "knob_tuning": knob_tuning,
             "uniform_batch": B,
             "uniform_batch_img_s": round(img_s_uniform, 4),
             "single_img_s": round(img_s_single, 4),
@@ -986,6 +1001,8 @@ def main():
     ap.add_argument("--ticks", type=int, default=5,
                     help="pipeline ticks per timed step (every tick runs every segment, i.e. the whole network, "
                          "for the group at each level; a group of images leaves per tick)")
+    ap.add_argument("--tune-knobs", action="store_true",
+                    help="measure images per MAC block and the key-switch batch on the device first (reported)")
     ap.add_argument("--tune-group", action="store_true",
                     help="pick the pipeline's images per tick by measurement (2, 4, 8) before the timed run")
     args = ap.parse_args()

@@ -118,6 +118,13 @@ int fhe_ctx_set_encode_scratch(fhe_ctx *ctx, size_t bytes);
  * max_items (0, the default: any number).  Pipelines size their per-segment
  * workspaces by it when they are created.  Bit-neutral. */
 int fhe_ctx_set_keyswitch_batch(fhe_ctx *ctx, int max_items);
+/* Images per block of the plaintext MAC (1, 2, 4 or 8; 0, the default: the
+ * batch rounded up to a power of two, at most 8).  A block owns 512 /
+ * images_per_cta coefficients of one limb for that many images, so the
+ * plaintext coefficients it loads serve every image of the block.
+ * Bit-neutral (the sums are exact mod q).  A pipeline keeps the value its
+ * graphs were captured with.  FHE_E_INVAL for other values. */
+int fhe_ctx_set_mac_images(fhe_ctx *ctx, int images_per_cta);
 /* Host-side fault injection (no counterpart in the paper): after `after`
  * further device allocations through the context succeed, the next one is
  * refused with FHE_E_OOM, as cudaMalloc's own refusal would be, and the

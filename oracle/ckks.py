@@ -693,6 +693,53 @@ class CKKS:
             out[step] = Ciphertext(c, lv, ct.scale)
         return out
 
+    # -- double hoisting: rotations left in the extended basis
+    def encode_ext(self, z, scale: float, level: int) -> np.ndarray:
+        """encode()'s integer polynomial reduced modulo every prime of
+        Q_level u P, NTT domain: [ext][N]."""
+        m = encode_coeffs(z, self.prm.logn, scale)
+        prm = self.prm
+        return np.stack([ntt(from_double(m, prm.primes[t]), prm.primes[t], prm.psi[t])
+                         for t in self.ext_primes(level)])
+
+    def rotate_hoisted_ext(self, ct: Ciphertext, steps: Sequence[int], keys: Keys) -> Dict[int, np.ndarray]:
+        """Rotations of one ciphertext sharing one ModUp, left in Q_l u P:
+        for each step the inner product of sigma_k(ModUp(c1)) with that
+        step's key, plus P sigma_k(c0) on the Q limbs (P is 0 modulo the
+        special primes).  [2][ext][N] per step; its ModDown is exactly the
+        rotation of rotate_hoisted, since P sigma_k(c0) divides by P with
+        no remainder."""
+        prm = self.prm
+        lv = ct.level
+        ext = self.modup(ct.c[1], lv)
+        out = {}
+        for step in steps:
+            k, key = self._galois_key(step, keys)
+            acc = self.inner_product([self.galois_ext(x, lv, k) for x in ext], lv, key)
+            g0 = self.galois_ext(np.concatenate([ct.c[0], np.zeros((prm.alpha, prm.N), dtype=np.uint64)]), lv, k)
+            for t in range(lv + 1):
+                qt = prm.primes[t]
+                acc[0, t] = vadd(acc[0, t], vmul_scalar(g0[t], prm.P % qt, qt), qt)
+            out[step] = acc
+        return out
+
+    def mul_plain_ext(self, pair: np.ndarray, pt_ext: np.ndarray, level: int) -> np.ndarray:
+        """[2][ext][N] pair times a plaintext over Q_level u P, limb by limb."""
+        prm = self.prm
+        out = np.empty_like(pair)
+        for r in range(2):
+            for k, t in enumerate(self.ext_primes(level)):
+                out[r, k] = vmul(pair[r, k], pt_ext[k], prm.primes[t])
+        return out
+
+    def add_ext(self, a: np.ndarray, b: np.ndarray, level: int) -> np.ndarray:
+        prm = self.prm
+        out = np.empty_like(a)
+        for r in range(2):
+            for k, t in enumerate(self.ext_primes(level)):
+                out[r, k] = vadd(a[r, k], b[r, k], prm.primes[t])
+        return out
+
     def rotate_sum_lazy(self, terms: Sequence, keys: Keys, base: Ciphertext) -> Ciphertext:
         """base + sum_g rot(ct_g, g) with one ModDown: each term's ModUp and
         inner product (sigma_g on the extended limbs) are summed over Q_l u P,

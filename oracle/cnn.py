@@ -431,18 +431,23 @@ class Compiler:
     diagonals, levels, scales and rescale points."""
 
     def __init__(self, prm: C.Params, layout_kind: str, giants: Optional[List[int]] = None, members: int = 1,
-                 input_lambda: int = 1):
+                 input_lambda: int = 1, hoists: Optional[List[int]] = None):
         """giants: the giant-step size of each linear step in program order
         (any split r = g + b with b = r mod G is a valid evaluation of the
         same diagonals; the choice only moves work between baby and giant
         rotations).  Default: one block for convolutions, 8 blocks for the
-        packed dense layer, the whole slot vector in the HW layout."""
+        packed dense layer, the whole slot vector in the HW layout.
+        hoists: per linear step, 1 (each baby-step rotation brought back to
+        Q_l by its own ModDown) or 2 (double hoisting: the rotations stay in
+        Q_l u P, their plaintext products are summed there and each output
+        group takes one ModDown); default 1."""
         self.prm = prm
         self.n = prm.N // 2
         self.log_delta = math.log2(prm.scale)
         self.kind = layout_kind
         self.prog = Program()
         self.giants = giants
+        self.hoists = hoists
         self.n_linear = 0
         self.members = members
         # the client encrypts the image at scale Delta^input_lambda
@@ -463,6 +468,7 @@ class Compiler:
         info = self.prog.tensors[src]
         if self.giants is not None:
             G = self.giants[self.n_linear]
+        hoist = self.hoists[self.n_linear] if self.hoists is not None else 1
         self.n_linear += 1
         baby, groups = _bsgs(diags, G, self.n)
         prod_scale = info.scale * w_scale
@@ -475,7 +481,7 @@ class Compiler:
                     self.prog.rot_steps.add(g)
         self.prog.steps.append({"op": "linear", "src": src, "dst": out, "w_scale": w_scale, "giant": G,
                                 "bias_scale": prod_scale, "baby": baby, "groups": groups,
-                                "bias": bias_vecs or {}, "n_out": Lout.n_ct})
+                                "bias": bias_vecs or {}, "n_out": Lout.n_ct, "hoist": hoist})
         return out
 
     def compile(self, net: List[Dict], t) -> Program:
@@ -699,8 +705,9 @@ class Compiler:
 
 
 def compile_he(net: List[Dict], t, prm: C.Params, layout_kind: str,
-               giants: Optional[List[int]] = None, members: int = 1, input_lambda: int = 1) -> Program:
-    return Compiler(prm, layout_kind, giants, members, input_lambda).compile(net, t)
+               giants: Optional[List[int]] = None, members: int = 1, input_lambda: int = 1,
+               hoists: Optional[List[int]] = None) -> Program:
+    return Compiler(prm, layout_kind, giants, members, input_lambda, hoists).compile(net, t)
 
 
 # =================================================================== running
@@ -744,22 +751,34 @@ def run_he(S: C.CKKS, keys: C.Keys, prog: Program, cts: List[C.Ciphertext],
             # steps: the rotated partial sums of one output share a ModDown
             xs = vals[st["src"]]
             level = xs[0].level
+            dh = st.get("hoist", 1) == 2
             rot = {}
             for i in range(len(xs)):
                 rot[(i, 0)] = xs[i]
                 steps_i = [b for (ii, b) in st["baby"] if ii == i]
                 if steps_i:
-                    for b, r in S.rotate_hoisted(xs[i], steps_i, keys).items():
+                    hoisted = S.rotate_hoisted_ext if dh else S.rotate_hoisted
+                    for b, r in hoisted(xs[i], steps_i, keys).items():
                         rot[(i, b)] = r
             outs = []
             for o in range(st["n_out"]):
                 partial = {}
                 for g in sorted(st["groups"].get(o, {})):
                     acc = None
+                    ext_acc = None
                     for (i, b, vec) in st["groups"][o][g]:
+                        if dh and b != 0:
+                            # double hoisting: the product and the sum in Q_l u P
+                            term = S.mul_plain_ext(rot[(i, b)], S.encode_ext(vec, st["w_scale"], level), level)
+                            ext_acc = term if ext_acc is None else S.add_ext(ext_acc, term, level)
+                            continue
                         pt = S.encode(vec, st["w_scale"], level)
                         term = S.mul_plain(rot[(i, b)], pt)
                         acc = term if acc is None else S.add(acc, term)
+                    if ext_acc is not None:
+                        # one ModDown for the group's rotated terms
+                        down = C.Ciphertext(S.moddown(ext_acc, level), level, xs[0].scale * st["w_scale"])
+                        acc = down if acc is None else S.add(acc, down)
                     partial[g] = acc
                 base = partial.get(0)
                 if base is None:

@@ -81,6 +81,7 @@ def lib() -> ctypes.CDLL:
             "fhe_ctx_destroy": (c_int, [V]),
             "fhe_ctx_set_encode_scratch": (c_int, [V, c_size]),
             "fhe_ctx_set_keyswitch_batch": (c_int, [V, c_int]),
+            "fhe_ctx_set_mac_images": (c_int, [V, c_int]),
             "fhe_ctx_set_linear_chunk": (c_int, [V, c_int]),
             "fhe_ctx_inject_alloc_failure": (c_int, [V, c_int]),
             "fhe_ctx_primes": (c_int, [V, P_U64, c_size, ctypes.POINTER(c_size)]),
@@ -197,6 +198,10 @@ def fhe_ctx_set_encode_scratch(ctx, n_bytes: int):
 
 def fhe_ctx_set_keyswitch_batch(ctx, max_items: int):
     _check(lib().fhe_ctx_set_keyswitch_batch(ctx, int(max_items)))
+
+
+def fhe_ctx_set_mac_images(ctx, images_per_cta: int):
+    _check(lib().fhe_ctx_set_mac_images(ctx, int(images_per_cta)))
 
 
 def fhe_ctx_primes(ctx) -> List[int]:
@@ -515,7 +520,7 @@ def fhe_sk_export(sk, n_words: int) -> np.ndarray:
 
 
 EXPORTED = ["fhe_last_error", "fhe_kernel_launches", "fhe_ctx_create", "fhe_ctx_destroy", "fhe_ctx_primes",
-            "fhe_ctx_set_linear_chunk", "fhe_ctx_set_encode_scratch", "fhe_ctx_set_keyswitch_batch",
+            "fhe_ctx_set_linear_chunk", "fhe_ctx_set_encode_scratch", "fhe_ctx_set_keyswitch_batch", "fhe_ctx_set_mac_images",
             "fhe_ctx_inject_alloc_failure", "fhe_keygen",
             "fhe_sk_free", "fhe_evk_free", "fhe_evk_galois", "fhe_encode", "fhe_pt_free", "fhe_encrypt",
             "fhe_decrypt", "fhe_decode", "fhe_ct_free", "fhe_ct_info", "fhe_ct_export", "fhe_ct_import",

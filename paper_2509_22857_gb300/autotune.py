@@ -20,6 +20,11 @@ hand, and the results are cached per device name and parameter set:
 * **Linear-step chunk size** (MAC sources per pass, `fhe_ctx_set_linear_chunk`):
   bit-neutral.  The tuner checks that every candidate gives identical
   ciphertexts and keeps the fastest.
+* **Images per MAC block** (`fhe_ctx_set_mac_images`: 1, 2, 4 or 8; a
+  block covers 512 / images coefficients of one limb for that many images,
+  its plaintext loads shared by them) and **key-switch batch** (items per
+  launch of a step's whole key switches, `fhe_ctx_set_keyswitch_batch`):
+  bit-neutral, same protocol as the chunk size.
 * **Pipeline group size** (images entering the mixed-level pipeline per
   tick): bit-neutral; measured as images leaving per second, one pipeline
   alive at a time.
@@ -152,27 +157,25 @@ def keyswitch_levels(prog) -> List[Tuple[int, float]]:
     return sorted(((lv, float(k)) for lv, k in M.keyswitch_census(prog).items()), reverse=True)
 
 
-def tune_linear_chunk(tuner: Tuner, ctx, model, evk, cts, n_img: int, n_out: int, N: int,
-                      candidates: Sequence[int] = (40, 80, 160, 320), reps: int = 2, F=None,
-                      device: Optional[str] = None, model_key: str = "", sync: Optional[Callable] = None) -> dict:
-    """Time fhe_infer with each chunk size (MAC sources per pass), check that
-    all candidates give identical ciphertexts, leave the fastest set in ctx.
-    Returns {"best": c, "ms": {c: ms}}."""
-    if F is None:
-        from . import _lib as F
+def _tune_infer_knob(tuner: Tuner, op: str, label: str, setter: Callable, candidates: Sequence[int], ctx, model,
+                     evk, cts, n_img: int, n_out: int, N: int, reps: int, F, device: Optional[str], model_key: str,
+                     sync: Optional[Callable]) -> dict:
+    """Time fhe_infer with each value of one bit-neutral context knob, check
+    that every value gives identical ciphertexts, leave the fastest set in
+    ctx.  Returns {"best": v, "ms": {v: ms}}."""
     if sync is None:
         import torch
         sync = torch.cuda.synchronize
     dev = device if device is not None else device_name()
-    key = _key("linear_chunk", dev, model=model_key, n_img=n_img, cands=",".join(map(str, candidates)))
+    key = _key(op, dev, model=model_key, n_img=n_img, cands=",".join(map(str, candidates)))
     hit = tuner.lookup(key)
     if hit is not None:
-        F.fhe_ctx_set_linear_chunk(ctx, hit["best"])
+        setter(ctx, hit["best"])
         return hit
     ref = None
     ms: Dict[int, float] = {}
     for c in candidates:
-        F.fhe_ctx_set_linear_chunk(ctx, c)
+        setter(ctx, c)
         best_t = None
         for r in range(reps + 1):          # first run warms up
             sync()
@@ -187,15 +190,53 @@ def tune_linear_chunk(tuner: Tuner, ctx, model, evk, cts, n_img: int, n_out: int
                 elif not all((a == b).all() for a, b in zip(ref, got)):
                     for h in outs:
                         F.fhe_ct_free(h)
-                    raise RuntimeError("chunk size %d changed the output ciphertexts" % c)
+                    raise RuntimeError("%s %d changed the output ciphertexts" % (label, c))
             else:
                 best_t = t if best_t is None else min(best_t, t)
             for h in outs:
                 F.fhe_ct_free(h)
         ms[c] = best_t
     best = min(candidates, key=lambda c: (ms[c], c))
-    F.fhe_ctx_set_linear_chunk(ctx, best)
+    setter(ctx, best)
     return tuner.record(key, {"best": best, "ms": {str(c): round(t, 3) for c, t in ms.items()}})
+
+
+def tune_linear_chunk(tuner: Tuner, ctx, model, evk, cts, n_img: int, n_out: int, N: int,
+                      candidates: Sequence[int] = (40, 80, 160, 320), reps: int = 2, F=None,
+                      device: Optional[str] = None, model_key: str = "", sync: Optional[Callable] = None) -> dict:
+    """Time fhe_infer with each chunk size (MAC sources per pass), check that
+    all candidates give identical ciphertexts, leave the fastest set in ctx.
+    Returns {"best": c, "ms": {c: ms}}."""
+    if F is None:
+        from . import _lib as F
+    return _tune_infer_knob(tuner, "linear_chunk", "chunk size", F.fhe_ctx_set_linear_chunk, candidates, ctx,
+                            model, evk, cts, n_img, n_out, N, reps, F, device, model_key, sync)
+
+
+def tune_mac_images(tuner: Tuner, ctx, model, evk, cts, n_img: int, n_out: int, N: int,
+                    candidates: Sequence[int] = (1, 2, 4, 8), reps: int = 2, F=None,
+                    device: Optional[str] = None, model_key: str = "", sync: Optional[Callable] = None) -> dict:
+    """Images per block of the plaintext MAC (fhe_ctx_set_mac_images): a
+    block's plaintext loads serve that many images, and the block covers
+    512 / images coefficients of a limb.  Same protocol as tune_linear_chunk."""
+    if F is None:
+        from . import _lib as F
+    return _tune_infer_knob(tuner, "mac_images", "images per MAC block", F.fhe_ctx_set_mac_images, candidates,
+                            ctx, model, evk, cts, n_img, n_out, N, reps, F, device, model_key, sync)
+
+
+def tune_keyswitch_batch(tuner: Tuner, ctx, model, evk, cts, n_img: int, n_out: int, N: int,
+                         candidates: Sequence[int] = (0, 2, 4), reps: int = 2, F=None,
+                         device: Optional[str] = None, model_key: str = "",
+                         sync: Optional[Callable] = None) -> dict:
+    """Items per launch of the whole key switches of a step
+    (fhe_ctx_set_keyswitch_batch; 0: all of the batch at once): fewer items
+    per launch shrink the workspace the passes stream, more share each key
+    read.  Same protocol as tune_linear_chunk."""
+    if F is None:
+        from . import _lib as F
+    return _tune_infer_knob(tuner, "keyswitch_batch", "key-switch batch", F.fhe_ctx_set_keyswitch_batch,
+                            candidates, ctx, model, evk, cts, n_img, n_out, N, reps, F, device, model_key, sync)
 
 
 def tune_pipeline_group(tuner: Tuner, ctx, model, evk, image_cts: Sequence[Sequence[int]], n_out: int, N: int,

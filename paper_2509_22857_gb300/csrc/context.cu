@@ -519,6 +519,14 @@ extern "C" int fhe_ctx_set_keyswitch_batch(fhe_ctx *ctx, int max_items) {
     return FHE_OK;
 }
 
+extern "C" int fhe_ctx_set_mac_images(fhe_ctx *ctx, int images_per_cta) {
+    if (!ctx || !(images_per_cta == 0 || images_per_cta == 1 || images_per_cta == 2 || images_per_cta == 4 ||
+                  images_per_cta == 8))
+        return fhe_fail(FHE_E_INVAL, "images per MAC block must be 0, 1, 2, 4 or 8");
+    ctx->mac_images = images_per_cta;
+    return FHE_OK;
+}
+
 extern "C" int fhe_ctx_primes(const fhe_ctx *ctx, uint64_t *out, size_t cap, size_t *n) {
     if (!ctx || !n) return fhe_fail(FHE_E_INVAL, "null argument");
     *n = ctx->primes.size();

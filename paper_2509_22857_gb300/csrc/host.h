@@ -85,6 +85,7 @@ struct fhe_ctx {
     int lin_chunk_srcs = 160;         // MAC sources per chunk of a linear step
     size_t on_demand_bytes = 4ull << 30;   // scratch of plaintexts encoded on demand (per linear step)
     int ks_item_cap = 0;              // whole key switches in launches of at most this many items (0: any)
+    int mac_images = 0;               // images per plaintext-MAC CTA (0: the batch rounded up to 2^k, <= 8)
     std::atomic<int> fail_alloc_after{-1};   // injected failure: allocations left before one is refused
     EncTab enc_dev;                   // device copy of the encoder's tables (on first use)
     bool enc_dev_ready = false;

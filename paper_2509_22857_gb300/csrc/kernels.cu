@@ -1518,9 +1518,12 @@ cudaError_t launch_decrypt(const DevCtx &c, const u64 *ct, const u64 *s_ntt, u64
 
 cudaError_t launch_mac(const DevCtx &c, const MacArgs &a, cudaStream_t s) {
     if (a.n_groups == 0) return cudaSuccess;
-    // images per CTA: the batch rounded up to a power of two, at most 8
-    int ib = 1;
-    while (ib < 8 && ib < a.n_items) ib *= 2;
+    // images per CTA: as asked, else the batch rounded up to a power of two,
+    // at most 8
+    int ib = a.images_per_cta;
+    if (ib == 0)
+        for (ib = 1; ib < 8 && ib < a.n_items;) ib *= 2;
+    if (ib != 1 && ib != 2 && ib != 4 && ib != 8) return cudaErrorInvalidValue;
     const int tc = 256 / ib;   // threads per image, two coefficients each
     if ((1ll << c.logN) % (2 * tc)) return cudaErrorInvalidValue;
     dim3 g((a.n_items + ib - 1) / ib, (unsigned)((1ll << c.logN) / (2 * tc)), a.level + 1);

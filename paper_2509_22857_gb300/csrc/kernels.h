@@ -184,6 +184,7 @@ struct MacArgs {
     int n_items;
     int level;
     int n_srcs;               // entries of srcs
+    int images_per_cta;       // 1, 2, 4, 8, or 0: the batch rounded up to 2^k, at most 8
 };
 cudaError_t launch_mac(const DevCtx &c, const MacArgs &a, cudaStream_t s);
 

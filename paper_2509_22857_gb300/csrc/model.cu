@@ -697,6 +697,7 @@ struct Exec {
                 ma.n_srcs = (int)hs.size();
                 ma.n_items = B;
                 ma.level = lv;
+                ma.images_per_cta = c->mac_images;
                 mark(11, true);
                 FHE_CU(launch_mac(c->dc, ma, s));
                 mark(11, false);

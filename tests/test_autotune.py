@@ -118,6 +118,10 @@ class FakeLib:
     def fhe_ctx_set_linear_chunk(self, ctx, c):
         self.chunk = c
 
+    # the other bit-neutral knobs drive the same fake timing table
+    fhe_ctx_set_mac_images = fhe_ctx_set_linear_chunk
+    fhe_ctx_set_keyswitch_batch = fhe_ctx_set_linear_chunk
+
     def fhe_infer(self, ctx, model, evk, cts, n_img, n_out):
         time.sleep(self.infer_ms[self.chunk] / 1e3)
         return [self._new(("ct", self.chunk, k)) for k in range(n_img * n_out)]
@@ -164,6 +168,20 @@ def test_linear_chunk_tuner_picks_fastest_and_checks_outputs():
         A.tune_linear_chunk(A.Tuner(), "ctx", "m", "evk", [], 1, 2, 4, candidates=(8, 40), reps=1, F=bad,
                             device="fake", sync=lambda: None)
     assert not bad.live
+
+
+@pytest.mark.parametrize("tune, label", [("tune_mac_images", "images per MAC block"),
+                                         ("tune_keyswitch_batch", "key-switch batch")])
+def test_other_knob_tuners_pick_fastest_and_check_outputs(tune, label):
+    fn = getattr(A, tune)
+    F = FakeLib(infer_ms={1: 9.0, 2: 3.0, 4: 6.0})
+    rec = fn(A.Tuner(), "ctx", "model", "evk", [], 2, 3, 4, candidates=(1, 2, 4), reps=1, F=F, device="fake",
+             sync=lambda: None)
+    assert rec["best"] == 2 and F.chunk == 2 and not F.live
+    bad = FakeLib(infer_ms={1: 1.0, 4: 1.0}, bad_chunk=4)
+    with pytest.raises(RuntimeError, match="%s 4" % label):
+        fn(A.Tuner(), "ctx", "m", "evk", [], 1, 2, 4, candidates=(1, 4), reps=1, F=bad, device="fake",
+           sync=lambda: None)
 
 
 def test_keyswitch_census_of_a_small_network():

@@ -57,6 +57,15 @@ def test_linear_chunk_tuning_keeps_outputs():
         rec = A.tune_linear_chunk(A.Tuner(), ctx, model, evk, cts, 2, n_out, N, candidates=(4, 160), reps=1,
                                   model_key="resnet_mini")
         assert rec["best"] in (4, 160) and all(t > 0 for t in rec["ms"].values())
+        # images per MAC block and key-switch batch: raise if a value changes any output
+        rec = A.tune_mac_images(A.Tuner(), ctx, model, evk, cts, 2, n_out, N, candidates=(0, 1, 2, 4, 8), reps=1,
+                                model_key="resnet_mini")
+        assert rec["best"] in (0, 1, 2, 4, 8)
+        rec = A.tune_keyswitch_batch(A.Tuner(), ctx, model, evk, cts, 2, n_out, N, candidates=(0, 1), reps=1,
+                                     model_key="resnet_mini")
+        assert rec["best"] in (0, 1)
+        with pytest.raises(F.FheError):
+            F.fhe_ctx_set_mac_images(ctx, 3)
         # the pipeline's group size: raises if a group size changes image 0's outputs
         n_in = len(cts) // 2
         images = [cts[i * n_in:(i + 1) * n_in] for i in range(2)]
