@@ -152,13 +152,16 @@ def ks_modmuls(level, alpha, logn):
     return sum(ks_parts(level, alpha, logn))
 
 
-def linear_ks_modmuls(level, alpha, logn, n_baby_inputs, n_babies, n_giants, n_giant_outputs):
+def linear_ks_modmuls(level, alpha, logn, n_baby_inputs, n_babies, n_giants, n_giant_outputs, n_rot_groups=None):
     """key-switching work of one linear step with hoisting: the baby-step
     rotations of one input share its ModUp (each needs an inner product and
-    a ModDown), the giant-step rotations of one output share its ModDown
-    (each needs a ModUp and an inner product)"""
+    a ModDown; with double hoisting, n_rot_groups given, the ModDowns are one
+    per output group with rotated terms instead), the giant-step rotations
+    of one output share its ModDown (each needs a ModUp and an inner
+    product)"""
     mu, ip, md = ks_parts(level, alpha, logn)
-    return n_baby_inputs * mu + n_babies * (ip + md) + n_giants * (mu + ip) + n_giant_outputs * md
+    baby_md = n_babies * md if n_rot_groups is None else n_rot_groups * md
+    return n_baby_inputs * mu + n_babies * ip + baby_md + n_giants * (mu + ip) + n_giant_outputs * md
 
 
 def image_modmuls(prog, alpha, logn):
@@ -171,8 +174,10 @@ def image_modmuls(prog, alpha, logn):
         if st["kind"] == 1:
             babies = {(int(i), int(b)) for i, b in zip(st["t_ct"], st["t_baby"]) if b}
             giants = {(int(o), int(g)) for o, g in zip(st["t_out"], st["t_giant"]) if g}
+            rot_groups = {(int(o), int(g)) for o, g, b in zip(st["t_out"], st["t_giant"], st["t_baby"]) if b}
             mm += linear_ks_modmuls(lv, alpha, logn, len({i for i, _ in babies}), len(babies), len(giants),
-                                    len({o for o, _ in giants}))
+                                    len({o for o, _ in giants}),
+                                    len(rot_groups) if st.get("hoist", 1) == 2 else None)
             n_ks += len(babies) + len(giants)
         else:
             k = M.keyswitches_of_step(prog, st)
@@ -191,8 +196,11 @@ def oracle_image_modmuls(prog, alpha, logn):
         if st["op"] == "linear":
             babies = set(st["baby"])
             giants = {(o, g) for o, gs in st["groups"].items() for g in gs if g}
+            rot_groups = {(o, g) for o, gs in st["groups"].items() for g, terms in gs.items()
+                          if any(b for (_, b, _) in terms)}
             mm += linear_ks_modmuls(lv, alpha, logn, len({i for i, _ in babies}), len(babies), len(giants),
-                                    len({o for o, _ in giants}))
+                                    len({o for o, _ in giants}),
+                                    len(rot_groups) if st.get("hoist", 1) == 2 else None)
         elif st["op"] == "act":
             mm += t_in.layout.n_ct * ks_modmuls(lv, alpha, logn)
         elif st["op"] == "rotsum":
@@ -200,34 +208,52 @@ def oracle_image_modmuls(prog, alpha, logn):
     return mm
 
 
-def mac_products(prog, N):
+def _ext_limbs(prog, st, alpha):
+    """limbs of a linear step's rotated terms: Q_l, or Q_l u P when the step
+    is double-hoisted"""
+    return prog.tensors[st["src"]].level + 1 + (alpha if st.get("hoist", 1) == 2 else 0)
+
+
+def mac_products(prog, N, alpha):
     """plaintext-ciphertext products of one image (both polynomials, every
-    active limb of every term)"""
-    return sum(len(st["t_out"]) * 2 * (prog.tensors[st["src"]].level + 1) * N
-               for st in prog.steps if st["kind"] == 1)
+    active limb of every term; a double-hoisted step's rotated terms run over
+    Q_l u P)"""
+    total = 0
+    for st in prog.steps:
+        if st["kind"] == 1:
+            nl = prog.tensors[st["src"]].level + 1
+            n_rot = int(np.count_nonzero(st["t_baby"]))
+            total += 2 * N * ((len(st["t_out"]) - n_rot) * nl + n_rot * _ext_limbs(prog, st, alpha))
+    return total
 
 
-def mac_bytes(prog, N, batch):
+def mac_bytes(prog, N, batch, alpha):
     """algorithmic HBM bytes of the MAC of a batch: every source ciphertext
     once per image, every distinct plaintext once per batch, every output
-    ciphertext once per image"""
+    ciphertext (a double-hoisted step: every group's sum over Q_l u P) once
+    per image"""
     total = 0
     for st in prog.steps:
         if st["kind"] != 1:
             continue
         W = (prog.tensors[st["src"]].level + 1) * N * 8
-        n_src = len({(int(i), int(b)) for i, b in zip(st["t_ct"], st["t_baby"])})
+        WX = _ext_limbs(prog, st, alpha) * N * 8
+        n_in = len({int(i) for i, b in zip(st["t_ct"], st["t_baby"]) if not b})
+        n_rot = len({(int(i), int(b)) for i, b in zip(st["t_ct"], st["t_baby"]) if b})
         n_out = prog.tensors[st["dst"]].layout.n_ct
-        total += batch * (2 * W * n_src + 2 * W * n_out) + W * (len(st["vecs"]) + len(st["bias"]))
+        n_grp = len({(int(o), int(g)) for o, g, b in zip(st["t_out"], st["t_giant"], st["t_baby"]) if b}) \
+            if st.get("hoist", 1) == 2 else 0
+        total += batch * (2 * W * n_in + 2 * WX * n_rot + 2 * W * n_out + 2 * WX * n_grp) \
+            + WX * len(st["vecs"]) + W * len(st["bias"])
     return total
 
 
-def plaintext_bytes(prog, N):
+def plaintext_bytes(prog, N, alpha):
     total = 0
     for st in prog.steps:
         if st["kind"] == 1:
-            n_pt = len(st["vecs"]) + len(st["bias"])
-            total += n_pt * (prog.tensors[st["src"]].level + 1) * N * 8
+            total += (len(st["vecs"]) * _ext_limbs(prog, st, alpha) + len(st["bias"]) * (
+                prog.tensors[st["src"]].level + 1)) * N * 8
     return total
 
 
@@ -423,9 +449,9 @@ def run_ours(args, rank, world):
     traffic = KS_TRAFFIC["bytes"] if (KS_TRAFFIC["bytes"] and g == KS_TRAFFIC["items"] and lv == KS_TRAFFIC["level"]
                                       and alpha == KS_TRAFFIC["alpha"]) else None
     # the MAC of the uniform batch (its phase timed with events on the stream)
-    mac_mm = B * mac_products(prog, N)
+    mac_mm = B * mac_products(prog, N, pre["alpha"])
     mac_s = phase_ms["linear_mac"] / 1e3
-    mac_b = mac_bytes(prog, N, B)
+    mac_b = mac_bytes(prog, N, B, pre["alpha"])
     img_s_batch = aggregate_throughput(T * g, world, ms_batch)
     img_s_uniform = aggregate_throughput(B, world, ms_uniform)
     img_s_single = aggregate_throughput(1, world, ms_single)
@@ -466,7 +492,7 @@ def run_ours(args, rank, world):
             "keyswitches_per_img": n_ks,
             "l2": "inputs larger than L2: every tick streams the %.1f GB of resident weight plaintexts once "
                   "(each segment its own layers'), %.0f GB per step; L2 is 0.13 GB"
-                  % (plaintext_bytes(prog, N) / 1e9, T * plaintext_bytes(prog, N) / 1e9),
+                  % (plaintext_bytes(prog, N, pre["alpha"]) / 1e9, T * plaintext_bytes(prog, N, pre["alpha"]) / 1e9),
             "setup_s": round(t_setup, 1),
             "uniform_batch_phase_ms": {k: round(v, 1) for k, v in phase_ms.items()},
             "parallelism": "replicas" if world > 1 else "single",
@@ -598,9 +624,9 @@ def run_reference(args, rank, world):
     # the same baby-step / giant-step schedule as the GPU arm (host planning only)
     from paper_2509_22857_gb300 import model as M
     lam = synth.INPUT_LAMBDA[PRESET]
-    giants = M.giant_steps(M.compile_network(net, raw, prm.q, pre["logn"], pre["log_scale"], "packed",
-                                             pre["alpha"], input_lambda=lam))
-    comp = cnn.Compiler(prm, "packed", giants, 1, lam)
+    plan = M.compile_network(net, raw, prm.q, pre["logn"], pre["log_scale"], "packed", pre["alpha"],
+                             input_lambda=lam)
+    comp = cnn.Compiler(prm, "packed", M.giant_steps(plan), 1, lam, M.hoists(plan))
     comp.n = 1 << (pre["logn"] - 1)
     prog = comp.compile(net, cnn.transform(net, raw))
     unit = oracle_image_modmuls(prog, pre["alpha"], pre["logn"]) / ks_modmuls(pre["L"], pre["alpha"], pre["logn"])
@@ -739,8 +765,8 @@ def run_vgg11(args):
            "batch": B, "img_s": round(B / (ms / 1e3), 4), "ms_per_batch": round(ms, 1),
            "phase_ms": {k: round(v, 1) for k, v in phase_ms.items()}, "compile_s": round(t_compile, 1),
            "setup_s": round(t_setup, 1), "keyswitches_per_img": n_ks, "rows_encoded_on_demand": rows,
-           "resident_plaintext_gb": round(plaintext_bytes(prog, N) / 1e9 - sum(
-               len(st["vecs"]) * (prog.tensors[st["src"]].level + 1) * N * 8 for st in prog.steps
+           "resident_plaintext_gb": round(plaintext_bytes(prog, N, pre["alpha"]) / 1e9 - sum(
+               len(st["vecs"]) * _ext_limbs(prog, st, pre["alpha"]) * N * 8 for st in prog.steps
                if st["kind"] == 1 and st["vecs"] and isinstance(st["vecs"][0], M.SparseVec)) / 1e9, 2)}
     print(json.dumps(res), flush=True)
     for h in outs + cts:
@@ -796,7 +822,7 @@ def run_resnet32(args):
            "batch": B, "img_s": round(B / (ms / 1e3), 5), "s_per_img": round(ms / 1e3 / B, 3),
            "ms_per_batch": round(ms, 1), "phase_ms": {k: round(v, 1) for k, v in phase_ms.items()},
            "setup_s": round(t_setup, 1), "keyswitches_per_img": n_ks,
-           "plaintext_gb": round(plaintext_bytes(prog, N) / 1e9, 1),
+           "plaintext_gb": round(plaintext_bytes(prog, N, pp["alpha"]) / 1e9, 1),
            "paper_cpu_s_per_img": {"value": 1833, "note": "ResNet-32 / CIFAR-10, slice clustering k=64, "
                                                           "2x AMD EPYC 64-core, SEAL 4.1 (context only)"}}
     print(json.dumps(res), flush=True)

@@ -302,6 +302,19 @@ typedef struct {
     const double *act_c1_vecs;
     const double *act_c0_vecs;
     double act_c1_scale, act_c0_scale;
+    /*
+     * LINEAR, double hoisting (hybrid key switching, Sec. 2: the special
+     * modulus P of ModUp / ModDown).  0: every baby-step rotation is brought
+     * back to Q_l by its own ModDown before the plaintext products.  1: the
+     * baby-step rotations stay in the extended basis Q_l u P (the inner
+     * product with the key plus P times the rotated c0), the terms with a
+     * baby rotation are multiplied by plaintexts encoded over Q_l u P and
+     * summed there, and each output group (out, giant step) takes one
+     * ModDown, added to the group's unrotated terms (plain products over
+     * Q_l) and bias.  The two differ only in the rounding of the ModDowns:
+     * a different, equally valid ciphertext of the same values.
+     */
+    int double_hoist;
 } fhe_step_desc;
 
 typedef struct {

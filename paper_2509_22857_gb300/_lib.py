@@ -42,7 +42,7 @@ class FheStepDesc(ctypes.Structure):
                 ("n_steps", c_int), ("steps", P_I32), ("level", c_int),
                 ("sparse_vec_begin", P_I64), ("sparse_slot", P_I32), ("sparse_val", P_DBL),
                 ("act_c1_vecs", P_DBL), ("act_c0_vecs", P_DBL), ("act_c1_scale", c_double),
-                ("act_c0_scale", c_double)]
+                ("act_c0_scale", c_double), ("double_hoist", c_int)]
 
 
 class FheModelDesc(ctypes.Structure):

@@ -612,13 +612,16 @@ int enc_tables(fhe_ctx *ctx, const EncTab **out) {
     return FHE_OK;
 }
 
-int op_encode_to(fhe_ctx *ctx, const double *m_host, int level, u64 *dst, cudaStream_t s) {
+int op_encode_to(fhe_ctx *ctx, const double *m_host, int level, u64 *dst, cudaStream_t s, bool ext) {
+    const int n_limbs = level + 1 + (ext ? ctx->alpha : 0);
+    std::vector<unsigned char> pidx(n_limbs);
+    for (int l = 0; l < n_limbs; l++) pidx[l] = (unsigned char)ext_prime(l, ext ? level : ctx->L, ctx->L);
     double *dm;
     FHE_ALLOC_ASYNC(&dm, ctx->N * sizeof(double), s);
     FHE_CU(cudaMemcpyAsync(dm, m_host, ctx->N * sizeof(double), cudaMemcpyHostToDevice, s));
-    FHE_CU(launch_double_to_limbs(ctx->dc, dm, dst, level + 1, s));
+    FHE_CU(launch_double_to_limbs(ctx->dc, dm, dst, n_limbs, s, ext ? level : -1));
     FHE_CU(cudaFreeAsync(dm, s));
-    FHE_TRY(op_ntt(ctx, dst, dst, 0, 1, level + 1, nullptr, false, s));
+    FHE_TRY(op_ntt(ctx, dst, dst, 0, 1, n_limbs, pidx.data(), false, s));
     return FHE_OK;
 }
 

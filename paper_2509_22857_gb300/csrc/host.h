@@ -137,4 +137,5 @@ int op_ntt(fhe_ctx *ctx, const u64 *src, u64 *dst, long long item, int n_items, 
 // the encoder's tables on the device, uploaded on the first call
 int enc_tables(fhe_ctx *ctx, const EncTab **out);
 // encode integral doubles into NTT-domain limbs 0..level (device)
-int op_encode_to(fhe_ctx *ctx, const double *m_host, int level, u64 *dst, cudaStream_t s);
+// ext: the level+1+alpha limbs of Q_level u P (else limbs 0..level)
+int op_encode_to(fhe_ctx *ctx, const double *m_host, int level, u64 *dst, cudaStream_t s, bool ext = false);

@@ -497,6 +497,16 @@ __device__ __forceinline__ ulonglong2 ld_pair(const u64 *p, bool swap) {
     return swap ? make_ulonglong2(v.y, v.x) : v;
 }
 
+// double hoisting: poly 0 of a rotation kept in Q_l u P is the inner product
+// plus P sigma(c0); on Q limb t that adds (P mod q_t) c0 at the gathered slot
+__device__ __forceinline__ ulonglong2 ip_fold_pair(const DevCtx &c, const KsArgs &a, int item, int t, int ip_col,
+                                                   bool ip_sw, ulonglong2 r0, const ModQ &m) {
+    const long long N = 1ll << c.logN;
+    const ulonglong2 f = ld_pair(a.ip_fold + item * a.ip_fold_item + (long long)t * N + (ip_col & ~1), ip_sw);
+    const u64 pm = c.md_pmod[t];
+    return make_ulonglong2(add_mod(r0.x, mulmod(f.x, pm, m), m.q), add_mod(r0.y, mulmod(f.y, pm, m), m.q));
+}
+
 template <int ND>
 __global__ void __launch_bounds__(256) k_ks_ip(DevCtx c, LevelTab lt, KsArgs a, KsLayout ly) {
     const int ext = lt.ext;
@@ -531,10 +541,12 @@ __global__ void __launch_bounds__(256) k_ks_ip(DevCtx c, LevelTab lt, KsArgs a, 
             mac(a10, x[j].x, k1[j].x);
             mac(a11, x[j].y, k1[j].y);
         }
-        ulonglong2 *o0 = (ulonglong2 *)(a.ws + item * a.ws_item + ly.acc + (long long)t * N + col);
+        u64 *ob = a.ip_out ? a.ip_out + item * a.ip_out_item : a.ws + item * a.ws_item + ly.acc;
+        ulonglong2 *o0 = (ulonglong2 *)(ob + (long long)t * N + col);
         ulonglong2 *o1 = (ulonglong2 *)((u64 *)o0 + (long long)ext * N);
         ulonglong2 r0 = make_ulonglong2(barrett(a00, m), barrett(a01, m));
         ulonglong2 r1 = make_ulonglong2(barrett(a10, m), barrett(a11, m));
+        if (a.ip_fold && t <= a.level) r0 = ip_fold_pair(c, a, item, t, ip_col, ip_sw, r0, m);
         if (a.ip_accumulate) {
             const ulonglong2 p0 = *o0, p1 = *o1;
             r0 = make_ulonglong2(add_mod(r0.x, p0.x, m.q), add_mod(r0.y, p0.y, m.q));
@@ -575,10 +587,12 @@ __global__ void __launch_bounds__(256) k_ks_ip_n(DevCtx c, LevelTab lt, KsArgs a
             mac(a10, x.x, k1.x);
             mac(a11, x.y, k1.y);
         }
-        ulonglong2 *o0 = (ulonglong2 *)(a.ws + item * a.ws_item + ly.acc + (long long)t * N + col);
+        u64 *ob = a.ip_out ? a.ip_out + item * a.ip_out_item : a.ws + item * a.ws_item + ly.acc;
+        ulonglong2 *o0 = (ulonglong2 *)(ob + (long long)t * N + col);
         ulonglong2 *o1 = (ulonglong2 *)((u64 *)o0 + (long long)ext * N);
         ulonglong2 r0 = make_ulonglong2(barrett(a00, m), barrett(a01, m));
         ulonglong2 r1 = make_ulonglong2(barrett(a10, m), barrett(a11, m));
+        if (a.ip_fold && t <= a.level) r0 = ip_fold_pair(c, a, item, t, ip_col, ip_sw, r0, m);
         if (a.ip_accumulate) {
             const ulonglong2 p0 = *o0, p1 = *o1;
             r0 = make_ulonglong2(add_mod(r0.x, p0.x, m.q), add_mod(r0.y, p0.y, m.q));
@@ -617,7 +631,8 @@ __global__ void __launch_bounds__(NT) k_ks_md_intt_row(DevCtx c, LevelTab lt, Ks
     const int tau = threadIdx.x % Gm::S, rl = threadIdx.x / Gm::S;
     const int row = blockIdx.x * Gm::T + rl;
     const long long N = 1ll << c.logN;
-    const u64 *s = a.ws + item * a.ws_item + ly.acc + ((long long)kk * lt.ext + a.level + 1 + m) * N + (row << LOGR);
+    const u64 *accb = a.md_in ? a.md_in + item * a.md_in_item : a.ws + item * a.ws_item + ly.acc;
+    const u64 *s = accb + ((long long)kk * lt.ext + a.level + 1 + m) * N + (row << LOGR);
     u64 *d = a.ws + item * a.ws_item + ly.z + ((long long)kk * al + m) * N + (row << LOGR);
     u64 x[16];
 #pragma unroll
@@ -746,7 +761,8 @@ __global__ void __launch_bounds__(NT, 3) k_ks_md_row_out(DevCtx c, LevelTab lt, 
     const int base = row << LOGR;
     const long long N = 1ll << c.logN;
     const u64 *s = a.ws + item * a.ws_item + ly.md + (long long)(kk * nl + i) * N + base;
-    const u64 *ac = a.ws + item * a.ws_item + ly.acc + ((long long)kk * lt.ext + i) * N + base;
+    const u64 *accb = a.md_in ? a.md_in + item * a.md_in_item : a.ws + item * a.ws_item + ly.acc;
+    const u64 *ac = accb + ((long long)kk * lt.ext + i) * N + base;
     const u64 *addp = kk == 0 ? a.add0 : a.add1;
     const ulonglong2 pinv = c.md_pinv[i];
     u64 x[16];
@@ -998,13 +1014,13 @@ __global__ void k_decrypt(DevCtx c, const u64 *ct, const u64 *s, u64 *m, int lev
 __global__ void __launch_bounds__(256, MAC_MINB) k_mac(DevCtx c, MacArgs a, int tc) {
     // each thread owns two adjacent coefficients (16-byte loads)
     const int limb = blockIdx.z;
-    const ModQ m = c.primes[limb].m;
+    const ModQ m = c.primes[a.ext ? ext_prime(limb, a.level, c.L) : limb].m;
     const long long N = 1ll << c.logN;
     const int cl = threadIdx.x % tc, il = threadIdx.x / tc;
     const int img = blockIdx.x * (256 / tc) + il;
     if (img >= a.n_items) return;
     const long long off = (long long)limb * N + (long long)blockIdx.y * 2 * tc + 2 * cl;
-    const long long P = (long long)(a.level + 1) * N;
+    const long long P = (long long)(a.level + 1 + (a.ext ? c.alpha : 0)) * N;
     // products summed before a reduction (one slot kept for the carried residue)
     const int kmax = (m.b >= 61 ? 2 : (1 << min(62 - m.b, 20))) - 1;
     for (int g = 0; g < a.n_groups; g++) {
@@ -1283,13 +1299,13 @@ __device__ u64 pow2_mod(int e, const ModQ &m) {
 
 // exact residue of an integral double: |v| < 2^63 through int64, else as a
 // 53-bit integer mantissa times 2^shift
-__global__ void k_double_to_limbs(DevCtx c, const double *v, u64 *out) {
+__global__ void k_double_to_limbs(DevCtx c, const double *v, u64 *out, int ext_level) {
     const long long N = 1ll << c.logN;
     const int limb = blockIdx.y;
     // vector blockIdx.z: N doubles in, gridDim.y limbs out
     v += (long long)blockIdx.z * N;
     out += (long long)blockIdx.z * gridDim.y * N;
-    const ModQ m = c.primes[limb].m;
+    const ModQ m = c.primes[ext_level >= 0 ? ext_prime(limb, ext_level, c.L) : limb].m;
     for (long long j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += (long long)gridDim.x * blockDim.x) {
         const double x = v[j];
         const double ax = fabs(x);
@@ -1359,12 +1375,15 @@ cudaError_t launch_keyswitch(const DevCtx &c, const LevelTab &lt, const KsArgs &
     for (int i0 = 0; i0 < args.n_items; i0 += per) {
         KsArgs a = args;
         a.n_items = std::min(per, args.n_items - i0);
-        a.d = args.d + (long long)i0 * args.d_item;
+        if (a.d) a.d = args.d + (long long)i0 * args.d_item;
         if (a.add0) a.add0 = args.add0 + (long long)i0 * args.add_item;
         if (a.add1) a.add1 = args.add1 + (long long)i0 * args.add_item;
         if (a.base) a.base = args.base + (long long)i0 * args.base_item;
-        a.out = args.out + (long long)i0 * args.out_item;
+        if (a.out) a.out = args.out + (long long)i0 * args.out_item;
         a.ws = args.ws + (long long)i0 * args.ws_item;
+        if (a.ip_out) a.ip_out = args.ip_out + (long long)i0 * args.ip_out_item;
+        if (a.ip_fold) a.ip_fold = args.ip_fold + (long long)i0 * args.ip_fold_item;
+        if (a.md_in) a.md_in = args.md_in + (long long)i0 * args.md_in_item;
         const cudaError_t e = launch_keyswitch_part(c, lt, a, s, i0 == 0 ? ev : nullptr, phases);
         if (e != cudaSuccess) return e;
     }
@@ -1526,7 +1545,7 @@ cudaError_t launch_mac(const DevCtx &c, const MacArgs &a, cudaStream_t s) {
     if (ib != 1 && ib != 2 && ib != 4 && ib != 8) return cudaErrorInvalidValue;
     const int tc = 256 / ib;   // threads per image, two coefficients each
     if ((1ll << c.logN) % (2 * tc)) return cudaErrorInvalidValue;
-    dim3 g((a.n_items + ib - 1) / ib, (unsigned)((1ll << c.logN) / (2 * tc)), a.level + 1);
+    dim3 g((a.n_items + ib - 1) / ib, (unsigned)((1ll << c.logN) / (2 * tc)), a.level + 1 + (a.ext ? c.alpha : 0));
     COUNT_LAUNCH();
     k_mac<<<g, 256, 0, s>>>(c, a, tc);
     return cudaGetLastError();
@@ -1575,17 +1594,19 @@ cudaError_t launch_axpy_limbs(const DevCtx &c, const u64 *x, const u64 *cst, u64
     return cudaGetLastError();
 }
 
-cudaError_t launch_double_to_limbs(const DevCtx &c, const double *v, u64 *out, int n_limbs, cudaStream_t s) {
+cudaError_t launch_double_to_limbs(const DevCtx &c, const double *v, u64 *out, int n_limbs, cudaStream_t s,
+                                   int ext_level) {
     COUNT_LAUNCH();
-    k_double_to_limbs<<<ew_grid(c, n_limbs, 1), 256, 0, s>>>(c, v, out);
+    k_double_to_limbs<<<ew_grid(c, n_limbs, 1), 256, 0, s>>>(c, v, out, ext_level);
     return cudaGetLastError();
 }
 
 cudaError_t launch_encode_sparse(const DevCtx &c, const EncTab &e, int V, const int *vids, const long long *begin,
                                  const int *slot, const double *val, double scale, int level, double *buf, u64 *pt,
-                                 cudaStream_t s) {
+                                 cudaStream_t s, bool ext) {
     if (V <= 0) return cudaSuccess;
-    if (V > 65535 || level + 1 > 65535) return cudaErrorInvalidValue;
+    const int n_limbs = level + 1 + (ext ? c.alpha : 0);
+    if (V > 65535 || n_limbs > FHE_MAX_LIMBS) return cudaErrorInvalidValue;
     const int n = 1 << (c.logN - 1);
     cudaError_t r = cudaMemsetAsync(buf, 0, (size_t)V * 2 * n * sizeof(double), s);
     if (r != cudaSuccess) return r;
@@ -1599,15 +1620,16 @@ cudaError_t launch_encode_sparse(const DevCtx &c, const EncTab &e, int V, const 
     COUNT_LAUNCH();
     k_enc_twist<<<dim3(bx, V), 256, 0, s>>>(n, e.tw_c, e.tw_s, scale / (double)n, buf);
     COUNT_LAUNCH();
-    k_double_to_limbs<<<dim3(std::min((int)((1ll << c.logN) / 256), 64), level + 1, V), 256, 0, s>>>(c, buf, pt);
+    k_double_to_limbs<<<dim3(std::min((int)((1ll << c.logN) / 256), 64), n_limbs, V), 256, 0, s>>>(
+        c, buf, pt, ext ? level : -1);
     NttArgs a;
     memset(&a, 0, sizeof(a));
     a.src = pt;
     a.dst = pt;
-    a.src_item = a.dst_item = (long long)(level + 1) << c.logN;
+    a.src_item = a.dst_item = (long long)n_limbs << c.logN;
     a.n_items = V;
-    a.n_limbs = level + 1;
-    for (int l = 0; l <= level; l++) a.pidx[l] = (unsigned char)l;
+    a.n_limbs = n_limbs;
+    for (int l = 0; l < n_limbs; l++) a.pidx[l] = (unsigned char)ext_prime(l, ext ? level : c.L, c.L);
     return launch_ntt(c, a, false, s);
 }
 

@@ -88,6 +88,13 @@ struct KsArgs {
     // z [2][alpha], md [2][level+1], u [2] limbs; sized by the caller
     u64 *ws;
     long long ws_item;      // words per item
+    // double hoisting (all nullable):
+    u64 *ip_out;            // the inner product writes its [2][ext] result here (+ i*ip_out_item), not to ws
+    long long ip_out_item;
+    const u64 *ip_fold;     // with ip_out: poly 0 also gets (P mod q_t) sigma_ip_galois(ip_fold)[t], limbs t <= level
+    long long ip_fold_item;
+    const u64 *md_in;       // ModDown reads its [2][ext] input here (+ i*md_in_item), not ws's accumulator
+    long long md_in_item;
 };
 
 size_t ks_workspace_words(const DevCtx &c, int level);
@@ -161,13 +168,13 @@ cudaError_t launch_decrypt(const DevCtx &c, const u64 *ct, const u64 *s_ntt, u64
 // run's sources are added mod q first and multiplied by the plaintext once
 // (grouped accumulation; the same residues, fewer products).
 struct MacSrc {
-    const u64 *base;      // image 0's ciphertext (2 polys x (level+1) limbs)
+    const u64 *base;      // image 0's ciphertext (2 polys x limbs, limbs as MacArgs.ext says)
     long long item;       // per-image stride
 };
 struct MacTerm {
     int src;              // index into srcs
     int run;              // first term of a run: the run's length (terms that share pt, consecutive); else 0 or 1
-    const u64 *pt;        // plaintext limbs (level+1) x N
+    const u64 *pt;        // plaintext limbs x N (its first level+1 limbs are Q's when ext)
 };
 struct MacGroup {
     u64 *out;             // image 0's output ciphertext
@@ -185,6 +192,7 @@ struct MacArgs {
     int level;
     int n_srcs;               // entries of srcs
     int images_per_cta;       // 1, 2, 4, 8, or 0: the batch rounded up to 2^k, at most 8
+    int ext;                  // 0: limbs 0..level of q_0..q_level; 1: the level+1+alpha limbs of Q_level u P
 };
 cudaError_t launch_mac(const DevCtx &c, const MacArgs &a, cudaStream_t s);
 
@@ -200,12 +208,13 @@ struct EncTab {
 };
 // On-demand encoding of V term vectors given sparsely (row vids[v] of
 // begin/slot/val) at `scale`, into NTT-domain limbs 0..level at
-// pt + v * (level+1) * N.  buf: V * N doubles of scratch.  The operations are
-// the host encoder's in its order (no contraction), so the limbs equal a
-// resident encoding of the same dense vector.
+// pt + v * (level+1) * N (ext: the level+1+alpha limbs of Q_level u P, at
+// pt + v * (level+1+alpha) * N).  buf: V * N doubles of scratch.  The
+// operations are the host encoder's in its order (no contraction), so the
+// limbs equal a resident encoding of the same dense vector.
 cudaError_t launch_encode_sparse(const DevCtx &c, const EncTab &e, int V, const int *vids, const long long *begin,
                                  const int *slot, const double *val, double scale, int level, double *buf, u64 *pt,
-                                 cudaStream_t s);
+                                 cudaStream_t s, bool ext = false);
 
 // ChaCha20-based samplers (the stream of one (seed, domain, id0, id1)).
 // uniform residues written directly as NTT-domain limbs
@@ -225,7 +234,9 @@ cudaError_t launch_mul_limbs(const DevCtx &c, const u64 *a, const u64 *b, const 
 cudaError_t launch_axpy_limbs(const DevCtx &c, const u64 *x, const u64 *cst, u64 *out, int n_limbs,
                               const unsigned char *pidx, cudaStream_t s);
 // integral doubles (any magnitude) -> residues of limbs 0..n_limbs-1 (prime l)
-cudaError_t launch_double_to_limbs(const DevCtx &c, const double *v, u64 *out, int n_limbs, cudaStream_t s);
+// ext_level >= 0: limb l takes prime ext_prime(l, ext_level, L) (Q_ext_level u P)
+cudaError_t launch_double_to_limbs(const DevCtx &c, const double *v, u64 *out, int n_limbs, cudaStream_t s,
+                                   int ext_level = -1);
 // NTT-domain automorphism of limbs (gather): out[j] = in[pi_k(j)]
 cudaError_t launch_automorphism(const DevCtx &c, const u64 *in, u64 *out, int n_limbs, int galois,
                                 cudaStream_t s);

@@ -32,6 +32,9 @@ struct MLinear {
     int *d_slot = nullptr;
     double *d_val = nullptr;
     std::vector<int> t_vid;                        // row of each term
+    // double hoisting: baby rotations stay in Q_l u P; plaintexts are
+    // encoded over Q_l u P (the unrotated terms use their first l+1 limbs)
+    bool dh = false;
 };
 
 struct MStep {
@@ -67,16 +70,16 @@ static int residues_of(fhe_model *m, double v, int level, u64 **out) {
     return FHE_OK;
 }
 
-static int encode_vec(fhe_model *m, const double *vec, double scale, int level, u64 **out) {
+static int encode_vec(fhe_model *m, const double *vec, double scale, int level, u64 **out, bool ext = false) {
     fhe_ctx *c = m->ctx;
     std::vector<double> coef(c->N);
     c->enc.encode(vec, nullptr, (size_t)c->N / 2, scale, coef.data());
     void *d;
-    const size_t bytes = (size_t)(level + 1) * c->N * 8;
+    const size_t bytes = (size_t)(level + 1 + (ext ? c->alpha : 0)) * c->N * 8;
     FHE_TRY(dev_alloc(c, &d, bytes));
     m->owned.push_back(d);
     m->pt_bytes += bytes;
-    FHE_TRY(op_encode_to(c, coef.data(), level, (u64 *)d, 0));
+    FHE_TRY(op_encode_to(c, coef.data(), level, (u64 *)d, 0, ext));
     *out = (u64 *)d;
     return FHE_OK;
 }
@@ -108,6 +111,7 @@ static int load_linear(fhe_model *m, const fhe_step_desc &sd, MStep &st) {
     MLinear &L = st.lin;
     const MTensor &tin = m->tensors[st.src], &tout = m->tensors[st.dst];
     L.level = tin.level;
+    L.dh = sd.double_hoist != 0;
     if (tout.level != tin.level) return fhe_fail(FHE_E_LEVEL, "linear step changes level");
     const size_t ns = (size_t)c->N / 2;
     if (sd.n_groups < 0 || (sd.n_groups > 0 && (!sd.group_out || !sd.group_giant || !sd.group_term_begin)))
@@ -180,7 +184,7 @@ static int load_linear(fhe_model *m, const fhe_step_desc &sd, MStep &st) {
             L.t_pt.push_back(nullptr);
             continue;
         }
-        if (!vec_pt[v]) FHE_TRY(encode_vec(m, sd.vecs + (size_t)v * ns, sd.w_scale, L.level, &vec_pt[v]));
+        if (!vec_pt[v]) FHE_TRY(encode_vec(m, sd.vecs + (size_t)v * ns, sd.w_scale, L.level, &vec_pt[v], L.dh));
         L.t_pt.push_back(vec_pt[v]);
     }
     for (auto &p : baby) {
@@ -475,11 +479,16 @@ struct Exec {
         const long long in_item = item(st.src), out_item = item(st.dst);
         const int n_in = m->tensors[st.src].n_ct;
         const long long nlN = (long long)(lv + 1) * c->N;
+        // double hoisting: a baby rotation, a rotated term's plaintext and a
+        // group's sum of rotated terms live in Q_l u P
+        const long long extN = (long long)(lv + 1 + c->alpha) * c->N;
+        const long long rcs = L.dh ? 2 * extN : cs;   // words of one rotated copy
+        const long long pt_limbs = L.dh ? extN : nlN;  // words of one plaintext
         // babies of each input, then the chunks
         std::vector<int> nb(n_in, 0), first_baby(n_in + 1, 0);
         for (size_t k = 0; k < L.baby_ct.size(); k++) nb[L.baby_ct[k]]++;
         for (int ct = 0; ct < n_in; ct++) first_baby[ct + 1] = first_baby[ct] + nb[ct];
-        const size_t baby_bytes = (size_t)B * cs * 8;
+        const size_t baby_bytes = (size_t)B * rcs * 8;
         std::vector<int> cut{0};
         int max_babies = 0;
         {
@@ -508,6 +517,18 @@ struct Exec {
         std::vector<u64 *> acc(ng, nullptr);
         for (int g = 0; g < ng; g++)
             if (galois_of_step(c, L.g_giant[g]) != 1) FHE_TRY(tmp(ti++, (size_t)B * cs * 8, &acc[g]));
+        // double hoisting: each group's sum of rotated terms over Q_l u P,
+        // for the groups that have rotated terms; written[g] tracks whether
+        // a MAC has written it yet (later pieces accumulate)
+        std::vector<u64 *> ext_sum(ng, nullptr);
+        std::vector<char> ext_written(ng, 0);
+        if (L.dh)
+            for (int g = 0; g < ng; g++)
+                for (int t = L.g_tb[g]; t < L.g_te[g]; t++)
+                    if (galois_of_step(c, L.t_baby[t]) != 1) {
+                        FHE_TRY(tmp(ti++, (size_t)B * 2 * extN * 8, &ext_sum[g]));
+                        break;
+                    }
         // scratch of the plaintexts encoded on demand: rows of one batch of
         // groups (FFT buffer N doubles + (lv+1) limbs per row, at most the
         // context's on_demand_bytes)
@@ -517,11 +538,11 @@ struct Exec {
         const EncTab *enc = nullptr;
         if (L.on_demand) {
             FHE_TRY(enc_tables(c, &enc));
-            const size_t per_row = (size_t)(lv + 2) * c->N * 8;
+            const size_t per_row = (size_t)(pt_limbs + c->N) * 8;
             od_rows = (int)std::min<size_t>((size_t)L.n_rows, std::max<size_t>(1, c->on_demand_bytes / per_row));
             od_rows = std::min(od_rows, 65535);
             FHE_TRY(tmp(ti++, (size_t)od_rows * c->N * 8, (u64 **)&od_buf));
-            FHE_TRY(tmp(ti++, (size_t)od_rows * nlN * 8, &od_pt));
+            FHE_TRY(tmp(ti++, (size_t)od_rows * pt_limbs * 8, &od_pt));
         }
         for (size_t ch = 0; ch + 1 < cut.size(); ch++) {
             const int lo = cut[ch], hi = cut[ch + 1];
@@ -548,6 +569,16 @@ struct Exec {
                     a.key = key;
                     a.key_digits_top = evk->digits;
                     a.ip_galois = gal;
+                    if (L.dh) {
+                        // the rotation stays in Q_l u P: inner product plus
+                        // P sigma(c0), no ModDown
+                        a.ip_out = rb[kk - first_baby[lo]];
+                        a.ip_out_item = rcs;
+                        a.ip_fold = x;
+                        a.ip_fold_item = in_item;
+                        FHE_TRY(keyswitch(a, KS_IP));
+                        continue;
+                    }
                     a.add0 = x;
                     a.add_item = in_item;
                     a.add_galois = gal;
@@ -558,13 +589,16 @@ struct Exec {
             }
             mark(10, false);
             // sources: the input ciphertexts, then this chunk's baby-step rotations
-            std::vector<MacSrc> hs;
+            // (double hoisting: the rotations are the sources of a second
+            // MAC over Q_l u P, numbered from 0)
+            std::vector<MacSrc> hs, hs_ext;
             for (int ct = 0; ct < n_in; ct++) hs.push_back(MacSrc{in + ct * cs, in_item});
-            for (int kk = first_baby[lo]; kk < first_baby[hi]; kk++) hs.push_back(MacSrc{rb[kk - first_baby[lo]], cs});
+            for (int kk = first_baby[lo]; kk < first_baby[hi]; kk++)
+                (L.dh ? hs_ext : hs).push_back(MacSrc{rb[kk - first_baby[lo]], rcs});
             auto src_of = [&](int ct, int b) -> int {
                 if (galois_of_step(c, b) == 1) return ct;
                 for (int kk = first_baby[ct]; kk < first_baby[ct + 1]; kk++)
-                    if (L.baby_step[kk] == b) return n_in + (kk - first_baby[lo]);
+                    if (L.baby_step[kk] == b) return (L.dh ? 0 : n_in) + (kk - first_baby[lo]);
                 return -1;
             };
             // the groups of this chunk with their term ranges
@@ -632,12 +666,59 @@ struct Exec {
                     list_sub = 0;
                     mark(13, true);
                     FHE_CU(launch_encode_sparse(c->dc, *enc, (int)rows.size(), (const int *)dv, L.d_begin, L.d_slot,
-                                                L.d_val, L.w_scale, lv, od_buf, od_pt, s));
+                                                L.d_val, L.w_scale, lv, od_buf, od_pt, s, L.dh));
                     mark(13, false);
                     if (!pers) cudaFreeAsync(dv, s);
                 }
-                std::vector<MacGroup> hg;
-                std::vector<MacTerm> ht;
+                // grouped accumulation: the group's terms that share a
+                // plaintext become one run (sources summed, one product);
+                // the sum mod q does not depend on the order of the terms
+                auto close_group = [](std::vector<MacTerm> &ht, MacGroup &G) {
+                    std::stable_sort(ht.begin() + G.term_begin, ht.end(),
+                                     [](const MacTerm &x, const MacTerm &y) { return x.pt < y.pt; });
+                    for (int t = G.term_begin; t < (int)ht.size();) {
+                        int e = t + 1;
+                        while (e < (int)ht.size() && ht[e].pt == ht[t].pt) {
+                            ht[e].run = 0;
+                            e++;
+                        }
+                        ht[t].run = e - t;
+                        t = e;
+                    }
+                    G.term_end = (int)ht.size();
+                };
+                // one MAC launch over its own work list (groups, terms, sources)
+                auto run_mac = [&](const std::vector<MacGroup> &hg, const std::vector<MacTerm> &ht,
+                                   const std::vector<MacSrc> &src, int ext, long long sub) -> int {
+                    if (hg.empty()) return FHE_OK;
+                    const size_t gb = hg.size() * sizeof(MacGroup), tb_ = ht.size() * sizeof(MacTerm),
+                                 sb = src.size() * sizeof(MacSrc);
+                    std::vector<char> lst(gb + tb_ + sb);
+                    memcpy(lst.data(), hg.data(), gb);
+                    if (tb_) memcpy(lst.data() + gb, ht.data(), tb_);
+                    if (sb) memcpy(lst.data() + gb + tb_, src.data(), sb);
+                    char *dw;
+                    list_sub = sub;
+                    FHE_TRY(work_list(lst.data(), lst.size(), &dw));
+                    list_sub = 0;
+                    MacArgs ma;
+                    ma.groups = (const MacGroup *)dw;
+                    ma.terms = (const MacTerm *)(dw + gb);
+                    ma.srcs = (const MacSrc *)(dw + gb + tb_);
+                    ma.n_groups = (int)hg.size();
+                    ma.n_srcs = (int)src.size();
+                    ma.n_items = B;
+                    ma.level = lv;
+                    ma.images_per_cta = c->mac_images;
+                    ma.ext = ext;
+                    mark(11, true);
+                    FHE_CU(launch_mac(c->dc, ma, s));
+                    mark(11, false);
+                    if (!pers) cudaFreeAsync(dw, s);
+                    return FHE_OK;
+                };
+                std::vector<MacGroup> hg, hg_ext;
+                std::vector<MacTerm> ht, ht_ext;
                 for (const Piece &pc : pcs) {
                     const int g = pc.g, tb = pc.tb, tc = pc.tc;
                     const int o = L.g_out[g];
@@ -653,56 +734,55 @@ struct Exec {
                     }
                     G.accumulate = (ch > 0 || pc.cont) ? 1 : 0;
                     G.term_begin = (int)ht.size();
+                    // double hoisting: the rotated terms form this group's
+                    // piece of the MAC over Q_l u P
+                    MacGroup GX;
+                    GX.out = ext_sum[g];
+                    GX.out_item = 2 * extN;
+                    GX.bias = nullptr;
+                    GX.accumulate = ext_written[g];
+                    GX.term_begin = (int)ht_ext.size();
                     for (int t = tb; t < tc; t++) {
                         MacTerm T;
                         T.src = src_of(L.t_ct[t], L.t_baby[t]);
                         T.run = 1;
                         if (T.src < 0) return fhe_fail(FHE_E_INVAL, "internal: missing baby rotation");
-                        T.pt = L.on_demand ? od_pt + (long long)row_slot[L.t_vid[t]] * nlN : L.t_pt[t];
-                        ht.push_back(T);
+                        T.pt = L.on_demand ? od_pt + (long long)row_slot[L.t_vid[t]] * pt_limbs : L.t_pt[t];
+                        (L.dh && galois_of_step(c, L.t_baby[t]) != 1 ? ht_ext : ht).push_back(T);
                     }
-                    // grouped accumulation: the group's terms that share a
-                    // plaintext become one run (sources summed, one product);
-                    // the sum mod q does not depend on the order of the terms
-                    std::stable_sort(ht.begin() + G.term_begin, ht.end(),
-                                     [](const MacTerm &x, const MacTerm &y) { return x.pt < y.pt; });
-                    for (int t = G.term_begin; t < (int)ht.size();) {
-                        int e = t + 1;
-                        while (e < (int)ht.size() && ht[e].pt == ht[t].pt) {
-                            ht[e].run = 0;
-                            e++;
-                        }
-                        ht[t].run = e - t;
-                        t = e;
-                    }
-                    G.term_end = (int)ht.size();
+                    close_group(ht, G);
                     hg.push_back(G);
+                    if ((int)ht_ext.size() > GX.term_begin) {
+                        close_group(ht_ext, GX);
+                        hg_ext.push_back(GX);
+                        ext_written[g] = 1;
+                    }
                 }
-                if (hg.empty()) continue;
-                const size_t gb = hg.size() * sizeof(MacGroup), tb_ = ht.size() * sizeof(MacTerm),
-                             sb = hs.size() * sizeof(MacSrc);
-                std::vector<char> lst(gb + tb_ + sb);
-                memcpy(lst.data(), hg.data(), gb);
-                if (tb_) memcpy(lst.data() + gb, ht.data(), tb_);
-                memcpy(lst.data() + gb + tb_, hs.data(), sb);
-                char *dw;
-                list_sub = ((long long)ch << 20) + 2 * (long long)bi;
-                FHE_TRY(work_list(lst.data(), lst.size(), &dw));
-                list_sub = 0;
-                MacArgs ma;
-                ma.groups = (const MacGroup *)dw;
-                ma.terms = (const MacTerm *)(dw + gb);
-                ma.srcs = (const MacSrc *)(dw + gb + tb_);
-                ma.n_groups = (int)hg.size();
-                ma.n_srcs = (int)hs.size();
-                ma.n_items = B;
-                ma.level = lv;
-                ma.images_per_cta = c->mac_images;
-                mark(11, true);
-                FHE_CU(launch_mac(c->dc, ma, s));
-                mark(11, false);
-                if (!pers) cudaFreeAsync(dw, s);
+                FHE_TRY(run_mac(hg, ht, hs, 0, ((long long)ch << 20) + 2 * (long long)bi));
+                FHE_TRY(run_mac(hg_ext, ht_ext, hs_ext, 1, ((long long)ch << 20) + (1ll << 19) + 2 * (long long)bi));
             }
+        }
+        // double hoisting: one ModDown per group of its rotated terms' sum,
+        // added to the group's unrotated terms and bias
+        if (L.dh) {
+            mark(10, true);
+            for (int g = 0; g < ng; g++) {
+                if (!ext_written[g]) continue;
+                u64 *dst = acc[g] ? acc[g] : out + L.g_out[g] * cs;
+                const long long dst_item = acc[g] ? cs : out_item;
+                KsArgs a;
+                memset(&a, 0, sizeof(a));
+                a.md_in = ext_sum[g];
+                a.md_in_item = 2 * extN;
+                a.base = dst;
+                a.base_item = dst_item;
+                a.out = dst;
+                a.out_item = dst_item;
+                a.n_items = B;
+                a.level = lv;
+                FHE_TRY(keyswitch(a, KS_MODDOWN));
+            }
+            mark(10, false);
         }
         mark(12, true);
         // giant steps: out_o += sum_g rot(acc_{o,g}, g) with one ModDown per
@@ -749,6 +829,7 @@ struct Exec {
         mark(12, false);
         for (auto p : rb) tmp_free(p);
         for (auto p : acc) tmp_free(p);
+        for (auto p : ext_sum) tmp_free(p);
         tmp_free(od_buf);
         tmp_free(od_pt);
         return FHE_OK;

@@ -376,6 +376,36 @@ def bsgs_cost(terms: Terms, giant: int, level: int, alpha: int) -> float:
             + len(np.unique(giants[:, 0])) * md)
 
 
+# Relative cost of one plaintext product per coefficient against one modular
+# product inside a key switch (measured on GB300 over ResNet-20: 0.72 us per
+# MAC unit against 0.96 us per key-switch unit), for comparing schedules that
+# trade key-switch work against MAC work.
+MAC_WEIGHT = 0.75
+
+
+def split_cost(terms: Terms, giant: int, level: int, alpha: int, hoist: int) -> float:
+    """Cost, in the units of ks_cost, of a linear layer split as r = g + b
+    (b = r mod giant) and evaluated with single (hoist 1) or double (hoist 2)
+    hoisting, the plaintext MAC included (MAC_WEIGHT per product and
+    coefficient, 1/8 of a limb transform).  Double hoisting keeps the baby
+    rotations in Q_l u P: a baby step costs only its inner product, each
+    output group (out, g) one ModDown, and the rotated terms' products run
+    over the alpha extra limbs."""
+    nl = level + 1
+    mac_q = len(terms.r) * 2 * nl / 8 * MAC_WEIGHT
+    if hoist == 1:
+        return bsgs_cost(terms, giant, level, alpha) + mac_q
+    mu, ip, md = ks_cost(level, alpha)
+    b = terms.r % giant
+    g = terms.r - b
+    babies = np.unique(np.stack([terms.ct[b != 0], b[b != 0]], axis=1), axis=0)
+    giants = np.unique(np.stack([terms.out[g != 0], g[g != 0]], axis=1), axis=0)
+    rot_groups = np.unique(np.stack([terms.out[b != 0], g[b != 0]], axis=1), axis=0)
+    mac = (len(terms.r) * 2 * nl + int(np.count_nonzero(b)) * 2 * alpha) / 8 * MAC_WEIGHT
+    return (len(np.unique(babies[:, 0])) * mu + len(babies) * ip + len(rot_groups) * md
+            + len(giants) * (mu + ip) + len(np.unique(giants[:, 0])) * md + mac)
+
+
 def groups_of(st: Dict) -> Dict[Tuple[int, int], List]:
     """{(out ct, giant step): [(in ct, baby step, vector)]} of a linear step"""
     groups: Dict[Tuple[int, int], List] = {}
@@ -397,9 +427,14 @@ CLASSIFIER_EXTRA_BITS = 6
 class Planner:
     def __init__(self, primes_q: Sequence[int], log_n: int, log_scale: float, layout: str, alpha: int = 3,
                  max_giant_blocks: int = 8, members: int = 1, input_lambda: int = 1,
-                 giants: Optional[Sequence[int]] = None, on_demand: bool = False):
+                 giants: Optional[Sequence[int]] = None, on_demand: bool = False, hoist="auto",
+                 hoists: Optional[Sequence[int]] = None):
         self.on_demand = on_demand
         self.giants = None if giants is None else list(giants)
+        if hoist not in ("auto", 1, 2):
+            raise ValueError("hoist must be 'auto', 1 or 2")
+        self.hoist = hoist
+        self.hoists = None if hoists is None else list(hoists)
         self.n_linear = 0
         self.members = members
         self.input_lambda = input_lambda
@@ -430,17 +465,29 @@ class Planner:
             return self._emit(kind=F.STEP_RESCALE, src=t, dst=self._t(info.layout, info.level - 1, info.scale / ql))
         return t
 
+    def _hoist_options(self) -> Tuple[int, ...]:
+        return (1, 2) if self.hoist == "auto" else (self.hoist,)
+
     def _pick_giant(self, terms: Terms, block: int, level: int) -> int:
         """giant step = k blocks, k in 1, 2, 4, .. max_giant_blocks: the
-        cheapest split by bsgs_cost (ties: the smaller k)"""
+        cheapest split by split_cost over the admitted hoisting modes (ties:
+        the smaller k, then single hoisting)"""
         best = None
         k = 1
         while k <= self.max_giant_blocks and k * block <= self.n:
-            c = bsgs_cost(terms, k * block, level, self.alpha)
-            if best is None or c < best[0]:
-                best = (c, k * block)
+            for h in self._hoist_options():
+                c = split_cost(terms, k * block, level, self.alpha, h)
+                if best is None or c < best[0]:
+                    best = (c, k * block)
             k *= 2
         return best[1]
+
+    def _pick_hoist(self, terms: Terms, giant: int, level: int) -> int:
+        if self.hoists is not None:
+            return int(self.hoists[self.n_linear])
+        opts = self._hoist_options()
+        costs = [split_cost(terms, giant, level, self.alpha, h) for h in opts]
+        return opts[int(np.argmin(costs))]
 
     def _bias_vecs(self, biases: Sequence[np.ndarray], layout: SlotMap) -> Dict[int, np.ndarray]:
         """bias of channel ch, replica k (the member biases[k]), on the
@@ -457,6 +504,7 @@ class Planner:
         info = self.p.tensors[src]
         if self.giants is not None:
             giant = self.giants[self.n_linear]
+        hoist = self._pick_hoist(terms, giant, info.level) if len(terms.r) else 1
         self.n_linear += 1
         prod = info.scale * w_scale
         dst = self._t(dst_layout, info.level, prod)
@@ -485,7 +533,7 @@ class Planner:
         self.p.rotations.update(int(x) for x in np.unique(g) if x)
         return self._emit(kind=F.STEP_LINEAR, src=src, dst=dst, w_scale=w_scale, bias_scale=prod,
                           t_out=terms.out[order], t_giant=g[order], t_ct=terms.ct[order], t_baby=b[order],
-                          t_vid=vid[order], vecs=vecs, bias=bias_vecs, giant=giant)
+                          t_vid=vid[order], vecs=vecs, bias=bias_vecs, giant=giant, hoist=hoist)
 
     def _shortcut_scale(self, info: TInfo, target: TInfo) -> float:
         ql = self.q[info.level]
@@ -694,7 +742,8 @@ class Planner:
 
 def compile_network(net, raw, primes_q, log_n, log_scale, layout, alpha: int = 3,
                     max_giant_blocks: int = 8, input_lambda: int = 1,
-                    giants: Optional[Sequence[int]] = None, on_demand: bool = False) -> Program:
+                    giants: Optional[Sequence[int]] = None, on_demand: bool = False, hoist="auto",
+                    hoists: Optional[Sequence[int]] = None) -> Program:
     """raw: one model's raw parameters, or a list of them (an ensemble, laid
     out with layout "hw_ens": member m in block m of every ciphertext).
     alpha: digit width of key switching (for the baby-step / giant-step
@@ -706,13 +755,17 @@ def compile_network(net, raw, primes_q, log_n, log_scale, layout, alpha: int = 3
     split evaluates the same diagonals).  on_demand: the weight vectors of
     the packed convolutions are kept sparse and encoded on the device each
     time their step runs, instead of being encoded once and held in HBM
-    (for layers whose plaintexts do not fit)."""
+    (for layers whose plaintexts do not fit).  hoist: 1 (every baby-step
+    rotation brought back to Q_l by its own ModDown), 2 (double hoisting:
+    rotations kept in Q_l u P, one ModDown per output group) or "auto" (per
+    linear step, the cheaper by split_cost); hoists: one mode per linear
+    step in place of that choice."""
     raws = raw if isinstance(raw, (list, tuple)) else [raw]
     if len(raws) > 1 and layout != "hw_ens":
         raise ValueError("an ensemble needs the hw_ens layout")
     prms = [prepare_params(net, r) for r in raws]
     return Planner(primes_q, log_n, log_scale, layout, alpha, max_giant_blocks, len(raws),
-                   input_lambda, giants, on_demand).compile(net, prms)
+                   input_lambda, giants, on_demand, hoist, hoists).compile(net, prms)
 
 
 def input_scale(prog: Program) -> float:
@@ -723,6 +776,12 @@ def input_scale(prog: Program) -> float:
 def giant_steps(prog: Program) -> List[int]:
     """the giant-step size of every linear step, in program order"""
     return [st["giant"] for st in prog.steps if st["kind"] == F.STEP_LINEAR]
+
+
+def hoists(prog: Program) -> List[int]:
+    """the hoisting mode (1 single, 2 double) of every linear step, in
+    program order"""
+    return [int(st.get("hoist", 1)) for st in prog.steps if st["kind"] == F.STEP_LINEAR]
 
 
 def keyswitches_of_step(prog: Program, st: dict) -> int:
@@ -794,6 +853,7 @@ class ModelDesc:
                     starts = np.zeros(0, dtype=np.int64)
                 d.w_scale = st["w_scale"]
                 d.bias_scale = st["bias_scale"]
+                d.double_hoist = 1 if st.get("hoist", 1) == 2 else 0
                 d.n_groups = len(starts)
                 d.group_out = p32(arr(t_out[starts] if n_t else [0], np.int32))
                 d.group_giant = p32(arr(t_g[starts] if n_t else [0], np.int32))

@@ -150,7 +150,7 @@ def test_resnet20_first_layers_bit_exact_at_full_size():
         assert F.fhe_ctx_primes(ctx) == list(prm.primes)
         pm = M.compile_network(net, raw, prm.primes[: pre["L"] + 1], pre["logn"], pre["log_scale"], "packed",
                                pre["alpha"], input_lambda=lam)
-        po = cnn.compile_he(net, cnn.transform(net, raw), prm, "packed", M.giant_steps(pm), 1, lam)
+        po = cnn.compile_he(net, cnn.transform(net, raw), prm, "packed", M.giant_steps(pm), 1, lam, M.hoists(pm))
         n_first = 3
         kinds = [st["kind"] for st in pm.steps[:n_first]]
         assert kinds == [F.STEP_LINEAR, F.STEP_RESCALE, F.STEP_ACT]

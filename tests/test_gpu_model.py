@@ -10,8 +10,11 @@ from oracle import cnn
 
 pytestmark = pytest.mark.gpu
 
-# (arch, preset, layout[, input scale as a power of Delta])
+# (arch, preset, layout[, input scale as a power of Delta[, hoisting mode]]);
+# the planner's default mode ("auto") picks double hoisting for most linear
+# steps of these networks, "mini_single" keeps every step single-hoisted
 CASES = {"tiny": ("tiny", "tiny", "hw"), "mini": ("resnet_mini", "resnet_mini", "packed", 2),
+         "mini_single": ("resnet_mini", "resnet_mini", "packed", 2, 1),
          "vgg_mini": ("vgg_mini", "resnet_mini", "packed"),
          # pre-activation blocks: batch norm fused into the activation after
          # it, per-channel quadratic coefficients (node fusing Case 1)
@@ -28,6 +31,7 @@ class Setup:
         from paper_2509_22857_gb300 import model as M
         arch, preset, layout = CASES[case][:3]
         lam = CASES[case][3] if len(CASES[case]) > 3 else 1
+        hoist = CASES[case][4] if len(CASES[case]) > 4 else "auto"
         self.F, self.M = F, M
         self.net = synth.ARCHS[arch]()
         if layout == "hw_ens":
@@ -45,10 +49,11 @@ class Setup:
         self.ctx = F.fhe_ctx_create(pre["logn"], pre["L"], pre["q_bits"], pre["q0_bits"], pre["p_bits"],
                                     pre["alpha"], pre["log_scale"])
         self.pm = M.compile_network(self.net, self.raw, F.fhe_ctx_primes(self.ctx)[: pre["L"] + 1], pre["logn"],
-                                    pre["log_scale"], layout, pre["alpha"], input_lambda=lam)
-        # the oracle evaluates the same diagonals with the package's baby-step / giant-step split
+                                    pre["log_scale"], layout, pre["alpha"], input_lambda=lam, hoist=hoist)
+        # the oracle evaluates the same diagonals with the package's baby-step
+        # / giant-step split and hoisting modes
         self.po = cnn.compile_he(self.net, t, self.prm, layout, M.giant_steps(self.pm),
-                                 ENSEMBLE if layout == "hw_ens" else 1, lam)
+                                 ENSEMBLE if layout == "hw_ens" else 1, lam, M.hoists(self.pm))
         self._oracle_cache = {}
         self.keys = self.S.keygen(synth.SEED_KEYS, sorted(self.po.rot_steps))
         self.sk, self.evk = F.fhe_keygen(self.ctx, synth.SEED_KEYS, sorted(self.pm.rotations))
@@ -262,8 +267,9 @@ def test_oracle_chosen_schedule_bit_exact(case):
     try:
         planned = M.giant_steps(M.compile_network(net, raw, F.fhe_ctx_primes(ctx)[: pre["L"] + 1], pre["logn"],
                                                   pre["log_scale"], layout, pre["alpha"], input_lambda=lam))
+        # the oracle's own default split, single-hoisted like the oracle's default
         pm = M.compile_network(net, raw, F.fhe_ctx_primes(ctx)[: pre["L"] + 1], pre["logn"], pre["log_scale"],
-                               layout, pre["alpha"], input_lambda=lam, giants=own)
+                               layout, pre["alpha"], input_lambda=lam, giants=own, hoist=1)
         assert M.giant_steps(pm) == own
         if case == "mini":
             assert own != planned     # the planner would have split differently
@@ -297,7 +303,7 @@ def test_oracle_chosen_schedule_bit_exact(case):
         F.fhe_ctx_destroy(ctx)
 
 
-@pytest.mark.parametrize("case", ["mini", "vgg_mini", "preact"])
+@pytest.mark.parametrize("case", ["mini", "mini_single", "vgg_mini", "preact"])
 def test_on_demand_encoding_equals_resident(case):
     """The same network with its packed convolutions' plaintexts encoded on
     the device each time a step runs (sparse rows, host encoder's operation
@@ -308,6 +314,7 @@ def test_on_demand_encoding_equals_resident(case):
     from paper_2509_22857_gb300 import model as M
     arch, preset, layout = CASES[case][:3]
     lam = CASES[case][3] if len(CASES[case]) > 3 else 1
+    hoist = CASES[case][4] if len(CASES[case]) > 4 else "auto"
     net = synth.ARCHS[arch]()
     raw = synth.params(net)
     pre = synth.PRESETS[preset]
@@ -317,9 +324,10 @@ def test_on_demand_encoding_equals_resident(case):
     try:
         primes = F.fhe_ctx_primes(ctx)[: pre["L"] + 1]
         pm = M.compile_network(net, raw, primes, pre["logn"], pre["log_scale"], layout, pre["alpha"],
-                               input_lambda=lam)
+                               input_lambda=lam, hoist=hoist)
         po = M.compile_network(net, raw, primes, pre["logn"], pre["log_scale"], layout, pre["alpha"],
-                               input_lambda=lam, on_demand=True)
+                               input_lambda=lam, on_demand=True, hoist=hoist)
+        assert M.hoists(po) == M.hoists(pm)
         assert any(st["kind"] == 1 and isinstance(st["vecs"][0], M.SparseVec) for st in po.steps)
         sk, evk = F.fhe_keygen(ctx, synth.SEED_KEYS, sorted(pm.rotations))
         dm, do = M.ModelDesc(pm, N // 2), M.ModelDesc(po, N // 2)

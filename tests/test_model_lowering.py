@@ -14,15 +14,16 @@ from paper_2509_22857_gb300 import model as M
 NAMES = {1: "linear", 2: "rescale", 3: "act", 4: "rotsum", 5: "cmul", 6: "drop", 7: "add"}
 
 
-def _both(arch, preset, layout):
+def _both(arch, preset, layout, hoist="auto"):
     net = synth.ARCHS[arch]()
     raw = synth.params(net)
     pre = synth.PRESETS[preset]
     prm = O.make_params(**dict(pre, logn=min(pre["logn"], 12)))   # primes' sizes fix the plan
-    pm = M.compile_network(net, raw, prm.q, pre["logn"], pre["log_scale"], layout, pre["alpha"])
-    # the baby-step / giant-step split is a schedule choice of the package's
-    # cost model; the oracle evaluates the same diagonals with the same split
-    c = cnn.Compiler(prm, layout, M.giant_steps(pm))
+    pm = M.compile_network(net, raw, prm.q, pre["logn"], pre["log_scale"], layout, pre["alpha"], hoist=hoist)
+    # the baby-step / giant-step split and the hoisting mode are schedule
+    # choices of the package's cost model; the oracle evaluates the same
+    # diagonals with the same split and mode
+    c = cnn.Compiler(prm, layout, M.giant_steps(pm), hoists=M.hoists(pm))
     c.n = 1 << (pre["logn"] - 1)
     po = c.compile(net, cnn.transform(net, raw))
     return po, pm
@@ -35,6 +36,7 @@ def _check(po, pm):
     assert ko == km
     lo = [s for s in po.steps if s["op"] == "linear"]
     lm = [s for s in pm.steps if s["kind"] == 1]
+    assert [s["hoist"] for s in lo] == M.hoists(pm)
     for a, b in zip(lo, lm):
         ga = {(o, g): sorted((i, bb, v.tobytes()) for (i, bb, v) in terms)
               for o, gs in a["groups"].items() for g, terms in gs.items()}
@@ -63,6 +65,13 @@ def test_tiny_hw_program_matches_oracle():
 
 def test_mini_resnet_program_matches_oracle():
     _check(*_both("resnet_mini", "resnet_mini", "packed"))
+
+
+@pytest.mark.parametrize("hoist", [1, 2])
+def test_forced_hoisting_mode_reaches_both_compilers(hoist):
+    po, pm = _both("resnet_mini", "resnet_mini", "packed", hoist=hoist)
+    assert set(M.hoists(pm)) == {hoist}
+    _check(po, pm)
 
 
 def test_mini_vgg_program_matches_oracle():
@@ -94,18 +103,40 @@ def test_input_slots_match_oracle():
     assert len(a) == len(b) and all(np.array_equal(x, y) for x, y in zip(a, b))
 
 
-def test_cost_model_prefers_wider_baby_steps_for_wide_layers():
+@pytest.mark.parametrize("hoist", [1, "auto"])
+def test_cost_model_prefers_wider_baby_steps_for_wide_layers(hoist):
     """A 16-channel packed convolution: giant steps of one block need 15 giant
     rotations per output; the cost model moves part of them to hoisted baby
-    steps, and never picks a split that costs more than one block."""
-    po, pm = _both("resnet_mini", "resnet_mini", "packed")
+    steps, and never picks a split (and hoisting mode) that costs more than
+    one block with either mode."""
+    po, pm = _both("resnet_mini", "resnet_mini", "packed", hoist=hoist)
     lin = [s for s in pm.steps if s["kind"] == 1]
     blk = pm.tensors[pm.input].layout.block
     assert any(s["giant"] > blk for s in lin)
+    modes = (1,) if hoist == 1 else (1, 2)
     for s in lin:
         terms = M.Terms(s["t_out"], s["t_ct"], s["t_giant"] + s["t_baby"], s["t_vid"], s["vecs"])
         lv = pm.tensors[s["src"]].level
-        assert M.bsgs_cost(terms, s["giant"], lv, 3) <= M.bsgs_cost(terms, blk, lv, 3)
+        chosen = M.split_cost(terms, s["giant"], lv, 3, s["hoist"])
+        assert chosen <= min(M.split_cost(terms, blk, lv, 3, h) for h in modes) + 1e-9
+        if hoist == 1:
+            assert M.bsgs_cost(terms, s["giant"], lv, 3) <= M.bsgs_cost(terms, blk, lv, 3)
+
+
+def test_double_hoisting_cost_counts_one_moddown_per_rotated_group():
+    """split_cost with double hoisting against a count by hand on a toy term
+    set: two inputs, baby steps {1, 2}, giant steps {0, 4}, one output."""
+    r = np.array([0, 1, 2, 4, 5, 6, 1])
+    ct = np.array([0, 0, 0, 0, 0, 0, 1])
+    terms = M.Terms(np.zeros(7, dtype=np.int64), ct, r, np.arange(7), [None] * 7)
+    mu, ip, md = M.ks_cost(5, 3)
+    nl, alpha = 6, 3
+    # babies (0,1) (0,2) (1,1); giants (0,4); rotated groups (0,0) (0,4)
+    ks = 2 * mu + 3 * ip + 2 * md + 1 * (mu + ip) + 1 * md
+    mac = (7 * 2 * nl + 5 * 2 * alpha) / 8 * M.MAC_WEIGHT
+    assert M.split_cost(terms, 4, 5, alpha, 2) == pytest.approx(ks + mac)
+    assert M.split_cost(terms, 4, 5, alpha, 1) == pytest.approx(M.bsgs_cost(terms, 4, 5, alpha) + 7 * 2 * nl / 8
+                                                                 * M.MAC_WEIGHT)
 
 
 
@@ -115,7 +146,8 @@ def _ensemble_both(k=4, members=3):
     pre = synth.PRESETS["resnet18_mini"]
     prm = O.make_params(**pre)
     pm = M.compile_network(net, raws, prm.q, pre["logn"], pre["log_scale"], "hw_ens", pre["alpha"])
-    po = cnn.compile_he(net, [cnn.transform(net, r) for r in raws], prm, "hw_ens", M.giant_steps(pm), members)
+    po = cnn.compile_he(net, [cnn.transform(net, r) for r in raws], prm, "hw_ens", M.giant_steps(pm), members,
+                        hoists=M.hoists(pm))
     return po, pm
 
 
@@ -145,7 +177,7 @@ def test_input_at_delta_squared_costs_no_level():
     for lam in (1, 2):
         pm = M.compile_network(net, raw, prm.q, pre["logn"], pre["log_scale"], "packed", pre["alpha"],
                                input_lambda=lam)
-        c = cnn.Compiler(prm, "packed", M.giant_steps(pm), 1, lam)
+        c = cnn.Compiler(prm, "packed", M.giant_steps(pm), 1, lam, M.hoists(pm))
         c.n = 1 << (pre["logn"] - 1)
         po = c.compile(net, cnn.transform(net, raw))
         _check(po, pm)

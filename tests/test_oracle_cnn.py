@@ -208,6 +208,29 @@ def test_resnet20_program_levels_follow_tower_reuse():
 
 
 @pytest.mark.slow
+def test_double_hoisted_network_under_ckks_matches_float64():
+    """The mini ResNet with every linear step double-hoisted (baby rotations
+    left in Q_l u P, one ModDown per output group): decrypted logits within
+    1e-3 of the float64 network, same argmax."""
+    net = synth.resnet_mini()
+    raw = synth.params(net)
+    t = cnn.transform(net, raw)
+    prm = C.make_params(**synth.PRESETS["resnet_mini"])
+    n_lin = sum(1 for s in cnn.compile_he(net, t, prm, "packed").steps if s["op"] == "linear")
+    prog = cnn.compile_he(net, t, prm, "packed", input_lambda=2, hoists=[2] * n_lin)
+    assert all(s["hoist"] == 2 for s in prog.steps if s["op"] == "linear")
+    S = C.CKKS(prm)
+    keys = S.keygen(synth.SEED_KEYS, sorted(prog.rot_steps))
+    img = synth.image(0, 3, 8, 8)
+    cts = cnn.encrypt_input(S, keys, prog, img, 0, synth.enc_seed)
+    vals = cnn.run_he(S, keys, prog, cts)
+    y = cnn.decrypt_logits(S, keys, prog, vals[prog.output_tensor])
+    ref = cnn.forward_plain(net, raw, img)
+    assert np.max(np.abs(y - ref)) < 1e-3
+    assert np.argmax(y) == np.argmax(ref)
+
+
+@pytest.mark.slow
 def test_giant_step_choice_keeps_the_layer_function():
     """The first convolution of the mini ResNet under CKKS with giant steps of
     one block and of four blocks (more baby steps, fewer giant steps): both

@@ -453,6 +453,57 @@ def test_hoisted_rotations_decrypt_to_rotated_slots(small):
     assert np.max(np.abs(d1 - d2)) < 1e-6
 
 
+def test_extended_basis_rotations_moddown_to_the_hoisted_ones(small):
+    """Double hoisting: a rotation kept in Q_l u P (inner product plus
+    P sigma(c0)) brought down by ModDown is bit for bit the single-hoisted
+    rotation, since P sigma(c0) is divided by P exactly; its special-prime
+    limbs hold only the inner product (P is 0 modulo each special prime)."""
+    prm, S, keys = small
+    rng = np.random.default_rng(13)
+    z = rng.uniform(-1, 1, prm.N // 2)
+    ct = S.encrypt(keys, S.encode(z, prm.scale, prm.L), 14)
+    steps = [1, 3, -1]
+    ext = S.rotate_hoisted_ext(ct, steps, keys)
+    single = S.rotate_hoisted(ct, steps, keys)
+    lv = ct.level
+    xd = S.modup(ct.c[1], lv)
+    for step in steps:
+        assert np.array_equal(S.moddown(ext[step], lv), single[step].c)
+        k, key = S._galois_key(step, keys)
+        ip = S.inner_product([S.galois_ext(x, lv, k) for x in xd], lv, key)
+        assert np.array_equal(ext[step][:, lv + 1:], ip[:, lv + 1:])
+        assert np.array_equal(ext[step][1], ip[1])
+
+
+def test_double_hoisted_sum_of_products_decrypts_to_the_sum(small):
+    """sum_b pt_b (.) rot_b(ct) formed in Q_l u P with plaintexts encoded over
+    Q_l u P, then one ModDown: decrypts to sum_b w_b * rotate(z, b), and
+    differs from the single-hoisted sum only by rounding (a few units of
+    the ciphertext modulus' last place after decoding)."""
+    prm, S, keys = small
+    rng = np.random.default_rng(14)
+    z = rng.uniform(-1, 1, prm.N // 2)
+    ws = {b: rng.uniform(-1, 1, prm.N // 2) for b in (1, 3, 5)}
+    ct = S.encrypt(keys, S.encode(z, prm.scale, prm.L), 15)
+    lv = ct.level
+    ext = S.rotate_hoisted_ext(ct, list(ws), keys)
+    acc = None
+    for b, w in ws.items():
+        term = S.mul_plain_ext(ext[b], S.encode_ext(w, prm.scale, lv), lv)
+        acc = term if acc is None else S.add_ext(acc, term, lv)
+    dh = C.Ciphertext(S.moddown(acc, lv), lv, prm.scale * prm.scale)
+    want = sum(w * np.roll(z, -b) for b, w in ws.items())
+    assert np.max(np.abs(S.decrypt_decode(keys, dh).real - want)) < 1e-6
+    single = S.rotate_hoisted(ct, list(ws), keys)
+    sacc = None
+    for b, w in ws.items():
+        term = S.mul_plain(single[b], S.encode(w, prm.scale, lv))
+        sacc = term if sacc is None else S.add(sacc, term)
+    assert np.max(np.abs(S.decrypt_decode(keys, dh) - S.decrypt_decode(keys, sacc))) < 1e-6
+    # the Q limbs of an extended-basis plaintext are the ordinary plaintext
+    assert np.array_equal(S.encode_ext(z, prm.scale, lv)[: lv + 1], S.encode(z, prm.scale, lv).m)
+
+
 def test_lazy_rotation_sum_decrypts_to_the_sum(small):
     """base + sum_g rot(ct_g, g) with a single ModDown decrypts to the sum."""
     prm, S, keys = small
