@@ -95,7 +95,11 @@ const char *fhe_last_error(void);
 uint64_t fhe_kernel_launches(void);
 
 /* Context: builds the prime chain, NTT tables and key-switching constants on
- * the device.  fhe_ctx_destroy frees everything the context made. */
+ * the device.  fhe_ctx_destroy frees everything the context made.  It also
+ * sets the device's default stream-ordered memory pool (this process's
+ * CUDA context only) to keep its memory mapped across synchronisations:
+ * step temporaries come from it, and the library hands unused pool memory
+ * back when a plain allocation of its own is refused. */
 int fhe_ctx_create(const fhe_params *params, fhe_ctx **out);
 int fhe_ctx_destroy(fhe_ctx *ctx);
 /* q_0..q_L then p_0..p_{alpha-1} into out[cap]; *n = count (test hook). */
@@ -403,9 +407,10 @@ int fhe_pipeline_free(fhe_pipeline *pipe);
  * queued per model and admitted into the next tick of their model's pipeline
  * while earlier requests are still inside it, and the workers of different
  * models tick concurrently.  fhe_server_add_model admits a model only if
- * cudaMemGetInfo reports at least reserve_bytes free (0: no check) and its
- * pipeline can be allocated (else FHE_E_OOM).  Weight plaintexts and
- * evaluation keys stay resident.
+ * cudaMemGetInfo reports at least reserve_bytes free (0: no check; the call
+ * first synchronises the device and returns the stream-ordered pool's
+ * unused memory to it) and its pipeline can be allocated (else FHE_E_OOM).
+ * Weight plaintexts and evaluation keys stay resident.
  * fhe_server_submit takes ownership of the model's n_in_ct input ciphertexts
  * of one image (they are freed once admitted) and returns a ticket.
  * fhe_server_poll returns the request's n_out_ct output ciphertexts (new

@@ -213,12 +213,27 @@ void Encoder::decode(const double *m, double scale, double *re, double *im, size
 
 // ================================================================ memory
 
+cudaError_t pool_trim() {
+    int dev = 0;
+    cudaMemPool_t pool;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaDeviceGetDefaultMemPool(&pool, dev);
+    if (e == cudaSuccess) e = cudaMemPoolTrimTo(pool, 0);
+    return e;
+}
+
 int dev_alloc(fhe_ctx *ctx, void **p, size_t bytes) {
     *p = nullptr;
     if (ctx && ctx->fail_alloc_after.load() >= 0 && ctx->fail_alloc_after.fetch_sub(1) == 0)
         return fhe_fail(FHE_E_OOM, "device allocation refused (injected failure)");
     if (bytes == 0) bytes = 8;
     cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaErrorMemoryAllocation) {
+        // the stream-ordered pool may hold freed memory: return it and retry
+        cudaGetLastError();
+        if (pool_trim() == cudaSuccess) e = cudaMalloc(p, bytes);
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         *p = nullptr;
@@ -446,6 +461,17 @@ extern "C" int fhe_ctx_create(const fhe_params *p, fhe_ctx **out) {
     FHE_CU(cudaGetDeviceCount(&ndev));
     if (p->device < 0 || p->device >= ndev) return fhe_fail(FHE_E_INVAL, "no such CUDA device");
     FHE_CU(cudaSetDevice(p->device));
+    {
+        // Temporaries of a step come from the device's stream-ordered pool.
+        // Keep what the pool has mapped across synchronisations (its default
+        // gives everything back at each one, and the next batch maps it
+        // again); dev_alloc trims the pool when a plain allocation is refused.
+        // The setting belongs to this process's context only.
+        cudaMemPool_t pool;
+        FHE_CU(cudaDeviceGetDefaultMemPool(&pool, p->device));
+        uint64_t keep = UINT64_MAX;
+        FHE_CU(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+    }
     std::unique_ptr<fhe_ctx> c(new fhe_ctx());
     c->prm = *p;
     c->dev = p->device;

@@ -117,6 +117,9 @@ struct fhe_evk {
     std::map<int, u64 *> galois;  // Galois element -> key
 };
 
+// hand the current device's stream-ordered pool memory that is not in use
+// back to the device (after a device synchronisation)
+cudaError_t pool_trim();
 int dev_alloc(fhe_ctx *ctx, void **p, size_t bytes);
 void dev_free(void *p);
 int ws_reserve(fhe_ctx *ctx, u64 **ws, size_t *have, size_t words);

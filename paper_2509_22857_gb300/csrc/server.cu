@@ -153,6 +153,7 @@ extern "C" int fhe_server_add_model(fhe_server *sv, const fhe_model *model, int 
     if (!sv || !model || !model_id || group < 1) return fhe_fail(FHE_E_INVAL, "bad argument");
     FHE_CU(cudaSetDevice(sv->ctx->dev));
     size_t free_b = 0, total_b = 0;
+    FHE_CU(pool_trim());   // freed temporaries held by the pool count as free
     FHE_CU(cudaMemGetInfo(&free_b, &total_b));
     if (reserve_bytes && free_b < reserve_bytes)
         return fhe_fail(FHE_E_OOM, "not enough free device memory to admit this model (" + std::to_string(free_b) +

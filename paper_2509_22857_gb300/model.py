@@ -896,6 +896,9 @@ class ModelDesc:
                                    steps)
         self._keep = keep
         self._steps = steps
+        # the struct holds raw pointers into these arrays: it keeps its owner
+        # alive, so `ModelDesc(...).desc` may be passed on by itself
+        self.desc._owner = self
 
 
 def input_slots(prog: Program, img: np.ndarray, n_slots: int) -> List[np.ndarray]:

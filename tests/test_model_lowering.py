@@ -253,3 +253,23 @@ def test_on_demand_program_describes_the_resident_one(arch, layout):
             if sparse:
                 assert np.count_nonzero(va) == len(vb)
     assert n_sparse >= 2     # the packed convolutions
+
+
+def test_model_descriptor_keeps_its_arrays_alive():
+    """The C descriptor points into arrays its ModelDesc owns; taken on its
+    own (the owner otherwise unreferenced) it still reads the program."""
+    import gc
+    import ctypes
+    pre = synth.PRESETS["resnet_mini"]
+    prm = O.make_params(**pre)
+    net = synth.resnet_mini()
+    pm = M.compile_network(net, synth.params(net), prm.q, pre["logn"], pre["log_scale"], "packed", pre["alpha"])
+    d = M.ModelDesc(pm, prm.N // 2).desc
+    gc.collect()
+    big = [np.full(1 << 16, 7, dtype=np.int64) for _ in range(64)]   # reuse freed memory if any was freed
+    assert d.n_steps == len(pm.steps) and d.n_tensors == len(pm.tensors)
+    assert [d.tensor_level[i] for i in range(d.n_tensors)] == [t.level for t in pm.tensors]
+    st = [d.steps[i] for i in range(d.n_steps)]
+    lin = [s for s in st if s.kind == 1]
+    assert ctypes.addressof(lin[0]) and lin[0].term_ct[0] == int(pm.steps[0]["t_ct"][0])
+    del big
