@@ -272,6 +272,7 @@ def run_ours(args, rank, world):
     t0 = time.time()
     ctx = F.fhe_ctx_create(pre["logn"], pre["L"], pre["q_bits"], pre["q0_bits"], pre["p_bits"], pre["alpha"],
                            pre["log_scale"], dev)
+    F.fhe_ctx_set_mac_images(ctx, args.mac_images)
     net = synth.resnet20()
     raw = synth.params(net)
     prog = M.compile_network(net, raw, F.fhe_ctx_primes(ctx)[: pre["L"] + 1], pre["logn"], pre["log_scale"],
@@ -367,7 +368,7 @@ def run_ours(args, rank, world):
         from paper_2509_22857_gb300 import autotune as A
         images = [cts[i * n_in:(i + 1) * n_in] for i in range(B)]
         group_tuning = A.tune_pipeline_group(A.Tuner(args.autotune_cache), ctx, model, evk, images, n_out, N,
-                                             candidates=(2, 4, 8), model_key=PRESET)
+                                             candidates=(4, 8, 16), model_key=PRESET)
         g = group_tuning["best"]
     elif args.group:
         g = args.group
@@ -484,6 +485,9 @@ def run_ours(args, rank, world):
                         % (S, g, T),
             "group_tuning": group_tuning,
             "knob_tuning": knob_tuning,
+            "mac_images_per_block": args.mac_images if knob_tuning is None else knob_tuning["mac_images"]["best"],
+            "hoisting": "per linear step by the cost model: %d of %d double-hoisted" % (
+                sum(1 for h in M.hoists(prog) if h == 2), len(M.hoists(prog))),
             "uniform_batch": B,
             "uniform_batch_img_s": round(img_s_uniform, 4),
             "single_img_s": round(img_s_single, 4),
@@ -1022,11 +1026,14 @@ def main():
                     help="rank the admissible digit widths by measured, census-weighted key-switch time and exit")
     ap.add_argument("--autotune-cache", default=None, help="--autotune: JSON cache file of the tuner")
     ap.add_argument("--group", type=int, default=8,
-                    help="images per pipeline tick (8: the best of 2, 4, 8 measured by --tune-group on GB300; "
+                    help="images per pipeline tick (8: the best of 4, 8, 16 measured by --tune-group on GB300; "
                          "0: the uniform batch spread over the segments)")
     ap.add_argument("--ticks", type=int, default=5,
                     help="pipeline ticks per timed step (every tick runs every segment, i.e. the whole network, "
                          "for the group at each level; a group of images leaves per tick)")
+    ap.add_argument("--mac-images", type=int, default=1,
+                    help="images per plaintext-MAC block (1: the best of 0, 1, 2, 4, 8 measured by --tune-knobs on "
+                         "GB300 for ResNet-20, 8 images; bit-neutral)")
     ap.add_argument("--tune-knobs", action="store_true",
                     help="measure images per MAC block and the key-switch batch on the device first (reported)")
     ap.add_argument("--tune-group", action="store_true",

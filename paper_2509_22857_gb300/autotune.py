@@ -263,8 +263,15 @@ def tune_pipeline_group(tuner: Tuner, ctx, model, evk, image_cts: Sequence[Seque
     n_img = len(image_cts)
     ref = None
     rate: Dict[int, float] = {}
+    refused: Dict[int, str] = {}
     for g in candidates:
-        pipe = F.fhe_pipeline_create(ctx, model, evk, g, True)
+        try:
+            pipe = F.fhe_pipeline_create(ctx, model, evk, g, True)
+        except F.FheError as e:
+            if e.code != F.FHE_E_OOM:
+                raise
+            refused[g] = str(e)       # does not fit in device memory
+            continue
         try:
             S = F.fhe_pipeline_info(pipe)[0]
             state = {"next": 0, "first": None}
@@ -279,8 +286,14 @@ def tune_pipeline_group(tuner: Tuner, ctx, model, evk, image_cts: Sequence[Seque
                 for h in outs:
                     F.fhe_ct_free(h)
 
-            for _ in range(S):          # fill: the first group leaves at the last of these ticks
-                tick()
+            try:
+                for _ in range(S):      # fill: the first group leaves at the last of these ticks
+                    tick()
+            except F.FheError as e:
+                if e.code != F.FHE_E_OOM:
+                    raise
+                refused[g] = str(e)
+                continue
             sync()
             t0 = time.perf_counter()
             for _ in range(steps * S):
@@ -293,5 +306,8 @@ def tune_pipeline_group(tuner: Tuner, ctx, model, evk, image_cts: Sequence[Seque
             ref = state["first"]
         elif state["first"] is None or not all((a == b).all() for a, b in zip(ref, state["first"])):
             raise RuntimeError("group size %d changed the output ciphertexts" % g)
-    best = max(candidates, key=lambda c: (rate[c], -c))
-    return tuner.record(key, {"best": best, "img_s": {str(g): round(r, 4) for g, r in rate.items()}})
+    if not rate:
+        raise RuntimeError("no pipeline group size fits in device memory: %s" % refused)
+    best = max(rate, key=lambda c: (rate[c], -c))
+    return tuner.record(key, {"best": best, "img_s": {str(g): round(r, 4) for g, r in rate.items()},
+                              "refused": {str(g): m for g, m in refused.items()}})

@@ -406,6 +406,16 @@ def split_cost(terms: Terms, giant: int, level: int, alpha: int, hoist: int) -> 
             + len(giants) * (mu + ip) + len(np.unique(giants[:, 0])) * md + mac)
 
 
+def dh_group_bytes(terms: Terms, giant: int, level: int, alpha: int, log_n: int) -> int:
+    """Device bytes per image that double hoisting holds for a step: one sum
+    over Q_l u P (two polynomials) per output group with rotated terms,
+    alive until the step's last chunk."""
+    b = terms.r % giant
+    g = terms.r - b
+    n_groups = len(np.unique(np.stack([terms.out[b != 0], g[b != 0]], axis=1), axis=0)) if np.any(b) else 0
+    return n_groups * 2 * (level + 1 + alpha) * (1 << log_n) * 8
+
+
 def groups_of(st: Dict) -> Dict[Tuple[int, int], List]:
     """{(out ct, giant step): [(in ct, baby step, vector)]} of a linear step"""
     groups: Dict[Tuple[int, int], List] = {}
@@ -428,8 +438,10 @@ class Planner:
     def __init__(self, primes_q: Sequence[int], log_n: int, log_scale: float, layout: str, alpha: int = 3,
                  max_giant_blocks: int = 8, members: int = 1, input_lambda: int = 1,
                  giants: Optional[Sequence[int]] = None, on_demand: bool = False, hoist="auto",
-                 hoists: Optional[Sequence[int]] = None):
+                 hoists: Optional[Sequence[int]] = None, dh_bytes: int = 1 << 30):
         self.on_demand = on_demand
+        self.log_n = log_n
+        self.dh_bytes = dh_bytes
         self.giants = None if giants is None else list(giants)
         if hoist not in ("auto", 1, 2):
             raise ValueError("hoist must be 'auto', 1 or 2")
@@ -465,8 +477,14 @@ class Planner:
             return self._emit(kind=F.STEP_RESCALE, src=t, dst=self._t(info.layout, info.level - 1, info.scale / ql))
         return t
 
-    def _hoist_options(self) -> Tuple[int, ...]:
-        return (1, 2) if self.hoist == "auto" else (self.hoist,)
+    def _hoist_options(self, terms: Optional[Terms] = None, giant: int = 0, level: int = 0) -> Tuple[int, ...]:
+        """the admitted modes; "auto" admits double hoisting only while its
+        group sums fit dh_bytes per image"""
+        if self.hoist != "auto":
+            return (self.hoist,)
+        if terms is not None and dh_group_bytes(terms, giant, level, self.alpha, self.log_n) > self.dh_bytes:
+            return (1,)
+        return (1, 2)
 
     def _pick_giant(self, terms: Terms, block: int, level: int) -> int:
         """giant step = k blocks, k in 1, 2, 4, .. max_giant_blocks: the
@@ -475,7 +493,7 @@ class Planner:
         best = None
         k = 1
         while k <= self.max_giant_blocks and k * block <= self.n:
-            for h in self._hoist_options():
+            for h in self._hoist_options(terms, k * block, level):
                 c = split_cost(terms, k * block, level, self.alpha, h)
                 if best is None or c < best[0]:
                     best = (c, k * block)
@@ -485,7 +503,7 @@ class Planner:
     def _pick_hoist(self, terms: Terms, giant: int, level: int) -> int:
         if self.hoists is not None:
             return int(self.hoists[self.n_linear])
-        opts = self._hoist_options()
+        opts = self._hoist_options(terms, giant, level)
         costs = [split_cost(terms, giant, level, self.alpha, h) for h in opts]
         return opts[int(np.argmin(costs))]
 
@@ -743,7 +761,7 @@ class Planner:
 def compile_network(net, raw, primes_q, log_n, log_scale, layout, alpha: int = 3,
                     max_giant_blocks: int = 8, input_lambda: int = 1,
                     giants: Optional[Sequence[int]] = None, on_demand: bool = False, hoist="auto",
-                    hoists: Optional[Sequence[int]] = None) -> Program:
+                    hoists: Optional[Sequence[int]] = None, dh_bytes: int = 1 << 30) -> Program:
     """raw: one model's raw parameters, or a list of them (an ensemble, laid
     out with layout "hw_ens": member m in block m of every ciphertext).
     alpha: digit width of key switching (for the baby-step / giant-step
@@ -758,14 +776,15 @@ def compile_network(net, raw, primes_q, log_n, log_scale, layout, alpha: int = 3
     (for layers whose plaintexts do not fit).  hoist: 1 (every baby-step
     rotation brought back to Q_l by its own ModDown), 2 (double hoisting:
     rotations kept in Q_l u P, one ModDown per output group) or "auto" (per
-    linear step, the cheaper by split_cost); hoists: one mode per linear
-    step in place of that choice."""
+    linear step, the cheaper by split_cost, double hoisting admitted only
+    where its group sums over Q_l u P take at most dh_bytes per image);
+    hoists: one mode per linear step in place of that choice."""
     raws = raw if isinstance(raw, (list, tuple)) else [raw]
     if len(raws) > 1 and layout != "hw_ens":
         raise ValueError("an ensemble needs the hw_ens layout")
     prms = [prepare_params(net, r) for r in raws]
     return Planner(primes_q, log_n, log_scale, layout, alpha, max_giant_blocks, len(raws),
-                   input_lambda, giants, on_demand, hoist, hoists).compile(net, prms)
+                   input_lambda, giants, on_demand, hoist, hoists, dh_bytes).compile(net, prms)
 
 
 def input_scale(prog: Program) -> float:

@@ -198,3 +198,45 @@ def test_keyswitch_census_of_a_small_network():
     assert [l for l, _ in lv] == sorted(census, reverse=True) and sum(k for _, k in lv) == sum(census.values())
     acts = [st for st in prog.steps if st["kind"] == 3]
     assert all(M.keyswitches_of_step(prog, st) == prog.tensors[st["src"]].layout.n_ct for st in acts)
+
+
+class FakePipeLib:
+    """Pipelines whose tick sleeps per group size; sizes in `oom` are refused
+    at creation, as fhe_pipeline_create refuses a pipeline that does not fit."""
+    FheError = None
+    FHE_E_OOM = -4
+
+    def __init__(self, tick_ms, oom=()):
+        from paper_2509_22857_gb300 import _lib
+        self.FheError = _lib.FheError
+        self.tick_ms, self.oom, self.live, self.n = tick_ms, set(oom), set(), 0
+
+    def fhe_pipeline_create(self, ctx, model, evk, g, graphs):
+        if g in self.oom:
+            raise self.FheError(self.FHE_E_OOM, "out of memory")
+        self.n += 1
+        h = ("pipe", g, self.n)
+        self.live.add(h)
+        return h
+
+    def fhe_pipeline_info(self, pipe):
+        return (3, 0, 1, 1)
+
+    def fhe_pipeline_tick(self, pipe, grp, g, n):
+        time.sleep(self.tick_ms[pipe[1]] / 1e3)
+        return [], 0, -1
+
+    def fhe_pipeline_free(self, pipe):
+        self.live.remove(pipe)
+
+
+def test_pipeline_group_tuner_skips_sizes_that_do_not_fit():
+    F = FakePipeLib({2: 4.0, 4: 5.0, 8: 6.0}, oom=(16,))
+    rec = A.tune_pipeline_group(A.Tuner(), "ctx", "m", "evk", [[1], [2]], 1, 4, candidates=(2, 4, 8, 16), F=F,
+                                device="fake", sync=lambda: None)
+    # images per second: 2/4 ms, 4/5 ms, 8/6 ms -> 8 is best; 16 refused
+    assert rec["best"] == 8 and set(rec["img_s"]) == {"2", "4", "8"} and "16" in rec["refused"]
+    assert not F.live
+    with pytest.raises(RuntimeError, match="fits"):
+        A.tune_pipeline_group(A.Tuner(), "ctx", "m", "evk", [[1]], 1, 4, candidates=(16,), F=FakePipeLib({}, (16,)),
+                              device="fake", sync=lambda: None)

@@ -273,3 +273,22 @@ def test_model_descriptor_keeps_its_arrays_alive():
     lin = [s for s in st if s.kind == 1]
     assert ctypes.addressof(lin[0]) and lin[0].term_ct[0] == int(pm.steps[0]["t_ct"][0])
     del big
+
+
+def test_double_hoisting_stays_within_its_memory_budget():
+    """The planner admits double hoisting only where a step's group sums
+    over Q_l u P fit the per-image budget: with a budget of 0 bytes every
+    step with baby rotations is single-hoisted, and every double-hoisted
+    step of the default plan fits the default budget."""
+    pre = synth.PRESETS["resnet_mini"]
+    prm = O.make_params(**pre)
+    net = synth.resnet_mini()
+    raw = synth.params(net)
+    tight = M.compile_network(net, raw, prm.q, pre["logn"], pre["log_scale"], "packed", pre["alpha"], dh_bytes=0)
+    assert set(M.hoists(tight)) == {1}
+    plan = M.compile_network(net, raw, prm.q, pre["logn"], pre["log_scale"], "packed", pre["alpha"])
+    for st in plan.steps:
+        if st["kind"] == 1 and st["hoist"] == 2:
+            terms = M.Terms(st["t_out"], st["t_ct"], st["t_giant"] + st["t_baby"], st["t_vid"], st["vecs"])
+            lv = plan.tensors[st["src"]].level
+            assert 0 < M.dh_group_bytes(terms, st["giant"], lv, pre["alpha"], pre["logn"]) <= 1 << 30
