@@ -507,7 +507,9 @@ __device__ __forceinline__ ulonglong2 ip_fold_pair(const DevCtx &c, const KsArgs
     return make_ulonglong2(add_mod(r0.x, mulmod(f.x, pm, m), m.q), add_mod(r0.y, mulmod(f.y, pm, m), m.q));
 }
 
-template <int ND>
+// XO: the double-hoisting form (ip_out / ip_fold honoured); the plain form
+// is its own instance, so its code is not burdened by the extra paths
+template <int ND, bool XO>
 __global__ void __launch_bounds__(256) k_ks_ip(DevCtx c, LevelTab lt, KsArgs a, KsLayout ly) {
     const int ext = lt.ext;
     const int t = blockIdx.y;
@@ -541,12 +543,12 @@ __global__ void __launch_bounds__(256) k_ks_ip(DevCtx c, LevelTab lt, KsArgs a, 
             mac(a10, x[j].x, k1[j].x);
             mac(a11, x[j].y, k1[j].y);
         }
-        u64 *ob = a.ip_out ? a.ip_out + item * a.ip_out_item : a.ws + item * a.ws_item + ly.acc;
+        u64 *ob = XO && a.ip_out ? a.ip_out + item * a.ip_out_item : a.ws + item * a.ws_item + ly.acc;
         ulonglong2 *o0 = (ulonglong2 *)(ob + (long long)t * N + col);
         ulonglong2 *o1 = (ulonglong2 *)((u64 *)o0 + (long long)ext * N);
         ulonglong2 r0 = make_ulonglong2(barrett(a00, m), barrett(a01, m));
         ulonglong2 r1 = make_ulonglong2(barrett(a10, m), barrett(a11, m));
-        if (a.ip_fold && t <= a.level) r0 = ip_fold_pair(c, a, item, t, ip_col, ip_sw, r0, m);
+        if (XO && a.ip_fold && t <= a.level) r0 = ip_fold_pair(c, a, item, t, ip_col, ip_sw, r0, m);
         if (a.ip_accumulate) {
             const ulonglong2 p0 = *o0, p1 = *o1;
             r0 = make_ulonglong2(add_mod(r0.x, p0.x, m.q), add_mod(r0.y, p0.y, m.q));
@@ -1417,16 +1419,25 @@ static cudaError_t launch_keyswitch_part(const DevCtx &c, const LevelTab &lt, co
     if (phases & KS_IP) {
         COUNT_LAUNCH();
         const dim3 g2((unsigned)((1ll << c.logN) / 512), ext);
+        const bool xo = a.ip_out || a.ip_fold;
+#define IP_CASE(n)                                                     \
+    case n:                                                            \
+        if (xo)                                                        \
+            k_ks_ip<n, true><<<g2, 256, 0, s>>>(c, lt, a, ly);         \
+        else                                                           \
+            k_ks_ip<n, false><<<g2, 256, 0, s>>>(c, lt, a, ly);        \
+        break;
         switch (nd) {
-        case 1: k_ks_ip<1><<<g2, 256, 0, s>>>(c, lt, a, ly); break;
-        case 2: k_ks_ip<2><<<g2, 256, 0, s>>>(c, lt, a, ly); break;
-        case 3: k_ks_ip<3><<<g2, 256, 0, s>>>(c, lt, a, ly); break;
-        case 4: k_ks_ip<4><<<g2, 256, 0, s>>>(c, lt, a, ly); break;
-        case 5: k_ks_ip<5><<<g2, 256, 0, s>>>(c, lt, a, ly); break;
-        case 6: k_ks_ip<6><<<g2, 256, 0, s>>>(c, lt, a, ly); break;
-        case 7: k_ks_ip<7><<<g2, 256, 0, s>>>(c, lt, a, ly); break;
+            IP_CASE(1)
+            IP_CASE(2)
+            IP_CASE(3)
+            IP_CASE(4)
+            IP_CASE(5)
+            IP_CASE(6)
+            IP_CASE(7)
         default: k_ks_ip_n<<<g2, 256, 0, s>>>(c, lt, a, ly);
         }
+#undef IP_CASE
     }
     KS_EV(4);
     if (phases & KS_MODDOWN) DISPATCH_LOGR(c.logR2, k_ks_md_intt_row, dim3(tc, B * 2 * c.alpha), c, lt, a, ly);
