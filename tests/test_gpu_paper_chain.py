@@ -1,8 +1,8 @@
 """The paper's own parameter set for ResNet-32 (its printed chain: q_0 of 28
 bits, 32 primes of ~52 bits, one 54-bit special prime, so 33 key-switching
 digits) on the device, at N = 2^12 (the primes are = 1 mod 2^17): rotation,
-relinearised square and rescales bit-equal to the oracle's; chains the
-library must refuse."""
+relinearised square, rescales and a double-hoisted convolution bit-equal to
+the oracle's; chains the library must refuse."""
 import numpy as np
 import pytest
 
@@ -145,3 +145,46 @@ def test_rescale_batch_beyond_one_launch(paper):
     for h in outs + cts:
         F.fhe_ct_free(h)
     F.fhe_model_free(model)
+
+
+def test_double_hoisted_convolution_on_the_papers_chain_bit_exact(paper):
+    """A 3x3 convolution (2 -> 4 channels, HW layout) at the top of the
+    33-digit chain, double-hoisted: its baby rotations stay in Q u P
+    through the many-digit inner product (the form that folds P sigma(c0)
+    in), the products run over Q u P and each output takes one ModDown
+    from the single special prime.  fhe_eval_conv's ciphertexts equal the
+    oracle's limb for limb."""
+    import synth
+    from oracle import cnn
+    from paper_2509_22857_gb300 import model as M
+    F, ctx, prm, S, _, _, _ = paper
+    net = [{"op": "input", "c": 2, "h": 8, "w": 8}, synth._conv(0, 2, 4, 3, 1, 1, "c1"), {"op": "act", "src": 1},
+           {"op": "pool", "src": 2, "k": 2}, {"op": "dense", "src": 3, "cin": 4 * 4 * 4, "cout": 10, "name": "fc"}]
+    raw = synth.params(net)
+    log_scale = int(round(np.log2(prm.scale)))
+    pm = M.compile_network(net, raw, prm.q, LOGN, log_scale, "hw", 1, hoist=2)
+    assert M.hoists(pm)[0] == 2 and pm.steps[0]["kind"] == F.STEP_LINEAR
+    po = cnn.compile_he(net, cnn.transform(net, raw), prm, "hw", M.giant_steps(pm), 1, 1, M.hoists(pm))
+    assert po.rot_steps == pm.rotations
+    keys = S.keygen(synth.SEED_KEYS, sorted(po.rot_steps))
+    sk, evk = F.fhe_keygen(ctx, synth.SEED_KEYS, sorted(pm.rotations))
+    desc = M.ModelDesc(pm, prm.N // 2)
+    model = F.fhe_model_load(ctx, desc.desc)
+    img = synth.image(0, 2, 8, 8)
+    ref = cnn.run_he(S, keys, po, cnn.encrypt_input(S, keys, po, img, 0, synth.enc_seed), stop_after=0)
+    ins = []
+    for k, v in enumerate(M.input_slots(pm, img, prm.N // 2)):
+        pt = F.fhe_encode(ctx, v, M.input_scale(pm), prm.L)
+        ins.append(F.fhe_encrypt(ctx, sk, pt, synth.enc_seed(0, k)))
+        F.fhe_pt_free(pt)
+    st = pm.steps[0]
+    outs = F.fhe_eval_conv(ctx, model, evk, 0, ins, pm.tensors[st["dst"]].layout.n_ct)
+    want = ref[po.steps[0]["dst"]]
+    assert len(outs) == len(want)
+    for h, r in zip(outs, want):
+        _same(F, S, r, h)
+    for h in outs + ins:
+        F.fhe_ct_free(h)
+    F.fhe_model_free(model)
+    F.fhe_evk_free(evk)
+    F.fhe_sk_free(sk)
