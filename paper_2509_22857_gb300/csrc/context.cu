@@ -579,6 +579,20 @@ int op_ntt(fhe_ctx *ctx, const u64 *src, u64 *dst, long long item, int n_items, 
     return FHE_OK;
 }
 
+int op_ks_ip_babies(fhe_ctx *ctx, KsArgs a, const IpBabies &bb, cudaStream_t s, u64 *ws) {
+    const size_t per = ks_workspace_words(ctx->dc, a.level);
+    if (!ws) {
+        // the ModUp that filled it reserved the same size: no reallocation here
+        if (ctx->ks_ws_words < per * (size_t)a.n_items)
+            return fhe_fail(FHE_E_INVAL, "internal: baby-step inner products without their ModUp");
+        ws = ctx->ks_ws;
+    }
+    a.ws = ws;
+    a.ws_item = (long long)per;
+    FHE_CU(launch_ks_ip_babies(ctx->dc, ctx->lt[a.level], a, bb, s));
+    return FHE_OK;
+}
+
 int op_keyswitch(fhe_ctx *ctx, KsArgs a, cudaStream_t s, u64 *ws, int phases) {
     const size_t per = ks_workspace_words(ctx->dc, a.level);
     if (!ws) {

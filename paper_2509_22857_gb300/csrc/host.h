@@ -133,6 +133,9 @@ u64 h_double_mod(double v, u64 q);
 // ws: caller-sized workspace, or nullptr for the context's growable one
 // phases: KS_MODUP | KS_IP | KS_MODDOWN (the workspace carries state between them)
 int op_keyswitch(fhe_ctx *ctx, KsArgs a, cudaStream_t s, u64 *ws = nullptr, int phases = KS_ALL);
+// inner products of several baby-step rotations of the ModUp just made in
+// ws (the context's workspace when null), each kept in Q_l u P
+int op_ks_ip_babies(fhe_ctx *ctx, KsArgs a, const IpBabies &bb, cudaStream_t s, u64 *ws = nullptr);
 int op_rescale(fhe_ctx *ctx, const u64 *in, long long in_item, u64 *out, long long out_item, int n_items,
                int n_poly, int level, cudaStream_t s, u64 *ws = nullptr);
 int op_ntt(fhe_ctx *ctx, const u64 *src, u64 *dst, long long item, int n_items, int n_limbs,

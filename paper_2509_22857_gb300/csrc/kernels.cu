@@ -559,6 +559,56 @@ __global__ void __launch_bounds__(256) k_ks_ip(DevCtx c, LevelTab lt, KsArgs a, 
     }
 }
 
+template <int ND>
+__global__ void __launch_bounds__(256) k_ks_ip_babies(DevCtx c, LevelTab lt, KsArgs a, KsLayout ly, IpBabies bb) {
+    const int ext = lt.ext;
+    const int t = blockIdx.y;
+    const int pi = ext_prime(t, a.level, c.L);
+    const ModQ m = c.primes[pi].m;
+    const long long N = 1ll << c.logN;
+    const int col = 2 * (blockIdx.x * blockDim.x + threadIdx.x);   // source slots col, col + 1
+    const long long key_limbs = c.L + 1 + c.alpha;
+    const int jt = t <= a.level ? t / c.alpha : -1;   // digit that holds limb t itself
+    const bool fold = a.ip_fold && t <= a.level;
+    const u64 pm = fold ? c.md_pmod[t] : 0;
+    for (int item = 0; item < a.n_items; item++) {
+        const u64 *mu = a.ws + item * a.ws_item + ly.mu + (long long)t * N + col;
+        const u64 *dd = a.d + item * a.d_item + (long long)t * N + col;
+        ulonglong2 x[ND];
+#pragma unroll
+        for (int j = 0; j < ND; j++)
+            x[j] = (j == jt) ? *(const ulonglong2 *)dd : *(const ulonglong2 *)(mu + (long long)j * ext * N);
+        const ulonglong2 f =
+            fold ? *(const ulonglong2 *)(a.ip_fold + item * a.ip_fold_item + (long long)t * N + col)
+                 : make_ulonglong2(0, 0);
+        for (int k = 0; k < bb.n; k++) {
+            // the output slots fed by source slots col, col + 1: an aligned
+            // pair, swapped when the first is odd
+            const int jo = galois_src(col, bb.gal_inv[k], c.logN);
+            const bool sw = jo & 1;
+            const long long jb = jo & ~1;
+            U128 a00 = {0, 0}, a01 = {0, 0}, a10 = {0, 0}, a11 = {0, 0};
+#pragma unroll
+            for (int j = 0; j < ND; j++) {
+                const u64 *kb = bb.key[k] + ((long long)(j * 2) * key_limbs + pi) * N + jb;
+                const ulonglong2 k0 = ld_pair(kb, sw);
+                const ulonglong2 k1 = ld_pair(kb + key_limbs * N, sw);
+                mac(a00, x[j].x, k0.x);
+                mac(a01, x[j].y, k0.y);
+                mac(a10, x[j].x, k1.x);
+                mac(a11, x[j].y, k1.y);
+            }
+            ulonglong2 r0 = make_ulonglong2(barrett(a00, m), barrett(a01, m));
+            const ulonglong2 r1 = make_ulonglong2(barrett(a10, m), barrett(a11, m));
+            if (fold)
+                r0 = make_ulonglong2(add_mod(r0.x, mulmod(f.x, pm, m), m.q), add_mod(r0.y, mulmod(f.y, pm, m), m.q));
+            u64 *ob = bb.out[k] + item * a.ip_out_item + (long long)t * N + jb;
+            *(ulonglong2 *)ob = sw ? make_ulonglong2(r0.y, r0.x) : r0;
+            *(ulonglong2 *)(ob + (long long)ext * N) = sw ? make_ulonglong2(r1.y, r1.x) : r1;
+        }
+    }
+}
+
 // Inner product for more than 7 digits (one special prime per digit, as in
 // the paper's own parameter sets): the digits are a loop and the key pairs
 // are loaded per item, since they no longer fit in registers.  Same layout,
@@ -1453,6 +1503,32 @@ static cudaError_t launch_keyswitch_part(const DevCtx &c, const LevelTab &lt, co
     if (phases & KS_MODDOWN) DISPATCH_LOGR(c.logR2, k_ks_md_row_out, dim3(tc, B * 2 * nl), c, lt, a, ly);
     KS_EV(8);
 #undef KS_EV
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ks_ip_babies(const DevCtx &c, const LevelTab &lt, const KsArgs &a, const IpBabies &bb,
+                                cudaStream_t s) {
+    const int nd = lt.n_digits;
+    if (bb.n < 1 || bb.n > KS_BABIES_MAX || nd < 1 || nd > 7 || c.logN < 9 || !a.ws || !a.d || !a.ip_out_item)
+        return cudaErrorInvalidValue;
+    if (((uintptr_t)a.d | (uintptr_t)a.ws | (uintptr_t)a.ip_fold) % 16 != 0 ||
+        ((a.d_item | a.ws_item | a.ip_fold_item | a.ip_out_item) & 1))
+        return cudaErrorMisalignedAddress;
+    for (int k = 0; k < bb.n; k++)
+        if (!bb.key[k] || !bb.out[k] || ((uintptr_t)bb.key[k] | (uintptr_t)bb.out[k]) % 16 != 0 || !(bb.gal_inv[k] & 1))
+            return cudaErrorInvalidValue;
+    KsLayout ly = ks_layout(a.level, nd, c.alpha, c.logN);
+    const dim3 g((unsigned)((1ll << c.logN) / 512), lt.ext);
+    COUNT_LAUNCH();
+    switch (nd) {
+    case 1: k_ks_ip_babies<1><<<g, 256, 0, s>>>(c, lt, a, ly, bb); break;
+    case 2: k_ks_ip_babies<2><<<g, 256, 0, s>>>(c, lt, a, ly, bb); break;
+    case 3: k_ks_ip_babies<3><<<g, 256, 0, s>>>(c, lt, a, ly, bb); break;
+    case 4: k_ks_ip_babies<4><<<g, 256, 0, s>>>(c, lt, a, ly, bb); break;
+    case 5: k_ks_ip_babies<5><<<g, 256, 0, s>>>(c, lt, a, ly, bb); break;
+    case 6: k_ks_ip_babies<6><<<g, 256, 0, s>>>(c, lt, a, ly, bb); break;
+    default: k_ks_ip_babies<7><<<g, 256, 0, s>>>(c, lt, a, ly, bb); break;
+    }
     return cudaGetLastError();
 }
 

@@ -98,6 +98,25 @@ struct KsArgs {
 };
 
 size_t ks_workspace_words(const DevCtx &c, int level);
+// Several baby-step rotations of one ModUp at once, each kept in Q_l u P
+// (double hoisting).  Rotation k's inner product at output slot j reads the
+// digits at sigma_k's source slot of j; here each thread takes two source
+// slots, reads the digits and c0 there once for all rotations, and for
+// rotation k reads its key at, and writes its result to, the output slots
+// that those source slots feed (gal_inv[k]: the inverse Galois element).
+// The products, sums and reductions are those of the one-rotation form.
+#define KS_BABIES_MAX 8
+struct IpBabies {
+    int n;
+    const u64 *key[KS_BABIES_MAX];
+    u64 *out[KS_BABIES_MAX];
+    int gal_inv[KS_BABIES_MAX];
+};
+// a: d (c1 of the input), ip_fold (its c0), ip_out_item, n_items, level, ws
+// / ws_item holding the ModUp digits.  Up to 7 digits; else
+// cudaErrorInvalidValue (the caller takes the one-rotation form).
+cudaError_t launch_ks_ip_babies(const DevCtx &c, const LevelTab &lt, const KsArgs &a, const IpBabies &bb,
+                                cudaStream_t s);
 // ev (nullable): 9 events recorded on s before each of the 8 kernels and after the last.
 // phases: KS_MODUP (inverse NTT, basis conversion, NTT), KS_IP (key inner
 // product), KS_MODDOWN (back to Q, output); a plain key switch runs all three.

@@ -106,6 +106,14 @@ static int encode_act_vecs(fhe_model *m, const fhe_step_desc &sd, const MTensor 
     return FHE_OK;
 }
 
+// inverse of an odd a modulo m = 2^k (Newton: each step doubles the correct
+// low bits; a * a = 1 mod 8 starts with three)
+static int inverse_mod_2n(int a, long long m) {
+    unsigned long long x = (unsigned long long)a, ua = (unsigned long long)a;
+    for (int i = 0; i < 6; i++) x = x * (2ull - ua * x);
+    return (int)(x & (unsigned long long)(m - 1));
+}
+
 static int load_linear(fhe_model *m, const fhe_step_desc &sd, MStep &st) {
     fhe_ctx *c = m->ctx;
     MLinear &L = st.lin;
@@ -437,6 +445,10 @@ struct Exec {
         return FHE_OK;
     }
 
+    int ip_babies(const KsArgs &a, const IpBabies &bb) {
+        return op_ks_ip_babies(m->ctx, a, bb, s, pers ? pers->ks_ws : nullptr);
+    }
+
     // out = base + rot(x, step) for n items of one tensor-like layout
     int rotate_items(const u64 *x, long long x_item, int step, const u64 *base, long long base_item, u64 *out,
                      long long out_item, int n, int level) {
@@ -561,6 +573,29 @@ struct Exec {
                 a.n_items = B;
                 a.level = lv;
                 FHE_TRY(keyswitch(a, KS_MODUP));
+                if (L.dh && c->lt[lv].n_digits <= 7) {
+                    // double hoisting: the input's rotations in batches, each
+                    // batch one pass over the ModUp digits and c0
+                    for (int k0 = first_baby[ct]; k0 < first_baby[ct + 1]; k0 += KS_BABIES_MAX) {
+                        IpBabies bb;
+                        memset(&bb, 0, sizeof(bb));
+                        for (int kk = k0; kk < std::min(k0 + KS_BABIES_MAX, first_baby[ct + 1]); kk++) {
+                            int err;
+                            const u64 *key = key_for(L.baby_step[kk], &err);
+                            if (!key) return err;
+                            bb.key[bb.n] = key;
+                            bb.out[bb.n] = rb[kk - first_baby[lo]];
+                            bb.gal_inv[bb.n] = inverse_mod_2n(galois_of_step(c, L.baby_step[kk]), 2 * c->N);
+                            bb.n++;
+                        }
+                        KsArgs b = a;
+                        b.ip_fold = x;
+                        b.ip_fold_item = in_item;
+                        b.ip_out_item = rcs;
+                        FHE_TRY(ip_babies(b, bb));
+                    }
+                    continue;
+                }
                 for (int kk = first_baby[ct]; kk < first_baby[ct + 1]; kk++) {
                     int err;
                     const u64 *key = key_for(L.baby_step[kk], &err);
