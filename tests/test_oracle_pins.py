@@ -229,6 +229,39 @@ def test_galois_automorphism_rotates_slots():
         assert np.max(np.abs(back - np.roll(z, -r))) < 1e-9
 
 
+def test_galois_map_in_the_ntt_domain_keeps_aligned_pairs():
+    """The NTT-domain form of sigma_k, derived here from the coefficient
+    definition (NTT of a(x^k) against NTT of a), is a permutation of slots
+    that (1) sends every aligned pair of slots onto an aligned pair and (2)
+    is inverted by the map of k^-1 mod 2N.  The key-switching kernels rely on
+    both: a gather reads two slots with one 16-byte load, and the batched
+    baby-step inner product scatters to the pair that the inverse map
+    gives."""
+    logn = 8
+    N = 1 << logn
+    prm = C.make_params(logn=logn, L=1, q_bits=50, q0_bits=50, p_bits=50, alpha=1, log_scale=20)
+    q, psi = prm.primes[0], prm.psi[0]
+    a = np.random.default_rng(5).integers(0, q, N, dtype=np.uint64)
+    base = C.ntt(a, q, psi)
+    where = {int(v): i for i, v in enumerate(base)}
+    assert len(where) == N                       # distinct values: positions identify slots
+
+    def slot_map(k):
+        # out[j] = in[src[j]] for the NTT of a(x^k)
+        img = C.ntt(C.automorphism_coeff(a, k, q), q, psi)
+        return np.array([where[int(v)] for v in img])
+
+    for r in (1, 3, -1, 17, N // 4 - 1):
+        k = C.galois_elt(r, N)
+        src = slot_map(k)
+        assert sorted(src) == list(range(N))
+        for j in range(0, N, 2):
+            assert src[j] ^ 1 == src[j + 1]
+        kinv = pow(k, -1, 2 * N)
+        inv = slot_map(kinv)
+        assert all(src[inv[i]] == i for i in range(N))
+
+
 # ------------------------------------------------------------------ RNS
 
 def test_basis_conversion_is_crt_plus_small_multiple():
